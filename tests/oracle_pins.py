@@ -1,0 +1,378 @@
+"""Pins that tie the CPU oracle to something other than itself.
+
+Each ``pin_*`` function takes an oracle instance (``oracle.Oracle``) and raises
+AssertionError when the oracle disagrees with the mathematics or the paper:
+
+  pin_phi_library       the Gaussian factor vs a 60-digit mpmath normal CDF
+  pin_edges_telescoping grid edges, and sum over an axis == mass of the axis
+  pin_closed_form_1d    1-D shift system: covering target == erf(h/(2 sqrt2 s)),
+                        lo/up == exact min/max over the cell found numerically
+  pin_bruteforce_2d     separable 2-D: lo at the cell corners, up == product of
+                        numerically maximised 1-D factors (the relaxation is
+                        exact there, Def. 3.1)
+  pin_mc_containment    coupled / nonlinear systems: P(t|x) and P(out|x) of
+                        random points x of the cell lie inside the bounds, and
+                        f(x) inside the interval image
+  pin_noise_sampling    simulating x+ = f(x,u) + w and binning lands inside
+                        [lo, up] (and the sink bounds) within 5 binomial sigma
+  pin_invariants        0 <= lo <= up <= 1, row sums (Def. 3.1), cutoff rule,
+                        ascending columns, trunc == dropped mass
+  pin_degenerate        point images: lo == up bit for bit, and the row's mass
+                        (kept + truncated + sink) sums to 1
+  pin_separable_sum     sum of all up == product of the per-dim maxima sums
+  pin_tie_kept          an up exactly equal to the cutoff is kept
+
+None of them re-evaluates the oracle's own formulas: they use library CDFs
+(scipy / mpmath), numerical optimisation, sampling and identities.
+"""
+
+from __future__ import annotations
+
+import math
+
+import numpy as np
+from scipy.optimize import minimize_scalar
+from scipy.special import ndtr
+
+from paper_2401_03555_gb300 import workloads as W
+
+# --------------------------------------------------------------------------
+# helpers written from the definitions (Def. 2.2: T(A|x,u) = P(f(x,u)+w in A))
+# --------------------------------------------------------------------------
+
+
+def grid_edges(prob, d):
+    """Edges lo + i*h (last = hi), computed here independently of the oracle."""
+    N = int(prob.cells[d])
+    e = prob.lo[d] + np.arange(N + 1) * ((prob.hi[d] - prob.lo[d]) / N)
+    e[-1] = prob.hi[d]
+    return e
+
+
+def cell_box(prob, cell):
+    idx = np.unravel_index(int(cell), tuple(int(c) for c in prob.cells))
+    lo = np.array([grid_edges(prob, d)[idx[d]] for d in range(prob.n)])
+    hi = np.array([grid_edges(prob, d)[idx[d] + 1] for d in range(prob.n)])
+    return lo, hi
+
+
+def dynamics(prob, x, u):
+    """f(x, u) for points x of shape (k, n)."""
+    x = np.atleast_2d(x)
+    if prob.kind == W.AFFINE:
+        off = (prob.B @ u if prob.B is not None and len(u) else 0.0) + (
+            prob.c if prob.c is not None else 0.0)
+        return x @ prob.A.T + off
+    if prob.kind == W.UNICYCLE:
+        v, om = u
+        return np.stack([x[:, 0] + v * np.cos(x[:, 2]), x[:, 1] + v * np.sin(x[:, 2]),
+                         x[:, 2] + om], axis=1)
+    raise ValueError("no dynamics for caller images")
+
+
+def interval_mass(c, e, mu, s):
+    """P(mu + w in [c, e]), w ~ N(0, s^2), via the library normal CDF; the side
+    with the smaller tail is used so the difference keeps its digits."""
+    a = (np.asarray(c) - mu) / s
+    b = (np.asarray(e) - mu) / s
+    right = ndtr(-a) - ndtr(-b)
+    left = ndtr(b) - ndtr(a)
+    return np.where(a + b > 0, right, left)
+
+
+def exact_probs(prob, mu):
+    """P(t | mean mu) for every target t (C order), and P(out | mu)."""
+    per_dim = []
+    inside = 1.0
+    for d in range(prob.n):
+        e = grid_edges(prob, d)
+        per_dim.append(interval_mass(e[:-1], e[1:], mu[d], prob.sigma[d]))
+        inside *= float(interval_mass(prob.lo[d], prob.hi[d], mu[d], prob.sigma[d]))
+    P = per_dim[0]
+    for f in per_dim[1:]:
+        P = np.multiply.outer(P, f)
+    return P.reshape(-1), 1.0 - inside
+
+
+# --------------------------------------------------------------------------
+# pins
+# --------------------------------------------------------------------------
+
+
+def pin_phi_library(orc, trials: int = 400, seed: int = 1):
+    try:
+        import mpmath as mp
+    except ImportError:  # pragma: no cover - mpmath ships with sympy here
+        mp = None
+    rng = np.random.default_rng(seed)
+    worst = 0.0
+    for k in range(trials):
+        s = float(np.exp(rng.uniform(np.log(0.05), np.log(5.0))))
+        m = float(rng.uniform(-3, 3))
+        a = float(rng.uniform(-12, 12))
+        w = float(np.exp(rng.uniform(np.log(1e-3), np.log(8.0))))
+        c, e = m + a * s, m + (a + w) * s
+        got = orc.phi_diff(c, e, m, s)
+        if mp is not None:
+            mp.mp.dps = 60
+            ref = float(mp.ncdf((mp.mpf(e) - m) / s) - mp.ncdf((mp.mpf(c) - m) / s))
+        else:
+            ref = float(interval_mass(c, e, m, s))
+        err = abs(got - ref)
+        assert err <= 1e-300 + 2e-13 * abs(ref) + 1e-17, (c, e, m, s, got, ref)
+        worst = max(worst, err)
+    # symmetry and limits
+    assert orc.phi_diff(-1e300, 1e300, 0.3, 1.0) == 1.0
+    assert abs(orc.phi_diff(-1.0, 1.0, 0.0, 1.0) - math.erf(1 / math.sqrt(2))) < 1e-15
+    assert orc.phi_diff(0.0, 1.0, 0.5, 0.7) == orc.phi_diff(0.0, 1.0, 0.5, 0.7)
+    return worst
+
+
+def pin_edges_telescoping(orc):
+    prob = W.room_5d(cells_per_dim=7, lo=17.0, hi=23.0)
+    for d in range(prob.n):
+        e = orc.edges(prob, d)
+        ref = grid_edges(prob, d)
+        assert e[0] == prob.lo[d] and e[-1] == prob.hi[d]
+        assert np.all(np.diff(e) > 0)
+        assert np.allclose(e, ref, rtol=0, atol=1e-13)
+        for mu in (16.0, 17.0, 18.3, 20.0, 22.99, 24.5):
+            total = sum(orc.phi_diff(e[i], e[i + 1], mu, 0.2) for i in range(len(e) - 1))
+            whole = float(interval_mass(prob.lo[d], prob.hi[d], mu, 0.2))
+            assert abs(total - whole) < 1e-14, (d, mu, total, whole)
+
+
+def one_dim_problem(n_cells=12, sigma=0.4, inputs=(-0.5, 0.3), cutoff=0.0):
+    return W.Problem(name="shift1d", kind=W.AFFINE, lo=np.array([-3.0]), hi=np.array([3.0]),
+                     cells=np.array([n_cells], np.int32),
+                     inputs=np.array(inputs, dtype=np.float64).reshape(-1, 1),
+                     sigma=np.array([sigma]), cutoff=cutoff,
+                     A=np.eye(1), B=np.eye(1), c=np.zeros(1))
+
+
+def _max_over_interval(fun, a, b):
+    """max of a smooth unimodal fun on [a, b]: endpoints + bounded Brent."""
+    best = max(fun(a), fun(b))
+    if b > a:
+        r = minimize_scalar(lambda x: -fun(x), bounds=(a, b), method="bounded",
+                            options={"xatol": 1e-12 * max(1.0, abs(b - a))})
+        best = max(best, -r.fun)
+    return best
+
+
+def pin_closed_form_1d(orc):
+    prob = one_dim_problem()
+    e = grid_edges(prob, 0)
+    h = e[1] - e[0]
+    s = prob.sigma[0]
+    plateau = math.erf(h / (2 * math.sqrt(2) * s))
+    for row in range(prob.rows):
+        cell, j = divmod(row, prob.n_inputs)
+        u = prob.inputs[j, 0]
+        up, lo, sink_lo, sink_up = orc.row_dense(prob, row)
+        xa, xb = e[cell], e[cell + 1]
+        for t in range(len(e) - 1):
+            c, f = e[t], e[t + 1]
+            mid = 0.5 * (c + f)
+            fun = lambda x: float(interval_mass(c, f, x + u, s))
+            lo_ref = min(fun(xa), fun(xb))
+            up_ref = _max_over_interval(fun, xa, xb)
+            assert abs(lo[t] - lo_ref) < 1e-14, (row, t, lo[t], lo_ref)
+            assert up[t] >= up_ref - 1e-14 and up[t] - up_ref < 1e-9, (row, t, up[t], up_ref)
+            if xa + u < mid < xb + u:
+                assert abs(up[t] - plateau) < 1e-14, (row, t, up[t], plateau)
+        out = lambda x: 1.0 - float(interval_mass(prob.lo[0], prob.hi[0], x + u, s))
+        assert abs(sink_up - max(out(xa), out(xb))) < 1e-14
+        inside_max = _max_over_interval(lambda x: 1.0 - out(x), xa, xb)
+        assert abs(sink_lo - (1.0 - inside_max)) < 1e-9
+
+
+def pin_bruteforce_2d(orc, cells_per_dim=5, rows=None):
+    prob = W.robot_2d(cells_per_dim=cells_per_dim)
+    rows = range(prob.rows) if rows is None else rows
+    for row in rows:
+        cell, j = divmod(row, prob.n_inputs)
+        u = prob.inputs[j]
+        up, lo, _, _ = orc.row_dense(prob, row)
+        bl, bh = cell_box(prob, cell)
+        corners = np.array([[bl[0], bl[1]], [bl[0], bh[1]], [bh[0], bl[1]], [bh[0], bh[1]]])
+        Pc = np.stack([exact_probs(prob, dynamics(prob, x, u)[0])[0] for x in corners])
+        assert np.all(np.abs(lo - Pc.min(axis=0)) < 1e-14), row
+        # separable: max of the product = product of the 1-D maxima
+        maxima = []
+        for d in range(2):
+            e = grid_edges(prob, d)
+            md = np.array([_max_over_interval(
+                lambda x, c=e[t], f=e[t + 1]: float(interval_mass(c, f, x + u[d], prob.sigma[d])),
+                bl[d], bh[d]) for t in range(len(e) - 1)])
+            maxima.append(md)
+        up_ref = np.multiply.outer(maxima[0], maxima[1]).reshape(-1)
+        assert np.all(up >= up_ref - 1e-14), row
+        assert np.all(up - up_ref < 1e-9), (row, float(np.max(up - up_ref)))
+        # and a 17x17 sample of the cell never leaves [lo, up]
+        g0 = np.linspace(bl[0], bh[0], 17)
+        g1 = np.linspace(bl[1], bh[1], 17)
+        for x0 in g0[::4]:
+            for x1 in g1[::4]:
+                P, _ = exact_probs(prob, dynamics(prob, np.array([x0, x1]), u)[0])
+                assert np.all(P <= up + 1e-14) and np.all(P >= lo - 1e-14)
+
+
+def pin_mc_containment(orc, prob, rows, samples=64, seed=3):
+    rng = np.random.default_rng(seed)
+    csr = orc.build_rows(prob, rows)
+    for k, row in enumerate(rows):
+        cell, j = divmod(int(row), prob.n_inputs)
+        u = prob.inputs[j]
+        bl, bh = cell_box(prob, cell)
+        up, lo, sink_lo, sink_up = orc.row_dense(prob, row)
+        m_lo, m_hi = orc.image(prob, row)
+        xs = bl + (bh - bl) * rng.random((samples, prob.n))
+        corners = np.array([[bh[d] if (c >> d) & 1 else bl[d] for d in range(prob.n)]
+                            for c in range(1 << prob.n)])
+        xs = np.concatenate([xs, corners], axis=0)
+        mus = dynamics(prob, xs, u)
+        tol = 1e-12 * np.maximum(1.0, np.abs(mus))
+        assert np.all(mus >= m_lo - tol) and np.all(mus <= m_hi + tol), row
+        if prob.kind == W.AFFINE:
+            cm = dynamics(prob, corners, u)  # a linear map's range is spanned by the corners
+            assert np.allclose(cm.min(axis=0), m_lo, atol=1e-12)
+            assert np.allclose(cm.max(axis=0), m_hi, atol=1e-12)
+        for mu in mus:
+            P, out = exact_probs(prob, mu)
+            assert np.all(P <= up + 1e-13), (row, float(np.max(P - up)))
+            assert np.all(P >= lo - 1e-13), (row, float(np.max(lo - P)))
+            assert sink_lo - 1e-13 <= out <= sink_up + 1e-13, (row, out, sink_lo, sink_up)
+        # the CSR row agrees with the dense evaluation
+        cols, clo, cup = csr.row(k)
+        keep = np.nonzero(up >= prob.cutoff)[0]
+        assert np.array_equal(cols, keep)
+        assert np.array_equal(clo, lo[keep]) and np.array_equal(cup, up[keep])
+
+
+def pin_unicycle_image(orc):
+    # 7 heading cells: 0 and +-pi/2 fall inside cells, not on their edges
+    prob = W.unicycle_3d(nx=4, ny=4, nth=7)
+    th_edges = grid_edges(prob, 2)
+    for cth in range(7):
+        for j in (0, 7, 13, 19):
+            cell = np.ravel_multi_index((1, 2, cth), (4, 4, 7))
+            row = cell * prob.n_inputs + j
+            m_lo, m_hi = orc.image(prob, row)
+            v, om = prob.inputs[j]
+            th = np.linspace(th_edges[cth], th_edges[cth + 1], 20001)
+            bl, bh = cell_box(prob, cell)
+            assert abs(m_lo[0] - (bl[0] + np.min(v * np.cos(th)))) < 1e-7
+            assert abs(m_hi[0] - (bh[0] + np.max(v * np.cos(th)))) < 1e-7
+            assert abs(m_lo[1] - (bl[1] + np.min(v * np.sin(th)))) < 1e-7
+            assert abs(m_hi[1] - (bh[1] + np.max(v * np.sin(th)))) < 1e-7
+            assert abs(m_lo[2] - (bl[2] + om)) < 1e-15 and abs(m_hi[2] - (bh[2] + om)) < 1e-15
+
+
+def pin_noise_sampling(orc, prob, row, draws=200_000, seed=5, top=12):
+    rng = np.random.default_rng(seed)
+    cell, j = divmod(int(row), prob.n_inputs)
+    u = prob.inputs[j]
+    bl, bh = cell_box(prob, cell)
+    x = bl + (bh - bl) * rng.random(prob.n)
+    mu = dynamics(prob, x, u)[0]
+    xp = mu + prob.sigma * rng.standard_normal((draws, prob.n))
+    inside = np.all((xp >= prob.lo) & (xp < prob.hi), axis=1)
+    idx = np.zeros(draws, dtype=np.int64)
+    for d in range(prob.n):
+        e = grid_edges(prob, d)
+        k = np.clip(np.searchsorted(e, xp[:, d], side="right") - 1, 0, len(e) - 2)
+        idx = idx * int(prob.cells[d]) + k
+    freq = np.bincount(idx[inside], minlength=prob.total_cells) / draws
+    out = 1.0 - inside.mean()
+    up, lo, sink_lo, sink_up = orc.row_dense(prob, row)
+    P, Pout = exact_probs(prob, mu)
+    order = np.argsort(-freq)[:top]
+    for t in order:
+        sd = math.sqrt(max(P[t] * (1 - P[t]), 1e-12) / draws)
+        assert lo[t] - 5 * sd <= freq[t] <= up[t] + 5 * sd, (t, freq[t], lo[t], up[t])
+        assert abs(freq[t] - P[t]) <= 5 * sd + 1e-6, (t, freq[t], P[t])
+    sd = math.sqrt(max(Pout * (1 - Pout), 1e-12) / draws)
+    assert sink_lo - 5 * sd <= out <= sink_up + 5 * sd, (out, sink_lo, sink_up)
+    assert abs(out - Pout) <= 5 * sd + 1e-6
+
+
+def pin_invariants(orc, prob, rows):
+    csr = orc.build_rows(prob, rows)
+    for k, row in enumerate(rows):
+        cols, lo, up = csr.row(k)
+        assert np.all(lo >= 0) and np.all(up <= 1) and np.all(lo <= up), row
+        assert np.all(up >= prob.cutoff), row
+        assert np.all(np.diff(cols) > 0), row
+        assert lo.sum() + csr.sink_lo[k] <= 1 + 1e-12, row
+        assert up.sum() + csr.sink_up[k] + csr.trunc[k] >= 1 - 1e-12, row
+        assert 0 <= csr.sink_lo[k] <= csr.sink_up[k] <= 1, row
+        dup, dlo, _, _ = orc.row_dense(prob, row)
+        dropped = dup[dup < prob.cutoff]
+        assert len(cols) + len(dropped) == prob.total_cells
+        assert abs(csr.trunc[k] - math.fsum(dropped.tolist())) <= 1e-15 * max(1, len(dropped))
+
+
+def pin_degenerate(orc, seed=11):
+    rng = np.random.default_rng(seed)
+    base = W.room_5d(cells_per_dim=4)
+    base = W.Problem(name="deg3d", kind=W.IMAGES, lo=base.lo[:3], hi=base.hi[:3],
+                     cells=np.array([4, 5, 3], np.int32), inputs=np.zeros((2, 1)),
+                     sigma=np.array([0.3, 0.5, 0.8]), cutoff=1e-8)
+    pts = rng.uniform(16.0, 24.0, size=(base.rows, 3))
+    images = np.stack([pts, pts], axis=2)
+    prob = W.with_images(base, images)
+    rows = np.arange(prob.rows)
+    csr = orc.build_rows(prob, rows)
+    assert np.array_equal(csr.lo, csr.up)
+    assert np.array_equal(csr.sink_lo, csr.sink_up)
+    for k in range(len(rows)):
+        _, lo, up = csr.row(k)
+        total = math.fsum(up.tolist()) + csr.trunc[k] + csr.sink_up[k]
+        assert abs(total - 1.0) < 1e-12, (k, total)
+        # a point image is a point x: the bounds are the exact probabilities
+        P, out = exact_probs(prob, pts[k])
+        cols, _, _ = csr.row(k)
+        assert np.allclose(up, P[cols], rtol=0, atol=1e-14)
+        assert abs(csr.sink_lo[k] - out) < 1e-13
+
+
+def pin_separable_sum(orc, prob, rows):
+    csr = orc.build_rows(prob, rows)
+    for k, row in enumerate(rows):
+        m_lo, m_hi = orc.image(prob, row)
+        total = 1.0
+        for d in range(prob.n):
+            one = W.Problem(name="axis", kind=W.IMAGES, lo=prob.lo[d:d + 1],
+                            hi=prob.hi[d:d + 1], cells=prob.cells[d:d + 1],
+                            inputs=np.zeros((1, 1)), sigma=prob.sigma[d:d + 1], cutoff=0.0,
+                            images=np.array([[[m_lo[d], m_hi[d]]]] * int(prob.cells[d])))
+            up1, _, _, _ = orc.row_dense(one, 0)
+            total *= math.fsum(up1.tolist())
+        _, _, up = csr.row(k)
+        got = math.fsum(up.tolist()) + csr.trunc[k]
+        assert abs(got - total) <= 1e-13 * total, (row, got, total)
+
+
+def pin_tie_kept(orc):
+    prob = W.robot_2d(cells_per_dim=7)
+    up, _, _, _ = orc.row_dense(prob, 40)
+    t = int(np.argsort(up)[len(up) // 2])
+    prob.cutoff = float(up[t])
+    csr = orc.build_rows(prob, [40])
+    cols, _, _ = csr.row(0)
+    assert t in set(cols.tolist())
+    assert np.all(up[cols] >= prob.cutoff)
+    assert len(cols) == int(np.sum(up >= prob.cutoff))
+
+
+def coupled_cases():
+    """(problem, rows) pairs with coupled or nonlinear dynamics, small grids."""
+    room = W.room_5d(cells_per_dim=4)
+    bas = W.bas_4d(eta_scale=2.0)
+    uni = W.unicycle_3d(nx=6, ny=6, nth=7)
+    lin = W.random_linear(7, min_cells=200, max_cells=2000)
+    b7 = W.building_7d(cells_per_dim=3)
+    return [(room, W.sample_rows(room, 4, seed=1)), (bas, W.sample_rows(bas, 4, seed=2)),
+            (uni, W.sample_rows(uni, 6, seed=3)), (lin, W.sample_rows(lin, 4, seed=4)),
+            (b7, W.sample_rows(b7, 2, seed=5, include_boundary=False))]

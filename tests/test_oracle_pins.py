@@ -1,0 +1,102 @@
+"""The CPU oracle against the mathematics and the paper (no GPU needed)."""
+
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import oracle_pins as P
+from paper_2401_03555_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def orc():
+    return oracle.default()
+
+
+def test_phi_matches_high_precision_cdf(orc):
+    worst = P.pin_phi_library(orc)
+    assert worst < 1e-15  # absolute
+
+
+def test_edges_and_axis_telescoping(orc):
+    P.pin_edges_telescoping(orc)
+
+
+def test_one_dimensional_closed_form(orc):
+    P.pin_closed_form_1d(orc)
+
+
+def test_separable_2d_equals_exact_min_max(orc):
+    P.pin_bruteforce_2d(orc)
+
+
+@pytest.mark.parametrize("case", range(5))
+def test_monte_carlo_containment(orc, case):
+    prob, rows = P.coupled_cases()[case]
+    P.pin_mc_containment(orc, prob, rows)
+
+
+def test_unicycle_interval_image(orc):
+    P.pin_unicycle_image(orc)
+
+
+@pytest.mark.parametrize("which", ["bas4d", "unicycle", "room5d"])
+def test_noise_sampling(orc, which):
+    prob = {"bas4d": W.bas_4d(eta_scale=2.0), "unicycle": W.unicycle_3d(nx=8, ny=8, nth=6),
+            "room5d": W.room_5d(cells_per_dim=5)}[which]
+    row = W.sample_rows(prob, 1, seed=9, include_boundary=False)[0]
+    P.pin_noise_sampling(orc, prob, row)
+
+
+@pytest.mark.parametrize("case", range(5))
+def test_invariants_coupled(orc, case):
+    prob, rows = P.coupled_cases()[case]
+    P.pin_invariants(orc, prob, rows)
+
+
+def test_invariants_robot_dense(orc):
+    prob = W.robot_2d(cells_per_dim=9)
+    P.pin_invariants(orc, prob, np.arange(prob.rows))
+
+
+def test_degenerate_point_images(orc):
+    P.pin_degenerate(orc)
+
+
+@pytest.mark.parametrize("case", [0, 2, 3])
+def test_sum_of_uppers_is_product_of_axis_sums(orc, case):
+    prob, rows = P.coupled_cases()[case]
+    P.pin_separable_sum(orc, prob, rows)
+
+
+def test_ties_with_cutoff_are_kept(orc):
+    P.pin_tie_kept(orc)
+
+
+def _parse_golden():
+    rows = []
+    with open(os.path.join(GOLDEN, "table1_grid_counts.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            rows.append([x.strip() for x in line.split("|")])
+    return rows
+
+
+@pytest.mark.parametrize("entry", _parse_golden(), ids=lambda e: e[0])
+def test_table1_grid_counts(entry):
+    name, slb, sub, seta, ilb, iub, ieta, wpts, nx, nu, nrows = entry
+    vec = lambda s: [float(v) for v in s.split(",")]
+    lo, hi, cells = W.grid_from_points(vec(slb), vec(sub), vec(seta))
+    assert int(np.prod(cells.astype(np.int64))) == int(nx)
+    n_inputs = 1 if ilb == "-" else len(W.input_points(vec(ilb), vec(iub), vec(ieta)))
+    assert n_inputs == int(nu)
+    prob = W.Problem(name=name, kind=W.AFFINE, lo=lo, hi=hi, cells=cells,
+                     inputs=np.zeros((n_inputs, 1)), sigma=np.ones(len(lo)), cutoff=0.0)
+    # rows of the transition matrices: |X| x |U| x |W| (Def. 3.1 / Table 1)
+    assert prob.rows * int(wpts) == int(nrows)
+    assert np.allclose(hi - lo, cells * np.array(vec(seta)))
