@@ -1,0 +1,202 @@
+/*
+ * impact.h -- C ABI of the GB300 interval-MDP abstraction builder.
+ *
+ * What the library computes (paper: Def. 3.1 for the bounds, Alg. 2 for the
+ * row-parallel construction, Sec. 4.4 for dropping entries whose upper bound
+ * is negligible, Remark 4.1 for the out-of-domain "sink"):
+ *
+ *   x+ = f(x, u) + w,  w ~ N(0, diag(sigma^2)),  state grid of N_d cells per
+ *   dimension on the box [lo, hi], a finite list of input points u_j.
+ *
+ *   Row r = cell * n_inputs + j (cell id in C order, last dimension fastest).
+ *   For each row, [m_lo, m_hi] is the interval image of f(., u_j) over the
+ *   closed source cell, and for target cell t with edges [c_d, e_d]:
+ *     g_d(m) = Phi((e_d - m)/sigma_d) - Phi((c_d - m)/sigma_d)
+ *     up_t   = prod_d g_d(clamp((c_d+e_d)/2, m_lo_d, m_hi_d))   (>= T_max)
+ *     lo_t   = prod_d min(g_d(m_lo_d), g_d(m_hi_d))             (<= T_min)
+ *   Target t is kept iff up_t >= cutoff (ties kept; cutoff 0 keeps all).
+ *   sink_lo / sink_up are the same bounds for landing outside [lo, hi];
+ *   trunc is the summed upper bound of the dropped targets, so that for every
+ *   row  sum(lo) + sink_lo <= 1 <= sum(up) + sink_up + trunc.
+ *
+ * Grid convention: edge i of dimension d is lo_d + i*(hi_d - lo_d)/N_d, and
+ * edge N_d is hi_d itself. Input points are points (no input cells).
+ *
+ * Precisions:
+ *   IMPACT_FP64_PLAIN  every factor of every pair evaluated in FP64 (erfc per
+ *                      pair and dimension); lo/up stored as double.
+ *   IMPACT_FP32_SOUND  factors from per-row FP32 tables with outward rounding:
+ *                      lo32 <= lo64 and up32 >= up64 for the FP64 values of
+ *                      the definition above; lo/up stored as float. The row
+ *                      terms (sink, trunc, row checks) are combined in FP64.
+ *
+ * Threading: every entry point may be called from several host threads; the
+ * last-error message is thread-local. Calls on one stream are ordered.
+ *
+ * Errors: every entry point returns an impact_status; no C++ exception
+ * crosses the ABI. On failure impact_last_error() describes the cause.
+ */
+#ifndef IMPACT_H
+#define IMPACT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    IMPACT_OK = 0,
+    IMPACT_ERR_ARG = 1,       /* invalid argument (sizes, pointers, ranges)          */
+    IMPACT_ERR_OOM = 2,       /* a device allocation failed                          */
+    IMPACT_ERR_CAPACITY = 3,  /* caller buffers too small; needed nnz written back   */
+    IMPACT_ERR_CUDA = 4,      /* a CUDA runtime call or a kernel launch failed       */
+    IMPACT_ERR_TIMEOUT = 5,   /* a bounded device wait gave up                       */
+    IMPACT_ERR_UNSOUND = 6    /* a row check proved a row-sum invariant violated     */
+} impact_status;
+
+typedef enum {
+    IMPACT_AFFINE = 0,    /* f(x,u) = A x + B u + c                                   */
+    IMPACT_UNICYCLE = 1,  /* n = 3, u = (v, om): x+v cos th, y+v sin th, th+om        */
+    IMPACT_IMAGES = 2     /* caller supplies [m_lo, m_hi] per row and dimension       */
+} impact_kind;
+
+typedef enum {
+    IMPACT_FP64_PLAIN = 0,
+    IMPACT_FP32_SOUND = 1
+} impact_precision;
+
+/* Row-check bits of impact_csr.row_flags (only set when a violation is proved). */
+#define IMPACT_ROW_LO_SUM_ABOVE_ONE  0x1u  /* sum(lo) + sink_lo > 1                  */
+#define IMPACT_ROW_UP_SUM_BELOW_ONE  0x2u  /* sum(up) + sink_up + trunc < 1          */
+
+/*
+ * The dynamics. Host pointers, read during the call only.
+ *   AFFINE:   A (n*n, row-major), B (n*m, row-major; NULL when m == 0),
+ *             c (n; NULL means zero).
+ *   UNICYCLE: n = 3, m = 2; A, B, c unused.
+ *   IMAGES:   dev_images is a DEVICE array of rows*n*2 doubles,
+ *             (m_lo, m_hi) per row and dimension, m_lo <= m_hi.
+ * params is reserved and must be NULL.
+ */
+typedef struct {
+    int kind;
+    int n;
+    int m;
+    const double *A;
+    const double *B;
+    const double *c;
+    const double *params;
+    const double *dev_images;
+} impact_system;
+
+/* The state grid (host arrays of length n): dimension d of [lo_d, hi_d] is
+ * cut into cells[d] >= 1 equal cells, lo_d < hi_d, product of cells < 2^31. */
+typedef struct {
+    int n;
+    const double *lo;
+    const double *hi;
+    const int32_t *cells;
+} impact_grid;
+
+/* The input points (host, count*m doubles, row-major). count >= 1; with m == 0
+ * (no input) pass count = 1 and points = NULL. */
+typedef struct {
+    int count;
+    int m;
+    const double *points;
+} impact_inputs;
+
+/*
+ * The result, a CSR matrix with one row per (cell, input) and int32 target
+ * cell ids in ascending order within each row. All arrays are DEVICE memory.
+ *   rows            out: number of rows
+ *   nnz             in: capacity of col/lo/up when the caller owns them;
+ *                   out: number of stored pairs
+ *   row_ptr         int64[rows+1]
+ *   col             int32[nnz]
+ *   lo, up          double[nnz] (FP64_PLAIN) or float[nnz] (FP32_SOUND)
+ *   sink_lo/sink_up double[rows]
+ *   trunc           double[rows]
+ *   row_flags       uint32[rows] (may be NULL: then no row checks are kept)
+ *   owned           set to 1 by the library when it allocated the arrays
+ * Ownership: if col == NULL on entry to impact_build, the library allocates
+ * every array stream-ordered on the given stream and impact_free releases
+ * them; otherwise all arrays are the caller's and nnz is their capacity.
+ */
+typedef struct {
+    int64_t rows;
+    int64_t nnz;
+    int64_t *row_ptr;
+    int32_t *col;
+    void *lo;
+    void *up;
+    double *sink_lo;
+    double *sink_up;
+    double *trunc;
+    uint32_t *row_flags;
+    int owned;
+} impact_csr;
+
+/*
+ * impact_plan -- host-only sizing, no GPU work.
+ * Writes the number of rows and an upper bound on nnz (the sum over rows of
+ * the product of per-dimension window widths, Sec. 4.4 "low-cost"
+ * truncation) and the device bytes that impact_build with library-owned
+ * output would need at that bound. Any output pointer may be NULL.
+ * Errors: IMPACT_ERR_ARG for invalid sizes or ranges.
+ */
+impact_status impact_plan(const impact_system *sys, const impact_grid *grid,
+                          const impact_inputs *inputs, const double *sigma, double cutoff,
+                          impact_precision precision, int64_t *rows, int64_t *nnz_upper_bound,
+                          int64_t *bytes_upper_bound);
+
+/*
+ * impact_build -- the whole abstraction (Alg. 2) on `stream` (a cudaStream_t;
+ * NULL is the legacy default stream). Runs the count pass, the row-pointer
+ * scan and the emit pass. Synchronizes `stream` once at the end (and once
+ * after the scan when the library allocates) to report nnz and status.
+ * Errors: IMPACT_ERR_ARG, IMPACT_ERR_OOM, IMPACT_ERR_CUDA;
+ *         IMPACT_ERR_CAPACITY when caller-owned col/lo/up hold fewer than the
+ *         needed pairs (out->nnz then holds the needed count, row_ptr and the
+ *         row terms are valid, col/lo/up are untouched);
+ *         IMPACT_ERR_UNSOUND when row_flags != NULL and some row check failed
+ *         (the output is complete; row_flags tells which rows).
+ */
+impact_status impact_build(const impact_system *sys, const impact_grid *grid,
+                           const impact_inputs *inputs, const double *sigma, double cutoff,
+                           impact_precision precision, impact_csr *out, void *stream);
+
+/*
+ * impact_count -- first half of impact_build with caller-owned arrays: writes
+ * out->row_ptr (rows+1 entries), sink_lo, sink_up, trunc and row_flags, then
+ * synchronizes `stream` and stores the total pair count in out->nnz.
+ * col/lo/up are not touched and may be NULL.
+ */
+impact_status impact_count(const impact_system *sys, const impact_grid *grid,
+                           const impact_inputs *inputs, const double *sigma, double cutoff,
+                           impact_precision precision, impact_csr *out, void *stream);
+
+/*
+ * impact_emit -- second half: given out->row_ptr from impact_count with the
+ * same arguments, writes col/lo/up (capacity out->nnz >= row_ptr[rows]).
+ * Asynchronous on `stream`; no synchronization.
+ */
+impact_status impact_emit(const impact_system *sys, const impact_grid *grid,
+                          const impact_inputs *inputs, const double *sigma, double cutoff,
+                          impact_precision precision, impact_csr *out, void *stream);
+
+/* Release library-owned arrays of a result (no-op for caller-owned ones). */
+impact_status impact_free(impact_csr *out);
+
+/* Message of the last failing call on this host thread ("" if none). */
+const char *impact_last_error(void);
+
+/* Library ABI version (major*100 + minor). */
+int impact_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IMPACT_H */

@@ -1,0 +1,594 @@
+// api.cu -- host planner and the C ABI entry points (include/impact.h).
+//
+// The planner validates the arguments, computes every per-build constant in
+// FP64 on the host (grid edges, per-term image tables, input offsets, window
+// margins, plateau and out-of-domain constants), packs them with the
+// descriptor into one device allocation, and runs the count -> scan -> emit
+// pipeline on the caller's stream.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/impact.h"
+#include "impact_desc.h"
+#include "kernels.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+impact_status fail(impact_status s, const std::string &msg)
+{
+    g_last_error = msg;
+    return s;
+}
+
+#define CK(expr)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (expr);                                                              \
+        if (e_ != cudaSuccess) {                                                              \
+            return fail(e_ == cudaErrorMemoryAllocation ? IMPACT_ERR_OOM : IMPACT_ERR_CUDA,   \
+                        std::string(#expr) + ": " + cudaGetErrorString(e_));                 \
+        }                                                                                     \
+    } while (0)
+
+double next_down(double x) { return nextafter(x, -INFINITY); }
+double next_up(double x) { return nextafter(x, INFINITY); }
+
+// Smallest float >= x (x finite, representable range).
+float f32_up(double x)
+{
+    float f = (float)x;
+    if ((double)f < x) f = nextafterf(f, INFINITY);
+    return f;
+}
+
+float f32_down(double x)
+{
+    float f = (float)x;
+    if ((double)f > x) f = nextafterf(f, -INFINITY);
+    return f;
+}
+
+// Range of cos / sin over [a, b]: endpoint values, widened to +-1 where an
+// extremum (k pi for cos, pi/2 + k pi for sin) lies inside. `slack` > 0 widens
+// the interval used for the extremum test and the endpoint values (outward).
+void trig_range(bool is_cos, double a, double b, double slack, double &lo, double &hi)
+{
+    double fa = is_cos ? cos(a) : sin(a);
+    double fb = is_cos ? cos(b) : sin(b);
+    lo = fa < fb ? fa : fb;
+    hi = fa < fb ? fb : fa;
+    double shift = is_cos ? 0.0 : M_PI_2;
+    double a2 = a - slack, b2 = b + slack;
+    for (long k = (long)ceil((a2 - shift) / M_PI); shift + (double)k * M_PI <= b2; ++k) {
+        if (k % 2 == 0) hi = 1.0; else lo = -1.0;
+    }
+    if (slack > 0.0) {
+        lo = std::max(-1.0, lo - 8.0 * 2.220446049250313e-16);
+        hi = std::min(1.0, hi + 8.0 * 2.220446049250313e-16);
+    }
+}
+
+struct Plan {
+    ImpactDesc desc;
+    std::vector<double> edges, term_rn, term_dn, term_up, off_rn, off_dn, off_up, uni_rn,
+        uni_sd, inputs;
+    int64_t rows = 0;
+    int64_t nnz_bound = 0;
+    int table_need = 0;   // upper bound of the staged entries per row (-1: unknown)
+};
+
+// Offsets (in bytes, 256-aligned) of the arrays in the device blob.
+struct BlobLayout {
+    size_t desc, edges, term_rn, term_dn, term_up, off_rn, off_dn, off_up, uni_rn, uni_sd,
+        inputs, status, total;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+BlobLayout layout_of(const Plan &p)
+{
+    BlobLayout L;
+    size_t o = 0;
+    auto put = [&](size_t bytes) {
+        size_t at = o;
+        o = align256(o + bytes);
+        return at;
+    };
+    L.desc = put(sizeof(ImpactDesc));
+    L.edges = put(p.edges.size() * 8);
+    L.term_rn = put(p.term_rn.size() * 8);
+    L.term_dn = put(p.term_dn.size() * 8);
+    L.term_up = put(p.term_up.size() * 8);
+    L.off_rn = put(p.off_rn.size() * 8);
+    L.off_dn = put(p.off_dn.size() * 8);
+    L.off_up = put(p.off_up.size() * 8);
+    L.uni_rn = put(p.uni_rn.size() * 8);
+    L.uni_sd = put(p.uni_sd.size() * 8);
+    L.inputs = put(p.inputs.size() * 8);
+    L.status = put(64);
+    L.total = o;
+    return L;
+}
+
+// z with P(Z >= z) = erfc(z/sqrt2)/2 <= p for a standard normal Z (bisection).
+double normal_quantile_upper(double p)
+{
+    double lo = 0.0, hi = 40.0;
+    for (int it = 0; it < 200; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (0.5 * erfc(mid * M_SQRT1_2) <= p) hi = mid; else lo = mid;
+    }
+    return hi;
+}
+
+impact_status make_plan(const impact_system *sys, const impact_grid *grid,
+                        const impact_inputs *inputs, const double *sigma, double cutoff,
+                        impact_precision precision, Plan &P)
+{
+    if (!sys || !grid || !inputs || !sigma) return fail(IMPACT_ERR_ARG, "null argument");
+    const int n = grid->n;
+    if (n < 1 || n > IMPACT_MAX_DIM) return fail(IMPACT_ERR_ARG, "grid.n must be in [1, 8]");
+    if (sys->n != n) return fail(IMPACT_ERR_ARG, "system.n != grid.n");
+    if (!grid->lo || !grid->hi || !grid->cells) return fail(IMPACT_ERR_ARG, "null grid array");
+    if (sys->kind < IMPACT_AFFINE || sys->kind > IMPACT_IMAGES)
+        return fail(IMPACT_ERR_ARG, "unknown system kind");
+    if (precision != IMPACT_FP64_PLAIN && precision != IMPACT_FP32_SOUND)
+        return fail(IMPACT_ERR_ARG, "unknown precision");
+    if (!(cutoff >= 0.0 && cutoff < 1.0)) return fail(IMPACT_ERR_ARG, "cutoff must be in [0, 1)");
+    if (sys->params) return fail(IMPACT_ERR_ARG, "system.params is reserved and must be NULL");
+    const int m = inputs->m;
+    if (inputs->count < 1) return fail(IMPACT_ERR_ARG, "inputs.count must be >= 1");
+    if (m < 0 || m > IMPACT_MAX_M) return fail(IMPACT_ERR_ARG, "inputs.m must be in [0, 8]");
+    if (m > 0 && !inputs->points) return fail(IMPACT_ERR_ARG, "null input points");
+    if (sys->kind == IMPACT_AFFINE) {
+        if (!sys->A) return fail(IMPACT_ERR_ARG, "affine system needs A");
+        if (sys->m != m) return fail(IMPACT_ERR_ARG, "system.m != inputs.m");
+        if (m > 0 && !sys->B) return fail(IMPACT_ERR_ARG, "affine system with inputs needs B");
+    } else if (sys->kind == IMPACT_UNICYCLE) {
+        if (n != 3 || m != 2) return fail(IMPACT_ERR_ARG, "unicycle needs n = 3, m = 2");
+    } else {
+        if (!sys->dev_images) return fail(IMPACT_ERR_ARG, "images system needs dev_images");
+    }
+    int64_t cells = 1;
+    for (int d = 0; d < n; ++d) {
+        if (grid->cells[d] < 1) return fail(IMPACT_ERR_ARG, "cells must be >= 1");
+        if (!(grid->lo[d] < grid->hi[d]) || !isfinite(grid->lo[d]) || !isfinite(grid->hi[d]))
+            return fail(IMPACT_ERR_ARG, "grid needs finite lo < hi");
+        if (!(sigma[d] > 0.0) || !isfinite(sigma[d]))
+            return fail(IMPACT_ERR_ARG, "sigma must be finite and > 0");
+        cells *= grid->cells[d];
+        if (cells >= ((int64_t)1 << 31)) return fail(IMPACT_ERR_ARG, "more than 2^31-1 cells");
+    }
+    const int n_inputs = inputs->count;
+    const int64_t rows = cells * n_inputs;
+
+    ImpactDesc &D = P.desc;
+    memset(&D, 0, sizeof(D));
+    D.n = n;
+    D.m = m;
+    D.kind = sys->kind;
+    D.prec = precision;
+    D.n_inputs = n_inputs;
+    D.n_in_split_min = 24;
+    D.rows = rows;
+    D.cells = cells;
+    D.cutoff = cutoff;
+    D.cutoff32 = f32_up(cutoff);
+    D.table_max = IMPACT_TABLE_MAX;
+    P.rows = rows;
+
+    // grid edges (E_i = lo + i*h, E_N = hi), per-dimension constants
+    int nmax = 0;
+    int64_t stride = 1;
+    for (int d = n - 1; d >= 0; --d) {
+        D.dim[d].stride = (int)stride;
+        stride *= grid->cells[d];
+    }
+    const double zc = cutoff > 0.0 ? normal_quantile_upper(0.5 * cutoff) : INFINITY;
+    for (int d = 0; d < n; ++d) {
+        ImpactDim &g = D.dim[d];
+        const int N = grid->cells[d];
+        nmax = std::max(nmax, N);
+        g.lo = grid->lo[d];
+        g.hi = grid->hi[d];
+        g.N = N;
+        g.h = (g.hi - g.lo) / (double)N;
+        g.inv_h = 1.0 / g.h;
+        g.sigma = sigma[d];
+        g.inv_s = 1.0 / (sigma[d] * M_SQRT2);
+        g.kappa = g.h * g.inv_s;
+        g.kappa_hi = (float)g.kappa;
+        g.kappa_lo = (float)(g.kappa - (double)g.kappa_hi);
+        g.delta = isfinite(zc) ? sigma[d] * zc * (1.0 + 1e-9) : INFINITY;
+        g.edge_off = (int)P.edges.size();
+        double hmax = 0.0;
+        for (int i = 0; i <= N; ++i) {
+            double e = (i == N) ? g.hi : g.lo + (double)i * g.h;
+            P.edges.push_back(e);
+            if (i > 0) hmax = std::max(hmax, e - P.edges[P.edges.size() - 2]);
+        }
+        double mag = std::max(fabs(g.lo), fabs(g.hi));
+        double dev = ldexp(mag + fabs(g.hi - g.lo), -51) + fabs(g.hi - (g.lo + (double)N * g.h)) +
+                     ldexp(fabs(g.hi), -50);
+        g.edge_err = f32_up(dev * g.inv_s * (1.0 + 1e-9) + 1e-300);
+        double xp = hmax * g.inv_s * 0.5 * (1.0 + 1e-12);
+        g.plateau_hi = std::min(1.0f, f32_up(erf(xp) + 4e-16));
+        double xq = (g.hi - g.lo) * g.inv_s * 0.5 * (1.0 + 1e-12);
+        g.qmin_lo = f32_down(erfc(xq) * (1.0 - 1e-13));
+    }
+    D.n_max = nmax;
+
+    // inputs
+    for (int j = 0; j < n_inputs; ++j)
+        for (int k = 0; k < m; ++k) P.inputs.push_back(inputs->points[(int64_t)j * m + k]);
+
+    // per-dimension window width bound -> nnz bound and staging need
+    std::vector<double> width(n, 0.0);
+    if (sys->kind == IMPACT_AFFINE) {
+        const double *A = sys->A;
+        // image terms: per (d, k, cell i of dim k) the range of A_dk * x_k
+        P.term_rn.assign((size_t)n * n * nmax * 2, 0.0);
+        P.term_dn.assign((size_t)n * n * nmax, 0.0);
+        P.term_up.assign((size_t)n * n * nmax, 0.0);
+        for (int d = 0; d < n; ++d) {
+            for (int k = 0; k < n; ++k) {
+                const double a = A[d * n + k];
+                if (!isfinite(a)) return fail(IMPACT_ERR_ARG, "A must be finite");
+                const ImpactDim &gk = D.dim[k];
+                for (int i = 0; i < gk.N; ++i) {
+                    double x0 = P.edges[gk.edge_off + i], x1 = P.edges[gk.edge_off + i + 1];
+                    double p0 = a * x0, p1 = a * x1;
+                    size_t t = ((size_t)(d * n + k) * nmax + i);
+                    P.term_rn[2 * t] = p0 < p1 ? p0 : p1;
+                    P.term_rn[2 * t + 1] = p0 < p1 ? p1 : p0;
+                    // the rounded products are within half an ulp of the exact ones
+                    P.term_dn[t] = std::min(next_down(p0), next_down(p1));
+                    P.term_up[t] = std::max(next_up(p0), next_up(p1));
+                }
+                width[d] += fabs(a) * gk.h;
+            }
+        }
+        // input offsets c_d + sum_k B_dk u_k, in the definition's order, and a bracket
+        P.off_rn.assign((size_t)n_inputs * n, 0.0);
+        P.off_dn.assign((size_t)n_inputs * n, 0.0);
+        P.off_up.assign((size_t)n_inputs * n, 0.0);
+        for (int j = 0; j < n_inputs; ++j) {
+            const double *u = inputs->points ? inputs->points + (int64_t)j * m : nullptr;
+            for (int d = 0; d < n; ++d) {
+                double off = sys->c ? sys->c[d] : 0.0;
+                double mag = fabs(off);
+                for (int k = 0; k < m; ++k) {
+                    double t = sys->B[d * m + k] * u[k];
+                    off += t;
+                    mag += fabs(t);
+                }
+                if (!isfinite(off)) return fail(IMPACT_ERR_ARG, "B, c and inputs must be finite");
+                double err = ldexp(mag, -50) * (double)(m + 2) + 1e-300;
+                P.off_rn[(size_t)j * n + d] = off;
+                P.off_dn[(size_t)j * n + d] = next_down(off - err);
+                P.off_up[(size_t)j * n + d] = next_up(off + err);
+            }
+        }
+    } else if (sys->kind == IMPACT_UNICYCLE) {
+        const ImpactDim &gt = D.dim[2];
+        P.uni_rn.assign((size_t)gt.N * n_inputs * 4, 0.0);
+        P.uni_sd.assign((size_t)gt.N * n_inputs * 4, 0.0);
+        double vmax = 0.0;
+        for (int i = 0; i < gt.N; ++i) {
+            double a = P.edges[gt.edge_off + i], b = P.edges[gt.edge_off + i + 1];
+            double cl, ch, sl, sh, cls, chs, sls, shs;
+            trig_range(true, a, b, 0.0, cl, ch);
+            trig_range(false, a, b, 0.0, sl, sh);
+            trig_range(true, a, b, 1e-12, cls, chs);
+            trig_range(false, a, b, 1e-12, sls, shs);
+            for (int j = 0; j < n_inputs; ++j) {
+                double v = inputs->points[(int64_t)j * m + 0];
+                vmax = std::max(vmax, fabs(v));
+                double *r = &P.uni_rn[((size_t)i * n_inputs + j) * 4];
+                double *s = &P.uni_sd[((size_t)i * n_inputs + j) * 4];
+                double c1 = v * cl, c2 = v * ch, s1 = v * sl, s2 = v * sh;
+                r[0] = c1 < c2 ? c1 : c2;
+                r[1] = c1 < c2 ? c2 : c1;
+                r[2] = s1 < s2 ? s1 : s2;
+                r[3] = s1 < s2 ? s2 : s1;
+                double c3 = v * cls, c4 = v * chs, s3 = v * sls, s4 = v * shs;
+                s[0] = next_down(std::min(c3, c4));
+                s[1] = next_up(std::max(c3, c4));
+                s[2] = next_down(std::min(s3, s4));
+                s[3] = next_up(std::max(s3, s4));
+            }
+        }
+        width[0] = D.dim[0].h + 2.0 * vmax;
+        width[1] = D.dim[1].h + 2.0 * vmax;
+        width[2] = D.dim[2].h;
+    }
+    // window widths: image width + 2 delta, plus the 2-cell slack and rounding
+    int64_t box = 1;
+    int need = 0;
+    for (int d = 0; d < n; ++d) {
+        const ImpactDim &g = D.dim[d];
+        int64_t w = g.N;
+        if (sys->kind != IMPACT_IMAGES && isfinite(g.delta)) {
+            double cw = ceil((width[d] + 2.0 * g.delta) * g.inv_h) + 4.0;
+            if (cw < (double)g.N) w = (int64_t)cw;
+        }
+        box *= w;
+        need += (int)w;
+    }
+    P.table_need = (sys->kind == IMPACT_IMAGES) ? -1 : need;
+    if (box > cells) box = cells;
+    P.nnz_bound = box * rows;
+    if (P.table_need > IMPACT_TABLE_MAX)
+        return fail(IMPACT_ERR_ARG,
+                    "the per-row windows need " + std::to_string(P.table_need) +
+                        " staged factors (limit " + std::to_string(IMPACT_TABLE_MAX) +
+                        "): raise the cutoff or use fewer cells");
+    return IMPACT_OK;
+}
+
+// Device copy of a plan: one allocation holding the descriptor and tables.
+struct DeviceBlob {
+    unsigned char *base = nullptr;
+    BlobLayout L;
+    ImpactDesc *desc() const { return (ImpactDesc *)(base + L.desc); }
+    uint32_t *status() const { return (uint32_t *)(base + L.status); }
+};
+
+impact_status upload(Plan &P, DeviceBlob &B, cudaStream_t st, const double *dev_images)
+{
+    B.L = layout_of(P);
+    CK(cudaMallocAsync((void **)&B.base, B.L.total, st));
+    std::vector<unsigned char> host(B.L.total, 0);
+    ImpactDesc D = P.desc;
+    auto dptr = [&](size_t off, const std::vector<double> &v) -> const double * {
+        return v.empty() ? nullptr : (const double *)(B.base + off);
+    };
+    D.edges = dptr(B.L.edges, P.edges);
+    D.term_rn = dptr(B.L.term_rn, P.term_rn);
+    D.term_dn = dptr(B.L.term_dn, P.term_dn);
+    D.term_up = dptr(B.L.term_up, P.term_up);
+    D.off_rn = dptr(B.L.off_rn, P.off_rn);
+    D.off_dn = dptr(B.L.off_dn, P.off_dn);
+    D.off_up = dptr(B.L.off_up, P.off_up);
+    D.uni_rn = dptr(B.L.uni_rn, P.uni_rn);
+    D.uni_sd = dptr(B.L.uni_sd, P.uni_sd);
+    D.inputs = dptr(B.L.inputs, P.inputs);
+    D.images = dev_images;
+    memcpy(host.data() + B.L.desc, &D, sizeof(D));
+    auto put = [&](size_t off, const std::vector<double> &v) {
+        if (!v.empty()) memcpy(host.data() + off, v.data(), v.size() * 8);
+    };
+    put(B.L.edges, P.edges);
+    put(B.L.term_rn, P.term_rn);
+    put(B.L.term_dn, P.term_dn);
+    put(B.L.term_up, P.term_up);
+    put(B.L.off_rn, P.off_rn);
+    put(B.L.off_dn, P.off_dn);
+    put(B.L.off_up, P.off_up);
+    put(B.L.uni_rn, P.uni_rn);
+    put(B.L.uni_sd, P.uni_sd);
+    put(B.L.inputs, P.inputs);
+    // pageable source: returns once the bytes are staged, so `host` may go
+    CK(cudaMemcpyAsync(B.base, host.data(), B.L.total, cudaMemcpyHostToDevice, st));
+    return IMPACT_OK;
+}
+
+void configure_pool_once()
+{
+    static bool done = false;
+    if (done) return;
+    done = true;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess) return;
+    uint64_t keep = UINT64_MAX;   // keep freed blocks in the pool between builds
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+}
+
+bool is_device_ptr(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Stages of a build. `emit_capacity` < 0 skips the emit pass.
+impact_status run_count(const Plan &P, const DeviceBlob &B, impact_csr *out, cudaStream_t st)
+{
+    int64_t *scratch = nullptr;
+    CK(cudaMallocAsync((void **)&scratch, impact::scan_scratch_elems(P.rows) * 8, st));
+    impact::RowOutputs o{out->row_ptr, nullptr, nullptr, nullptr, out->sink_lo, out->sink_up,
+                         out->trunc, out->row_flags, B.status(), -1, P.rows};
+    CK(impact::launch_rows(B.desc(), P.desc.prec, false, 0, P.rows, o, st));
+    CK(impact::launch_scan(out->row_ptr, P.rows, scratch, st));
+    CK(cudaFreeAsync(scratch, st));
+    return IMPACT_OK;
+}
+
+impact_status run_emit(const Plan &P, const DeviceBlob &B, impact_csr *out, int64_t capacity,
+                       cudaStream_t st)
+{
+    impact::RowOutputs o{out->row_ptr, out->col, out->lo, out->up, nullptr, nullptr, nullptr,
+                         nullptr, B.status(), capacity, P.rows};
+    CK(impact::launch_rows(B.desc(), P.desc.prec, true, 0, P.rows, o, st));
+    return IMPACT_OK;
+}
+
+impact_status check_row_arrays(const impact_csr *out)
+{
+    if (!is_device_ptr(out->row_ptr) || !is_device_ptr(out->sink_lo) ||
+        !is_device_ptr(out->sink_up) || !is_device_ptr(out->trunc))
+        return fail(IMPACT_ERR_ARG, "row_ptr, sink_lo, sink_up and trunc must be device arrays");
+    if (out->row_flags && !is_device_ptr(out->row_flags))
+        return fail(IMPACT_ERR_ARG, "row_flags must be a device array or NULL");
+    return IMPACT_OK;
+}
+
+impact_status status_result(uint32_t status)
+{
+    if (status & IMPACT_STATUS_TABLE_OVERFLOW)
+        return fail(IMPACT_ERR_ARG,
+                    "a row's windows exceeded the per-row factor staging (raise the cutoff)");
+    if (status & IMPACT_STATUS_EMIT_MISMATCH)
+        return fail(IMPACT_ERR_CUDA, "internal: the emit pass disagreed with the count pass");
+    if (status & IMPACT_STATUS_UNSOUND)
+        return fail(IMPACT_ERR_UNSOUND, "a row check proved a row-sum invariant violated");
+    return IMPACT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+impact_status impact_plan(const impact_system *sys, const impact_grid *grid,
+                          const impact_inputs *inputs, const double *sigma, double cutoff,
+                          impact_precision precision, int64_t *rows, int64_t *nnz_upper_bound,
+                          int64_t *bytes_upper_bound)
+{
+    Plan P;
+    impact_status s = make_plan(sys, grid, inputs, sigma, cutoff, precision, P);
+    if (s != IMPACT_OK) return s;
+    if (rows) *rows = P.rows;
+    if (nnz_upper_bound) *nnz_upper_bound = P.nnz_bound;
+    if (bytes_upper_bound) {
+        int64_t per_pair = precision == IMPACT_FP32_SOUND ? 12 : 20;
+        *bytes_upper_bound = P.nnz_bound * per_pair + (P.rows + 1) * 8 + P.rows * (3 * 8 + 4) +
+                             (int64_t)layout_of(P).total;
+    }
+    return IMPACT_OK;
+}
+
+impact_status impact_count(const impact_system *sys, const impact_grid *grid,
+                           const impact_inputs *inputs, const double *sigma, double cutoff,
+                           impact_precision precision, impact_csr *out, void *stream)
+{
+    if (!out) return fail(IMPACT_ERR_ARG, "null output");
+    Plan P;
+    impact_status s = make_plan(sys, grid, inputs, sigma, cutoff, precision, P);
+    if (s != IMPACT_OK) return s;
+    if ((s = check_row_arrays(out)) != IMPACT_OK) return s;
+    configure_pool_once();
+    cudaStream_t st = (cudaStream_t)stream;
+    DeviceBlob B;
+    if ((s = upload(P, B, st, sys->dev_images)) != IMPACT_OK) return s;
+    CK(cudaMemsetAsync(B.status(), 0, 64, st));
+    if ((s = run_count(P, B, out, st)) != IMPACT_OK) return s;
+    int64_t nnz = 0;
+    uint32_t status = 0;
+    CK(cudaMemcpyAsync(&nnz, out->row_ptr + P.rows, 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&status, B.status(), 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaFreeAsync(B.base, st));
+    CK(cudaStreamSynchronize(st));
+    out->rows = P.rows;
+    out->nnz = nnz;
+    return status_result(status);
+}
+
+impact_status impact_emit(const impact_system *sys, const impact_grid *grid,
+                          const impact_inputs *inputs, const double *sigma, double cutoff,
+                          impact_precision precision, impact_csr *out, void *stream)
+{
+    if (!out) return fail(IMPACT_ERR_ARG, "null output");
+    Plan P;
+    impact_status s = make_plan(sys, grid, inputs, sigma, cutoff, precision, P);
+    if (s != IMPACT_OK) return s;
+    if (!is_device_ptr(out->row_ptr)) return fail(IMPACT_ERR_ARG, "row_ptr must be a device array");
+    if (out->nnz > 0 && (!is_device_ptr(out->col) || !is_device_ptr(out->lo) ||
+                         !is_device_ptr(out->up)))
+        return fail(IMPACT_ERR_ARG, "col, lo and up must be device arrays");
+    configure_pool_once();
+    cudaStream_t st = (cudaStream_t)stream;
+    DeviceBlob B;
+    if ((s = upload(P, B, st, sys->dev_images)) != IMPACT_OK) return s;
+    CK(cudaMemsetAsync(B.status(), 0, 64, st));
+    if ((s = run_emit(P, B, out, out->nnz, st)) != IMPACT_OK) return s;
+    CK(cudaFreeAsync(B.base, st));
+    out->rows = P.rows;
+    return IMPACT_OK;
+}
+
+impact_status impact_build(const impact_system *sys, const impact_grid *grid,
+                           const impact_inputs *inputs, const double *sigma, double cutoff,
+                           impact_precision precision, impact_csr *out, void *stream)
+{
+    if (!out) return fail(IMPACT_ERR_ARG, "null output");
+    Plan P;
+    impact_status s = make_plan(sys, grid, inputs, sigma, cutoff, precision, P);
+    if (s != IMPACT_OK) return s;
+    configure_pool_once();
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool lib_owned = (out->col == nullptr);
+    const size_t vbytes = precision == IMPACT_FP32_SOUND ? 4 : 8;
+    if (lib_owned) {
+        memset(out, 0, sizeof(*out));
+        CK(cudaMallocAsync((void **)&out->row_ptr, (P.rows + 1) * 8, st));
+        CK(cudaMallocAsync((void **)&out->sink_lo, P.rows * 8, st));
+        CK(cudaMallocAsync((void **)&out->sink_up, P.rows * 8, st));
+        CK(cudaMallocAsync((void **)&out->trunc, P.rows * 8, st));
+        CK(cudaMallocAsync((void **)&out->row_flags, P.rows * 4, st));
+        out->owned = 1;
+    } else {
+        if ((s = check_row_arrays(out)) != IMPACT_OK) return s;
+        if (out->nnz > 0 && (!is_device_ptr(out->col) || !is_device_ptr(out->lo) ||
+                             !is_device_ptr(out->up)))
+            return fail(IMPACT_ERR_ARG, "col, lo and up must be device arrays");
+    }
+    DeviceBlob B;
+    if ((s = upload(P, B, st, sys->dev_images)) != IMPACT_OK) return s;
+    CK(cudaMemsetAsync(B.status(), 0, 64, st));
+    if ((s = run_count(P, B, out, st)) != IMPACT_OK) return s;
+    int64_t capacity = out->nnz;
+    if (lib_owned) {
+        int64_t nnz = 0;
+        CK(cudaMemcpyAsync(&nnz, out->row_ptr + P.rows, 8, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        size_t k = (size_t)std::max<int64_t>(nnz, 1);
+        CK(cudaMallocAsync((void **)&out->col, k * 4, st));
+        CK(cudaMallocAsync(&out->lo, k * vbytes, st));
+        CK(cudaMallocAsync(&out->up, k * vbytes, st));
+        capacity = nnz;
+    }
+    if ((s = run_emit(P, B, out, capacity, st)) != IMPACT_OK) return s;
+    int64_t nnz = 0;
+    uint32_t status = 0;
+    CK(cudaMemcpyAsync(&nnz, out->row_ptr + P.rows, 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&status, B.status(), 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaFreeAsync(B.base, st));
+    CK(cudaStreamSynchronize(st));
+    out->rows = P.rows;
+    out->nnz = nnz;
+    if (status & IMPACT_STATUS_CAPACITY)
+        return fail(IMPACT_ERR_CAPACITY, "output capacity " + std::to_string(capacity) +
+                                             " < needed pairs " + std::to_string(nnz));
+    return status_result(status);
+}
+
+impact_status impact_free(impact_csr *out)
+{
+    if (!out) return fail(IMPACT_ERR_ARG, "null output");
+    if (!out->owned) return IMPACT_OK;
+    void *ptrs[] = {out->row_ptr, out->col, out->lo, out->up, out->sink_lo,
+                    out->sink_up, out->trunc, out->row_flags};
+    for (void *p : ptrs)
+        if (p) CK(cudaFree(p));
+    memset(out, 0, sizeof(*out));
+    return IMPACT_OK;
+}
+
+const char *impact_last_error(void) { return g_last_error.c_str(); }
+
+int impact_version(void) { return 100; }
+
+}  // extern "C"

@@ -1,0 +1,67 @@
+// impact_desc.h -- the per-build descriptor the host planner uploads once and
+// every kernel of the build reads. Plain data, shared by host and device code.
+#pragma once
+#include <stdint.h>
+
+#define IMPACT_MAX_DIM 8
+#define IMPACT_MAX_M 8
+
+// Per-dimension constants (computed on the host in FP64).
+struct ImpactDim {
+    double lo, hi;        // domain [lo, hi]
+    double h;             // (hi - lo) / N, the nominal cell width
+    double inv_h;         // RN(1 / h)
+    double sigma;         // noise standard deviation
+    double inv_s;         // RN(1 / (sigma * sqrt 2))
+    double kappa;         // RN(h * inv_s): cell width in erf-argument units
+    double delta;         // window margin sigma * z_c (+inf when cutoff == 0)
+    float kappa_hi, kappa_lo;   // kappa as an FP32 pair (hi + lo)
+    float edge_err;       // bound on |(E_i - E_a)*inv_s - (i-a)*kappa| (erf units)
+    float plateau_hi;     // FP32 upper bound of erf(h_max * inv_s / 2), the max factor
+    float qmin_lo;        // FP32 lower bound of the least out-of-domain mass 2*T(halfwidth)
+    int N;                // number of cells
+    int stride;           // C-order column stride
+    int edge_off;         // offset of this dim's N+1 FP64 edges in the edge table
+    int pad;
+};
+
+// Kinds (match impact_kind) and precisions (match impact_precision).
+enum { KIND_AFFINE = 0, KIND_UNICYCLE = 1, KIND_IMAGES = 2 };
+enum { PREC_FP64_PLAIN = 0, PREC_FP32_SOUND = 1 };
+
+struct ImpactDesc {
+    int n;                // state dimension
+    int m;                // input dimension
+    int kind;
+    int prec;
+    int n_inputs;
+    int n_in_split_min;   // inner enumeration block: grow inner dims until >= this
+    int64_t rows;         // rows = cells * n_inputs
+    int64_t cells;        // total cells
+    double cutoff;        // keep iff up >= cutoff
+    float cutoff32;       // smallest float >= cutoff (FP32 keep test)
+    int table_max;        // per-row window entries the kernel can stage
+    ImpactDim dim[IMPACT_MAX_DIM];
+
+    // Device pointers into the same allocation (set by the planner).
+    const double *edges;      // per dim N_d + 1 edges (oracle definition)
+    // AFFINE: per (d, k, i) image terms of A_dk * x_k over cell i of dim k.
+    //   term_rn[d][k][i]  = min/max in round-to-nearest, lo then hi (2 doubles)
+    //   term_dn[d][k][i]  = lower bound (directed), term_up = upper bound
+    const double *term_rn;    // [n][n][Nmax][2]
+    const double *term_dn;    // [n][n][Nmax]
+    const double *term_up;    // [n][n][Nmax]
+    // AFFINE: per input j, offset c_d + sum_k B_dk u_k: RN, and a bracket.
+    const double *off_rn;     // [n_inputs][n]
+    const double *off_dn;     // [n_inputs][n]
+    const double *off_up;     // [n_inputs][n]
+    // UNICYCLE: per (heading cell i, input j): range of v cos th and v sin th
+    //   over the heading cell, RN [4] = (cos lo, cos hi, sin lo, sin hi) and a
+    //   bracketing version.
+    const double *uni_rn;     // [N_th][n_inputs][4]
+    const double *uni_sd;     // [N_th][n_inputs][4] outward
+    const double *inputs;     // [n_inputs][m]
+    const double *images;     // IMAGES: [rows][n][2], caller's device array
+    int n_max;                // max N_d
+    int pad1;
+};

@@ -1,0 +1,36 @@
+// kernels.h -- launchers the host planner (api.cu) uses; internal interface.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "impact_desc.h"
+
+#define IMPACT_TABLE_MAX 512              // factor entries staged per row (all dims)
+#define IMPACT_STATUS_TABLE_OVERFLOW 0x1u // some row's windows exceeded IMPACT_TABLE_MAX
+#define IMPACT_STATUS_UNSOUND 0x2u        // some row check proved a violation
+#define IMPACT_STATUS_CAPACITY 0x4u       // emit skipped: output capacity too small
+#define IMPACT_STATUS_EMIT_MISMATCH 0x8u  // emit found a different pair count than count
+
+namespace impact {
+
+struct RowOutputs {
+    int64_t *row_ptr;   // count pass: per-row counts out; emit pass: row offsets in
+    int32_t *col;
+    void *lo;
+    void *up;
+    double *sink_lo;
+    double *sink_up;
+    double *trunc;
+    uint32_t *flags;
+    uint32_t *status;
+    int64_t capacity;   // emit: pairs the col/lo/up arrays hold (< 0: unchecked)
+    int64_t total_at;   // emit: index of the total count in row_ptr (rows)
+};
+
+cudaError_t launch_rows(const ImpactDesc *d_desc, int prec, bool emit, int64_t row_begin,
+                        int64_t row_end, const RowOutputs &o, cudaStream_t stream);
+
+int64_t scan_scratch_elems(int64_t n);
+cudaError_t launch_scan(int64_t *row_ptr, int64_t n, int64_t *scratch, cudaStream_t stream);
+
+}  // namespace impact

@@ -1,0 +1,62 @@
+// erf_ulp.cu -- test-only kernel: the largest error, in ulps, of CUDA's
+// single-precision erff and erfcf over every finite float argument, against
+// the double-precision erf/erfc (whose own error, ~1e-16 relative, is far
+// below a float ulp). The FP32-sound path assumes 2 and 4 ulps respectively.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+__device__ __forceinline__ double ulp32_of(double ref)
+{
+    double a = fabs(ref);
+    if (a == 0.0) return ldexp(1.0, -149);
+    int e;
+    frexp(a, &e);                      // a = f * 2^e, f in [0.5, 1)
+    int p = e - 24;                    // ulp of a float in [2^(e-1), 2^e)
+    if (p < -149) p = -149;
+    return ldexp(1.0, p);
+}
+
+__global__ void scan(unsigned int *max_bits)
+{
+    float m_erf = 0.0f, m_erfc = 0.0f;
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (1ull << 32); i += stride) {
+        uint32_t bits = (uint32_t)i;
+        float x = __uint_as_float(bits);
+        if (!isfinite(x)) continue;
+        double xd = (double)x;
+        double r1 = erf(xd), r2 = erfc(xd);
+        float y1 = erff(x), y2 = erfcf(x);
+        float e1 = (float)(fabs((double)y1 - r1) / ulp32_of(r1));
+        float e2 = (float)(fabs((double)y2 - r2) / ulp32_of(r2));
+        m_erf = fmaxf(m_erf, e1);
+        m_erfc = fmaxf(m_erfc, e2);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        m_erf = fmaxf(m_erf, __shfl_xor_sync(0xffffffffu, m_erf, o));
+        m_erfc = fmaxf(m_erfc, __shfl_xor_sync(0xffffffffu, m_erfc, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&max_bits[0], __float_as_uint(m_erf));
+        atomicMax(&max_bits[1], __float_as_uint(m_erfc));
+    }
+}
+
+extern "C" int erf_ulp_scan(float *out)
+{
+    unsigned int *d = nullptr;
+    if (cudaMalloc(&d, 8) != cudaSuccess) return 1;
+    cudaMemset(d, 0, 8);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+    scan<<<sms * 8, 256>>>(d);
+    unsigned int h[2] = {0, 0};
+    cudaError_t e = cudaMemcpy(h, d, 8, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return 2;
+    memcpy(&out[0], &h[0], 4);
+    memcpy(&out[1], &h[1], 4);
+    return 0;
+}

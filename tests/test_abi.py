@@ -1,0 +1,79 @@
+"""The C-ABI library builds, loads and exports what include/impact.h declares
+(CPU only: no compute call needs a GPU here)."""
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2401_03555_gb300 import build as B
+from paper_2401_03555_gb300 import impact, workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "impact.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(impact_\w+)\s*\(", text, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return impact.load()
+
+
+def test_header_lists_the_entry_points():
+    assert set(declared_functions()) == set(impact.ENTRY_POINTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    raw = ctypes.CDLL(B.LIB)
+    for name in declared_functions():
+        assert hasattr(raw, name), name
+
+
+def test_version(lib):
+    assert impact.version() == 100
+
+
+@pytest.mark.parametrize("make", [W.robot_2d, W.room_5d, W.unicycle_3d, W.building_7d])
+def test_plan_counts_rows_and_bounds(lib, make):
+    prob = make()
+    rows, nnz_bound, nbytes = impact.plan(prob, "fp32")
+    assert rows == prob.rows
+    assert prob.rows <= nnz_bound <= prob.rows * prob.total_cells
+    assert nbytes >= nnz_bound * 12
+
+
+def test_plan_dense_bound_is_exact(lib):
+    prob = W.robot_2d()
+    rows, nnz_bound, _ = impact.plan(prob, "fp64")
+    assert nnz_bound == prob.rows * prob.total_cells   # cutoff 0 keeps every pair
+
+
+@pytest.mark.parametrize("mutate, msg", [
+    (lambda p: setattr(p, "cutoff", 1.0), "cutoff"),
+    (lambda p: setattr(p, "cutoff", -0.1), "cutoff"),
+    (lambda p: setattr(p, "sigma", np.zeros(p.n)), "sigma"),
+    (lambda p: setattr(p, "hi", p.lo.copy()), "lo < hi"),
+    (lambda p: setattr(p, "cells", np.zeros(p.n, np.int32)), "cells"),
+    (lambda p: setattr(p, "cells", np.full(p.n, 50000, np.int32)), "2^31"),
+])
+def test_plan_rejects_bad_arguments(lib, mutate, msg):
+    prob = W.room_5d()
+    mutate(prob)
+    with pytest.raises(impact.ImpactError) as e:
+        impact.plan(prob, "fp32")
+    assert e.value.status == impact.IMPACT_ERR_ARG
+    assert msg in str(e.value)
+
+
+def test_plan_rejects_windows_beyond_staging(lib):
+    prob = W.robot_2d(cells_per_dim=400)   # dense: a 400-cell window per dimension
+    with pytest.raises(impact.ImpactError) as e:
+        impact.plan(prob, "fp32")
+    assert "staged" in str(e.value)
