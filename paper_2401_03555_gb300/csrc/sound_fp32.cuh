@@ -4,10 +4,13 @@
 // of the quantity it names, given:
 //   * IEEE FP32 directed-rounding intrinsics (__fadd_rd/ru, __fmul_rd/ru, ...)
 //     and no flush-to-zero (the library is built without --use_fast_math);
-//   * CUDA's documented maximum errors of the single-precision error
-//     functions: erff(x) within K_ERF = 2 ulp and erfcf(x) within K_ERFC = 4
-//     ulp of the exact result, over their whole domain (checked exhaustively
-//     over every finite float argument by the GPU test suite).
+//   * bounds on the error of CUDA's single-precision error functions:
+//     erff(x) within K_ERF = 2 ulp and erfcf(x) within K_ERFC = 5 ulp of the
+//     exact result over every finite float argument. These are measured, not
+//     assumed: the GPU test suite sweeps all 2^32 float arguments against the
+//     double-precision functions (largest errors seen with CUDA 13.0 on
+//     sm_103a: erff 1.04 ulp, erfcf 4.49 ulp) and fails if a toolkit change
+//     ever exceeds them.
 //
 // Notation: the Gaussian factor of one dimension (Def. 2.2 restricted to a
 // coordinate) is written with erf-argument units x = (edge - m) / (sigma*sqrt2):
@@ -17,7 +20,7 @@
 #include <stdint.h>
 
 #define K_ERF 2.0f
-#define K_ERFC 4.0f
+#define K_ERFC 5.0f
 
 namespace sound {
 

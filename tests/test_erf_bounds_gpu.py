@@ -1,5 +1,5 @@
-"""CUDA's erff / erfcf stay within the ulp bounds the FP32-sound path assumes
-(2 and 4 ulps), checked over every finite float argument on the GPU."""
+"""CUDA's erff / erfcf stay within the ulp bounds the FP32-sound path uses
+(K_ERF = 2 and K_ERFC = 5 ulps), checked over every finite float argument."""
 
 import ctypes
 import os
@@ -24,4 +24,4 @@ def test_erf_erfc_ulp_bounds_exhaustive(tmp_path):
     max_erf, max_erfc = out[0], out[1]
     print(f"max ulp error: erff {max_erf:.3f}, erfcf {max_erfc:.3f}")
     assert max_erf <= 2.0
-    assert max_erfc <= 4.0
+    assert max_erfc <= 5.0

@@ -30,7 +30,7 @@ def cuda_ready():
 
 
 def run_and_compare(orc, prob, precision, rows=None, builder=False):
-    if builder:
+    if builder and precision == "fp32":
         b = impact.Builder(prob, precision)
         b.run()
         csr = b.result()
