@@ -195,6 +195,42 @@ const char *impact_last_error(void);
 /* Library ABI version (major*100 + minor). */
 int impact_version(void);
 
+/* Largest `rows` that impact_scan_rows_static accepts. */
+#define IMPACT_SCAN_STATIC_MAX_ROWS (1LL << 27)
+
+/*
+ * impact_scan_rows_static -- the row-pointer scan of impact_count, for callers
+ * that must not allocate device memory. The paper has no counterpart: this is
+ * a deployment convenience, not part of the method.
+ *
+ * Who needs it: code that cannot call cudaMalloc (or cudaMallocAsync) at the
+ * point where it builds row pointers -- for example a host program whose
+ * device memory is all reserved up front by its own arena allocator and may
+ * not grow afterwards (a real-time controller that forbids allocation after
+ * start-up), or a plugin whose host framework owns every device allocation.
+ * Such a caller can count pairs into its own buffer and turn the counts into
+ * CSR row pointers here without the library allocating anything.
+ *
+ * Arguments: row_ptr is a DEVICE array of rows+1 int64. On entry
+ * row_ptr[0..rows) holds the per-row pair counts; on return (stream-ordered
+ * on `stream`, a cudaStream_t or NULL) row_ptr[r] is the exclusive prefix sum
+ * and row_ptr[rows] the total. Nothing is allocated or freed, no library
+ * routine that allocates is called, and the call does not synchronize.
+ *
+ * Scratch: a fixed device array of IMPACT_SCAN_STATIC_MAX_ROWS/4096 + 1 int64
+ * (256 KiB), declared at file scope in the library, so every GPU that loads
+ * the library holds it until the process exits. The first call on a device
+ * looks up that array's device address (with the device current); make that
+ * first call before any stream capture. All calls share the array and every
+ * call overwrites the part it uses before reading it: calls whose work
+ * overlaps on the GPU (different streams, or different host threads on one
+ * device) race and must be serialized by the caller.
+ *
+ * Errors: IMPACT_ERR_ARG when rows < 1, rows > IMPACT_SCAN_STATIC_MAX_ROWS or
+ * row_ptr is NULL; IMPACT_ERR_CUDA when the address lookup or a launch fails.
+ */
+impact_status impact_scan_rows_static(int64_t *row_ptr, int64_t rows, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -450,6 +450,10 @@ impact_status status_result(uint32_t status)
 
 }  // namespace
 
+namespace impact {
+void set_last_error(const std::string &msg) { g_last_error = msg; }
+}  // namespace impact
+
 extern "C" {
 
 impact_status impact_plan(const impact_system *sys, const impact_grid *grid,

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "impact_desc.h"
 
 #define IMPACT_TABLE_MAX 512              // factor entries staged per row (all dims)
@@ -31,6 +33,9 @@ cudaError_t launch_rows(const ImpactDesc *d_desc, int prec, bool emit, int64_t r
                         int64_t row_end, const RowOutputs &o, cudaStream_t stream);
 
 int64_t scan_scratch_elems(int64_t n);
+
+// Sets the message impact_last_error() returns on this host thread.
+void set_last_error(const std::string &msg);
 cudaError_t launch_scan(int64_t *row_ptr, int64_t n, int64_t *scratch, cudaStream_t stream);
 
 }  // namespace impact

@@ -28,7 +28,7 @@ FP64_PLAIN, FP32_SOUND = 0, 1
 _PREC = {"fp64": FP64_PLAIN, "fp32": FP32_SOUND, FP64_PLAIN: FP64_PLAIN, FP32_SOUND: FP32_SOUND}
 
 ENTRY_POINTS = ("impact_plan", "impact_build", "impact_count", "impact_emit", "impact_free",
-                "impact_last_error", "impact_version")
+                "impact_last_error", "impact_version", "impact_scan_rows_static")
 
 
 class ImpactError(RuntimeError):
@@ -95,6 +95,8 @@ def load(build_if_missing: bool = True):
         lib.impact_last_error.argtypes = []
         lib.impact_version.restype = ctypes.c_int
         lib.impact_version.argtypes = []
+        lib.impact_scan_rows_static.restype = ctypes.c_int
+        lib.impact_scan_rows_static.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
         _lib = lib
         return lib
 
@@ -280,6 +282,15 @@ def build_library_owned(prob, precision="fp32", stream=None):
     rows, nnz, owned = int(c.rows), int(c.nnz), int(c.owned)
     _check(lib.impact_free(ctypes.byref(c)))
     return rows, nnz, owned
+
+
+def scan_rows_static(row_ptr: torch.Tensor, rows: int, stream=None) -> None:
+    """In-place exclusive scan of per-row counts (row_ptr[0..rows)) into CSR
+    row pointers with the allocation-free entry point impact_scan_rows_static."""
+    if row_ptr.dtype != torch.int64 or not row_ptr.is_cuda or row_ptr.numel() < rows + 1:
+        raise ValueError("row_ptr must be a CUDA int64 tensor of rows+1 entries")
+    _check(load().impact_scan_rows_static(ctypes.c_void_p(row_ptr.data_ptr()), int(rows),
+                                          ctypes.c_void_p(_stream_handle(stream))))
 
 
 def version() -> int:
