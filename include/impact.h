@@ -120,6 +120,9 @@ typedef struct {
  *   trunc           double[rows]
  *   row_flags       uint32[rows] (may be NULL: then no row checks are kept)
  *   owned           set to 1 by the library when it allocated the arrays
+ *   workspace       optional DEVICE scratch of workspace_bytes bytes (see
+ *                   impact_workspace_bytes); NULL lets the library allocate
+ *                   and free its scratch stream-ordered inside each call
  * Ownership: if col == NULL on entry to impact_build, the library allocates
  * every array stream-ordered on the given stream and impact_free releases
  * them; otherwise all arrays are the caller's and nnz is their capacity.
@@ -136,6 +139,8 @@ typedef struct {
     double *trunc;
     uint32_t *row_flags;
     int owned;
+    void *workspace;
+    int64_t workspace_bytes;
 } impact_csr;
 
 /*
@@ -168,10 +173,21 @@ impact_status impact_build(const impact_system *sys, const impact_grid *grid,
                            impact_precision precision, impact_csr *out, void *stream);
 
 /*
+ * impact_workspace_bytes -- host-only: the device scratch one build uses (the
+ * uploaded descriptor and tables, the scan partial sums and, for
+ * IMPACT_FP32_SOUND, one record of per-row factor tables per row).
+ */
+impact_status impact_workspace_bytes(const impact_system *sys, const impact_grid *grid,
+                                     const impact_inputs *inputs, const double *sigma,
+                                     double cutoff, impact_precision precision, int64_t *bytes);
+
+/*
  * impact_count -- first half of impact_build with caller-owned arrays: writes
  * out->row_ptr (rows+1 entries), sink_lo, sink_up, trunc and row_flags, then
  * synchronizes `stream` and stores the total pair count in out->nnz.
- * col/lo/up are not touched and may be NULL.
+ * col/lo/up are not touched and may be NULL. With a workspace of at least
+ * impact_workspace_bytes bytes, the per-row tables stay in it for a following
+ * impact_emit with the same arguments and the same workspace.
  */
 impact_status impact_count(const impact_system *sys, const impact_grid *grid,
                            const impact_inputs *inputs, const double *sigma, double cutoff,
@@ -180,7 +196,10 @@ impact_status impact_count(const impact_system *sys, const impact_grid *grid,
 /*
  * impact_emit -- second half: given out->row_ptr from impact_count with the
  * same arguments, writes col/lo/up (capacity out->nnz >= row_ptr[rows]).
- * Asynchronous on `stream`; no synchronization.
+ * Asynchronous on `stream`; no synchronization. If out->workspace is the one
+ * impact_count filled for these arguments, its tables are reused; otherwise
+ * (NULL, or filled for other arguments: IMPACT_ERR_ARG) pass NULL and the
+ * tables are recomputed.
  */
 impact_status impact_emit(const impact_system *sys, const impact_grid *grid,
                           const impact_inputs *inputs, const double *sigma, double cutoff,

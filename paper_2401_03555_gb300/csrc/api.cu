@@ -11,7 +11,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/impact.h"
@@ -75,19 +77,47 @@ void trig_range(bool is_cos, double a, double b, double slack, double &lo, doubl
     }
 }
 
+// Fast division by N for x < 2^31: q = (umulhi(x, m) + x) >> s.
+void div_magic(uint32_t N, uint32_t &m, int &s)
+{
+    int l = 0;
+    while (((uint64_t)1 << l) < N) ++l;
+    m = (uint32_t)(((((uint64_t)1 << l) - N) << 32) / N + 1);
+    s = l;
+}
+
+float2 pair_of(double v)
+{
+    float hi = (float)v;
+    float lo = (float)(v - (double)hi);
+    return make_float2(hi, lo);
+}
+
+uint64_t fnv(uint64_t h, const void *p, size_t bytes)
+{
+    const unsigned char *c = (const unsigned char *)p;
+    for (size_t i = 0; i < bytes; ++i) h = (h ^ c[i]) * 1099511628211ull;
+    return h;
+}
+
 struct Plan {
     ImpactDesc desc;
     std::vector<double> edges, term_rn, term_dn, term_up, off_rn, off_dn, off_up, uni_rn,
         uni_sd, inputs;
+    // FP32-sound table path
+    std::vector<float2> ea, ta_lo, ta_hi, oa, ua, oma;
+    std::vector<float> mu_lo, mu_hi, mo, um, omm;
     int64_t rows = 0;
     int64_t nnz_bound = 0;
     int table_need = 0;   // upper bound of the staged entries per row (-1: unknown)
+    uint64_t hash = 0;    // identifies the arguments (workspace reuse check)
 };
 
 // Offsets (in bytes, 256-aligned) of the arrays in the device blob.
 struct BlobLayout {
     size_t desc, edges, term_rn, term_dn, term_up, off_rn, off_dn, off_up, uni_rn, uni_sd,
-        inputs, status, total;
+        inputs, ea, ta_lo, ta_hi, oa, ua, oma, mu_lo, mu_hi, mo, um, omm, status, scan, rec,
+        total;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -112,10 +142,26 @@ BlobLayout layout_of(const Plan &p)
     L.uni_rn = put(p.uni_rn.size() * 8);
     L.uni_sd = put(p.uni_sd.size() * 8);
     L.inputs = put(p.inputs.size() * 8);
+    L.ea = put(p.ea.size() * 8);
+    L.ta_lo = put(p.ta_lo.size() * 8);
+    L.ta_hi = put(p.ta_hi.size() * 8);
+    L.oa = put(p.oa.size() * 8);
+    L.ua = put(p.ua.size() * 8);
+    L.oma = put(p.oma.size() * 8);
+    L.mu_lo = put(p.mu_lo.size() * 4);
+    L.mu_hi = put(p.mu_hi.size() * 4);
+    L.mo = put(p.mo.size() * 4);
+    L.um = put(p.um.size() * 4);
+    L.omm = put(p.omm.size() * 4);
     L.status = put(64);
+    L.scan = put((size_t)impact::scan_scratch_elems(p.rows) * 8);
+    L.rec = put(p.desc.prec == PREC_FP32_SOUND ? (size_t)p.rows * p.desc.rec_stride : 0);
     L.total = o;
     return L;
 }
+
+// The uploaded part of the workspace (descriptor and tables) ends here.
+size_t upload_bytes(const BlobLayout &L) { return L.status; }
 
 // z with P(Z >= z) = erfc(z/sqrt2)/2 <= p for a standard normal Z (bisection).
 double normal_quantile_upper(double p)
@@ -312,8 +358,9 @@ impact_status make_plan(const impact_system *sys, const impact_grid *grid,
     // window widths: image width + 2 delta, plus the 2-cell slack and rounding
     int64_t box = 1;
     int need = 0;
+    int tsum = 0;
     for (int d = 0; d < n; ++d) {
-        const ImpactDim &g = D.dim[d];
+        ImpactDim &g = D.dim[d];
         int64_t w = g.N;
         if (sys->kind != IMPACT_IMAGES && isfinite(g.delta)) {
             double cw = ceil((width[d] + 2.0 * g.delta) * g.inv_h) + 4.0;
@@ -321,76 +368,227 @@ impact_status make_plan(const impact_system *sys, const impact_grid *grid,
         }
         box *= w;
         need += (int)w;
+        g.wcap = (int)std::min<int64_t>(w, IMPACT_WINDOW_MAX);
+        g.delta_cells = isfinite(g.delta) ? (float)(g.delta * g.inv_h) : INFINITY;
+        div_magic((uint32_t)g.N, g.div_m, g.div_s);
+        if (precision == IMPACT_FP32_SOUND && sys->kind != IMPACT_IMAGES && w > IMPACT_WINDOW_MAX)
+            return fail(IMPACT_ERR_ARG,
+                        "dimension " + std::to_string(d) + " needs a window of " +
+                            std::to_string(w) + " cells (FP32 limit " +
+                            std::to_string(IMPACT_WINDOW_MAX) +
+                            "): raise the cutoff or use fewer cells");
+        tsum += g.wcap;
     }
+    div_magic((uint32_t)n_inputs, D.inp_div_m, D.inp_div_s);
     P.table_need = (sys->kind == IMPACT_IMAGES) ? -1 : need;
     if (box > cells) box = cells;
     P.nnz_bound = box * rows;
-    if (P.table_need > IMPACT_TABLE_MAX)
+    if (precision == IMPACT_FP64_PLAIN && P.table_need > IMPACT_TABLE_MAX)
         return fail(IMPACT_ERR_ARG,
                     "the per-row windows need " + std::to_string(P.table_need) +
                         " staged factors (limit " + std::to_string(IMPACT_TABLE_MAX) +
                         "): raise the cutoff or use fewer cells");
+    if (precision == IMPACT_FP32_SOUND) {
+        if (tsum > IMPACT_TSUM_MAX)
+            return fail(IMPACT_ERR_ARG,
+                        "the per-row windows need " + std::to_string(tsum) +
+                            " staged factors (FP32 limit " + std::to_string(IMPACT_TSUM_MAX) +
+                            "): raise the cutoff or use fewer cells");
+        D.tsum_cap = tsum;
+        D.rec_stride = (int)impact::record_stride(n, tsum);
+        // tables in erf units (x / (sigma sqrt2)) as FP32 pairs, and in cells
+        for (int d = 0; d < n; ++d) {
+            const ImpactDim &g = D.dim[d];
+            for (int i = 0; i <= g.N; ++i) P.ea.push_back(pair_of(P.edges[g.edge_off + i] * g.inv_s));
+        }
+        if (sys->kind == IMPACT_AFFINE) {
+            P.ta_lo.resize((size_t)n * n * nmax);
+            P.ta_hi.resize((size_t)n * n * nmax);
+            P.mu_lo.resize((size_t)n * n * nmax);
+            P.mu_hi.resize((size_t)n * n * nmax);
+            for (int d = 0; d < n; ++d) {
+                const ImpactDim &g = D.dim[d];
+                for (int k = 0; k < n; ++k)
+                    for (int i = 0; i < D.dim[k].N; ++i) {
+                        size_t t = (size_t)(d * n + k) * nmax + i;
+                        P.ta_lo[t] = pair_of(P.term_rn[2 * t] * g.inv_s);
+                        P.ta_hi[t] = pair_of(P.term_rn[2 * t + 1] * g.inv_s);
+                        P.mu_lo[t] = (float)(P.term_rn[2 * t] * g.inv_h);
+                        P.mu_hi[t] = (float)(P.term_rn[2 * t + 1] * g.inv_h);
+                    }
+            }
+            P.oa.resize((size_t)n_inputs * n);
+            P.mo.resize((size_t)n_inputs * n);
+            for (int j = 0; j < n_inputs; ++j)
+                for (int d = 0; d < n; ++d) {
+                    const ImpactDim &g = D.dim[d];
+                    double off = P.off_rn[(size_t)j * n + d];
+                    P.oa[(size_t)j * n + d] = pair_of(off * g.inv_s);
+                    P.mo[(size_t)j * n + d] = (float)((off - g.lo) * g.inv_h);
+                }
+        } else if (sys->kind == IMPACT_UNICYCLE) {
+            const ImpactDim &gx = D.dim[0], &gy = D.dim[1], &gt = D.dim[2];
+            size_t cnt = (size_t)gt.N * n_inputs * 4;
+            P.ua.resize(cnt);
+            P.um.resize(cnt);
+            for (size_t t = 0; t < cnt; ++t) {
+                const ImpactDim &g = (t % 4) < 2 ? gx : gy;
+                P.ua[t] = pair_of(P.uni_sd[t] * g.inv_s);
+                P.um[t] = (float)(P.uni_sd[t] * g.inv_h);
+            }
+            for (int j = 0; j < n_inputs; ++j) {
+                double om = inputs->points[(int64_t)j * m + 1];
+                P.oma.push_back(pair_of(om * gt.inv_s));
+                P.omm.push_back((float)(om * gt.inv_h));
+            }
+        }
+    }
+    // identity of the arguments, for reusing a caller's workspace
+    uint64_t h = 1469598103934665603ull;
+    int hdr[5] = {sys->kind, n, m, (int)precision, n_inputs};
+    h = fnv(h, hdr, sizeof(hdr));
+    h = fnv(h, &cutoff, 8);
+    h = fnv(h, grid->lo, 8 * n);
+    h = fnv(h, grid->hi, 8 * n);
+    h = fnv(h, grid->cells, 4 * n);
+    h = fnv(h, sigma, 8 * n);
+    if (sys->kind == IMPACT_AFFINE) {
+        h = fnv(h, sys->A, 8 * n * n);
+        if (m > 0) h = fnv(h, sys->B, 8 * n * m);
+        if (sys->c) h = fnv(h, sys->c, 8 * n);
+    }
+    if (m > 0) h = fnv(h, inputs->points, 8 * (size_t)n_inputs * m);
+    h = fnv(h, &sys->dev_images, sizeof(void *));
+    P.hash = h;
     return IMPACT_OK;
 }
 
-// Device copy of a plan: one allocation holding the descriptor and tables.
-struct DeviceBlob {
+// The device workspace of one build: descriptor and tables (uploaded), the
+// status word, the scan partial sums and (FP32) the per-row records.
+struct Work {
     unsigned char *base = nullptr;
     BlobLayout L;
+    bool owned = false;
     ImpactDesc *desc() const { return (ImpactDesc *)(base + L.desc); }
     uint32_t *status() const { return (uint32_t *)(base + L.status); }
+    int64_t *scan() const { return (int64_t *)(base + L.scan); }
+    unsigned char *rec() const { return base + L.rec; }
 };
 
-impact_status upload(Plan &P, DeviceBlob &B, cudaStream_t st, const double *dev_images)
+std::mutex g_ws_mu;
+std::unordered_map<const void *, uint64_t> g_ws_tag;   // caller workspace -> filled for plan
+
+void ws_tag(const void *ws, uint64_t h)
 {
-    B.L = layout_of(P);
-    CK(cudaMallocAsync((void **)&B.base, B.L.total, st));
-    std::vector<unsigned char> host(B.L.total, 0);
+    std::lock_guard<std::mutex> lock(g_ws_mu);
+    if (h) g_ws_tag[ws] = h; else g_ws_tag.erase(ws);
+}
+
+bool ws_has(const void *ws, uint64_t h)
+{
+    std::lock_guard<std::mutex> lock(g_ws_mu);
+    auto it = g_ws_tag.find(ws);
+    return it != g_ws_tag.end() && it->second == h;
+}
+
+impact_status get_work(const Plan &P, const impact_csr *out, cudaStream_t st, Work &W)
+{
+    W.L = layout_of(P);
+    if (out && out->workspace) {
+        if (out->workspace_bytes < (int64_t)W.L.total)
+            return fail(IMPACT_ERR_ARG, "workspace too small: " +
+                                            std::to_string(out->workspace_bytes) + " < " +
+                                            std::to_string(W.L.total) + " bytes");
+        if (((uintptr_t)out->workspace & 255) != 0)
+            return fail(IMPACT_ERR_ARG, "workspace must be 256-byte aligned");
+        W.base = (unsigned char *)out->workspace;
+        W.owned = false;
+        return IMPACT_OK;
+    }
+    CK(cudaMallocAsync((void **)&W.base, W.L.total, st));
+    W.owned = true;
+    return IMPACT_OK;
+}
+
+impact_status release(Work &W, cudaStream_t st)
+{
+    if (W.owned && W.base) CK(cudaFreeAsync(W.base, st));
+    W.base = nullptr;
+    return IMPACT_OK;
+}
+
+impact_status upload(Plan &P, Work &W, cudaStream_t st, const double *dev_images)
+{
+    const BlobLayout &L = W.L;
+    std::vector<unsigned char> host(upload_bytes(L), 0);
     ImpactDesc D = P.desc;
-    auto dptr = [&](size_t off, const std::vector<double> &v) -> const double * {
-        return v.empty() ? nullptr : (const double *)(B.base + off);
+    auto dp = [&](size_t off, size_t count) -> const void * {
+        return count == 0 ? nullptr : (const void *)(W.base + off);
     };
-    D.edges = dptr(B.L.edges, P.edges);
-    D.term_rn = dptr(B.L.term_rn, P.term_rn);
-    D.term_dn = dptr(B.L.term_dn, P.term_dn);
-    D.term_up = dptr(B.L.term_up, P.term_up);
-    D.off_rn = dptr(B.L.off_rn, P.off_rn);
-    D.off_dn = dptr(B.L.off_dn, P.off_dn);
-    D.off_up = dptr(B.L.off_up, P.off_up);
-    D.uni_rn = dptr(B.L.uni_rn, P.uni_rn);
-    D.uni_sd = dptr(B.L.uni_sd, P.uni_sd);
-    D.inputs = dptr(B.L.inputs, P.inputs);
+    D.edges = (const double *)dp(L.edges, P.edges.size());
+    D.term_rn = (const double *)dp(L.term_rn, P.term_rn.size());
+    D.term_dn = (const double *)dp(L.term_dn, P.term_dn.size());
+    D.term_up = (const double *)dp(L.term_up, P.term_up.size());
+    D.off_rn = (const double *)dp(L.off_rn, P.off_rn.size());
+    D.off_dn = (const double *)dp(L.off_dn, P.off_dn.size());
+    D.off_up = (const double *)dp(L.off_up, P.off_up.size());
+    D.uni_rn = (const double *)dp(L.uni_rn, P.uni_rn.size());
+    D.uni_sd = (const double *)dp(L.uni_sd, P.uni_sd.size());
+    D.inputs = (const double *)dp(L.inputs, P.inputs.size());
+    D.ea = (const float2 *)dp(L.ea, P.ea.size());
+    D.ta_lo = (const float2 *)dp(L.ta_lo, P.ta_lo.size());
+    D.ta_hi = (const float2 *)dp(L.ta_hi, P.ta_hi.size());
+    D.oa = (const float2 *)dp(L.oa, P.oa.size());
+    D.ua = (const float2 *)dp(L.ua, P.ua.size());
+    D.oma = (const float2 *)dp(L.oma, P.oma.size());
+    D.mu_lo = (const float *)dp(L.mu_lo, P.mu_lo.size());
+    D.mu_hi = (const float *)dp(L.mu_hi, P.mu_hi.size());
+    D.mo = (const float *)dp(L.mo, P.mo.size());
+    D.um = (const float *)dp(L.um, P.um.size());
+    D.omm = (const float *)dp(L.omm, P.omm.size());
     D.images = dev_images;
-    memcpy(host.data() + B.L.desc, &D, sizeof(D));
-    auto put = [&](size_t off, const std::vector<double> &v) {
-        if (!v.empty()) memcpy(host.data() + off, v.data(), v.size() * 8);
+    memcpy(host.data() + L.desc, &D, sizeof(D));
+    auto put = [&](size_t off, const void *src, size_t bytes) {
+        if (bytes) memcpy(host.data() + off, src, bytes);
     };
-    put(B.L.edges, P.edges);
-    put(B.L.term_rn, P.term_rn);
-    put(B.L.term_dn, P.term_dn);
-    put(B.L.term_up, P.term_up);
-    put(B.L.off_rn, P.off_rn);
-    put(B.L.off_dn, P.off_dn);
-    put(B.L.off_up, P.off_up);
-    put(B.L.uni_rn, P.uni_rn);
-    put(B.L.uni_sd, P.uni_sd);
-    put(B.L.inputs, P.inputs);
+    put(L.edges, P.edges.data(), P.edges.size() * 8);
+    put(L.term_rn, P.term_rn.data(), P.term_rn.size() * 8);
+    put(L.term_dn, P.term_dn.data(), P.term_dn.size() * 8);
+    put(L.term_up, P.term_up.data(), P.term_up.size() * 8);
+    put(L.off_rn, P.off_rn.data(), P.off_rn.size() * 8);
+    put(L.off_dn, P.off_dn.data(), P.off_dn.size() * 8);
+    put(L.off_up, P.off_up.data(), P.off_up.size() * 8);
+    put(L.uni_rn, P.uni_rn.data(), P.uni_rn.size() * 8);
+    put(L.uni_sd, P.uni_sd.data(), P.uni_sd.size() * 8);
+    put(L.inputs, P.inputs.data(), P.inputs.size() * 8);
+    put(L.ea, P.ea.data(), P.ea.size() * 8);
+    put(L.ta_lo, P.ta_lo.data(), P.ta_lo.size() * 8);
+    put(L.ta_hi, P.ta_hi.data(), P.ta_hi.size() * 8);
+    put(L.oa, P.oa.data(), P.oa.size() * 8);
+    put(L.ua, P.ua.data(), P.ua.size() * 8);
+    put(L.oma, P.oma.data(), P.oma.size() * 8);
+    put(L.mu_lo, P.mu_lo.data(), P.mu_lo.size() * 4);
+    put(L.mu_hi, P.mu_hi.data(), P.mu_hi.size() * 4);
+    put(L.mo, P.mo.data(), P.mo.size() * 4);
+    put(L.um, P.um.data(), P.um.size() * 4);
+    put(L.omm, P.omm.data(), P.omm.size() * 4);
     // pageable source: returns once the bytes are staged, so `host` may go
-    CK(cudaMemcpyAsync(B.base, host.data(), B.L.total, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(W.base, host.data(), host.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(W.status(), 0, 64, st));
     return IMPACT_OK;
 }
 
 void configure_pool_once()
 {
-    static bool done = false;
-    if (done) return;
-    done = true;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return;
-    cudaMemPool_t pool;
-    if (cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess) return;
-    uint64_t keep = UINT64_MAX;   // keep freed blocks in the pool between builds
-    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    static std::once_flag once;
+    std::call_once(once, [] {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return;
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess) return;
+        uint64_t keep = UINT64_MAX;   // keep freed blocks in the pool between builds
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    });
 }
 
 bool is_device_ptr(const void *p)
@@ -404,25 +602,36 @@ bool is_device_ptr(const void *p)
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-// Stages of a build. `emit_capacity` < 0 skips the emit pass.
-impact_status run_count(const Plan &P, const DeviceBlob &B, impact_csr *out, cudaStream_t st)
+// count pass + scan: row_ptr, sink_lo, sink_up, trunc, row_flags
+impact_status run_count(const Plan &P, const Work &W, impact_csr *out, cudaStream_t st)
 {
-    int64_t *scratch = nullptr;
-    CK(cudaMallocAsync((void **)&scratch, impact::scan_scratch_elems(P.rows) * 8, st));
     impact::RowOutputs o{out->row_ptr, nullptr, nullptr, nullptr, out->sink_lo, out->sink_up,
-                         out->trunc, out->row_flags, B.status(), -1, P.rows};
-    CK(impact::launch_rows(B.desc(), P.desc.prec, false, 0, P.rows, o, st));
-    CK(impact::launch_scan(out->row_ptr, P.rows, scratch, st));
-    CK(cudaFreeAsync(scratch, st));
+                         out->trunc, out->row_flags, W.status(), -1, P.rows};
+    if (P.desc.prec == PREC_FP32_SOUND) {
+        CK(impact::launch_setup_fp32(W.desc(), 0, P.rows, W.rec(), out->sink_lo, out->sink_up,
+                                     out->trunc, W.status(), st));
+        CK(impact::launch_tree_fp32(W.desc(), false, 0, P.rows, W.rec(), o, st));
+    } else {
+        CK(impact::launch_rows(W.desc(), P.desc.prec, false, 0, P.rows, o, st));
+    }
+    CK(impact::launch_scan(out->row_ptr, P.rows, W.scan(), st));
     return IMPACT_OK;
 }
 
-impact_status run_emit(const Plan &P, const DeviceBlob &B, impact_csr *out, int64_t capacity,
-                       cudaStream_t st)
+// emit pass; `tables_ready`: the FP32 records in W are valid for P
+impact_status run_emit(const Plan &P, const Work &W, impact_csr *out, int64_t capacity,
+                       bool tables_ready, cudaStream_t st)
 {
     impact::RowOutputs o{out->row_ptr, out->col, out->lo, out->up, nullptr, nullptr, nullptr,
-                         nullptr, B.status(), capacity, P.rows};
-    CK(impact::launch_rows(B.desc(), P.desc.prec, true, 0, P.rows, o, st));
+                         nullptr, W.status(), capacity, P.rows};
+    if (P.desc.prec == PREC_FP32_SOUND) {
+        if (!tables_ready)
+            CK(impact::launch_setup_fp32(W.desc(), 0, P.rows, W.rec(), nullptr, nullptr, nullptr,
+                                         W.status(), st));
+        CK(impact::launch_tree_fp32(W.desc(), true, 0, P.rows, W.rec(), o, st));
+    } else {
+        CK(impact::launch_rows(W.desc(), P.desc.prec, true, 0, P.rows, o, st));
+    }
     return IMPACT_OK;
 }
 
@@ -474,6 +683,17 @@ impact_status impact_plan(const impact_system *sys, const impact_grid *grid,
     return IMPACT_OK;
 }
 
+impact_status impact_workspace_bytes(const impact_system *sys, const impact_grid *grid,
+                                     const impact_inputs *inputs, const double *sigma,
+                                     double cutoff, impact_precision precision, int64_t *bytes)
+{
+    Plan P;
+    impact_status s = make_plan(sys, grid, inputs, sigma, cutoff, precision, P);
+    if (s != IMPACT_OK) return s;
+    if (bytes) *bytes = (int64_t)layout_of(P).total;
+    return IMPACT_OK;
+}
+
 impact_status impact_count(const impact_system *sys, const impact_grid *grid,
                            const impact_inputs *inputs, const double *sigma, double cutoff,
                            impact_precision precision, impact_csr *out, void *stream)
@@ -485,19 +705,22 @@ impact_status impact_count(const impact_system *sys, const impact_grid *grid,
     if ((s = check_row_arrays(out)) != IMPACT_OK) return s;
     configure_pool_once();
     cudaStream_t st = (cudaStream_t)stream;
-    DeviceBlob B;
-    if ((s = upload(P, B, st, sys->dev_images)) != IMPACT_OK) return s;
-    CK(cudaMemsetAsync(B.status(), 0, 64, st));
-    if ((s = run_count(P, B, out, st)) != IMPACT_OK) return s;
+    Work W;
+    if ((s = get_work(P, out, st, W)) != IMPACT_OK) return s;
+    if (!W.owned) ws_tag(W.base, 0);
+    if ((s = upload(P, W, st, sys->dev_images)) != IMPACT_OK) return s;
+    if ((s = run_count(P, W, out, st)) != IMPACT_OK) return s;
     int64_t nnz = 0;
     uint32_t status = 0;
     CK(cudaMemcpyAsync(&nnz, out->row_ptr + P.rows, 8, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(&status, B.status(), 4, cudaMemcpyDeviceToHost, st));
-    CK(cudaFreeAsync(B.base, st));
+    CK(cudaMemcpyAsync(&status, W.status(), 4, cudaMemcpyDeviceToHost, st));
+    if ((s = release(W, st)) != IMPACT_OK) return s;
     CK(cudaStreamSynchronize(st));
     out->rows = P.rows;
     out->nnz = nnz;
-    return status_result(status);
+    s = status_result(status);
+    if (!W.owned && (s == IMPACT_OK || s == IMPACT_ERR_UNSOUND)) ws_tag(out->workspace, P.hash);
+    return s;
 }
 
 impact_status impact_emit(const impact_system *sys, const impact_grid *grid,
@@ -514,11 +737,22 @@ impact_status impact_emit(const impact_system *sys, const impact_grid *grid,
         return fail(IMPACT_ERR_ARG, "col, lo and up must be device arrays");
     configure_pool_once();
     cudaStream_t st = (cudaStream_t)stream;
-    DeviceBlob B;
-    if ((s = upload(P, B, st, sys->dev_images)) != IMPACT_OK) return s;
-    CK(cudaMemsetAsync(B.status(), 0, 64, st));
-    if ((s = run_emit(P, B, out, out->nnz, st)) != IMPACT_OK) return s;
-    CK(cudaFreeAsync(B.base, st));
+    bool ready = false;
+    if (out->workspace) {
+        if (!ws_has(out->workspace, P.hash))
+            return fail(IMPACT_ERR_ARG,
+                        "workspace was not filled by impact_count for these arguments");
+        ready = true;
+    }
+    Work W;
+    if ((s = get_work(P, out, st, W)) != IMPACT_OK) return s;
+    if (!ready) {
+        if ((s = upload(P, W, st, sys->dev_images)) != IMPACT_OK) return s;
+    } else {
+        CK(cudaMemsetAsync(W.status(), 0, 64, st));
+    }
+    if ((s = run_emit(P, W, out, out->nnz, ready, st)) != IMPACT_OK) return s;
+    if ((s = release(W, st)) != IMPACT_OK) return s;
     out->rows = P.rows;
     return IMPACT_OK;
 }
@@ -536,7 +770,11 @@ impact_status impact_build(const impact_system *sys, const impact_grid *grid,
     const bool lib_owned = (out->col == nullptr);
     const size_t vbytes = precision == IMPACT_FP32_SOUND ? 4 : 8;
     if (lib_owned) {
+        void *ws = out->workspace;
+        int64_t wsb = out->workspace_bytes;
         memset(out, 0, sizeof(*out));
+        out->workspace = ws;
+        out->workspace_bytes = wsb;
         CK(cudaMallocAsync((void **)&out->row_ptr, (P.rows + 1) * 8, st));
         CK(cudaMallocAsync((void **)&out->sink_lo, P.rows * 8, st));
         CK(cudaMallocAsync((void **)&out->sink_up, P.rows * 8, st));
@@ -549,10 +787,11 @@ impact_status impact_build(const impact_system *sys, const impact_grid *grid,
                              !is_device_ptr(out->up)))
             return fail(IMPACT_ERR_ARG, "col, lo and up must be device arrays");
     }
-    DeviceBlob B;
-    if ((s = upload(P, B, st, sys->dev_images)) != IMPACT_OK) return s;
-    CK(cudaMemsetAsync(B.status(), 0, 64, st));
-    if ((s = run_count(P, B, out, st)) != IMPACT_OK) return s;
+    Work W;
+    if ((s = get_work(P, out, st, W)) != IMPACT_OK) return s;
+    if (!W.owned) ws_tag(W.base, 0);
+    if ((s = upload(P, W, st, sys->dev_images)) != IMPACT_OK) return s;
+    if ((s = run_count(P, W, out, st)) != IMPACT_OK) return s;
     int64_t capacity = out->nnz;
     if (lib_owned) {
         int64_t nnz = 0;
@@ -564,12 +803,12 @@ impact_status impact_build(const impact_system *sys, const impact_grid *grid,
         CK(cudaMallocAsync(&out->up, k * vbytes, st));
         capacity = nnz;
     }
-    if ((s = run_emit(P, B, out, capacity, st)) != IMPACT_OK) return s;
+    if ((s = run_emit(P, W, out, capacity, true, st)) != IMPACT_OK) return s;
     int64_t nnz = 0;
     uint32_t status = 0;
     CK(cudaMemcpyAsync(&nnz, out->row_ptr + P.rows, 8, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(&status, B.status(), 4, cudaMemcpyDeviceToHost, st));
-    CK(cudaFreeAsync(B.base, st));
+    CK(cudaMemcpyAsync(&status, W.status(), 4, cudaMemcpyDeviceToHost, st));
+    if ((s = release(W, st)) != IMPACT_OK) return s;
     CK(cudaStreamSynchronize(st));
     out->rows = P.rows;
     out->nnz = nnz;
@@ -587,12 +826,16 @@ impact_status impact_free(impact_csr *out)
                     out->sink_up, out->trunc, out->row_flags};
     for (void *p : ptrs)
         if (p) CK(cudaFree(p));
+    void *ws = out->workspace;
+    int64_t wsb = out->workspace_bytes;
     memset(out, 0, sizeof(*out));
+    out->workspace = ws;
+    out->workspace_bytes = wsb;
     return IMPACT_OK;
 }
 
 const char *impact_last_error(void) { return g_last_error.c_str(); }
 
-int impact_version(void) { return 100; }
+int impact_version(void) { return 200; }
 
 }  // extern "C"

@@ -22,7 +22,11 @@ struct ImpactDim {
     int N;                // number of cells
     int stride;           // C-order column stride
     int edge_off;         // offset of this dim's N+1 FP64 edges in the edge table
-    int pad;
+    int wcap;             // largest window (cells) a row can stage in this dim
+    float delta_cells;    // delta / h
+    uint32_t div_m;       // fast division by N: q = (umulhi(x, div_m) + x) >> div_s
+    int div_s;
+    int pad2;
 };
 
 // Kinds (match impact_kind) and precisions (match impact_precision).
@@ -64,4 +68,24 @@ struct ImpactDesc {
     const double *images;     // IMAGES: [rows][n][2], caller's device array
     int n_max;                // max N_d
     int pad1;
+
+    // FP32-sound table path. Values "in erf units" of dimension d are
+    // multiplied by 1/(sigma_d sqrt2) on the host in FP64 and stored as FP32
+    // pairs (hi + lo); values "in cells" are divided by h_d (FP32, used only
+    // to place the windows, with slack).
+    uint32_t inp_div_m;       // fast division by n_inputs
+    int inp_div_s;
+    int rec_stride;           // bytes per row record in the workspace
+    int tsum_cap;             // factor entries a row record holds (all dims)
+    const float2 *ea;         // per dim: N+1 edges in erf units, offset edge_off
+    const float2 *ta_lo;      // AFFINE [n][n][Nmax]: min term A_dk x_k in erf units of d
+    const float2 *ta_hi;      //                      max term
+    const float *mu_lo;       // AFFINE [n][n][Nmax]: min term divided by h_d
+    const float *mu_hi;       //                      max term divided by h_d
+    const float2 *oa;         // AFFINE [n_inputs][n]: offset c + B u in erf units
+    const float *mo;          // AFFINE [n_inputs][n]: (offset - lo_d) / h_d
+    const float2 *ua;         // UNICYCLE [N_th][n_inputs][4]: v cos / v sin ranges, erf units
+    const float *um;          // UNICYCLE [N_th][n_inputs][4]: the same in cells
+    const float2 *oma;        // UNICYCLE [n_inputs]: om in erf units of the heading
+    const float *omm;         // UNICYCLE [n_inputs]: om in heading cells
 };

@@ -1,7 +1,9 @@
-// kernels.cu -- the hot path of the IMDP abstraction on sm_103a.
+// kernels.cu -- the FP64-plain path and the row-pointer scan.
 //
-// One warp builds one row (source cell x input) at a time (Alg. 2: rows are
-// independent). Per row:
+// FP64 plain: one warp builds one row (source cell x input) at a time (Alg. 2:
+// rows are independent) and evaluates every factor of every candidate pair in
+// FP64 (the comparison baseline; the FP32-sound path is in tree_fp32.cu).
+// Per row:
 //   1. interval image [m_lo, m_hi] of f over the cell (table lookups + sums)
 //   2. per dimension, a window of target cells outside of which every upper
 //      factor is below cutoff/2 (Sec. 4.4: entries whose upper bound is
@@ -22,7 +24,6 @@
 
 #include "impact_desc.h"
 #include "kernels.h"
-#include "sound_fp32.cuh"
 
 namespace {
 
@@ -144,376 +145,6 @@ __device__ __forceinline__ void window_dim(const ImpactDim &g, double mlo, doubl
     a = (int)xa;
     b = (int)xb;
     if (b < a) b = a - 1;   // empty
-}
-
-// ---------------------------------------------------------------------------
-// FP32-sound row kernel
-// ---------------------------------------------------------------------------
-
-struct WarpSm32 {
-    float U[kTab];
-    float L[kTab];
-    float lp_up[kChunk];
-    float lp_lo[kChunk];
-    int lp_col[kChunk];
-    double mlo[IMPACT_MAX_DIM], mhi[IMPACT_MAX_DIM];
-    double O[IMPACT_MAX_DIM];     // upper bound of the out-of-window mass per dim
-    float r0h[IMPACT_MAX_DIM], r0l[IMPACT_MAX_DIM];   // rho at m_lo (pair)
-    float r1h[IMPACT_MAX_DIM], r1l[IMPACT_MAX_DIM];   // rho at m_hi (pair)
-    float M[IMPACT_MAX_DIM];      // max U in the trimmed window
-    float SW[IMPACT_MAX_DIM];     // sum of U in the trimmed window (upper bound)
-    float qlo[IMPACT_MAX_DIM], qhi[IMPACT_MAX_DIM];   // out-of-domain mass bounds
-    int a[IMPACT_MAX_DIM], w[IMPACT_MAX_DIM], cum[IMPACT_MAX_DIM];
-    int ta[IMPACT_MAX_DIM], tw[IMPACT_MAX_DIM], toff[IMPACT_MAX_DIM];
-};
-
-// alpha interval of edge (a + k) for the dimension's rho pair.
-__device__ __forceinline__ void alpha_at(const ImpactDim &g, int k, float rh, float rl, float &lo,
-                                         float &hi)
-{
-    sound::alpha_interval(k, g.kappa_hi, g.kappa_lo, g.edge_err, rh, rl, lo, hi);
-}
-
-template <bool EMIT>
-__global__ void __launch_bounds__(kThreads)
-rows_fp32(const ImpactDesc *__restrict__ Dp, int64_t row_begin, int64_t row_end,
-          int64_t *__restrict__ row_ptr, int32_t *__restrict__ out_col,
-          float *__restrict__ out_lo, float *__restrict__ out_up,
-          double *__restrict__ sink_lo, double *__restrict__ sink_up,
-          double *__restrict__ trunc, uint32_t *__restrict__ flags,
-          uint32_t *__restrict__ status, int64_t capacity, int64_t total_at)
-{
-    __shared__ WarpSm32 sm_all[kWarpsPerBlock];
-    const ImpactDesc &D = *Dp;
-    const int lane = threadIdx.x & 31;
-    WarpSm32 &S = sm_all[threadIdx.x >> 5];
-    const int n = D.n;
-    const float cut32 = D.cutoff32;
-    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const unsigned lt = lanemask_lt();
-    if (EMIT && capacity >= 0 && row_ptr[total_at] > capacity) {
-        if (threadIdx.x == 0 && blockIdx.x == 0) atomicOr(status, IMPACT_STATUS_CAPACITY);
-        return;
-    }
-
-    for (int64_t row = row_begin + warp0; row < row_end; row += nwarps) {
-        int idx[IMPACT_MAX_DIM];
-        int j;
-        decode_row(D, row, idx, j);
-
-        // 1-2. image, window and rho pairs of dimension `lane`
-        if (lane < n) {
-            const ImpactDim &g = D.dim[lane];
-            double mlo, mhi;
-            image_dim<true>(D, row, idx, j, lane, mlo, mhi);
-            int a, b;
-            window_dim(g, mlo, mhi, a, b);
-            const double Ea = D.edges[g.edge_off + a];
-            float h0, l0, h1, l1;
-            sound::split_pair((Ea - mlo) * g.inv_s, h0, l0);
-            sound::split_pair((Ea - mhi) * g.inv_s, h1, l1);
-            S.mlo[lane] = mlo;
-            S.mhi[lane] = mhi;
-            S.a[lane] = a;
-            S.w[lane] = b - a + 1;
-            S.r0h[lane] = h0; S.r0l[lane] = l0;
-            S.r1h[lane] = h1; S.r1l[lane] = l1;
-        }
-        __syncwarp();
-        int total = 0;
-        for (int d = 0; d < n; ++d) {
-            if (lane == 0) S.cum[d] = total;
-            total += S.w[d];
-        }
-        __syncwarp();
-        if (total > kTab) {   // cannot stage this row: report, store nothing
-            if (lane == 0) {
-                atomicOr(status, IMPACT_STATUS_TABLE_OVERFLOW);
-                if (!EMIT) row_ptr[row] = 0;
-            }
-            continue;
-        }
-
-        // 2. factor tables: U (upper bound of the max over the image) and L
-        //    (lower bound of the min), both sound.
-        for (int e = lane; e < total; e += 32) {
-            int d = 0;
-            while (d + 1 < n && e >= S.cum[d + 1]) ++d;
-            const ImpactDim &g = D.dim[d];
-            int k = e - S.cum[d];
-            float c0l, c0h, e0l, e0h, c1l, c1h, e1l, e1h;
-            alpha_at(g, k, S.r0h[d], S.r0l[d], c0l, c0h);
-            alpha_at(g, k + 1, S.r0h[d], S.r0l[d], e0l, e0h);
-            alpha_at(g, k, S.r1h[d], S.r1l[d], c1l, c1h);
-            alpha_at(g, k + 1, S.r1h[d], S.r1l[d], e1l, e1h);
-            float U;
-            if (__fadd_ru(c0h, e0h) <= 0.0f)          // target midpoint <= m_lo
-                U = sound::mass_hi(c0l, c0h, e0l, e0h);
-            else if (__fadd_rd(c1l, e1l) >= 0.0f)     // target midpoint >= m_hi
-                U = sound::mass_hi(c1l, c1h, e1l, e1h);
-            else                                       // midpoint may be inside
-                U = g.plateau_hi;
-            float L = fminf(sound::mass_lo(c0l, c0h, e0l, e0h), sound::mass_lo(c1l, c1h, e1l, e1h));
-            S.U[e] = U;
-            S.L[e] = L;
-        }
-        __syncwarp();
-
-        // trim each window to the targets whose U passes the cutoff; sums
-        bool empty = false;
-        for (int d = 0; d < n; ++d) {
-            const int base = S.cum[d], W = S.w[d];
-            int first = -1, last = -1;
-            for (int c0 = 0; c0 < W; c0 += 32) {
-                int t = c0 + lane;
-                bool pass = t < W && S.U[base + t] >= cut32;
-                unsigned bal = __ballot_sync(0xffffffffu, pass);
-                if (bal) {
-                    if (first < 0) first = c0 + __ffs(bal) - 1;
-                    last = c0 + 31 - __clz(bal);
-                }
-            }
-            float sw = 0.0f, ow = 0.0f, mx = 0.0f;
-            for (int c0 = 0; c0 < W; c0 += 32) {
-                int t = c0 + lane;
-                if (t < W) {
-                    float v = S.U[base + t];
-                    if (t >= first && t <= last && first >= 0) {
-                        sw = __fadd_ru(sw, v);
-                        mx = fmaxf(mx, v);
-                    } else {
-                        ow = __fadd_ru(ow, v);
-                    }
-                }
-            }
-            sw = warp_sum_ru(sw);
-            ow = warp_sum_ru(ow);
-            mx = warp_max(mx);
-            if (lane == 0) {
-                const ImpactDim &g = D.dim[d];
-                const int a = S.a[d], b = a + W - 1;
-                double O = (double)ow;
-                float al, ah, bl, bh;
-                if (a > 0) {   // cells 0..a-1 lie left of the image: mass at m_lo
-                    alpha_at(g, -a, S.r0h[d], S.r0l[d], al, ah);
-                    alpha_at(g, 0, S.r0h[d], S.r0l[d], bl, bh);
-                    O += (double)sound::mass_hi(al, ah, bl, bh);
-                }
-                if (b < g.N - 1) {   // cells b+1..N-1 lie right of it: mass at m_hi
-                    alpha_at(g, b + 1 - a, S.r1h[d], S.r1l[d], al, ah);
-                    alpha_at(g, g.N - a, S.r1h[d], S.r1l[d], bl, bh);
-                    O += (double)sound::mass_hi(al, ah, bl, bh);
-                }
-                S.O[d] = O * (1.0 + 1e-15);
-                S.SW[d] = sw;
-                S.M[d] = mx;
-                if (first < 0) {
-                    S.tw[d] = 0;
-                    S.ta[d] = a;
-                    S.toff[d] = base;
-                } else {
-                    S.ta[d] = a + first;
-                    S.tw[d] = last - first + 1;
-                    S.toff[d] = base + first;
-                }
-            }
-            empty |= (first < 0);
-        }
-
-        // 4a. out-of-domain mass bounds per dimension (sink, Remark 4.1):
-        //     Q(m) = P(m + w < lo) + P(m + w > hi) = T(-alpha_lo) + T(alpha_hi)
-        if (!EMIT && lane < n) {
-            const ImpactDim &g = D.dim[lane];
-            const int a = S.a[lane];
-            float l0l, l0h, h0l, h0h, l1l, l1h, h1l, h1h;
-            alpha_at(g, -a, S.r0h[lane], S.r0l[lane], l0l, l0h);        // domain lo, at m_lo
-            alpha_at(g, g.N - a, S.r0h[lane], S.r0l[lane], h0l, h0h);   // domain hi, at m_lo
-            alpha_at(g, -a, S.r1h[lane], S.r1l[lane], l1l, l1h);        // domain lo, at m_hi
-            alpha_at(g, g.N - a, S.r1h[lane], S.r1l[lane], h1l, h1h);   // domain hi, at m_hi
-            float q0 = __fadd_ru(sound::tail_hi(-l0h), sound::tail_hi(h0l));
-            float q1 = __fadd_ru(sound::tail_hi(-l1h), sound::tail_hi(h1l));
-            float qhi = fminf(fmaxf(q0, q1), 1.0f);
-            float qlo;
-            if (__fadd_ru(l0h, h0h) <= 0.0f)          // domain midpoint <= m_lo
-                qlo = __fadd_rd(sound::tail_lo(-l0l), sound::tail_lo(h0h));
-            else if (__fadd_rd(l1l, h1l) >= 0.0f)     // domain midpoint >= m_hi
-                qlo = __fadd_rd(sound::tail_lo(-l1l), sound::tail_lo(h1h));
-            else
-                qlo = g.qmin_lo;
-            S.qlo[lane] = fminf(qlo, 1.0f);
-            S.qhi[lane] = qhi;
-        }
-        __syncwarp();
-
-        // 3. enumeration of the trimmed window box
-        float drop = 0.0f, slo = 0.0f, sup = 0.0f;   // per-lane partial sums
-        int64_t cnt = 0;
-        int64_t out_base = 0, out_end = 0, written = 0;
-        if (EMIT) {
-            out_base = row_ptr[row];
-            out_end = row_ptr[row + 1];
-        }
-        if (!empty) {
-            int s = n;
-            int64_t Bin = 1;
-            while (s > 0 && Bin < D.n_in_split_min) {
-                --s;
-                Bin *= S.tw[s];
-            }
-            int64_t Obox = 1;
-            for (int d = 0; d < s; ++d) Obox *= S.tw[d];
-            float swin = 1.0f;
-            for (int d = s; d < n; ++d) swin = __fmul_ru(swin, S.SW[d]);
-            // lane's first inner position (j = lane) and the step of 32
-            int tin0[IMPACT_MAX_DIM], sd[IMPACT_MAX_DIM];
-            int i0 = (int)(lane / Bin);
-            uint32_t q = (uint32_t)(lane - (int64_t)i0 * Bin);
-            uint32_t qs = (uint32_t)(32 % Bin);
-            const int stepi = (int)(32 / Bin);
-            for (int d = n - 1; d >= s; --d) {
-                uint32_t W = (uint32_t)S.tw[d];
-                tin0[d] = (int)(q % W);
-                q /= W;
-                sd[d] = (int)(qs % W);
-                qs /= W;
-            }
-            for (int64_t ob = 0; ob < Obox; ob += kChunk) {
-                // phase 1: outer prefixes of this chunk, pruned by their bound
-                int nlive = 0;
-                for (int k0 = 0; k0 < kChunk; k0 += 32) {
-                    int64_t o = ob + k0 + lane;
-                    bool valid = o < Obox;
-                    bool live = false;
-                    float Pu = 1.0f, Pl = 1.0f;
-                    int colp = 0;
-                    if (valid) {
-                        uint32_t r = (uint32_t)o;
-                        int tt[IMPACT_MAX_DIM];
-                        for (int d = s - 1; d >= 0; --d) {
-                            uint32_t W = (uint32_t)S.tw[d];
-                            uint32_t qq = r / W;
-                            tt[d] = (int)(r - qq * W);
-                            r = qq;
-                        }
-                        for (int d = 0; d < s; ++d) {
-                            int e = S.toff[d] + tt[d];
-                            Pu = (d == 0) ? S.U[e] : __fmul_ru(Pu, S.U[e]);
-                            Pl = (d == 0) ? S.L[e] : __fmul_rd(Pl, S.L[e]);
-                            colp += (S.ta[d] + tt[d]) * D.dim[d].stride;
-                        }
-                        float bound = Pu;
-                        for (int d = s; d < n; ++d) bound = __fmul_ru(bound, S.M[d]);
-                        live = bound >= cut32;
-                        if (!EMIT && !live) drop = __fadd_ru(drop, __fmul_ru(Pu, swin));
-                    }
-                    unsigned bal = __ballot_sync(0xffffffffu, live);
-                    if (live) {
-                        int p = nlive + __popc(bal & lt);
-                        S.lp_up[p] = Pu;
-                        S.lp_lo[p] = Pl;
-                        S.lp_col[p] = colp;
-                    }
-                    nlive += __popc(bal);
-                    if (ob + k0 + 32 >= Obox) break;
-                }
-                __syncwarp();
-                // phase 2: every live prefix x every inner target
-                int i = i0;
-                int tin[IMPACT_MAX_DIM];
-                for (int d = s; d < n; ++d) tin[d] = tin0[d];
-                while (__any_sync(0xffffffffu, i < nlive)) {
-                    bool valid = i < nlive;
-                    bool keep = false;
-                    float uv = 0.0f, lv = 0.0f;
-                    int cv = 0;
-                    if (valid) {
-                        uv = S.lp_up[i];
-                        lv = S.lp_lo[i];
-                        cv = S.lp_col[i];
-                        for (int d = s; d < n; ++d) {
-                            int e = S.toff[d] + tin[d];
-                            uv = (d == 0) ? S.U[e] : __fmul_ru(uv, S.U[e]);
-                            lv = (d == 0) ? S.L[e] : __fmul_rd(lv, S.L[e]);
-                            cv += (S.ta[d] + tin[d]) * D.dim[d].stride;
-                        }
-                        keep = uv >= cut32;
-                    }
-                    unsigned bal = __ballot_sync(0xffffffffu, keep);
-                    if (EMIT) {
-                        if (keep) {
-                            int64_t p = out_base + written + __popc(bal & lt);
-                            if (p < out_end) {
-                                out_col[p] = cv;
-                                out_lo[p] = lv;
-                                out_up[p] = uv;
-                            }
-                        }
-                        written += __popc(bal);
-                    } else {
-                        cnt += __popc(bal);
-                        if (keep) {
-                            slo = __fadd_rd(slo, lv);
-                            sup = __fadd_ru(sup, uv);
-                        } else if (valid) {
-                            drop = __fadd_ru(drop, uv);
-                        }
-                    }
-                    // advance this lane's position by 32 in mixed radix
-                    int carry = 0;
-                    for (int d = n - 1; d >= s; --d) {
-                        int t = tin[d] + sd[d] + carry;
-                        carry = t >= S.tw[d];
-                        tin[d] = carry ? t - S.tw[d] : t;
-                    }
-                    i += stepi + carry;
-                }
-                __syncwarp();
-            }
-        }
-
-        if (EMIT && lane == 0 && out_base + written != out_end)
-            atomicOr(status, IMPACT_STATUS_EMIT_MISMATCH);
-
-        // 4b. per-row terms (count pass)
-        if (!EMIT) {
-            double dsum = warp_sum_d((double)drop);
-            double lsum = warp_sum_d((double)slo);
-            double usum = warp_sum_d((double)sup);
-            if (lane == 0) {
-                // mass of the targets outside the window box: partition by the
-                // first dimension whose index leaves the window
-                double outside = 0.0;
-                for (int d = 0; d < n; ++d) {
-                    double t = S.O[d];
-                    for (int k = 0; k < d; ++k) t *= (double)S.SW[k];
-                    for (int k = d + 1; k < n; ++k) t *= (double)S.SW[k] + S.O[k];
-                    outside += t;
-                }
-                double tr = (outside + dsum) * (1.0 + 1e-13);
-                // sink bounds: 1 - prod(1 - Q) with outward FP64 rounding
-                double pin_up = 1.0, pin_dn = 1.0;
-                for (int d = 0; d < n; ++d) {
-                    pin_up = __dmul_ru(pin_up, __dsub_ru(1.0, (double)S.qlo[d]));
-                    pin_dn = __dmul_rd(pin_dn, __dsub_rd(1.0, (double)S.qhi[d]));
-                }
-                double slo_v = fmax(__dsub_rd(1.0, pin_up), 0.0);
-                double sup_v = fmin(__dsub_ru(1.0, pin_dn), 1.0);
-                row_ptr[row] = cnt;
-                sink_lo[row] = slo_v;
-                sink_up[row] = sup_v;
-                trunc[row] = tr;
-                if (flags) {
-                    uint32_t f = 0;
-                    if (__dadd_rd(lsum * (1.0 - 1e-13), slo_v) > 1.0) f |= 0x1u;
-                    if (__dadd_ru(__dadd_ru(usum * (1.0 + 1e-13), sup_v), tr) < 1.0) f |= 0x2u;
-                    flags[row] = f;
-                    if (f) atomicOr(status, IMPACT_STATUS_UNSOUND);
-                }
-            }
-        }
-        __syncwarp();
-    }
 }
 
 // ---------------------------------------------------------------------------
@@ -878,19 +509,8 @@ cudaError_t launch_rows(const ImpactDesc *d_desc, int prec, bool emit, int64_t r
 {
     int64_t rows = row_end - row_begin;
     if (rows <= 0) return cudaSuccess;
-    if (prec == PREC_FP32_SOUND) {
-        if (emit) {
-            int g = grid_for((const void *)rows_fp32<true>, rows);
-            rows_fp32<true><<<g, kThreads, 0, stream>>>(
-                d_desc, row_begin, row_end, o.row_ptr, o.col, (float *)o.lo, (float *)o.up,
-                o.sink_lo, o.sink_up, o.trunc, o.flags, o.status, o.capacity, o.total_at);
-        } else {
-            int g = grid_for((const void *)rows_fp32<false>, rows);
-            rows_fp32<false><<<g, kThreads, 0, stream>>>(
-                d_desc, row_begin, row_end, o.row_ptr, o.col, (float *)o.lo, (float *)o.up,
-                o.sink_lo, o.sink_up, o.trunc, o.flags, o.status, o.capacity, o.total_at);
-        }
-    } else {
+    if (prec != PREC_FP64_PLAIN) return cudaErrorInvalidValue;
+    {
         if (emit) {
             int g = grid_for((const void *)rows_fp64<true>, rows);
             rows_fp64<true><<<g, kThreads, 0, stream>>>(

@@ -27,8 +27,9 @@ IMPACT_ERR_CUDA, IMPACT_ERR_TIMEOUT, IMPACT_ERR_UNSOUND = 4, 5, 6
 FP64_PLAIN, FP32_SOUND = 0, 1
 _PREC = {"fp64": FP64_PLAIN, "fp32": FP32_SOUND, FP64_PLAIN: FP64_PLAIN, FP32_SOUND: FP32_SOUND}
 
-ENTRY_POINTS = ("impact_plan", "impact_build", "impact_count", "impact_emit", "impact_free",
-                "impact_last_error", "impact_version", "impact_scan_rows_static")
+ENTRY_POINTS = ("impact_plan", "impact_workspace_bytes", "impact_build", "impact_count",
+                "impact_emit", "impact_free", "impact_last_error", "impact_version",
+                "impact_scan_rows_static")
 
 
 class ImpactError(RuntimeError):
@@ -58,7 +59,8 @@ class _CSR(ctypes.Structure):
                 ("lo", ctypes.c_void_p), ("up", ctypes.c_void_p),
                 ("sink_lo", ctypes.c_void_p), ("sink_up", ctypes.c_void_p),
                 ("trunc", ctypes.c_void_p), ("row_flags", ctypes.c_void_p),
-                ("owned", ctypes.c_int)]
+                ("owned", ctypes.c_int), ("workspace", ctypes.c_void_p),
+                ("workspace_bytes", ctypes.c_int64)]
 
 
 _lib = None
@@ -85,6 +87,8 @@ def load(build_if_missing: bool = True):
                   ctypes.c_void_p, ctypes.c_double, ctypes.c_int]
         lib.impact_plan.restype = ctypes.c_int
         lib.impact_plan.argtypes = common + [ctypes.POINTER(ctypes.c_int64)] * 3
+        lib.impact_workspace_bytes.restype = ctypes.c_int
+        lib.impact_workspace_bytes.argtypes = common + [ctypes.POINTER(ctypes.c_int64)]
         for name in ("impact_build", "impact_count", "impact_emit"):
             f = getattr(lib, name)
             f.restype = ctypes.c_int
@@ -181,6 +185,23 @@ def plan(prob, precision="fp32"):
     return rows.value, nnz.value, nbytes.value
 
 
+def workspace_bytes(prob, precision="fp32") -> int:
+    """Device scratch bytes of one build (descriptor, tables, scan, row records)."""
+    a = _Args(prob, need_images=False)
+    if prob.kind == 2:
+        a.sys.dev_images = 1
+    b = ctypes.c_int64()
+    _check(load().impact_workspace_bytes(ctypes.byref(a.sys), ctypes.byref(a.grid),
+                                         ctypes.byref(a.inp), a.sigma_ptr, a.cutoff,
+                                         _PREC[precision], ctypes.byref(b)))
+    return b.value
+
+
+def alloc_workspace(prob, precision="fp32", device=None) -> torch.Tensor:
+    dev = device or torch.device("cuda")
+    return torch.empty(max(workspace_bytes(prob, precision), 256), dtype=torch.uint8, device=dev)
+
+
 def alloc_rows(rows: int, device=None):
     dev = device or torch.device("cuda")
     return dict(row_ptr=torch.empty(rows + 1, dtype=torch.int64, device=dev),
@@ -198,9 +219,12 @@ def alloc_pairs(nnz: int, precision="fp32", device=None):
                 lo=torch.empty(k, dtype=vt, device=dev), up=torch.empty(k, dtype=vt, device=dev))
 
 
-def _csr_struct(rows_buf, pairs_buf=None, capacity=0):
+def _csr_struct(rows_buf, pairs_buf=None, capacity=0, workspace=None):
     p = lambda t: t.data_ptr()
     c = _CSR()
+    if workspace is not None:
+        c.workspace = workspace.data_ptr()
+        c.workspace_bytes = workspace.numel()
     c.rows = 0
     c.nnz = capacity
     c.row_ptr = p(rows_buf["row_ptr"])
@@ -221,7 +245,8 @@ def build(prob, precision="fp32", stream=None, check_unsound: bool = True) -> CS
     prec = _PREC[precision]
     rows = prob.rows
     rb = alloc_rows(rows)
-    c = _csr_struct(rb)
+    ws = alloc_workspace(prob, precision)
+    c = _csr_struct(rb, workspace=ws)
     st = _stream_handle(stream)
     status = lib.impact_count(ctypes.byref(a.sys), ctypes.byref(a.grid), ctypes.byref(a.inp),
                               a.sigma_ptr, a.cutoff, prec, ctypes.byref(c), ctypes.c_void_p(st))
@@ -229,7 +254,7 @@ def build(prob, precision="fp32", stream=None, check_unsound: bool = True) -> CS
         _check(status)
     nnz = int(c.nnz)
     pb = alloc_pairs(nnz, precision)
-    c2 = _csr_struct(rb, pb, capacity=nnz)
+    c2 = _csr_struct(rb, pb, capacity=nnz, workspace=ws)
     _check(lib.impact_emit(ctypes.byref(a.sys), ctypes.byref(a.grid), ctypes.byref(a.inp),
                            a.sigma_ptr, a.cutoff, prec, ctypes.byref(c2), ctypes.c_void_p(st)))
     return CSR("fp32" if prec == FP32_SOUND else "fp64", rb["row_ptr"], pb["col"][:nnz],
@@ -251,12 +276,14 @@ class Builder:
             capacity = build(prob, precision).nnz
         self.capacity = int(capacity)
         self.pairs_buf = alloc_pairs(self.capacity, precision)
+        self.workspace = alloc_workspace(prob, precision)
         self.nnz = 0
 
     def run(self, stream=None) -> int:
         lib = load()
         a = self.args
-        c = _csr_struct(self.rows_buf, self.pairs_buf, capacity=self.capacity)
+        c = _csr_struct(self.rows_buf, self.pairs_buf, capacity=self.capacity,
+                        workspace=self.workspace)
         _check(lib.impact_build(ctypes.byref(a.sys), ctypes.byref(a.grid), ctypes.byref(a.inp),
                                 a.sigma_ptr, a.cutoff, self.prec, ctypes.byref(c),
                                 ctypes.c_void_p(_stream_handle(stream))))

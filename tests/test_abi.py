@@ -37,7 +37,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_version(lib):
-    assert impact.version() == 100
+    assert impact.version() == 200
 
 
 @pytest.mark.parametrize("make", [W.robot_2d, W.room_5d, W.unicycle_3d, W.building_7d])
@@ -72,8 +72,26 @@ def test_plan_rejects_bad_arguments(lib, mutate, msg):
     assert msg in str(e.value)
 
 
-def test_plan_rejects_windows_beyond_staging(lib):
+@pytest.mark.parametrize("precision, msg", [("fp32", "window of 400 cells"),
+                                             ("fp64", "staged factors")])
+def test_plan_rejects_windows_beyond_staging(lib, precision, msg):
     prob = W.robot_2d(cells_per_dim=400)   # dense: a 400-cell window per dimension
     with pytest.raises(impact.ImpactError) as e:
-        impact.plan(prob, "fp32")
-    assert "staged" in str(e.value)
+        impact.plan(prob, precision)
+    assert msg in str(e.value)
+
+
+def test_fast_division_constants_are_exact():
+    """The kernels divide cell ids by N with q = (umulhi(x, m) + x) >> s; the
+    host builds (m, s). Check the formula on every x class that matters."""
+    rng = np.random.default_rng(0)
+    for N in list(range(1, 300)) + [1021, 4096, 65535, 65536, 100003, 2**20 + 7, 2**30 + 3]:
+        l = 0
+        while (1 << l) < N:
+            l += 1
+        m = ((((1 << l) - N) << 32) // N + 1) & 0xffffffff
+        xs = np.concatenate([rng.integers(0, 2**31, 2000), np.arange(0, 3 * N + 5),
+                             [2**31 - 1, 2**31 - N, (2**31 - 1) // N * N]]).astype(np.int64)
+        xs = xs[(xs >= 0) & (xs < 2**31)]
+        q = ((xs * m) >> 32) + xs >> l
+        assert np.array_equal(q, xs // N), N
