@@ -386,6 +386,7 @@ struct TreeSm {
     float U[kTsum], L[kTsum], T[kTsum];
     float pu_up[kTsum + IMPACT_MAX_DIM], pu_dn[kTsum + IMPACT_MAX_DIM];   // prefix sums of U
     float pl_up[kTsum + IMPACT_MAX_DIM], pl_dn[kTsum + IMPACT_MAX_DIM];   // prefix sums of L
+    float su_up[kTsum + IMPACT_MAX_DIM];                                   // suffix sums of U
     float npu[kPool], npl[kPool];
     int ncol[kPool];
     float bpu[32], bpl[32];
@@ -427,12 +428,13 @@ __device__ __forceinline__ void run_of(const TreeSm &S, int dim, float P, int &l
     l = pk + 1 - cl;
 }
 
-// Upper bound of the sum of U over the window of `dim` outside [l, l + c).
+// Upper bound of the sum of U over the window of `dim` outside [l, l + c):
+// a prefix sum plus a suffix sum, both rounded up (no cancellation).
 __device__ __forceinline__ float outside_sum(const TreeSm &S, int dim, int l, int c)
 {
     const int po = S.toff[dim] + dim, tw = S.tw[dim];
     if (c == 0) return S.pu_up[po + tw];
-    return __fadd_ru(S.pu_up[po + l], fmaxf(__fsub_ru(S.pu_up[po + tw], S.pu_dn[po + l + c]), 0.0f));
+    return __fadd_ru(S.pu_up[po + l], S.su_up[po + l + c]);
 }
 
 template <bool EMIT>
@@ -497,6 +499,12 @@ tree_fp32(const ImpactDesc *__restrict__ Dp, int64_t row_begin, int64_t row_end,
                 S.pu_dn[po + t + 1] = b;
                 S.pl_up[po + t + 1] = c;
                 S.pl_dn[po + t + 1] = e;
+            }
+            float z = 0.0f;
+            S.su_up[po + tw] = 0.0f;
+            for (int t = tw - 1; t >= 0; --t) {
+                z = __fadd_ru(z, S.U[off + t]);
+                S.su_up[po + t] = z;
             }
         }
         __syncwarp();
