@@ -396,6 +396,23 @@ impact_status make_plan(const impact_system *sys, const impact_grid *grid,
                             "): raise the cutoff or use fewer cells");
         D.tsum_cap = tsum;
         D.rec_stride = (int)impact::record_stride(n, tsum);
+        int ro = 0;
+        for (int d = 0; d < n; ++d) {
+            D.dim[d].rec_off = ro;
+            ro += D.dim[d].wcap;
+        }
+        // prefix-tree walk: pick the parent batch so that a warp's shared
+        // memory stays near the target (more warps per SM)
+        int inner = 0;
+        for (int d = 1; d <= n - 2; ++d) inner += D.dim[d].wcap;
+        int B = 32;
+        auto pool_for = [&](int b) { return (n >= 2 ? D.dim[0].wcap + b * inner : 0) + 1; };
+        while (B > 1 && impact::tree_smem_bytes(tsum, pool_for(B)) > IMPACT_TREE_SMEM_TARGET) B /= 2;
+        D.tree_B = B;
+        D.pool_cap = pool_for(B);
+        D.tree_smem = impact::tree_smem_bytes(tsum, D.pool_cap);
+        if ((int64_t)D.tree_smem * impact::tree_warps_per_block() > 200 * 1024)
+            return fail(IMPACT_ERR_ARG, "the per-row windows are too wide for the FP32 tree walk");
         // tables in erf units (x / (sigma sqrt2)) as FP32 pairs, and in cells
         for (int d = 0; d < n; ++d) {
             const ImpactDim &g = D.dim[d];
@@ -608,9 +625,8 @@ impact_status run_count(const Plan &P, const Work &W, impact_csr *out, cudaStrea
     impact::RowOutputs o{out->row_ptr, nullptr, nullptr, nullptr, out->sink_lo, out->sink_up,
                          out->trunc, out->row_flags, W.status(), -1, P.rows};
     if (P.desc.prec == PREC_FP32_SOUND) {
-        CK(impact::launch_setup_fp32(W.desc(), 0, P.rows, W.rec(), out->sink_lo, out->sink_up,
-                                     out->trunc, W.status(), st));
-        CK(impact::launch_tree_fp32(W.desc(), false, 0, P.rows, W.rec(), o, st));
+        CK(impact::launch_setup_fp32(W.desc(), P.desc.n, 0, P.rows, W.rec(), W.status(), st));
+        CK(impact::launch_tree_fp32(W.desc(), P.desc.tree_smem, false, 0, P.rows, W.rec(), o, st));
     } else {
         CK(impact::launch_rows(W.desc(), P.desc.prec, false, 0, P.rows, o, st));
     }
@@ -626,9 +642,8 @@ impact_status run_emit(const Plan &P, const Work &W, impact_csr *out, int64_t ca
                          nullptr, W.status(), capacity, P.rows};
     if (P.desc.prec == PREC_FP32_SOUND) {
         if (!tables_ready)
-            CK(impact::launch_setup_fp32(W.desc(), 0, P.rows, W.rec(), nullptr, nullptr, nullptr,
-                                         W.status(), st));
-        CK(impact::launch_tree_fp32(W.desc(), true, 0, P.rows, W.rec(), o, st));
+            CK(impact::launch_setup_fp32(W.desc(), P.desc.n, 0, P.rows, W.rec(), W.status(), st));
+        CK(impact::launch_tree_fp32(W.desc(), P.desc.tree_smem, true, 0, P.rows, W.rec(), o, st));
     } else {
         CK(impact::launch_rows(W.desc(), P.desc.prec, true, 0, P.rows, o, st));
     }

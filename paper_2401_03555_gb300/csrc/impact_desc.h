@@ -26,7 +26,7 @@ struct ImpactDim {
     float delta_cells;    // delta / h
     uint32_t div_m;       // fast division by N: q = (umulhi(x, div_m) + x) >> div_s
     int div_s;
-    int pad2;
+    int rec_off;          // FP32 path: offset (entries) of this dim's tables in a row record
 };
 
 // Kinds (match impact_kind) and precisions (match impact_precision).
@@ -77,6 +77,9 @@ struct ImpactDesc {
     int inp_div_s;
     int rec_stride;           // bytes per row record in the workspace
     int tsum_cap;             // factor entries a row record holds (all dims)
+    int tree_B;               // prefix-tree walk: parents expanded per batch
+    int pool_cap;             // prefix-tree walk: nodes staged per warp
+    int tree_smem;            // prefix-tree walk: shared-memory bytes per warp
     const float2 *ea;         // per dim: N+1 edges in erf units, offset edge_off
     const float2 *ta_lo;      // AFFINE [n][n][Nmax]: min term A_dk x_k in erf units of d
     const float2 *ta_hi;      //                      max term

@@ -30,7 +30,6 @@ namespace {
 constexpr int kWarpsPerBlock = 8;
 constexpr int kThreads = kWarpsPerBlock * 32;
 constexpr int kTab = IMPACT_TABLE_MAX;   // staged factor entries per row (all dims)
-constexpr int kChunk = 64;               // outer prefixes per enumeration chunk
 
 __device__ __forceinline__ unsigned lanemask_lt()
 {
@@ -43,20 +42,6 @@ __device__ __forceinline__ double warp_sum_d(double v)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-__device__ __forceinline__ float warp_sum_ru(float v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = __fadd_ru(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-
-__device__ __forceinline__ float warp_max(float v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
 }
 

@@ -137,6 +137,86 @@ __device__ __forceinline__ void alpha_interval(int k, float kappa_hi, float kapp
     ah = __fadd_ru(a, err);
 }
 
+// Bounds of T(x) and T(-x) over an argument interval [xm - dx, xm + dx] from
+// ONE library evaluation at xm, widened by a bound on the derivative:
+//   |xm| < 1/2 : erf branch, |d erf/dx| <= 2/sqrt(pi) < 1.1284
+//   |xm| >= 1/2: erfc(|xm|) (the small tail) with the relative bound
+//                erfc(x - dx) <= erfc(x) exp(dx (2x + 2dx + sqrt2)) for x >= 0
+//                (from erfc(x) >= 2/sqrt(pi) e^{-x^2} / (x + sqrt(x^2 + 2))), and
+//                exp(z) - 1 <= z (1 + z) for 0 <= z <= 1.
+// The tail that is small keeps its relative accuracy; the other is 1 minus it.
+struct TailPair {
+    float p_lo, p_hi;   // T(x)
+    float m_lo, m_hi;   // T(-x)
+};
+
+__device__ __noinline__ TailPair tails(float xm, float dx)
+{
+    TailPair r;
+    float ax = fabsf(xm);
+    if (ax < 0.5f) {
+        float y = erff(xm);
+        float w = __fadd_ru(lib_err(y, K_ERF), __fmul_ru(1.1284f, dx));
+        float ylo = fmaxf(__fsub_rd(y, w), -1.0f), yhi = fminf(__fadd_ru(y, w), 1.0f);
+        r.p_hi = __fmul_ru(0.5f, __fsub_ru(1.0f, ylo));
+        r.p_lo = __fmul_rd(0.5f, __fsub_rd(1.0f, yhi));
+        r.m_hi = __fmul_ru(0.5f, __fadd_ru(1.0f, yhi));
+        r.m_lo = __fmul_rd(0.5f, __fadd_rd(1.0f, ylo));
+        return r;
+    }
+    float y = erfcf(ax);
+    float le = lib_err(y, K_ERFC);
+    float z = __fmul_ru(dx, __fadd_ru(__fmul_ru(2.0f, __fadd_ru(ax, dx)), 1.4143f));
+    z = fminf(z, 1.0f);
+    float rho = __fmul_ru(z, __fadd_ru(1.0f, z));
+    float shi = __fmul_ru(0.5f, __fmul_ru(__fadd_ru(y, le), __fadd_ru(1.0f, rho)));
+    float slo = __fmul_rd(0.5f, __fmul_rd(fmaxf(__fsub_rd(y, le), 0.0f), __fsub_rd(1.0f, rho)));
+    shi = fminf(shi, 0.5f);
+    float bhi = __fsub_ru(1.0f, slo), blo = __fsub_rd(1.0f, shi);
+    if (xm >= 0.0f) {
+        r.p_lo = slo; r.p_hi = shi; r.m_lo = blo; r.m_hi = bhi;
+    } else {
+        r.m_lo = slo; r.m_hi = shi; r.p_lo = blo; r.p_hi = bhi;
+    }
+    return r;
+}
+
+// Mass g = T(ac) - T(ae) of a target cell [c, e] from the tails of its two
+// edges (c left of e), upper and lower bounds, in the form whose terms are
+// the small tails: c right of the mean, e left of it, or the mean inside.
+__device__ __forceinline__ float cell_hi(float ac, const TailPair &c, float ae, const TailPair &e)
+{
+    float r;
+    if (ac >= 0.0f) r = __fsub_ru(c.p_hi, e.p_lo);
+    else if (ae <= 0.0f) r = __fsub_ru(e.m_hi, c.m_lo);
+    else r = __fsub_ru(__fsub_ru(1.0f, c.m_lo), e.p_lo);
+    return fminf(fmaxf(r, 0.0f), 1.0f);
+}
+
+__device__ __forceinline__ float cell_lo(float ac, const TailPair &c, float ae, const TailPair &e)
+{
+    float r;
+    if (ac >= 0.0f) r = __fsub_rd(c.p_lo, e.p_hi);
+    else if (ae <= 0.0f) r = __fsub_rd(e.m_lo, c.m_hi);
+    else r = __fsub_rd(__fsub_rd(1.0f, c.m_hi), e.p_hi);
+    return fminf(fmaxf(r, 0.0f), 1.0f);
+}
+
+// Point estimate and half-width of alpha_i (see alpha_interval).
+__device__ __forceinline__ void alpha_point(int k, float kappa_hi, float kappa_lo, float edge_err,
+                                            float r_hi, float r_lo, float &a, float &err)
+{
+    float kf = (float)k;
+    float p = __fmul_rn(kf, kappa_hi);
+    float pe = __fmaf_rn(kf, kappa_hi, -p);
+    float s = __fadd_rn(p, r_hi);
+    float t = __fadd_rn(pe, __fmaf_rn(kf, kappa_lo, r_lo));
+    a = __fadd_rn(s, t);
+    err = __fadd_ru(__fmul_ru(__fadd_ru(fabsf(a), fabsf(s)), 1.1920929e-7f),
+                    __fadd_ru(__fmul_ru(__fadd_ru(fabsf(p), fabsf(r_hi)), 5.6843419e-14f),
+                              edge_err));
+}
+
 // Split an FP64 value into an FP32 pair hi + lo (|hi + lo - v| <= 2^-48 |v|).
 __device__ __forceinline__ void split_pair(double v, float &hi, float &lo)
 {

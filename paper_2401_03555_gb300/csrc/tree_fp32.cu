@@ -1,24 +1,26 @@
 // tree_fp32.cu -- FP32-sound construction (Def. 3.1 with outward rounding,
-// Sec. 4.4 cutoff, Remark 4.1 sink) in three kernels:
+// Sec. 4.4 cutoff, Remark 4.1 sink) in two kernels plus the row scan:
 //
-//   setup_fp32  8 threads per row, thread d owns dimension d. From the
-//               interval image of the cell it computes the window of target
-//               cells that can pass the cutoff, the factor table U_d[t]
-//               (upper bound of the largest Gaussian mass over the image) and
-//               L_d[t] (lower bound of the smallest), trims the window to the
-//               targets whose U passes, makes U unimodal (a running maximum
-//               from each end: only raises upper bounds), and turns U into
-//               exact pruning thresholds TH_d[t]. The row's sink bounds and
-//               the mass of every target outside the window box are finished
-//               here in FP64. Output: one fixed-size record per row.
-//   tree_fp32   one warp per row walks the prefix tree of target cells in C
-//               order. A node at depth d is a prefix (t_0..t_d) with the
-//               RU-rounded running product P of its upper factors; its
-//               children that can still reach the cutoff are exactly
-//               {t : TH_{d+1}[t] <= P}, a contiguous run because U is
-//               unimodal. Count pass: pairs per row, the in-box truncated
-//               mass and the row checks, from per-node run sums. Emit pass:
-//               the same walk, leaves written with warp-contiguous stores.
+//   setup_fp32  one thread per (row, dimension). From the interval image of
+//               the cell it finds the window of target cells that can pass
+//               the cutoff and the factor table of the window: U[t], an upper
+//               bound of the largest Gaussian mass of target t over the image
+//               (T_max of Def. 3.1, relaxed to the image box) and L[t], a
+//               lower bound of the smallest (T_min). Each window edge needs
+//               one erf/erfc evaluation at the image's lower end and one at
+//               its upper end; neighbouring targets share them. It also
+//               stores the mass outside the trimmed window and the
+//               out-of-domain bounds of this dimension.
+//   tree_fp32   one warp per row. It makes each U table unimodal (a running
+//               maximum from both ends: only raises upper bounds), turns it
+//               into exact pruning thresholds, then walks the prefix tree of
+//               target cells in C order: a node at depth d is a prefix
+//               (t_0..t_d) with the RU-rounded running product P of its
+//               upper factors, and its children that can still reach the
+//               cutoff are exactly {t : TH_{d+1}[t] <= P}, a contiguous run.
+//               Count pass: pairs per row, sink bounds, truncated mass and
+//               row checks (FP64 combination). Emit pass: the same walk,
+//               leaves written with warp-contiguous stores.
 //
 // Products run left to right over the dimensions with directed rounding
 // (up: round up, lo: round down) whatever the enumeration order, so every
@@ -27,6 +29,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "impact_desc.h"
 #include "kernels.h"
 #include "sound_fp32.cuh"
@@ -34,14 +38,12 @@
 namespace {
 
 constexpr int kSetupThreads = 256;
-constexpr int kWin = IMPACT_WINDOW_MAX;   // window entries per (row, dim) in setup
-constexpr int kTsum = IMPACT_TSUM_MAX;    // factor entries per row record (all dims)
-constexpr int kPool = 384;                // prefix nodes staged per warp
-constexpr int kSeg = 512;                 // pairs staged per leaf batch
-constexpr int kTreeWarps = 4;
+constexpr int kTreeWarps = 8;
 constexpr int kTreeThreads = kTreeWarps * 32;
-constexpr float kTwoM44 = 5.6843419e-14f;    // 2^-44
-constexpr float kGrow18 = 1.0000038147f;     // 1 + 2^-18
+constexpr int kSeg = IMPACT_TREE_SEG;      // pairs staged per leaf batch
+constexpr int kHdr = IMPACT_TREE_HDR;      // bytes of per-row scalars per warp
+constexpr float kTwoM44 = 5.6843419e-14f;  // 2^-44
+constexpr float kGrow18 = 1.0000038147f;   // 1 + 2^-18
 
 __device__ __forceinline__ uint32_t fastdiv(uint32_t x, uint32_t m, int s)
 {
@@ -80,32 +82,46 @@ __device__ __forceinline__ float threshold(float c, float r)
     return fsucc(__fdiv_rd(fpred(c), r));
 }
 
-struct Alpha {
+// Edge point: alpha = (E - m)/(sigma sqrt2) at one image end, and its tails.
+struct EdgePt {
+    float a, da;
+    sound::TailPair t;
+};
+
+struct RhoPair {
     float kh, kl, err, rh, rl;
-    __device__ __forceinline__ void at(int k, float &lo, float &hi) const
+    __device__ __forceinline__ EdgePt at(int k) const
     {
-        sound::alpha_interval(k, kh, kl, err, rh, rl, lo, hi);
+        EdgePt e;
+        sound::alpha_point(k, kh, kl, err, rh, rl, e.a, e.da);
+        e.t = sound::tails(e.a, e.da);
+        return e;
     }
 };
 
+// The target midpoint lies at or below / at or above the mean, certainly.
+__device__ __forceinline__ bool mid_below(const EdgePt &c, const EdgePt &e)
+{
+    return __fadd_ru(__fadd_ru(c.a, c.da), __fadd_ru(e.a, e.da)) <= 0.0f;
+}
+__device__ __forceinline__ bool mid_above(const EdgePt &c, const EdgePt &e)
+{
+    return __fadd_rd(__fsub_rd(c.a, c.da), __fsub_rd(e.a, e.da)) >= 0.0f;
+}
+
 __global__ void __launch_bounds__(kSetupThreads)
 setup_fp32(const ImpactDesc *__restrict__ Dp, int64_t row_begin, int64_t row_end,
-           unsigned char *__restrict__ rec, double *__restrict__ sink_lo,
-           double *__restrict__ sink_up, double *__restrict__ trunc,
-           uint32_t *__restrict__ status)
+           unsigned char *__restrict__ rec, uint32_t *__restrict__ status)
 {
     const ImpactDesc &D = *Dp;
     const int n = D.n;
-    const int lane = threadIdx.x & 31;
-    const int d = lane & 7;
-    const unsigned gmask = 0xffu << (lane & 24);
-    const bool act = d < n;
     const float cut = D.cutoff32;
-    const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
-    const int64_t ng = ((int64_t)gridDim.x * blockDim.x) >> 3;
-    float u[kWin], l[kWin];
-
-    for (int64_t row = row_begin + g0; row < row_end; row += ng) {
+    const int64_t total = (row_end - row_begin) * n;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total; p += stride) {
+        const int64_t rl = p / n;
+        const int d = (int)(p - rl * n);
+        const int64_t row = row_begin + rl;
         // row -> (cell digits, input)
         int64_t cell;
         int j;
@@ -129,252 +145,165 @@ setup_fp32(const ImpactDesc *__restrict__ Dp, int64_t row_begin, int64_t row_end
                 }
             }
         }
-        const ImpactDim &g = D.dim[act ? d : 0];
+        int my_idx = 0;
+#pragma unroll
+        for (int k = 0; k < IMPACT_MAX_DIM; ++k)
+            if (k == d) my_idx = idx[k];
+        const ImpactDim &g = D.dim[d];
 
         // image of dimension d: window estimate (cells) and, in erf units,
         // rho = (E_a - m)/(sigma sqrt2) at m_lo and m_hi as FP32 pairs
         float mulo = 0.0f, muhi = 0.0f;
         float m0h = 0.0f, m0l = 0.0f, m1h = 0.0f, m1l = 0.0f, mag = 0.0f;
         double dmlo = 0.0, dmhi = 0.0;
-        if (act) {
-            if (D.kind == KIND_AFFINE) {
+        if (D.kind == KIND_AFFINE) {
 #pragma unroll
-                for (int k = 0; k < IMPACT_MAX_DIM; ++k) {
-                    if (k < n) {
-                        int t = (d * n + k) * D.n_max + idx[k];
-                        mulo += D.mu_lo[t];
-                        muhi += D.mu_hi[t];
-                        float2 pl = D.ta_lo[t], ph = D.ta_hi[t];
-                        acc_pair(m0h, m0l, pl);
-                        acc_pair(m1h, m1l, ph);
-                        mag += fabsf(pl.x) + fabsf(ph.x);
-                    }
+            for (int k = 0; k < IMPACT_MAX_DIM; ++k) {
+                if (k < n) {
+                    int t = (d * n + k) * D.n_max + idx[k];
+                    mulo += D.mu_lo[t];
+                    muhi += D.mu_hi[t];
+                    float2 pl = D.ta_lo[t], ph = D.ta_hi[t];
+                    acc_pair(m0h, m0l, pl);
+                    acc_pair(m1h, m1l, ph);
+                    mag += fabsf(pl.x) + fabsf(ph.x);
                 }
-                float2 o = D.oa[j * n + d];
-                acc_pair(m0h, m0l, o);
-                acc_pair(m1h, m1l, o);
-                mag += 2.0f * fabsf(o.x);
-                float mo = D.mo[j * n + d];
-                mulo += mo;
-                muhi += mo;
-            } else if (D.kind == KIND_UNICYCLE) {
-                const float2 *ea = D.ea + g.edge_off;
-                float2 xlo = ea[idx[d]], xhi = ea[idx[d] + 1];
-                acc_pair(m0h, m0l, xlo);
-                acc_pair(m1h, m1l, xhi);
-                float2 vl, vh;
-                float cl, ch;
-                if (d == 2) {
-                    vl = vh = D.oma[j];
-                    cl = ch = D.omm[j];
-                } else {
-                    int t = ((int)idx[2] * D.n_inputs + j) * 4 + 2 * d;
-                    vl = D.ua[t];
-                    vh = D.ua[t + 1];
-                    cl = D.um[t];
-                    ch = D.um[t + 1];
-                }
-                acc_pair(m0h, m0l, vl);
-                acc_pair(m1h, m1l, vh);
-                mag += fabsf(xlo.x) + fabsf(xhi.x) + fabsf(vl.x) + fabsf(vh.x);
-                mulo = (float)idx[d] + cl;
-                muhi = (float)(idx[d] + 1) + ch;
-            } else {
-                const double *im = D.images + (row * n + d) * 2;
-                dmlo = im[0];
-                dmhi = im[1];
-                mulo = (float)((dmlo - g.lo) * g.inv_h);
-                muhi = (float)((dmhi - g.lo) * g.inv_h);
             }
+            float2 o = D.oa[j * n + d];
+            acc_pair(m0h, m0l, o);
+            acc_pair(m1h, m1l, o);
+            mag += 2.0f * fabsf(o.x);
+            float mo = D.mo[j * n + d];
+            mulo += mo;
+            muhi += mo;
+        } else if (D.kind == KIND_UNICYCLE) {
+            const float2 *ea = D.ea + g.edge_off;
+            float2 xlo = ea[my_idx], xhi = ea[my_idx + 1];
+            acc_pair(m0h, m0l, xlo);
+            acc_pair(m1h, m1l, xhi);
+            float2 vl, vh;
+            float cl, ch;
+            if (d == 2) {
+                vl = vh = D.oma[j];
+                cl = ch = D.omm[j];
+            } else {
+                int t = (idx[2] * D.n_inputs + j) * 4 + 2 * d;
+                vl = D.ua[t];
+                vh = D.ua[t + 1];
+                cl = D.um[t];
+                ch = D.um[t + 1];
+            }
+            acc_pair(m0h, m0l, vl);
+            acc_pair(m1h, m1l, vh);
+            mag += fabsf(xlo.x) + fabsf(xhi.x) + fabsf(vl.x) + fabsf(vh.x);
+            mulo = (float)my_idx + cl;
+            muhi = (float)(my_idx + 1) + ch;
+        } else {
+            const double *im = D.images + (row * n + d) * 2;
+            dmlo = im[0];
+            dmhi = im[1];
+            mulo = (float)((dmlo - g.lo) * g.inv_h);
+            muhi = (float)((dmhi - g.lo) * g.inv_h);
         }
-        // conservative window [a, b]
-        int a = 0, W = 0;
-        bool bad = false;
-        if (act) {
-            float dc = g.delta_cells;
-            float xa = floorf(mulo - dc - 1e-3f - 1e-5f * fabsf(mulo));
-            float xb = floorf(muhi + dc + 1e-3f + 1e-5f * fabsf(muhi));
-            float top = (float)(g.N - 1);
-            xa = fminf(fmaxf(xa, 0.0f), top);
-            xb = fminf(fmaxf(xb, 0.0f), top);
-            a = (int)xa;
-            int b = (int)xb;
-            W = b - a + 1;
-            if (W < 1) W = 1;
-            if (W > kWin || W > g.wcap) bad = true;
+        // conservative window [a, a + W): every target outside has U below
+        // the cutoff (its cell lies more than delta beyond the image)
+        const float dc = g.delta_cells;
+        float xa = floorf(mulo - dc - 1e-3f - 1e-5f * fabsf(mulo));
+        float xb = floorf(muhi + dc + 1e-3f + 1e-5f * fabsf(muhi));
+        const float top = (float)(g.N - 1);
+        xa = fminf(fmaxf(xa, 0.0f), top);
+        xb = fminf(fmaxf(xb, 0.0f), top);
+        const int a = (int)xa;
+        const int W = max((int)xb - a + 1, 1);
+        unsigned char *rr = rec + rl * (int64_t)D.rec_stride;
+        if (W > g.wcap) {
+            reinterpret_cast<int4 *>(rr)[2 * d] = make_int4(a, 0, 0, 1);
+            reinterpret_cast<float4 *>(rr)[2 * d + 1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            atomicOr(status, IMPACT_STATUS_TABLE_OVERFLOW);
+            continue;
         }
-        Alpha A0, A1;
-        if (act && !bad) {
+        RhoPair R0, R1;
+        {
             float2 ea = D.ea[g.edge_off + a];
             if (D.kind == KIND_IMAGES) {
                 const double Ea = D.edges[g.edge_off + a];
-                sound::split_pair((Ea - dmlo) * g.inv_s, A0.rh, A0.rl);
-                sound::split_pair((Ea - dmhi) * g.inv_s, A1.rh, A1.rl);
+                sound::split_pair((Ea - dmlo) * g.inv_s, R0.rh, R0.rl);
+                sound::split_pair((Ea - dmhi) * g.inv_s, R1.rh, R1.rl);
                 mag = (float)((fabs(Ea) + fabs(dmlo) + fabs(dmhi)) * g.inv_s);
             } else {
-                sub_pair(ea, m0h, m0l, A0.rh, A0.rl);
-                sub_pair(ea, m1h, m1l, A1.rh, A1.rl);
+                sub_pair(ea, m0h, m0l, R0.rh, R0.rl);
+                sub_pair(ea, m1h, m1l, R1.rh, R1.rl);
                 mag += fabsf(ea.x);
             }
-            A0.kh = A1.kh = g.kappa_hi;
-            A0.kl = A1.kl = g.kappa_lo;
-            A0.err = A1.err = __fadd_ru(g.edge_err, __fmul_ru(__fmul_ru(mag, 4.0f), kTwoM44));
+            R0.kh = R1.kh = g.kappa_hi;
+            R0.kl = R1.kl = g.kappa_lo;
+            R0.err = R1.err = __fadd_ru(g.edge_err, __fmul_ru(__fmul_ru(mag, 4.0f), kTwoM44));
         }
 
-        // factor table of the window
-        float M = 0.0f, SW = 0.0f, O = 0.0f, qlo = 0.0f, qhi = 0.0f;
-        int first = -1, last = -1, pk = 0;
-        if (act && !bad) {
-            float c0l, c0h, c1l, c1h;
-            A0.at(0, c0l, c0h);
-            A1.at(0, c1l, c1h);
-            for (int k = 0; k < W; ++k) {
-                float e0l, e0h, e1l, e1h;
-                A0.at(k + 1, e0l, e0h);
-                A1.at(k + 1, e1l, e1h);
-                float U;
-                if (__fadd_ru(c0h, e0h) <= 0.0f)          // target midpoint <= m_lo
-                    U = sound::mass_hi(c0l, c0h, e0l, e0h);
-                else if (__fadd_rd(c1l, e1l) >= 0.0f)     // target midpoint >= m_hi
-                    U = sound::mass_hi(c1l, c1h, e1l, e1h);
-                else                                       // midpoint may be inside
-                    U = g.plateau_hi;
-                float L = fminf(sound::mass_lo(c0l, c0h, e0l, e0h),
-                                sound::mass_lo(c1l, c1h, e1l, e1h));
-                u[k] = U;
-                l[k] = L;
-                if (U >= cut) {
-                    if (first < 0) first = k;
-                    last = k;
+        // factor table of the window: U[k], L[k] for target a + k
+        float *RU = reinterpret_cast<float *>(rr + 32 * n) + g.rec_off;
+        float *RL = RU + D.tsum_cap;
+        EdgePt c0 = R0.at(0), c1 = R1.at(0);
+        const EdgePt w0 = c0;   // edge a at m_lo (left tail below)
+        int first = -1, last = -1;
+        float pre = 0.0f, mid = 0.0f, post = 0.0f;
+        for (int k = 0; k < W; ++k) {
+            EdgePt e0 = R0.at(k + 1), e1 = R1.at(k + 1);
+            float U, L;
+            if (mid_below(c0, e0)) {            // target midpoint <= m_lo
+                U = sound::cell_hi(c0.a, c0.t, e0.a, e0.t);
+                L = sound::cell_lo(c1.a, c1.t, e1.a, e1.t);
+            } else if (mid_above(c1, e1)) {     // target midpoint >= m_hi
+                U = sound::cell_hi(c1.a, c1.t, e1.a, e1.t);
+                L = sound::cell_lo(c0.a, c0.t, e0.a, e0.t);
+            } else {                            // midpoint may be inside
+                U = g.plateau_hi;
+                L = fminf(sound::cell_lo(c0.a, c0.t, e0.a, e0.t),
+                          sound::cell_lo(c1.a, c1.t, e1.a, e1.t));
+            }
+            RU[k] = U;
+            RL[k] = L;
+            if (U >= cut) {
+                if (first < 0) {
+                    first = k;
+                    mid = U;
+                } else {
+                    mid = __fadd_ru(mid, __fadd_ru(post, U));
+                    post = 0.0f;
                 }
-                c0l = e0l; c0h = e0h; c1l = e1l; c1h = e1h;
+                last = k;
+            } else if (first < 0) {
+                pre = __fadd_ru(pre, U);
+            } else {
+                post = __fadd_ru(post, U);
             }
-            // unimodal envelope of U on the trimmed window, its max and sums
-            if (first >= 0) {
-                pk = first;
-                for (int k = first + 1; k <= last; ++k)
-                    if (u[k] > u[pk]) pk = k;
-                for (int k = first + 1; k < pk; ++k) u[k] = fmaxf(u[k], u[k - 1]);
-                for (int k = last - 1; k > pk; --k) u[k] = fmaxf(u[k], u[k + 1]);
-                M = u[pk];
-                for (int k = first; k <= last; ++k) SW = __fadd_ru(SW, u[k]);
-            }
-            for (int k = 0; k < W; ++k)
-                if (first < 0 || k < first || k > last) O = __fadd_ru(O, u[k]);
-            // cells left of the window (all left of the image): mass at m_lo;
-            // cells right of it: mass at m_hi (telescoped over the cells)
-            float al, ah, bl, bh;
-            if (a > 0) {
-                A0.at(-a, al, ah);
-                A0.at(0, bl, bh);
-                O = __fadd_ru(O, sound::mass_hi(al, ah, bl, bh));
-            }
-            if (a + W < g.N) {
-                A1.at(W, al, ah);
-                A1.at(g.N - a, bl, bh);
-                O = __fadd_ru(O, sound::mass_hi(al, ah, bl, bh));
-            }
-            // out-of-domain mass Q(m) = T(-alpha(lo_D)) + T(alpha(hi_D))
-            float l0l, l0h, h0l, h0h, l1l, l1h, h1l, h1h;
-            A0.at(-a, l0l, l0h);
-            A0.at(g.N - a, h0l, h0h);
-            A1.at(-a, l1l, l1h);
-            A1.at(g.N - a, h1l, h1h);
-            float q0 = __fadd_ru(sound::tail_hi(-l0h), sound::tail_hi(h0l));
-            float q1 = __fadd_ru(sound::tail_hi(-l1h), sound::tail_hi(h1l));
-            qhi = fminf(fmaxf(q0, q1), 1.0f);
-            if (__fadd_ru(l0h, h0h) <= 0.0f)
-                qlo = __fadd_rd(sound::tail_lo(-l0l), sound::tail_lo(h0h));
-            else if (__fadd_rd(l1l, h1l) >= 0.0f)
-                qlo = __fadd_rd(sound::tail_lo(-l1l), sound::tail_lo(h1h));
-            else
-                qlo = g.qmin_lo;
-            qlo = fminf(qlo, 1.0f);
+            c0 = e0;
+            c1 = e1;
         }
-        int tw = (act && !bad && first >= 0) ? last - first + 1 : 0;
-        bool any_bad = __any_sync(gmask, bad);
-
-        // cross-dimension terms within the row's 8 threads
-        float R = 1.0f, SWR = 1.0f;
-        int toff = 0, tsum = 0;
-        for (int k = 0; k < n; ++k) {
-            float Mk = __shfl_sync(gmask, M, k, 8);
-            float SWk = __shfl_sync(gmask, SW, k, 8);
-            int twk = __shfl_sync(gmask, tw, k, 8);
-            if (k > d) {
-                R = __fmul_ru(R, Mk);
-                SWR = __fmul_ru(SWR, SWk);
-            }
-            if (k < d) toff += twk;
-            tsum += twk;
-        }
-        if (tsum > D.tsum_cap) any_bad = true;
-        if (any_bad) {
-            tw = 0;
-            tsum = 0;
-            toff = 0;
-        }
-        // thresholds: a child t of a depth-(d-1) node with product P is kept
-        // iff TH_d[t] <= P, i.e. RU(RU(P U_d[t]) R') >= cutoff, R' bounding the
-        // product of the remaining dimensions' largest factors
-        float cp = 0.0f;
-        if (cut > 0.0f) cp = (d == n - 1) ? cut : threshold(cut, __fmul_ru(R, kGrow18));
-
-        unsigned char *rr = rec + (row - row_begin) * (int64_t)D.rec_stride;
-        if (act) {
-            int4 h = make_int4(a + (first >= 0 ? first : 0), tw, pk - (first >= 0 ? first : 0),
-                               __float_as_int(SWR));
-            reinterpret_cast<int4 *>(rr)[d] = h;
-            float *RU = reinterpret_cast<float *>(rr + 16 * n) + toff;
-            float *RL = RU + D.tsum_cap;
-            float *RT = RL + D.tsum_cap;
-            for (int k = 0; k < tw; ++k) {
-                float uk = u[first + k];
-                RU[k] = uk;
-                RL[k] = l[first + k];
-                RT[k] = (cp > 0.0f) ? threshold(cp, uk) : 0.0f;
-            }
-        }
-
-        // row terms (thread 0 of the row): sink bounds and the mass outside
-        // the window box, combined in FP64 with outward rounding
-        float gq_lo[IMPACT_MAX_DIM], gq_hi[IMPACT_MAX_DIM], gsw[IMPACT_MAX_DIM], go[IMPACT_MAX_DIM];
-#pragma unroll
-        for (int k = 0; k < IMPACT_MAX_DIM; ++k) {
-            gq_lo[k] = __shfl_sync(gmask, qlo, k, 8);
-            gq_hi[k] = __shfl_sync(gmask, qhi, k, 8);
-            gsw[k] = __shfl_sync(gmask, SW, k, 8);
-            go[k] = __shfl_sync(gmask, O, k, 8);
-        }
-        if (d == 0) {
-            double pin_up = 1.0, pin_dn = 1.0, outside = 0.0, pre = 1.0;
-#pragma unroll
-            for (int k = 0; k < IMPACT_MAX_DIM; ++k) {
-                if (k < n) {
-                    pin_up = __dmul_ru(pin_up, __dsub_ru(1.0, (double)gq_lo[k]));
-                    pin_dn = __dmul_rd(pin_dn, __dsub_rd(1.0, (double)gq_hi[k]));
-                }
-            }
-            // partition the targets outside the box by the first dimension whose
-            // index leaves the window: prod_{k<d} SW_k * O_d * prod_{k>d} (SW_k + O_k)
-#pragma unroll
-            for (int k = 0; k < IMPACT_MAX_DIM; ++k) {
-                if (k < n) {
-                    double post = 1.0;
-#pragma unroll
-                    for (int q = k + 1; q < IMPACT_MAX_DIM; ++q)
-                        if (q < n) post *= (double)gsw[q] + (double)go[q];
-                    outside += pre * (double)go[k] * post;
-                    pre *= (double)gsw[k];
-                }
-            }
-            if (sink_lo) {
-                sink_lo[row] = fmax(__dsub_rd(1.0, pin_up), 0.0);
-                sink_up[row] = fmin(__dsub_ru(1.0, pin_dn), 1.0);
-                trunc[row] = outside * (1.0 + 1e-12);
-            }
-            if (any_bad) atomicOr(status, IMPACT_STATUS_TABLE_OVERFLOW);
-        }
+        // c1 is now edge a + W at m_hi
+        float O = __fadd_ru(pre, post);
+        const EdgePt lo0 = R0.at(-a), hi0 = R0.at(g.N - a);   // domain edges at m_lo
+        const EdgePt lo1 = R1.at(-a), hi1 = R1.at(g.N - a);   // domain edges at m_hi
+        if (a > 0)   // cells 0..a-1 lie left of the image: their mass at m_lo
+            O = __fadd_ru(O, sound::cell_hi(lo0.a, lo0.t, w0.a, w0.t));
+        if (a + W < g.N)   // cells right of the window: their mass at m_hi
+            O = __fadd_ru(O, sound::cell_hi(c1.a, c1.t, hi1.a, hi1.t));
+        // out-of-domain mass Q(m) = T(-alpha(lo_D)) + T(alpha(hi_D))
+        float q0 = __fadd_ru(lo0.t.m_hi, hi0.t.p_hi);
+        float q1 = __fadd_ru(lo1.t.m_hi, hi1.t.p_hi);
+        float qhi = fminf(fmaxf(q0, q1), 1.0f);
+        float qlo;
+        if (mid_below(lo0, hi0))
+            qlo = __fadd_rd(lo0.t.m_lo, hi0.t.p_lo);
+        else if (mid_above(lo1, hi1))
+            qlo = __fadd_rd(lo1.t.m_lo, hi1.t.p_lo);
+        else
+            qlo = g.qmin_lo;
+        qlo = fminf(qlo, 1.0f);
+        const int tw = first >= 0 ? last - first + 1 : 0;
+        const int f0 = first >= 0 ? first : 0;
+        reinterpret_cast<int4 *>(rr)[2 * d] = make_int4(a + f0, tw, f0, 0);
+        reinterpret_cast<float4 *>(rr)[2 * d + 1] = make_float4(mid, O, qlo, qhi);
     }
 }
 
@@ -382,26 +311,50 @@ setup_fp32(const ImpactDesc *__restrict__ Dp, int64_t row_begin, int64_t row_end
 // the prefix-tree walk
 // ---------------------------------------------------------------------------
 
-struct TreeSm {
-    float U[kTsum], L[kTsum], T[kTsum];
-    float pu_up[kTsum + IMPACT_MAX_DIM], pu_dn[kTsum + IMPACT_MAX_DIM];   // prefix sums of U
-    float pl_up[kTsum + IMPACT_MAX_DIM], pl_dn[kTsum + IMPACT_MAX_DIM];   // prefix sums of L
-    float su_up[kTsum + IMPACT_MAX_DIM];                                   // suffix sums of U
-    float npu[kPool], npl[kPool];
-    int ncol[kPool];
-    float bpu[32], bpl[32];
-    int bcol[32], bl[32], bo[32];
-    unsigned char seg[kSeg];
+// Per-warp shared memory: a header of per-row scalars, then (entries)
+//   U, L, T                      3 * tcap      factor tables, thresholds
+//   pu_up, pu_dn, pl_up, pl_dn   4 * (tcap+8)  prefix sums (count pass)
+//   su_up                        (tcap+8)      suffix sums of U (count pass)
+//   npu, npl, ncol               3 * pool      prefix-tree nodes
+//   bq                           32 float4     leaf parents (emit pass)
+//   seg                          kSeg bytes    pair -> parent (emit pass)
+struct Hdr {
     int ta[IMPACT_MAX_DIM], tw[IMPACT_MAX_DIM], pk[IMPACT_MAX_DIM], toff[IMPACT_MAX_DIM];
-    float swr[IMPACT_MAX_DIM];
-    int cnt[IMPACT_MAX_DIM], cur[IMPACT_MAX_DIM], base[IMPACT_MAX_DIM];
+    int first[IMPACT_MAX_DIM], cnt[IMPACT_MAX_DIM], cur[IMPACT_MAX_DIM], base[IMPACT_MAX_DIM];
+    float M[IMPACT_MAX_DIM], SW[IMPACT_MAX_DIM], O[IMPACT_MAX_DIM], qlo[IMPACT_MAX_DIM];
+    float qhi[IMPACT_MAX_DIM], cp[IMPACT_MAX_DIM], swr[IMPACT_MAX_DIM];
+};
+static_assert(sizeof(Hdr) <= kHdr, "row header does not fit");
+
+struct Smem {
+    Hdr *h;
+    float *U, *L, *T, *pu_up, *pu_dn, *pl_up, *pl_dn, *su_up, *npu, *npl;
+    int *ncol;
+    float4 *bq;
+    unsigned char *seg;
 };
 
-__device__ __forceinline__ unsigned lanemask_lt()
+__device__ __forceinline__ Smem carve(unsigned char *base, int tcap, int pool)
 {
-    unsigned m;
-    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-    return m;
+    Smem S;
+    S.h = reinterpret_cast<Hdr *>(base);
+    float *f = reinterpret_cast<float *>(base + kHdr);
+    S.U = f; f += tcap;
+    S.L = f; f += tcap;
+    S.T = f; f += tcap;
+    const int tp = tcap + IMPACT_MAX_DIM;
+    S.pu_up = f; f += tp;
+    S.pu_dn = f; f += tp;
+    S.pl_up = f; f += tp;
+    S.pl_dn = f; f += tp;
+    S.su_up = f; f += tp;
+    S.npu = f; f += pool;
+    S.npl = f; f += pool;
+    S.ncol = reinterpret_cast<int *>(f); f += pool;
+    uintptr_t q = ((uintptr_t)f + 15) & ~(uintptr_t)15;
+    S.bq = reinterpret_cast<float4 *>(q);
+    S.seg = reinterpret_cast<unsigned char *>(S.bq + 32);
+    return S;
 }
 
 __device__ __forceinline__ int warp_excl_scan(int v, int &total)
@@ -418,21 +371,24 @@ __device__ __forceinline__ int warp_excl_scan(int v, int &total)
 }
 
 // Run of dimension `dim` kept under a node with product P: [l, l + c).
-__device__ __forceinline__ void run_of(const TreeSm &S, int dim, float P, int &l, int &c)
+__device__ __forceinline__ void run_of(const Smem &S, int dim, float P, int &l, int &c)
 {
-    const int off = S.toff[dim], pk = S.pk[dim], tw = S.tw[dim];
+    const int off = S.h->toff[dim], pk = S.h->pk[dim], tw = S.h->tw[dim];
+    const float *T = S.T + off;
     int cl = 0, cr = 0;
-    for (int t = 0; t <= pk; ++t) cl += (S.T[off + t] <= P) ? 1 : 0;
-    for (int t = pk + 1; t < tw; ++t) cr += (S.T[off + t] <= P) ? 1 : 0;
+#pragma unroll 4
+    for (int t = 0; t <= pk; ++t) cl += (T[t] <= P) ? 1 : 0;
+#pragma unroll 4
+    for (int t = pk + 1; t < tw; ++t) cr += (T[t] <= P) ? 1 : 0;
     c = cl > 0 ? cl + cr : 0;
     l = pk + 1 - cl;
 }
 
 // Upper bound of the sum of U over the window of `dim` outside [l, l + c):
 // a prefix sum plus a suffix sum, both rounded up (no cancellation).
-__device__ __forceinline__ float outside_sum(const TreeSm &S, int dim, int l, int c)
+__device__ __forceinline__ float outside_sum(const Smem &S, int dim, int l, int c)
 {
-    const int po = S.toff[dim] + dim, tw = S.tw[dim];
+    const int po = S.h->toff[dim] + dim, tw = S.h->tw[dim];
     if (c == 0) return S.pu_up[po + tw];
     return __fadd_ru(S.pu_up[po + l], S.su_up[po + l + c]);
 }
@@ -442,18 +398,20 @@ __global__ void __launch_bounds__(kTreeThreads)
 tree_fp32(const ImpactDesc *__restrict__ Dp, int64_t row_begin, int64_t row_end,
           const unsigned char *__restrict__ rec, int64_t *__restrict__ row_ptr,
           int32_t *__restrict__ out_col, float *__restrict__ out_lo, float *__restrict__ out_up,
-          const double *__restrict__ sink_lo, const double *__restrict__ sink_up,
+          double *__restrict__ sink_lo, double *__restrict__ sink_up,
           double *__restrict__ trunc, uint32_t *__restrict__ flags, uint32_t *__restrict__ status,
           int64_t capacity, int64_t total_at)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const ImpactDesc &D = *Dp;
     const int lane = threadIdx.x & 31;
-    TreeSm &S = reinterpret_cast<TreeSm *>(smem_raw)[threadIdx.x >> 5];
     const int n = D.n;
+    const int tcap = D.tsum_cap;
+    const Smem S = carve(smem_raw + (size_t)(threadIdx.x >> 5) * D.tree_smem, tcap, D.pool_cap);
+    Hdr &H = *S.h;
+    const float cut = D.cutoff32;
     const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const unsigned lt = lanemask_lt();
     if (EMIT && capacity >= 0 && row_ptr[total_at] > capacity) {
         if (threadIdx.x == 0 && blockIdx.x == 0) atomicOr(status, IMPACT_STATUS_CAPACITY);
         return;
@@ -461,35 +419,82 @@ tree_fp32(const ImpactDesc *__restrict__ Dp, int64_t row_begin, int64_t row_end,
 
     for (int64_t row = row_begin + warp0; row < row_end; row += nwarps) {
         const unsigned char *rr = rec + (row - row_begin) * (int64_t)D.rec_stride;
-        // load the row record
+        // 1. the row record: per-dimension scalars, then the trimmed tables
         if (lane < n) {
-            int4 h = reinterpret_cast<const int4 *>(rr)[lane];
-            S.ta[lane] = h.x;
-            S.tw[lane] = h.y;
-            S.pk[lane] = h.z;
-            S.swr[lane] = __int_as_float(h.w);
+            int4 hi = reinterpret_cast<const int4 *>(rr)[2 * lane];
+            float4 hf = reinterpret_cast<const float4 *>(rr)[2 * lane + 1];
+            H.ta[lane] = hi.x;
+            H.tw[lane] = hi.y;
+            H.first[lane] = hi.z;
+            H.SW[lane] = hf.x;
+            H.O[lane] = hf.y;
+            H.qlo[lane] = hf.z;
+            H.qhi[lane] = hf.w;
+            if (hi.w) atomicOr(status, IMPACT_STATUS_TABLE_OVERFLOW);
         }
         __syncwarp();
-        int tsum = 0;
         bool empty = false;
-        for (int k = 0; k < n; ++k) {
-            if (lane == 0) S.toff[k] = tsum;
-            tsum += S.tw[k];
-            empty |= (S.tw[k] == 0);
-        }
         {
-            const float *RU = reinterpret_cast<const float *>(rr + 16 * n);
-            for (int i = lane; i < tsum; i += 32) {
-                S.U[i] = RU[i];
-                S.L[i] = RU[D.tsum_cap + i];
-                S.T[i] = RU[2 * D.tsum_cap + i];
+            int tsum = 0;
+            for (int k = 0; k < n; ++k) {
+                if (lane == 0) H.toff[k] = tsum;
+                tsum += H.tw[k];
+                empty |= (H.tw[k] == 0);
             }
         }
         __syncwarp();
-        if (!EMIT && lane < n) {   // prefix sums of U and L per dimension
-            const int off = S.toff[lane], po = off + lane, tw = S.tw[lane];
+        {
+            const float *RU = reinterpret_cast<const float *>(rr + 32 * n);
+            for (int k = 0; k < n; ++k) {
+                const int src = D.dim[k].rec_off + H.first[k], dst = H.toff[k], tw = H.tw[k];
+                for (int i = lane; i < tw; i += 32) {
+                    S.U[dst + i] = RU[src + i];
+                    S.L[dst + i] = RU[tcap + src + i];
+                }
+            }
+        }
+        __syncwarp();
+        // 2. unimodal envelope of each U table (one lane per dimension)
+        if (lane < n) {
+            float *U = S.U + H.toff[lane];
+            const int tw = H.tw[lane];
+            int pk = 0;
+            for (int t = 1; t < tw; ++t)
+                if (U[t] > U[pk]) pk = t;
+            for (int t = 1; t < pk; ++t) U[t] = fmaxf(U[t], U[t - 1]);
+            for (int t = tw - 2; t > pk; --t) U[t] = fmaxf(U[t], U[t + 1]);
+            H.pk[lane] = pk;
+            H.M[lane] = tw > 0 ? U[pk] : 0.0f;
+        }
+        __syncwarp();
+        // 3. pruning thresholds: a child t of a node with product P survives
+        //    iff RU(RU(P U_d[t]) R') >= cutoff, R' bounding the product of the
+        //    later dimensions' largest factors; TH_d[t] is the least such P
+        if (lane < n) {
+            float R = 1.0f, SR = 1.0f;
+            for (int k = lane + 1; k < n; ++k) {
+                R = __fmul_ru(R, H.M[k]);
+                SR = __fmul_ru(SR, H.SW[k]);
+            }
+            float cp = 0.0f;
+            if (cut > 0.0f) cp = (lane == n - 1) ? cut : threshold(cut, __fmul_ru(R, kGrow18));
+            H.cp[lane] = cp;
+            H.swr[lane] = SR;
+        }
+        __syncwarp();
+        for (int k = 0; k < n; ++k) {
+            const int off = H.toff[k], tw = H.tw[k];
+            const float cp = H.cp[k];
+            for (int i = lane; i < tw; i += 32)
+                S.T[off + i] = cp > 0.0f ? threshold(cp, S.U[off + i]) : 0.0f;
+        }
+        if (!EMIT && lane < n) {   // prefix and suffix sums of U and L per dimension
+            const int off = H.toff[lane], po = off + lane, tw = H.tw[lane];
             float a = 0.0f, b = 0.0f, c = 0.0f, e = 0.0f;
-            S.pu_up[po] = 0.0f; S.pu_dn[po] = 0.0f; S.pl_up[po] = 0.0f; S.pl_dn[po] = 0.0f;
+            S.pu_up[po] = 0.0f;
+            S.pu_dn[po] = 0.0f;
+            S.pl_up[po] = 0.0f;
+            S.pl_dn[po] = 0.0f;
             for (int t = 0; t < tw; ++t) {
                 a = __fadd_ru(a, S.U[off + t]);
                 b = __fadd_rd(b, S.U[off + t]);
@@ -519,37 +524,33 @@ tree_fp32(const ImpactDesc *__restrict__ Dp, int64_t row_begin, int64_t row_end,
         bool overflow = false;
         if (!empty) {
             const int leaf = n - 1;
+            const int B = D.tree_B;
             // node buffers: level 0 holds the children of the root (<= tw_0);
-            // a deeper level holds the children of one batch of B parents
-            int B = 32;
-            if (n >= 3) {
-                int s = 0;
-                for (int k = 1; k <= n - 2; ++k) s += S.tw[k];
-                B = min(32, (kPool - S.tw[0]) / max(s, 1));
-            }
+            // a deeper level the children of one batch of <= B parents
             if (lane == 0) {
                 int bse = 0;
                 for (int k = 0; k <= n - 2; ++k) {
-                    S.base[k] = bse;
-                    bse += (k == 0) ? S.tw[0] : B * S.tw[k];
+                    H.base[k] = bse;
+                    bse += (k == 0) ? H.tw[0] : B * H.tw[k];
                 }
+                if (bse > D.pool_cap - 1) H.base[0] = -1;
             }
             __syncwarp();
-            if (B < 1) overflow = true;
-            const int LB = min(32, kSeg / max(S.tw[leaf], 1));   // leaf parents per batch
+            if (n >= 2 && H.base[0] < 0) overflow = true;
+            const int LB = min(32, kSeg / max(H.tw[leaf], 1));   // leaf parents per batch
 
             // leaf processing of parents [p0, p0 + np) of a parent array
             auto leaf_batch = [&](const float *ppu, const float *ppl, const int *pcol, int p0,
                                   int np) {
-                bool act = lane < np;
-                float P = act ? ppu[p0 + lane] : 0.0f;
-                float Pl = act ? ppl[p0 + lane] : 0.0f;
-                int cb = act ? pcol[p0 + lane] : 0;
+                const bool act = lane < np;
+                const float P = act ? ppu[p0 + lane] : 0.0f;
+                const float Pl = act ? ppl[p0 + lane] : 0.0f;
+                const int cb = act ? pcol[p0 + lane] : 0;
                 int l = 0, c = 0;
                 if (act) run_of(S, leaf, P, l, c);
                 if (!EMIT) {
                     if (act) {
-                        const int po = S.toff[leaf] + leaf;
+                        const int po = H.toff[leaf] + leaf;
                         cnt += c;
                         if (c > 0) {
                             float su = fmaxf(__fsub_ru(S.pu_up[po + l + c], S.pu_dn[po + l]), 0.0f);
@@ -561,25 +562,21 @@ tree_fp32(const ImpactDesc *__restrict__ Dp, int64_t row_begin, int64_t row_end,
                     }
                 } else {
                     int C;
-                    int o = warp_excl_scan(c, C);
-                    S.bpu[lane] = P;
-                    S.bpl[lane] = Pl;
-                    S.bcol[lane] = cb + S.ta[leaf];
-                    S.bl[lane] = l;
-                    S.bo[lane] = o;
+                    const int o = warp_excl_scan(c, C);
+                    S.bq[lane] = make_float4(P, Pl, __int_as_float(cb + H.ta[leaf]),
+                                             __int_as_float(l - o));
                     for (int k = 0; k < c; ++k) S.seg[o + k] = (unsigned char)lane;
                     __syncwarp();
-                    const int off = S.toff[leaf];
+                    const float *U = S.U + H.toff[leaf];
+                    const float *L = S.L + H.toff[leaf];
                     for (int e = lane; e < C; e += 32) {
-                        int p = S.seg[e];
-                        int t = S.bl[p] + e - S.bo[p];
-                        float uv = __fmul_ru(S.bpu[p], S.U[off + t]);
-                        float lv = __fmul_rd(S.bpl[p], S.L[off + t]);
-                        int64_t pos = out_base + written + e;
+                        const float4 q = S.bq[S.seg[e]];
+                        const int t = e + __float_as_int(q.w);
+                        const int64_t pos = out_base + written + e;
                         if (pos < out_end) {
-                            out_col[pos] = S.bcol[p] + t;
-                            out_lo[pos] = lv;
-                            out_up[pos] = uv;
+                            out_col[pos] = __float_as_int(q.z) + t;
+                            out_lo[pos] = __fmul_rd(q.y, L[t]);
+                            out_up[pos] = __fmul_ru(q.x, U[t]);
                         }
                     }
                     written += C;
@@ -587,74 +584,80 @@ tree_fp32(const ImpactDesc *__restrict__ Dp, int64_t row_begin, int64_t row_end,
                 }
             };
 
-            // expansion of parents [p0, p0 + np) into the children on `dim`
+            // expansion of parents [p0, p0 + np) into their children on `dim`
             auto expand = [&](const float *ppu, const float *ppl, const int *pcol, int p0, int np,
                               int dim) -> int {
-                bool act = lane < np;
-                float P = act ? ppu[p0 + lane] : 0.0f;
-                float Pl = act ? ppl[p0 + lane] : 0.0f;
-                int cb = act ? pcol[p0 + lane] : 0;
+                const bool act = lane < np;
+                const float P = act ? ppu[p0 + lane] : 0.0f;
+                const float Pl = act ? ppl[p0 + lane] : 0.0f;
+                const int cb = act ? pcol[p0 + lane] : 0;
                 int l = 0, c = 0;
                 if (act) run_of(S, dim, P, l, c);
                 int C;
-                int o = warp_excl_scan(c, C);
-                const int off = S.toff[dim], st = D.dim[dim].stride, ta = S.ta[dim];
-                const int bse = S.base[dim];
+                const int o = warp_excl_scan(c, C);
+                const int off = H.toff[dim], st = D.dim[dim].stride, ta = H.ta[dim];
+                const int bse = H.base[dim];
                 for (int k = 0; k < c; ++k) {
-                    int t = l + k;
-                    S.npu[bse + o + k] = (dim == 0) ? S.U[off + t] : __fmul_ru(P, S.U[off + t]);
-                    S.npl[bse + o + k] = (dim == 0) ? S.L[off + t] : __fmul_rd(Pl, S.L[off + t]);
+                    const int t = l + k;
+                    S.npu[bse + o + k] = __fmul_ru(P, S.U[off + t]);
+                    S.npl[bse + o + k] = __fmul_rd(Pl, S.L[off + t]);
                     S.ncol[bse + o + k] = cb + (ta + t) * st;
                 }
                 if (!EMIT && act)
                     drop = __fadd_ru(drop, __fmul_ru(__fmul_ru(P, outside_sum(S, dim, l, c)),
-                                                     S.swr[dim]));
+                                                     H.swr[dim]));
                 __syncwarp();
                 return C;
             };
 
             if (!overflow) {
                 if (n == 1) {
-                    if (lane == 0) {
-                        S.bpu[0] = 1.0f;   // the root: empty product
-                        S.bpl[0] = 1.0f;
-                        S.bcol[0] = 0;
+                    if (lane == 0) {   // the root: empty product
+                        S.npu[0] = 1.0f;
+                        S.npl[0] = 1.0f;
+                        S.ncol[0] = 0;
                     }
                     __syncwarp();
-                    leaf_batch(S.bpu, S.bpl, S.bcol, 0, 1);
+                    leaf_batch(S.npu, S.npl, S.ncol, 0, 1);
                 } else {
-                    float one_u = 1.0f, one_l = 1.0f;
-                    int zero = 0;
-                    int c0 = expand(&one_u, &one_l, &zero, 0, 1, 0);
+                    const int root = D.pool_cap - 1;   // the root sits past the level buffers
                     if (lane == 0) {
-                        S.cnt[0] = c0;
-                        S.cur[0] = 0;
+                        S.npu[root] = 1.0f;
+                        S.npl[root] = 1.0f;
+                        S.ncol[root] = 0;
+                    }
+                    __syncwarp();
+                    const int c0 = expand(S.npu, S.npl, S.ncol, root, 1, 0);
+                    if (lane == 0) {
+                        H.cnt[0] = c0;
+                        H.cur[0] = 0;
                     }
                     __syncwarp();
                     int lev = 0;
                     while (true) {
                         if (lev == n - 2) {
-                            const int bse = S.base[lev];
-                            for (int p = 0; p < S.cnt[lev]; p += LB)
+                            const int bse = H.base[lev];
+                            for (int p = 0; p < H.cnt[lev]; p += LB)
                                 leaf_batch(S.npu + bse, S.npl + bse, S.ncol + bse, p,
-                                           min(LB, S.cnt[lev] - p));
+                                           min(LB, H.cnt[lev] - p));
                             if (lev == 0) break;
                             --lev;
                             continue;
                         }
-                        if (S.cur[lev] >= S.cnt[lev]) {
+                        if (H.cur[lev] >= H.cnt[lev]) {
                             if (lev == 0) break;
                             --lev;
                             continue;
                         }
-                        const int bse = S.base[lev];
-                        int p0 = S.cur[lev];
-                        int np = min(B, S.cnt[lev] - p0);
-                        int cc = expand(S.npu + bse, S.npl + bse, S.ncol + bse, p0, np, lev + 1);
+                        const int bse = H.base[lev];
+                        const int p0 = H.cur[lev];
+                        const int np = min(B, H.cnt[lev] - p0);
+                        const int cc = expand(S.npu + bse, S.npl + bse, S.ncol + bse, p0, np,
+                                              lev + 1);
                         if (lane == 0) {
-                            S.cur[lev] = p0 + np;
-                            S.cnt[lev + 1] = cc;
-                            S.cur[lev + 1] = 0;
+                            H.cur[lev] = p0 + np;
+                            H.cnt[lev + 1] = cc;
+                            H.cur[lev + 1] = 0;
                         }
                         __syncwarp();
                         ++lev;
@@ -678,18 +681,38 @@ tree_fp32(const ImpactDesc *__restrict__ Dp, int64_t row_begin, int64_t row_end,
                 csum += __shfl_xor_sync(0xffffffffu, csum, o);
             }
             if (lane == 0) {
+                // sink bounds: 1 - prod_d (1 - Q_d), outward in FP64
+                double pin_up = 1.0, pin_dn = 1.0;
+                for (int k = 0; k < n; ++k) {
+                    pin_up = __dmul_ru(pin_up, __dsub_ru(1.0, (double)H.qlo[k]));
+                    pin_dn = __dmul_rd(pin_dn, __dsub_rd(1.0, (double)H.qhi[k]));
+                }
+                const double sl = fmax(__dsub_rd(1.0, pin_up), 0.0);
+                const double su = fmin(__dsub_ru(1.0, pin_dn), 1.0);
+                // mass of the targets outside the window box, partitioned by
+                // the first dimension whose index leaves the window:
+                // prod_{k<d} SW_k * O_d * prod_{k>d} (SW_k + O_k)
+                double suf = 1.0, outside = 0.0;
+                for (int k = n - 1; k >= 0; --k) {
+                    double pre = 1.0;
+                    for (int q = 0; q < k; ++q) pre *= (double)H.SW[q];
+                    outside += pre * (double)H.O[k] * suf;
+                    suf *= (double)H.SW[k] + (double)H.O[k];
+                }
+                const double tr = (outside + dsum) * (1.0 + 1e-12);
                 row_ptr[row] = overflow ? 0 : csum;
-                double tr = trunc[row] + dsum * (1.0 + 1e-12);
+                sink_lo[row] = sl;
+                sink_up[row] = su;
                 trunc[row] = tr;
                 if (overflow) atomicOr(status, IMPACT_STATUS_TABLE_OVERFLOW);
                 if (flags) {
                     // the emitted values are RU / RD products of the factors:
                     // widen the run sums by their rounding before testing
-                    double lo_sum = lsum * (1.0 - 1e-6);
-                    double up_sum = usum * (1.0 + 1e-6);
+                    const double lo_sum = lsum * (1.0 - 1e-6);
+                    const double up_sum = usum * (1.0 + 1e-6);
                     uint32_t f = 0;
-                    if (__dadd_rd(lo_sum, sink_lo[row]) > 1.0) f |= 0x1u;
-                    if (__dadd_ru(__dadd_ru(up_sum, sink_up[row]), tr) < 1.0) f |= 0x2u;
+                    if (__dadd_rd(lo_sum, sl) > 1.0) f |= 0x1u;
+                    if (__dadd_ru(__dadd_ru(up_sum, su), tr) < 1.0) f |= 0x2u;
                     flags[row] = f;
                     if (f) atomicOr(status, IMPACT_STATUS_UNSOUND);
                 }
@@ -718,36 +741,39 @@ namespace impact {
 
 int64_t record_stride(int n, int tsum_cap)
 {
-    return ((int64_t)16 * n + (int64_t)12 * tsum_cap + 15) / 16 * 16;
+    return ((int64_t)32 * n + (int64_t)8 * tsum_cap + 15) / 16 * 16;
 }
 
-cudaError_t launch_setup_fp32(const ImpactDesc *d_desc, int64_t row_begin, int64_t row_end,
-                              unsigned char *rec, double *sink_lo, double *sink_up, double *trunc,
-                              uint32_t *status, cudaStream_t stream)
+int tree_smem_bytes(int tsum_cap, int pool_cap)
+{
+    int64_t b = kHdr + 4 * (int64_t)(3 * tsum_cap + 5 * (tsum_cap + IMPACT_MAX_DIM) + 3 * pool_cap);
+    b = (b + 15) / 16 * 16 + 32 * 16 + kSeg;
+    return (int)((b + 15) / 16 * 16);
+}
+
+int tree_warps_per_block() { return kTreeWarps; }
+
+cudaError_t launch_setup_fp32(const ImpactDesc *d_desc, int n, int64_t row_begin,
+                              int64_t row_end, unsigned char *rec, uint32_t *status,
+                              cudaStream_t stream)
 {
     int64_t rows = row_end - row_begin;
     if (rows <= 0) return cudaSuccess;
-    int g = occupancy_grid((const void *)setup_fp32, kSetupThreads, 0, rows, kSetupThreads / 8);
-    setup_fp32<<<g, kSetupThreads, 0, stream>>>(d_desc, row_begin, row_end, rec, sink_lo,
-                                                sink_up, trunc, status);
+    int g = occupancy_grid((const void *)setup_fp32, kSetupThreads, 0, rows * n, kSetupThreads);
+    setup_fp32<<<g, kSetupThreads, 0, stream>>>(d_desc, row_begin, row_end, rec, status);
     return cudaGetLastError();
 }
 
-cudaError_t launch_tree_fp32(const ImpactDesc *d_desc, bool emit, int64_t row_begin,
-                             int64_t row_end, const unsigned char *rec, const RowOutputs &o,
-                             cudaStream_t stream)
+cudaError_t launch_tree_fp32(const ImpactDesc *d_desc, int tree_smem, bool emit,
+                             int64_t row_begin, int64_t row_end, const unsigned char *rec,
+                             const RowOutputs &o, cudaStream_t stream)
 {
     int64_t rows = row_end - row_begin;
     if (rows <= 0) return cudaSuccess;
-    const size_t smem = sizeof(TreeSm) * kTreeWarps;
+    const size_t smem = (size_t)tree_smem * kTreeWarps;
     const void *k = emit ? (const void *)tree_fp32<true> : (const void *)tree_fp32<false>;
-    static bool attr_set[2] = {false, false};
-    if (!attr_set[emit]) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_set[emit] = true;
-    }
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     int g = occupancy_grid(k, kTreeThreads, smem, rows, kTreeWarps);
     if (emit)
         tree_fp32<true><<<g, kTreeThreads, smem, stream>>>(
