@@ -401,17 +401,28 @@ impact_status make_plan(const impact_system *sys, const impact_grid *grid,
             D.dim[d].rec_off = ro;
             ro += D.dim[d].wcap;
         }
-        // prefix-tree walk: pick the parent batch so that a warp's shared
-        // memory stays near the target (more warps per SM)
-        int inner = 0;
-        for (int d = 1; d <= n - 2; ++d) inner += D.dim[d].wcap;
-        int B = 32;
-        auto pool_for = [&](int b) { return (n >= 2 ? D.dim[0].wcap + b * inner : 0) + 1; };
-        while (B > 1 && impact::tree_smem_bytes(tsum, pool_for(B)) > IMPACT_TREE_SMEM_TARGET) B /= 2;
-        D.tree_B = B;
-        D.pool_cap = pool_for(B);
-        D.tree_smem = impact::tree_smem_bytes(tsum, D.pool_cap);
-        if ((int64_t)D.tree_smem * impact::tree_warps_per_block() > 200 * 1024)
+        // prefix-tree walk: parent batches of 32 into the level above the
+        // leaves (full leaf batches), smaller ones above it, shrunk until a
+        // warp's shared memory stays near the target (more warps per SM)
+        int upper = 0;
+        for (int d = 1; d <= n - 3; ++d) upper += D.dim[d].wcap;
+        const int lastw = n >= 3 ? D.dim[n - 2].wcap : 0;
+        int Bu = 8, Bl = 32;
+        auto pool_for = [&](int bu, int bl) {
+            return (n >= 2 ? D.dim[0].wcap + bu * upper + bl * lastw : 0) + 1;
+        };
+        auto worst = [&](int bu, int bl) {
+            return std::max(impact::tree_smem_bytes(tsum, pool_for(bu, bl), false),
+                            impact::tree_smem_bytes(tsum, pool_for(bu, bl), true));
+        };
+        while (Bu > 1 && worst(Bu, Bl) > IMPACT_TREE_SMEM_TARGET) Bu /= 2;
+        while (Bl > 4 && worst(Bu, Bl) > IMPACT_TREE_SMEM_TARGET) Bl /= 2;
+        D.tree_B = Bu;
+        D.tree_B_last = Bl;
+        D.pool_cap = pool_for(Bu, Bl);
+        D.tree_smem_count = impact::tree_smem_bytes(tsum, D.pool_cap, false);
+        D.tree_smem_emit = impact::tree_smem_bytes(tsum, D.pool_cap, true);
+        if ((int64_t)worst(Bu, Bl) * impact::tree_warps_per_block() > 200 * 1024)
             return fail(IMPACT_ERR_ARG, "the per-row windows are too wide for the FP32 tree walk");
         // tables in erf units (x / (sigma sqrt2)) as FP32 pairs, and in cells
         for (int d = 0; d < n; ++d) {
@@ -626,7 +637,7 @@ impact_status run_count(const Plan &P, const Work &W, impact_csr *out, cudaStrea
                          out->trunc, out->row_flags, W.status(), -1, P.rows};
     if (P.desc.prec == PREC_FP32_SOUND) {
         CK(impact::launch_setup_fp32(W.desc(), P.desc.n, 0, P.rows, W.rec(), W.status(), st));
-        CK(impact::launch_tree_fp32(W.desc(), P.desc.tree_smem, false, 0, P.rows, W.rec(), o, st));
+        CK(impact::launch_tree_fp32(W.desc(), P.desc.tree_smem_count, false, 0, P.rows, W.rec(), o, st));
     } else {
         CK(impact::launch_rows(W.desc(), P.desc.prec, false, 0, P.rows, o, st));
     }
@@ -643,7 +654,7 @@ impact_status run_emit(const Plan &P, const Work &W, impact_csr *out, int64_t ca
     if (P.desc.prec == PREC_FP32_SOUND) {
         if (!tables_ready)
             CK(impact::launch_setup_fp32(W.desc(), P.desc.n, 0, P.rows, W.rec(), W.status(), st));
-        CK(impact::launch_tree_fp32(W.desc(), P.desc.tree_smem, true, 0, P.rows, W.rec(), o, st));
+        CK(impact::launch_tree_fp32(W.desc(), P.desc.tree_smem_emit, true, 0, P.rows, W.rec(), o, st));
     } else {
         CK(impact::launch_rows(W.desc(), P.desc.prec, true, 0, P.rows, o, st));
     }

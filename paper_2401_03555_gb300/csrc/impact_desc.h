@@ -77,9 +77,11 @@ struct ImpactDesc {
     int inp_div_s;
     int rec_stride;           // bytes per row record in the workspace
     int tsum_cap;             // factor entries a row record holds (all dims)
-    int tree_B;               // prefix-tree walk: parents expanded per batch
+    int tree_B;               // prefix-tree walk: parents per batch above the last level
+    int tree_B_last;          // prefix-tree walk: parents per batch into the last level
     int pool_cap;             // prefix-tree walk: nodes staged per warp
-    int tree_smem;            // prefix-tree walk: shared-memory bytes per warp
+    int tree_smem_count;      // prefix-tree walk: shared-memory bytes per warp, count pass
+    int tree_smem_emit;       // prefix-tree walk: shared-memory bytes per warp, emit pass
     const float2 *ea;         // per dim: N+1 edges in erf units, offset edge_off
     const float2 *ta_lo;      // AFFINE [n][n][Nmax]: min term A_dk x_k in erf units of d
     const float2 *ta_hi;      //                      max term

@@ -313,11 +313,13 @@ setup_fp32(const ImpactDesc *__restrict__ Dp, int64_t row_begin, int64_t row_end
 
 // Per-warp shared memory: a header of per-row scalars, then (entries)
 //   U, L, T                      3 * tcap      factor tables, thresholds
-//   pu_up, pu_dn, pl_up, pl_dn   4 * (tcap+8)  prefix sums (count pass)
-//   su_up                        (tcap+8)      suffix sums of U (count pass)
 //   npu, npl, ncol               3 * pool      prefix-tree nodes
-//   bq                           32 float4     leaf parents (emit pass)
-//   seg                          kSeg bytes    pair -> parent (emit pass)
+// and, count pass:
+//   pu_up, pu_dn, pl_up, pl_dn   4 * (tcap+8)  prefix sums
+//   su_up                        (tcap+8)      suffix sums of U
+// or, emit pass:
+//   bq                           32 float4     leaf parents
+//   seg                          kSeg bytes    pair -> parent
 struct Hdr {
     int ta[IMPACT_MAX_DIM], tw[IMPACT_MAX_DIM], pk[IMPACT_MAX_DIM], toff[IMPACT_MAX_DIM];
     int first[IMPACT_MAX_DIM], cnt[IMPACT_MAX_DIM], cur[IMPACT_MAX_DIM], base[IMPACT_MAX_DIM];
@@ -334,6 +336,7 @@ struct Smem {
     unsigned char *seg;
 };
 
+template <bool EMIT>
 __device__ __forceinline__ Smem carve(unsigned char *base, int tcap, int pool)
 {
     Smem S;
@@ -342,18 +345,24 @@ __device__ __forceinline__ Smem carve(unsigned char *base, int tcap, int pool)
     S.U = f; f += tcap;
     S.L = f; f += tcap;
     S.T = f; f += tcap;
-    const int tp = tcap + IMPACT_MAX_DIM;
-    S.pu_up = f; f += tp;
-    S.pu_dn = f; f += tp;
-    S.pl_up = f; f += tp;
-    S.pl_dn = f; f += tp;
-    S.su_up = f; f += tp;
     S.npu = f; f += pool;
     S.npl = f; f += pool;
     S.ncol = reinterpret_cast<int *>(f); f += pool;
-    uintptr_t q = ((uintptr_t)f + 15) & ~(uintptr_t)15;
-    S.bq = reinterpret_cast<float4 *>(q);
-    S.seg = reinterpret_cast<unsigned char *>(S.bq + 32);
+    if (!EMIT) {
+        const int tp = tcap + IMPACT_MAX_DIM;
+        S.pu_up = f; f += tp;
+        S.pu_dn = f; f += tp;
+        S.pl_up = f; f += tp;
+        S.pl_dn = f; f += tp;
+        S.su_up = f; f += tp;
+        S.bq = nullptr;
+        S.seg = nullptr;
+    } else {
+        S.pu_up = S.pu_dn = S.pl_up = S.pl_dn = S.su_up = nullptr;
+        uintptr_t q = ((uintptr_t)f + 15) & ~(uintptr_t)15;
+        S.bq = reinterpret_cast<float4 *>(q);
+        S.seg = reinterpret_cast<unsigned char *>(S.bq + 32);
+    }
     return S;
 }
 
@@ -407,7 +416,8 @@ tree_fp32(const ImpactDesc *__restrict__ Dp, int64_t row_begin, int64_t row_end,
     const int lane = threadIdx.x & 31;
     const int n = D.n;
     const int tcap = D.tsum_cap;
-    const Smem S = carve(smem_raw + (size_t)(threadIdx.x >> 5) * D.tree_smem, tcap, D.pool_cap);
+    const int wsm = EMIT ? D.tree_smem_emit : D.tree_smem_count;
+    const Smem S = carve<EMIT>(smem_raw + (size_t)(threadIdx.x >> 5) * wsm, tcap, D.pool_cap);
     Hdr &H = *S.h;
     const float cut = D.cutoff32;
     const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -524,14 +534,15 @@ tree_fp32(const ImpactDesc *__restrict__ Dp, int64_t row_begin, int64_t row_end,
         bool overflow = false;
         if (!empty) {
             const int leaf = n - 1;
-            const int B = D.tree_B;
             // node buffers: level 0 holds the children of the root (<= tw_0);
-            // a deeper level the children of one batch of <= B parents
+            // a deeper level the children of one batch of parents: tree_B_last
+            // parents for the last level above the leaves, tree_B above it
+            auto batch_of = [&](int level) { return level == n - 2 ? D.tree_B_last : D.tree_B; };
             if (lane == 0) {
                 int bse = 0;
                 for (int k = 0; k <= n - 2; ++k) {
                     H.base[k] = bse;
-                    bse += (k == 0) ? H.tw[0] : B * H.tw[k];
+                    bse += (k == 0) ? H.tw[0] : batch_of(k) * H.tw[k];
                 }
                 if (bse > D.pool_cap - 1) H.base[0] = -1;
             }
@@ -651,7 +662,7 @@ tree_fp32(const ImpactDesc *__restrict__ Dp, int64_t row_begin, int64_t row_end,
                         }
                         const int bse = H.base[lev];
                         const int p0 = H.cur[lev];
-                        const int np = min(B, H.cnt[lev] - p0);
+                        const int np = min(batch_of(lev + 1), H.cnt[lev] - p0);
                         const int cc = expand(S.npu + bse, S.npl + bse, S.ncol + bse, p0, np,
                                               lev + 1);
                         if (lane == 0) {
@@ -744,10 +755,13 @@ int64_t record_stride(int n, int tsum_cap)
     return ((int64_t)32 * n + (int64_t)8 * tsum_cap + 15) / 16 * 16;
 }
 
-int tree_smem_bytes(int tsum_cap, int pool_cap)
+int tree_smem_bytes(int tsum_cap, int pool_cap, bool emit)
 {
-    int64_t b = kHdr + 4 * (int64_t)(3 * tsum_cap + 5 * (tsum_cap + IMPACT_MAX_DIM) + 3 * pool_cap);
-    b = (b + 15) / 16 * 16 + 32 * 16 + kSeg;
+    int64_t b = kHdr + 4 * (int64_t)(3 * tsum_cap + 3 * pool_cap);
+    if (emit)
+        b = (b + 15) / 16 * 16 + 32 * 16 + kSeg;
+    else
+        b += 4 * (int64_t)5 * (tsum_cap + IMPACT_MAX_DIM);
     return (int)((b + 15) / 16 * 16);
 }
 
