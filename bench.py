@@ -40,8 +40,18 @@ sys.path.insert(0, ROOT)
 
 METRIC = "IMDP lo/up bound pairs/sec, FP32-sound vs FP64 plain; served p50/p99 latency"
 UNIT = "pairs/s"
-WORKLOAD = ("5-D room temperature: A=0.85I+0.03 ring, B on rooms 1,3,5 / 2,4, c=1.8, "
-            "[17,23]^5 on 11^5 cells, inputs {0,0.5,1}^2, sigma 0.2, cutoff 1e-8, FP32-sound")
+
+
+def workload_name(cells=11):
+    return ("5-D room temperature: A=0.85I+0.03 ring, B on rooms 1,3,5 / 2,4, c=1.8, "
+            f"[17,23]^5 on {cells}^5 cells, inputs {{0,0.5,1}}^2, sigma 0.2, cutoff 1e-8, "
+            "FP32-sound")
+
+
+WORKLOAD = workload_name()
+# kernels one count + emit step launches: setup, prep, tree count, three scan
+# stages, tree emit
+LAUNCHES_PER_STEP = 7
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -290,11 +300,11 @@ def run_ours(args, rank, world, local_rank):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
            "data": "synthetic",
-           "config": {"workload": WORKLOAD, "rows": rows, "pairs_per_step": nnz,
+           "config": {"workload": workload_name(args.cells), "rows": rows, "pairs_per_step": nnz,
                       "parallelism": f"replicas{world}" if world > 1 else "single",
                       "l2": "flushed between steps (512 MiB write); output 33 GB >> L2"},
            "roofline": roofline, "clocks": clk,
-           "gpu_launches": 6 * args.steps, "wall_s": round(wall_s, 3)}
+           "gpu_launches": LAUNCHES_PER_STEP * args.steps, "wall_s": round(wall_s, 3)}
     del pbuf, flush, wbuf
     torch.cuda.empty_cache()
 

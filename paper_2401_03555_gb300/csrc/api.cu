@@ -401,28 +401,55 @@ impact_status make_plan(const impact_system *sys, const impact_grid *grid,
             D.dim[d].rec_off = ro;
             ro += D.dim[d].wcap;
         }
-        // prefix-tree walk: parent batches of 32 into the level above the
-        // leaves (full leaf batches), smaller ones above it, shrunk until a
-        // warp's shared memory stays near the target (more warps per SM)
-        int upper = 0;
-        for (int d = 1; d <= n - 3; ++d) upper += D.dim[d].wcap;
-        const int lastw = n >= 3 ? D.dim[n - 2].wcap : 0;
-        int Bu = 8, Bl = 32;
-        auto pool_for = [&](int bu, int bl) {
-            return (n >= 2 ? D.dim[0].wcap + bu * upper + bl * lastw : 0) + 1;
-        };
-        auto worst = [&](int bu, int bl) {
-            return std::max(impact::tree_smem_bytes(tsum, pool_for(bu, bl), false),
-                            impact::tree_smem_bytes(tsum, pool_for(bu, bl), true));
-        };
-        while (Bu > 1 && worst(Bu, Bl) > IMPACT_TREE_SMEM_TARGET) Bu /= 2;
-        while (Bl > 4 && worst(Bu, Bl) > IMPACT_TREE_SMEM_TARGET) Bl /= 2;
-        D.tree_B = Bu;
-        D.tree_B_last = Bl;
-        D.pool_cap = pool_for(Bu, Bl);
-        D.tree_smem_count = impact::tree_smem_bytes(tsum, D.pool_cap, false);
-        D.tree_smem_emit = impact::tree_smem_bytes(tsum, D.pool_cap, true);
-        if ((int64_t)worst(Bu, Bl) * impact::tree_warps_per_block() > 200 * 1024)
+        // prefix-tree walk. Each lane finally enumerates the last K dimensions
+        // of one parent: count pass K = 2 when the last window is narrow (a
+        // lane's serial work stays short), else 1; emit pass K = 1 (pairs are
+        // spread over the lanes for coalesced stores). Levels 0..Lp (Lp =
+        // n - 1 - K) keep a ring of nodes each, a power of two: level 0 holds
+        // the root's children, the deepest level room for a full batch plus
+        // one parent's children; rings shrink from the largest while a warp's
+        // shared memory exceeds the target.
+        D.tree_k = (n >= 3 && D.dim[n - 1].wcap <= 16) ? 2 : 1;
+        int worst = 0;
+        for (int pass = 0; pass < 2; ++pass) {
+            const int K = pass == 0 ? D.tree_k : 1;
+            const int Lp = n - 1 - K;
+            int lg[IMPACT_MAX_DIM] = {0}, lmin[IMPACT_MAX_DIM] = {0};
+            auto log2_ceil = [](int v) {
+                int l = 0;
+                while ((1 << l) < v) ++l;
+                return l;
+            };
+            for (int k = 0; k <= Lp; ++k) {
+                const int w = D.dim[k].wcap;
+                const int need = (k == Lp) ? 32 + w : w;
+                lmin[k] = log2_ceil(need);
+                lg[k] = (k == 0 && k < Lp) ? lmin[k] : std::max(lmin[k], log2_ceil(k == Lp ? 128 : 64));
+            }
+            auto bytes = [&]() {
+                int pool = 0;
+                for (int k = 0; k <= Lp; ++k) pool += 1 << lg[k];
+                return impact::tree_smem_bytes(tsum, std::max(pool, 1), pass == 1);
+            };
+            while (bytes() > IMPACT_TREE_SMEM_TARGET) {
+                int big = -1;
+                for (int k = 0; k <= Lp; ++k)
+                    if (lg[k] > lmin[k] && (big < 0 || lg[k] > lg[big])) big = k;
+                if (big < 0) break;
+                --lg[big];
+            }
+            int pool = 0;
+            for (int k = 0; k < IMPACT_MAX_DIM; ++k) {
+                D.ring_log2[pass][k] = k <= Lp ? lg[k] : 0;
+                D.ring_off[pass][k] = pool;
+                if (k <= Lp) pool += 1 << lg[k];
+            }
+            D.pool_cap[pass] = std::max(pool, 1);
+            worst = std::max(worst, bytes());
+        }
+        D.tree_smem_count = impact::tree_smem_bytes(tsum, D.pool_cap[0], false);
+        D.tree_smem_emit = impact::tree_smem_bytes(tsum, D.pool_cap[1], true);
+        if ((int64_t)worst * impact::tree_warps_per_block() > 200 * 1024)
             return fail(IMPACT_ERR_ARG, "the per-row windows are too wide for the FP32 tree walk");
         // tables in erf units (x / (sigma sqrt2)) as FP32 pairs, and in cells
         for (int d = 0; d < n; ++d) {
@@ -637,6 +664,8 @@ impact_status run_count(const Plan &P, const Work &W, impact_csr *out, cudaStrea
                          out->trunc, out->row_flags, W.status(), -1, P.rows};
     if (P.desc.prec == PREC_FP32_SOUND) {
         CK(impact::launch_setup_fp32(W.desc(), P.desc.n, 0, P.rows, W.rec(), W.status(), st));
+        CK(impact::launch_prep_fp32(W.desc(), P.desc.n, 0, P.rows, W.rec(), out->sink_lo,
+                                    out->sink_up, out->trunc, st));
         CK(impact::launch_tree_fp32(W.desc(), P.desc.tree_smem_count, false, 0, P.rows, W.rec(), o, st));
     } else {
         CK(impact::launch_rows(W.desc(), P.desc.prec, false, 0, P.rows, o, st));
@@ -652,8 +681,11 @@ impact_status run_emit(const Plan &P, const Work &W, impact_csr *out, int64_t ca
     impact::RowOutputs o{out->row_ptr, out->col, out->lo, out->up, nullptr, nullptr, nullptr,
                          nullptr, W.status(), capacity, P.rows};
     if (P.desc.prec == PREC_FP32_SOUND) {
-        if (!tables_ready)
+        if (!tables_ready) {   // rebuild the records; the row outputs stay as counted
             CK(impact::launch_setup_fp32(W.desc(), P.desc.n, 0, P.rows, W.rec(), W.status(), st));
+            CK(impact::launch_prep_fp32(W.desc(), P.desc.n, 0, P.rows, W.rec(), nullptr, nullptr,
+                                        nullptr, st));
+        }
         CK(impact::launch_tree_fp32(W.desc(), P.desc.tree_smem_emit, true, 0, P.rows, W.rec(), o, st));
     } else {
         CK(impact::launch_rows(W.desc(), P.desc.prec, true, 0, P.rows, o, st));

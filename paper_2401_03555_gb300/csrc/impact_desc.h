@@ -77,9 +77,12 @@ struct ImpactDesc {
     int inp_div_s;
     int rec_stride;           // bytes per row record in the workspace
     int tsum_cap;             // factor entries a row record holds (all dims)
-    int tree_B;               // prefix-tree walk: parents per batch above the last level
-    int tree_B_last;          // prefix-tree walk: parents per batch into the last level
-    int pool_cap;             // prefix-tree walk: nodes staged per warp
+    int tree_k;               // prefix-tree walk, count pass: dimensions a lane enumerates
+                              // at the end (1 or 2; the emit pass always 1)
+    int ring_log2[2][IMPACT_MAX_DIM];   // prefix-tree walk: log2 capacity of the node ring
+                                        // of each level, [0] count pass, [1] emit pass
+    int ring_off[2][IMPACT_MAX_DIM];    // prefix-tree walk: first node of each ring
+    int pool_cap[2];          // prefix-tree walk: nodes of all rings, per pass
     int tree_smem_count;      // prefix-tree walk: shared-memory bytes per warp, count pass
     int tree_smem_emit;       // prefix-tree walk: shared-memory bytes per warp, emit pass
     const float2 *ea;         // per dim: N+1 edges in erf units, offset edge_off

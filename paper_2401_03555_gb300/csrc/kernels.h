@@ -11,8 +11,8 @@
 #define IMPACT_WINDOW_MAX 64              // FP32 path: window cells per (row, dim)
 #define IMPACT_TSUM_MAX 256               // FP32 path: factor entries per row record
 #define IMPACT_TREE_SEG 512               // FP32 path: pairs staged per leaf batch
-#define IMPACT_TREE_HDR 512               // FP32 path: per-row scalars per warp (bytes)
-#define IMPACT_TREE_SMEM_TARGET 8192      // FP32 path: per-warp shared memory aimed for
+#define IMPACT_TREE_HDR 256               // FP32 path: per-row scalars per warp (bytes)
+#define IMPACT_TREE_SMEM_TARGET 10240     // FP32 path: per-warp shared memory aimed for
 #define IMPACT_STATUS_TABLE_OVERFLOW 0x1u // some row's windows exceeded IMPACT_TABLE_MAX
 #define IMPACT_STATUS_UNSOUND 0x2u        // some row check proved a violation
 #define IMPACT_STATUS_CAPACITY 0x4u       // emit skipped: output capacity too small
@@ -45,6 +45,9 @@ void set_last_error(const std::string &msg);
 // FP32-sound table path (tree_fp32.cu).
 int64_t record_stride(int n, int tsum_cap);
 int tree_smem_bytes(int tsum_cap, int pool_cap, bool emit);
+cudaError_t launch_prep_fp32(const ImpactDesc *d_desc, int n, int64_t row_begin, int64_t row_end,
+                             unsigned char *rec, double *sink_lo, double *sink_up, double *trunc,
+                             cudaStream_t stream);
 int tree_warps_per_block();
 cudaError_t launch_setup_fp32(const ImpactDesc *d_desc, int n, int64_t row_begin,
                               int64_t row_end, unsigned char *rec, uint32_t *status,

@@ -1,5 +1,5 @@
 // tree_fp32.cu -- FP32-sound construction (Def. 3.1 with outward rounding,
-// Sec. 4.4 cutoff, Remark 4.1 sink) in two kernels plus the row scan:
+// Sec. 4.4 cutoff, Remark 4.1 sink) in three kernels plus the row scan:
 //
 //   setup_fp32  one thread per (row, dimension). From the interval image of
 //               the cell it finds the window of target cells that can pass
@@ -8,19 +8,23 @@
 //               (T_max of Def. 3.1, relaxed to the image box) and L[t], a
 //               lower bound of the smallest (T_min). Each window edge needs
 //               one erf/erfc evaluation at the image's lower end and one at
-//               its upper end; neighbouring targets share them. It also
-//               stores the mass outside the trimmed window and the
-//               out-of-domain bounds of this dimension.
-//   tree_fp32   one warp per row. It makes each U table unimodal (a running
-//               maximum from both ends: only raises upper bounds), turns it
-//               into exact pruning thresholds, then walks the prefix tree of
-//               target cells in C order: a node at depth d is a prefix
-//               (t_0..t_d) with the RU-rounded running product P of its
-//               upper factors, and its children that can still reach the
-//               cutoff are exactly {t : TH_{d+1}[t] <= P}, a contiguous run.
-//               Count pass: pairs per row, sink bounds, truncated mass and
-//               row checks (FP64 combination). Emit pass: the same walk,
-//               leaves written with warp-contiguous stores.
+//               its upper end; neighbouring targets share them. It trims the
+//               window to the targets that pass on their own, makes U
+//               unimodal there (a running maximum from each end towards the
+//               peak: only raises upper bounds) and stores the mass outside
+//               the trimmed window and the out-of-domain bounds.
+//   prep_fp32   one thread per (row, dimension) once all tables exist: the
+//               exact pruning thresholds of the dimension, and per row the
+//               sink bounds and the mass of the targets outside the window box.
+//   tree_fp32   one warp per row. It walks the prefix tree of target cells in
+//               C order: a node at depth d is a prefix (t_0..t_d) with the
+//               RU-rounded running product P of its upper factors, and its
+//               children that can still reach the cutoff are exactly
+//               {t : TH_{d+1}[t] <= P}, a contiguous run. Nodes wait in one
+//               ring buffer per level; every step works on up to 32 of them
+//               (one per lane). Count pass: pairs per row, truncated mass and
+//               row checks. Emit pass: the same walk, each batch's pairs
+//               spread over the lanes for warp-contiguous stores.
 //
 // Products run left to right over the dimensions with directed rounding
 // (up: round up, lo: round down) whatever the enumeration order, so every
@@ -38,7 +42,7 @@
 namespace {
 
 constexpr int kSetupThreads = 256;
-constexpr int kTreeWarps = 8;
+constexpr int kTreeWarps = 4;
 constexpr int kTreeThreads = kTreeWarps * 32;
 constexpr int kSeg = IMPACT_TREE_SEG;      // pairs staged per leaf batch
 constexpr int kHdr = IMPACT_TREE_HDR;      // bytes of per-row scalars per warp
@@ -217,8 +221,9 @@ setup_fp32(const ImpactDesc *__restrict__ Dp, int64_t row_begin, int64_t row_end
         const int W = max((int)xb - a + 1, 1);
         unsigned char *rr = rec + rl * (int64_t)D.rec_stride;
         if (W > g.wcap) {
-            reinterpret_cast<int4 *>(rr)[2 * d] = make_int4(a, 0, 0, 1);
-            reinterpret_cast<float4 *>(rr)[2 * d + 1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            reinterpret_cast<int4 *>(rr)[3 * d] = make_int4(a, 0, 0, 0);
+            reinterpret_cast<float4 *>(rr)[3 * d + 1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            reinterpret_cast<float4 *>(rr)[3 * d + 2] = make_float4(0.0f, 0.0f, 1.0f, 0.0f);
             atomicOr(status, IMPACT_STATUS_TABLE_OVERFLOW);
             continue;
         }
@@ -241,7 +246,7 @@ setup_fp32(const ImpactDesc *__restrict__ Dp, int64_t row_begin, int64_t row_end
         }
 
         // factor table of the window: U[k], L[k] for target a + k
-        float *RU = reinterpret_cast<float *>(rr + 32 * n) + g.rec_off;
+        float *RU = reinterpret_cast<float *>(rr + 48 * n) + g.rec_off;
         float *RL = RU + D.tsum_cap;
         EdgePt c0 = R0.at(0), c1 = R1.at(0);
         const EdgePt w0 = c0;   // edge a at m_lo (left tail below)
@@ -302,8 +307,94 @@ setup_fp32(const ImpactDesc *__restrict__ Dp, int64_t row_begin, int64_t row_end
         qlo = fminf(qlo, 1.0f);
         const int tw = first >= 0 ? last - first + 1 : 0;
         const int f0 = first >= 0 ? first : 0;
-        reinterpret_cast<int4 *>(rr)[2 * d] = make_int4(a + f0, tw, f0, 0);
-        reinterpret_cast<float4 *>(rr)[2 * d + 1] = make_float4(mid, O, qlo, qhi);
+        // unimodal envelope of U on the trimmed window (running maximum from
+        // each end towards the peak); raw U is unimodal up to rounding, so
+        // this rarely changes a value, and it only raises upper bounds
+        int pk = 0;
+        float M = 0.0f;
+        if (tw > 0) {
+            float *u = RU + f0;
+            for (int t = 0; t < tw; ++t)
+                if (u[t] > M) { M = u[t]; pk = t; }
+            float run = u[0];
+            for (int t = 1; t < pk; ++t) {
+                float v = u[t];
+                if (v < run) u[t] = run; else run = v;
+            }
+            run = u[tw - 1];
+            for (int t = tw - 2; t > pk; --t) {
+                float v = u[t];
+                if (v < run) u[t] = run; else run = v;
+            }
+        }
+        reinterpret_cast<int4 *>(rr)[3 * d] = make_int4(a + f0, tw, f0, pk);
+        reinterpret_cast<float4 *>(rr)[3 * d + 1] = make_float4(mid, O, qlo, qhi);
+        reinterpret_cast<float4 *>(rr)[3 * d + 2] = make_float4(M, 0.0f, 1.0f, 0.0f);
+    }
+}
+
+// prep_fp32: one thread per (row, dimension) once every dimension's table
+// exists. Pruning thresholds of this dimension: a child t of a node with
+// product P survives iff RU(RU(P U_d[t]) R') >= cutoff, R' bounding the
+// product of the later dimensions' largest factors; TH_d[t] is the least
+// such P. Thread 0 of a row also finishes the row's sink bounds and the mass
+// of the targets outside the window box (FP64, outward rounding), unless the
+// row outputs are null (records rebuilt for an emit pass).
+__global__ void __launch_bounds__(kSetupThreads)
+prep_fp32(const ImpactDesc *__restrict__ Dp, int64_t row_begin, int64_t row_end,
+          unsigned char *__restrict__ rec, double *__restrict__ sink_lo,
+          double *__restrict__ sink_up, double *__restrict__ trunc)
+{
+    const ImpactDesc &D = *Dp;
+    const int n = D.n;
+    const float cut = D.cutoff32;
+    const int64_t total = (row_end - row_begin) * n;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total; p += stride) {
+        const int64_t rl = p / n;
+        const int d = (int)(p - rl * n);
+        unsigned char *rr = rec + rl * (int64_t)D.rec_stride;
+        const int4 *hi = reinterpret_cast<const int4 *>(rr);
+        const float4 *hf = reinterpret_cast<const float4 *>(rr);
+        float R = 1.0f, SR = 1.0f;
+        for (int k = d + 1; k < n; ++k) {
+            R = __fmul_ru(R, hf[3 * k + 2].x);
+            SR = __fmul_ru(SR, hf[3 * k + 1].x);
+        }
+        float cp = 0.0f;
+        if (cut > 0.0f) cp = (d == n - 1) ? cut : threshold(cut, __fmul_ru(R, kGrow18));
+        const int4 h = hi[3 * d];
+        float4 c = hf[3 * d + 2];
+        c.y = cp;
+        c.z = SR;
+        reinterpret_cast<float4 *>(rr)[3 * d + 2] = c;
+        const float *RU = reinterpret_cast<const float *>(rr + 48 * n) + D.dim[d].rec_off + h.z;
+        float *RT = reinterpret_cast<float *>(rr + 48 * n) + 2 * D.tsum_cap + D.dim[d].rec_off + h.z;
+        for (int t = 0; t < h.y; ++t) RT[t] = cp > 0.0f ? threshold(cp, RU[t]) : 0.0f;
+        if (d == 0 && trunc) {
+            // sink bounds: 1 - prod_d (1 - Q_d)
+            double pin_up = 1.0, pin_dn = 1.0;
+            for (int k = 0; k < n; ++k) {
+                const float4 b = hf[3 * k + 1];
+                pin_up = __dmul_ru(pin_up, __dsub_ru(1.0, (double)b.z));
+                pin_dn = __dmul_rd(pin_dn, __dsub_rd(1.0, (double)b.w));
+            }
+            // mass of the targets outside the window box, partitioned by the
+            // first dimension whose index leaves the window:
+            // prod_{k<d} SW_k * O_d * prod_{k>d} (SW_k + O_k)
+            double suf = 1.0, outside = 0.0;
+            for (int k = n - 1; k >= 0; --k) {
+                double pre = 1.0;
+                for (int q = 0; q < k; ++q) pre *= (double)hf[3 * q + 1].x;
+                const float4 b = hf[3 * k + 1];
+                outside += pre * (double)b.y * suf;
+                suf *= (double)b.x + (double)b.y;
+            }
+            const int64_t row = row_begin + rl;
+            sink_lo[row] = fmax(__dsub_rd(1.0, pin_up), 0.0);
+            sink_up[row] = fmin(__dsub_ru(1.0, pin_dn), 1.0);
+            trunc[row] = outside * (1.0 + 1e-12);
+        }
     }
 }
 
@@ -313,20 +404,20 @@ setup_fp32(const ImpactDesc *__restrict__ Dp, int64_t row_begin, int64_t row_end
 
 // Per-warp shared memory: a header of per-row scalars, then (entries)
 //   U, L, T                      3 * tcap      factor tables, thresholds
-//   npu, npl, ncol               3 * pool      prefix-tree nodes
+//   npu, npl, ncol               3 * pool      node rings of all levels
 // and, count pass:
 //   pu_up, pu_dn, pl_up, pl_dn   4 * (tcap+8)  prefix sums
 //   su_up                        (tcap+8)      suffix sums of U
 // or, emit pass:
-//   bq                           32 float4     leaf parents
-//   seg                          kSeg bytes    pair -> parent
+//   bq (32 float4) + seg (kSeg bytes)          leaf runs of one batch
 struct Hdr {
     int ta[IMPACT_MAX_DIM], tw[IMPACT_MAX_DIM], pk[IMPACT_MAX_DIM], toff[IMPACT_MAX_DIM];
-    int first[IMPACT_MAX_DIM], cnt[IMPACT_MAX_DIM], cur[IMPACT_MAX_DIM], base[IMPACT_MAX_DIM];
-    float M[IMPACT_MAX_DIM], SW[IMPACT_MAX_DIM], O[IMPACT_MAX_DIM], qlo[IMPACT_MAX_DIM];
-    float qhi[IMPACT_MAX_DIM], cp[IMPACT_MAX_DIM], swr[IMPACT_MAX_DIM];
+    int first[IMPACT_MAX_DIM];
+    float swr[IMPACT_MAX_DIM];
 };
 static_assert(sizeof(Hdr) <= kHdr, "row header does not fit");
+
+constexpr int kEmitStageBytes = 32 * 16 + kSeg;
 
 struct Smem {
     Hdr *h;
@@ -348,6 +439,9 @@ __device__ __forceinline__ Smem carve(unsigned char *base, int tcap, int pool)
     S.npu = f; f += pool;
     S.npl = f; f += pool;
     S.ncol = reinterpret_cast<int *>(f); f += pool;
+    S.pu_up = S.pu_dn = S.pl_up = S.pl_dn = S.su_up = nullptr;
+    S.bq = nullptr;
+    S.seg = nullptr;
     if (!EMIT) {
         const int tp = tcap + IMPACT_MAX_DIM;
         S.pu_up = f; f += tp;
@@ -355,13 +449,10 @@ __device__ __forceinline__ Smem carve(unsigned char *base, int tcap, int pool)
         S.pl_up = f; f += tp;
         S.pl_dn = f; f += tp;
         S.su_up = f; f += tp;
-        S.bq = nullptr;
-        S.seg = nullptr;
     } else {
-        S.pu_up = S.pu_dn = S.pl_up = S.pl_dn = S.su_up = nullptr;
-        uintptr_t q = ((uintptr_t)f + 15) & ~(uintptr_t)15;
+        unsigned char *q = reinterpret_cast<unsigned char *>(((uintptr_t)f + 15) & ~(uintptr_t)15);
         S.bq = reinterpret_cast<float4 *>(q);
-        S.seg = reinterpret_cast<unsigned char *>(S.bq + 32);
+        S.seg = q + 32 * 16;
     }
     return S;
 }
@@ -380,14 +471,13 @@ __device__ __forceinline__ int warp_excl_scan(int v, int &total)
 }
 
 // Run of dimension `dim` kept under a node with product P: [l, l + c).
+// TH is non-increasing up to the peak and non-decreasing after it.
 __device__ __forceinline__ void run_of(const Smem &S, int dim, float P, int &l, int &c)
 {
     const int off = S.h->toff[dim], pk = S.h->pk[dim], tw = S.h->tw[dim];
     const float *T = S.T + off;
     int cl = 0, cr = 0;
-#pragma unroll 4
     for (int t = 0; t <= pk; ++t) cl += (T[t] <= P) ? 1 : 0;
-#pragma unroll 4
     for (int t = pk + 1; t < tw; ++t) cr += (T[t] <= P) ? 1 : 0;
     c = cl > 0 ? cl + cr : 0;
     l = pk + 1 - cl;
@@ -417,9 +507,11 @@ tree_fp32(const ImpactDesc *__restrict__ Dp, int64_t row_begin, int64_t row_end,
     const int n = D.n;
     const int tcap = D.tsum_cap;
     const int wsm = EMIT ? D.tree_smem_emit : D.tree_smem_count;
-    const Smem S = carve<EMIT>(smem_raw + (size_t)(threadIdx.x >> 5) * wsm, tcap, D.pool_cap);
+    const int pool = D.pool_cap[EMIT ? 1 : 0];
+    const Smem S = carve<EMIT>(smem_raw + (size_t)(threadIdx.x >> 5) * wsm, tcap, pool);
     Hdr &H = *S.h;
-    const float cut = D.cutoff32;
+    const int K = EMIT ? 1 : D.tree_k;   // dimensions a lane enumerates at the end
+    const int Lp = n - 1 - K;         // level of the block parents (-1: the root)
     const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     if (EMIT && capacity >= 0 && row_ptr[total_at] > capacity) {
@@ -431,16 +523,13 @@ tree_fp32(const ImpactDesc *__restrict__ Dp, int64_t row_begin, int64_t row_end,
         const unsigned char *rr = rec + (row - row_begin) * (int64_t)D.rec_stride;
         // 1. the row record: per-dimension scalars, then the trimmed tables
         if (lane < n) {
-            int4 hi = reinterpret_cast<const int4 *>(rr)[2 * lane];
-            float4 hf = reinterpret_cast<const float4 *>(rr)[2 * lane + 1];
+            const int4 hi = reinterpret_cast<const int4 *>(rr)[3 * lane];
+            const float4 hc = reinterpret_cast<const float4 *>(rr)[3 * lane + 2];
             H.ta[lane] = hi.x;
             H.tw[lane] = hi.y;
             H.first[lane] = hi.z;
-            H.SW[lane] = hf.x;
-            H.O[lane] = hf.y;
-            H.qlo[lane] = hf.z;
-            H.qhi[lane] = hf.w;
-            if (hi.w) atomicOr(status, IMPACT_STATUS_TABLE_OVERFLOW);
+            H.pk[lane] = hi.w;
+            H.swr[lane] = hc.z;
         }
         __syncwarp();
         bool empty = false;
@@ -454,50 +543,17 @@ tree_fp32(const ImpactDesc *__restrict__ Dp, int64_t row_begin, int64_t row_end,
         }
         __syncwarp();
         {
-            const float *RU = reinterpret_cast<const float *>(rr + 32 * n);
+            const float *RA = reinterpret_cast<const float *>(rr + 48 * n);
             for (int k = 0; k < n; ++k) {
                 const int src = D.dim[k].rec_off + H.first[k], dst = H.toff[k], tw = H.tw[k];
                 for (int i = lane; i < tw; i += 32) {
-                    S.U[dst + i] = RU[src + i];
-                    S.L[dst + i] = RU[tcap + src + i];
+                    S.U[dst + i] = RA[src + i];
+                    S.L[dst + i] = RA[tcap + src + i];
+                    S.T[dst + i] = RA[2 * tcap + src + i];
                 }
             }
         }
         __syncwarp();
-        // 2. unimodal envelope of each U table (one lane per dimension)
-        if (lane < n) {
-            float *U = S.U + H.toff[lane];
-            const int tw = H.tw[lane];
-            int pk = 0;
-            for (int t = 1; t < tw; ++t)
-                if (U[t] > U[pk]) pk = t;
-            for (int t = 1; t < pk; ++t) U[t] = fmaxf(U[t], U[t - 1]);
-            for (int t = tw - 2; t > pk; --t) U[t] = fmaxf(U[t], U[t + 1]);
-            H.pk[lane] = pk;
-            H.M[lane] = tw > 0 ? U[pk] : 0.0f;
-        }
-        __syncwarp();
-        // 3. pruning thresholds: a child t of a node with product P survives
-        //    iff RU(RU(P U_d[t]) R') >= cutoff, R' bounding the product of the
-        //    later dimensions' largest factors; TH_d[t] is the least such P
-        if (lane < n) {
-            float R = 1.0f, SR = 1.0f;
-            for (int k = lane + 1; k < n; ++k) {
-                R = __fmul_ru(R, H.M[k]);
-                SR = __fmul_ru(SR, H.SW[k]);
-            }
-            float cp = 0.0f;
-            if (cut > 0.0f) cp = (lane == n - 1) ? cut : threshold(cut, __fmul_ru(R, kGrow18));
-            H.cp[lane] = cp;
-            H.swr[lane] = SR;
-        }
-        __syncwarp();
-        for (int k = 0; k < n; ++k) {
-            const int off = H.toff[k], tw = H.tw[k];
-            const float cp = H.cp[k];
-            for (int i = lane; i < tw; i += 32)
-                S.T[off + i] = cp > 0.0f ? threshold(cp, S.U[off + i]) : 0.0f;
-        }
         if (!EMIT && lane < n) {   // prefix and suffix sums of U and L per dimension
             const int off = H.toff[lane], po = off + lane, tw = H.tw[lane];
             float a = 0.0f, b = 0.0f, c = 0.0f, e = 0.0f;
@@ -506,10 +562,11 @@ tree_fp32(const ImpactDesc *__restrict__ Dp, int64_t row_begin, int64_t row_end,
             S.pl_up[po] = 0.0f;
             S.pl_dn[po] = 0.0f;
             for (int t = 0; t < tw; ++t) {
-                a = __fadd_ru(a, S.U[off + t]);
-                b = __fadd_rd(b, S.U[off + t]);
-                c = __fadd_ru(c, S.L[off + t]);
-                e = __fadd_rd(e, S.L[off + t]);
+                const float ut = S.U[off + t], lt = S.L[off + t];
+                a = __fadd_ru(a, ut);
+                b = __fadd_rd(b, ut);
+                c = __fadd_ru(c, lt);
+                e = __fadd_rd(e, lt);
                 S.pu_up[po + t + 1] = a;
                 S.pu_dn[po + t + 1] = b;
                 S.pl_up[po + t + 1] = c;
@@ -531,156 +588,205 @@ tree_fp32(const ImpactDesc *__restrict__ Dp, int64_t row_begin, int64_t row_end,
             out_base = row_ptr[row];
             out_end = row_ptr[row + 1];
         }
-        bool overflow = false;
-        if (!empty) {
-            const int leaf = n - 1;
-            // node buffers: level 0 holds the children of the root (<= tw_0);
-            // a deeper level the children of one batch of parents: tree_B_last
-            // parents for the last level above the leaves, tree_B above it
-            auto batch_of = [&](int level) { return level == n - 2 ? D.tree_B_last : D.tree_B; };
-            if (lane == 0) {
-                int bse = 0;
-                for (int k = 0; k <= n - 2; ++k) {
-                    H.base[k] = bse;
-                    bse += (k == 0) ? H.tw[0] : batch_of(k) * H.tw[k];
-                }
-                if (bse > D.pool_cap - 1) H.base[0] = -1;
+        // count-pass bookkeeping of one leaf run [l, l + c) under P (dim dl)
+        auto leaf_sums = [&](int dl, float P, float Pl, int l, int c) {
+            const int po = H.toff[dl] + dl;
+            cnt += c;
+            if (c > 0) {
+                float su = fmaxf(__fsub_ru(S.pu_up[po + l + c], S.pu_dn[po + l]), 0.0f);
+                float sl = fmaxf(__fsub_rd(S.pl_dn[po + l + c], S.pl_up[po + l]), 0.0f);
+                sup = __fadd_ru(sup, __fmul_ru(P, su));
+                slo = __fadd_rd(slo, __fmul_rd(Pl, sl));
             }
-            __syncwarp();
-            if (n >= 2 && H.base[0] < 0) overflow = true;
-            const int LB = min(32, kSeg / max(H.tw[leaf], 1));   // leaf parents per batch
+            drop = __fadd_ru(drop, __fmul_ru(P, outside_sum(S, dl, l, c)));
+        };
 
-            // leaf processing of parents [p0, p0 + np) of a parent array
-            auto leaf_batch = [&](const float *ppu, const float *ppl, const int *pcol, int p0,
-                                  int np) {
-                const bool act = lane < np;
-                const float P = act ? ppu[p0 + lane] : 0.0f;
-                const float Pl = act ? ppl[p0 + lane] : 0.0f;
-                const int cb = act ? pcol[p0 + lane] : 0;
-                int l = 0, c = 0;
-                if (act) run_of(S, leaf, P, l, c);
-                if (!EMIT) {
-                    if (act) {
-                        const int po = H.toff[leaf] + leaf;
-                        cnt += c;
-                        if (c > 0) {
-                            float su = fmaxf(__fsub_ru(S.pu_up[po + l + c], S.pu_dn[po + l]), 0.0f);
-                            float sl = fmaxf(__fsub_rd(S.pl_dn[po + l + c], S.pl_up[po + l]), 0.0f);
-                            sup = __fadd_ru(sup, __fmul_ru(P, su));
-                            slo = __fadd_rd(slo, __fmul_rd(Pl, sl));
-                        }
-                        drop = __fadd_ru(drop, __fmul_ru(P, outside_sum(S, leaf, l, c)));
+        // K = 1: each active lane's parent (P, Pl, cb) owns one run of the
+        // last dimension; emit spreads the batch's pairs over the lanes
+        auto leaf_batch = [&](bool act, float P, float Pl, int cb) {
+            const int dl = n - 1;
+            int l = 0, c = 0;
+            if (act) run_of(S, dl, P, l, c);
+            if (!EMIT) {
+                if (act) leaf_sums(dl, P, Pl, l, c);
+            } else {
+                int C;
+                const int o = warp_excl_scan(c, C);
+                S.bq[lane] = make_float4(P, Pl, __int_as_float(cb + H.ta[dl]),
+                                         __int_as_float(l - o));
+                for (int k = 0; k < c; ++k) S.seg[o + k] = (unsigned char)lane;
+                __syncwarp();
+                const float *U = S.U + H.toff[dl];
+                const float *L = S.L + H.toff[dl];
+                for (int e = lane; e < C; e += 32) {
+                    const float4 q = S.bq[S.seg[e]];
+                    const int t = e + __float_as_int(q.w);
+                    const int64_t pos = out_base + written + e;
+                    if (pos < out_end) {
+                        out_col[pos] = __float_as_int(q.z) + t;
+                        out_lo[pos] = __fmul_rd(q.y, L[t]);
+                        out_up[pos] = __fmul_ru(q.x, U[t]);
                     }
-                } else {
-                    int C;
-                    const int o = warp_excl_scan(c, C);
-                    S.bq[lane] = make_float4(P, Pl, __int_as_float(cb + H.ta[leaf]),
-                                             __int_as_float(l - o));
-                    for (int k = 0; k < c; ++k) S.seg[o + k] = (unsigned char)lane;
-                    __syncwarp();
-                    const float *U = S.U + H.toff[leaf];
-                    const float *L = S.L + H.toff[leaf];
-                    for (int e = lane; e < C; e += 32) {
-                        const float4 q = S.bq[S.seg[e]];
-                        const int t = e + __float_as_int(q.w);
-                        const int64_t pos = out_base + written + e;
-                        if (pos < out_end) {
-                            out_col[pos] = __float_as_int(q.z) + t;
-                            out_lo[pos] = __fmul_rd(q.y, L[t]);
-                            out_up[pos] = __fmul_ru(q.x, U[t]);
-                        }
-                    }
-                    written += C;
-                    __syncwarp();
                 }
-            };
+                written += C;
+                __syncwarp();
+            }
+        };
 
-            // expansion of parents [p0, p0 + np) into their children on `dim`
-            auto expand = [&](const float *ppu, const float *ppl, const int *pcol, int p0, int np,
-                              int dim) -> int {
+        // K = 2 (count pass): each active lane's parent owns the subtree of
+        // the last two dimensions, a run of the middle dimension with a leaf
+        // run under each of its nodes, walked serially by the lane
+        auto block_batch = [&](bool act, float P, float Pl) {
+            const int dm = n - 2, dl = n - 1;
+            const int offm = H.toff[dm];
+            int lm = 0, cm = 0;
+            if (act) run_of(S, dm, P, lm, cm);
+            if (act) {
+                drop = __fadd_ru(drop, __fmul_ru(__fmul_ru(P, outside_sum(S, dm, lm, cm)),
+                                                 H.swr[dm]));
+                for (int i = 0; i < cm; ++i) {
+                    const int m = lm + i;
+                    const float P2 = __fmul_ru(P, S.U[offm + m]);
+                    const float Pl2 = __fmul_rd(Pl, S.L[offm + m]);
+                    int l1, c1;
+                    run_of(S, dl, P2, l1, c1);
+                    leaf_sums(dl, P2, Pl2, l1, c1);
+                }
+            }
+        };
+
+        // The walk keeps one ring buffer of nodes per level 0..Lp (level k
+        // holds prefixes of k + 1 dimensions, in C order). Lane k keeps the
+        // head and size of ring k. A step either consumes a batch of the
+        // deepest ring (Lp) or expands a batch of parents of the deepest
+        // other ring that has room below it; the parents taken are the
+        // longest prefix of the batch whose children fit. Rings are FIFOs and
+        // expansions append in order, so pairs leave in C order.
+        const int pass = EMIT ? 1 : 0;
+        int my_head = 0, my_size = 0;   // ring `lane`
+        const int my_cap = lane < n ? (1 << D.ring_log2[pass][lane]) : 0;
+        const int my_off = lane < n ? D.ring_off[pass][lane] : 0;
+        const int LB = (K == 1 && EMIT) ? min(32, kSeg / max(H.tw[n - 1], 1)) : 32;
+        if (!empty) {
+            // every step takes at least one node off a ring (or is the root
+            // step), so the nodes of levels 0..Lp bound the steps; the guard
+            // only turns a broken invariant into an error instead of a hang
+            int64_t guard = 2, prod = 1;
+            for (int k = 0; k <= Lp; ++k) {
+                prod = min(prod * H.tw[k], (int64_t)1 << 40);
+                guard += 2 * prod;
+            }
+            bool root_pending = true;
+            while (true) {
+                if (--guard < 0) {
+                    if (lane == 0) atomicOr(status, IMPACT_STATUS_TABLE_OVERFLOW);
+                    break;
+                }
+                const int nxt_size = __shfl_down_sync(0xffffffffu, my_size, 1);
+                const int nxt_cap = __shfl_down_sync(0xffffffffu, my_cap, 1);
+                const int nxt_tw = (lane + 1 < n) ? H.tw[lane + 1] : 0;
+                const unsigned up_any = __ballot_sync(0xffffffffu, lane < Lp && my_size > 0);
+                const unsigned can = __ballot_sync(
+                    0xffffffffu, lane < Lp && my_size > 0 && nxt_cap - nxt_size >= nxt_tw);
+                const int szL = Lp >= 0 ? __shfl_sync(0xffffffffu, my_size, Lp) : 0;
+                const bool more_above = up_any != 0u || root_pending;
+                if (Lp >= 0 && (szL >= LB || (szL > 0 && !more_above))) {
+                    // consume a batch of the deepest ring
+                    const int np = min(LB, szL);
+                    const int hd = __shfl_sync(0xffffffffu, my_head, Lp);
+                    const int cap = __shfl_sync(0xffffffffu, my_cap, Lp);
+                    const int off = __shfl_sync(0xffffffffu, my_off, Lp);
+                    const bool act = lane < np;
+                    const int ix = off + ((hd + lane) & (cap - 1));
+                    const float P = act ? S.npu[ix] : 0.0f;
+                    const float Pl = act ? S.npl[ix] : 0.0f;
+                    const int cb = act ? S.ncol[ix] : 0;
+                    if (K == 1)
+                        leaf_batch(act, P, Pl, cb);
+                    else
+                        block_batch(act, P, Pl);
+                    if (lane == Lp) {
+                        my_head = (my_head + np) & (cap - 1);
+                        my_size -= np;
+                    }
+                    continue;
+                }
+                int src;   // level of the parents to expand (-1: the root)
+                if (can != 0u) {
+                    src = 31 - __clz(can);
+                } else if (root_pending) {
+                    src = -1;
+                    root_pending = false;
+                } else {
+                    break;
+                }
+                const int dim = src + 1;
+                if (dim > Lp) {   // Lp < 0: the root is the only parent
+                    if (K == 1)
+                        leaf_batch(lane == 0, 1.0f, 1.0f, 0);
+                    else
+                        block_batch(lane == 0, 1.0f, 1.0f);
+                    continue;
+                }
+                int np, hd = 0, scap = 1, soff = 0;
+                if (src >= 0) {
+                    np = min(32, __shfl_sync(0xffffffffu, my_size, src));
+                    hd = __shfl_sync(0xffffffffu, my_head, src);
+                    scap = __shfl_sync(0xffffffffu, my_cap, src);
+                    soff = __shfl_sync(0xffffffffu, my_off, src);
+                } else {
+                    np = 1;
+                }
+                const int dsize = __shfl_sync(0xffffffffu, my_size, dim);
+                const int dhead = __shfl_sync(0xffffffffu, my_head, dim);
+                const int dcap = __shfl_sync(0xffffffffu, my_cap, dim);
+                const int doff = __shfl_sync(0xffffffffu, my_off, dim);
                 const bool act = lane < np;
-                const float P = act ? ppu[p0 + lane] : 0.0f;
-                const float Pl = act ? ppl[p0 + lane] : 0.0f;
-                const int cb = act ? pcol[p0 + lane] : 0;
+                float P = 1.0f, Pl = 1.0f;
+                int cb = 0;
+                if (src >= 0 && act) {
+                    const int ix = soff + ((hd + lane) & (scap - 1));
+                    P = S.npu[ix];
+                    Pl = S.npl[ix];
+                    cb = S.ncol[ix];
+                }
                 int l = 0, c = 0;
                 if (act) run_of(S, dim, P, l, c);
                 int C;
                 const int o = warp_excl_scan(c, C);
-                const int off = H.toff[dim], st = D.dim[dim].stride, ta = H.ta[dim];
-                const int bse = H.base[dim];
-                for (int k = 0; k < c; ++k) {
-                    const int t = l + k;
-                    S.npu[bse + o + k] = __fmul_ru(P, S.U[off + t]);
-                    S.npl[bse + o + k] = __fmul_rd(Pl, S.L[off + t]);
-                    S.ncol[bse + o + k] = cb + (ta + t) * st;
+                const bool take = act && o + c <= dcap - dsize;
+                const unsigned tk = __ballot_sync(0xffffffffu, take);
+                const int nt = __popc(tk);
+                if (take) {
+                    const int off = H.toff[dim], st = D.dim[dim].stride, ta = H.ta[dim];
+                    const int base = dhead + dsize + o;
+                    for (int k = 0; k < c; ++k) {
+                        const int t = l + k;
+                        const int ix = doff + ((base + k) & (dcap - 1));
+                        S.npu[ix] = __fmul_ru(P, S.U[off + t]);
+                        S.npl[ix] = __fmul_rd(Pl, S.L[off + t]);
+                        S.ncol[ix] = cb + (ta + t) * st;
+                    }
+                    if (!EMIT)
+                        drop = __fadd_ru(drop, __fmul_ru(__fmul_ru(P, outside_sum(S, dim, l, c)),
+                                                         H.swr[dim]));
                 }
-                if (!EMIT && act)
-                    drop = __fadd_ru(drop, __fmul_ru(__fmul_ru(P, outside_sum(S, dim, l, c)),
-                                                     H.swr[dim]));
+                // children appended: the sum of the taken lanes' runs
+                int added = take ? c : 0;
+#pragma unroll
+                for (int s2 = 16; s2 > 0; s2 >>= 1) added += __shfl_xor_sync(0xffffffffu, added, s2);
+                if (lane == dim) my_size += added;
+                if (src >= 0 && lane == src) {
+                    my_head = (my_head + nt) & (scap - 1);
+                    my_size -= nt;
+                }
                 __syncwarp();
-                return C;
-            };
-
-            if (!overflow) {
-                if (n == 1) {
-                    if (lane == 0) {   // the root: empty product
-                        S.npu[0] = 1.0f;
-                        S.npl[0] = 1.0f;
-                        S.ncol[0] = 0;
-                    }
-                    __syncwarp();
-                    leaf_batch(S.npu, S.npl, S.ncol, 0, 1);
-                } else {
-                    const int root = D.pool_cap - 1;   // the root sits past the level buffers
-                    if (lane == 0) {
-                        S.npu[root] = 1.0f;
-                        S.npl[root] = 1.0f;
-                        S.ncol[root] = 0;
-                    }
-                    __syncwarp();
-                    const int c0 = expand(S.npu, S.npl, S.ncol, root, 1, 0);
-                    if (lane == 0) {
-                        H.cnt[0] = c0;
-                        H.cur[0] = 0;
-                    }
-                    __syncwarp();
-                    int lev = 0;
-                    while (true) {
-                        if (lev == n - 2) {
-                            const int bse = H.base[lev];
-                            for (int p = 0; p < H.cnt[lev]; p += LB)
-                                leaf_batch(S.npu + bse, S.npl + bse, S.ncol + bse, p,
-                                           min(LB, H.cnt[lev] - p));
-                            if (lev == 0) break;
-                            --lev;
-                            continue;
-                        }
-                        if (H.cur[lev] >= H.cnt[lev]) {
-                            if (lev == 0) break;
-                            --lev;
-                            continue;
-                        }
-                        const int bse = H.base[lev];
-                        const int p0 = H.cur[lev];
-                        const int np = min(batch_of(lev + 1), H.cnt[lev] - p0);
-                        const int cc = expand(S.npu + bse, S.npl + bse, S.ncol + bse, p0, np,
-                                              lev + 1);
-                        if (lane == 0) {
-                            H.cur[lev] = p0 + np;
-                            H.cnt[lev + 1] = cc;
-                            H.cur[lev + 1] = 0;
-                        }
-                        __syncwarp();
-                        ++lev;
-                    }
-                }
             }
         }
 
         if (EMIT) {
-            if (lane == 0 && (overflow || out_base + written != out_end))
-                atomicOr(status, overflow ? IMPACT_STATUS_TABLE_OVERFLOW
-                                          : IMPACT_STATUS_EMIT_MISMATCH);
+            if (lane == 0 && out_base + written != out_end)
+                atomicOr(status, IMPACT_STATUS_EMIT_MISMATCH);
         } else {
             double dsum = (double)drop, usum = (double)sup, lsum = (double)slo;
             long long csum = cnt;
@@ -692,38 +798,17 @@ tree_fp32(const ImpactDesc *__restrict__ Dp, int64_t row_begin, int64_t row_end,
                 csum += __shfl_xor_sync(0xffffffffu, csum, o);
             }
             if (lane == 0) {
-                // sink bounds: 1 - prod_d (1 - Q_d), outward in FP64
-                double pin_up = 1.0, pin_dn = 1.0;
-                for (int k = 0; k < n; ++k) {
-                    pin_up = __dmul_ru(pin_up, __dsub_ru(1.0, (double)H.qlo[k]));
-                    pin_dn = __dmul_rd(pin_dn, __dsub_rd(1.0, (double)H.qhi[k]));
-                }
-                const double sl = fmax(__dsub_rd(1.0, pin_up), 0.0);
-                const double su = fmin(__dsub_ru(1.0, pin_dn), 1.0);
-                // mass of the targets outside the window box, partitioned by
-                // the first dimension whose index leaves the window:
-                // prod_{k<d} SW_k * O_d * prod_{k>d} (SW_k + O_k)
-                double suf = 1.0, outside = 0.0;
-                for (int k = n - 1; k >= 0; --k) {
-                    double pre = 1.0;
-                    for (int q = 0; q < k; ++q) pre *= (double)H.SW[q];
-                    outside += pre * (double)H.O[k] * suf;
-                    suf *= (double)H.SW[k] + (double)H.O[k];
-                }
-                const double tr = (outside + dsum) * (1.0 + 1e-12);
-                row_ptr[row] = overflow ? 0 : csum;
-                sink_lo[row] = sl;
-                sink_up[row] = su;
+                const double tr = trunc[row] + dsum * (1.0 + 1e-12);
+                row_ptr[row] = csum;
                 trunc[row] = tr;
-                if (overflow) atomicOr(status, IMPACT_STATUS_TABLE_OVERFLOW);
                 if (flags) {
                     // the emitted values are RU / RD products of the factors:
                     // widen the run sums by their rounding before testing
                     const double lo_sum = lsum * (1.0 - 1e-6);
                     const double up_sum = usum * (1.0 + 1e-6);
                     uint32_t f = 0;
-                    if (__dadd_rd(lo_sum, sl) > 1.0) f |= 0x1u;
-                    if (__dadd_ru(__dadd_ru(up_sum, su), tr) < 1.0) f |= 0x2u;
+                    if (__dadd_rd(lo_sum, sink_lo[row]) > 1.0) f |= 0x1u;
+                    if (__dadd_ru(__dadd_ru(up_sum, sink_up[row]), tr) < 1.0) f |= 0x2u;
                     flags[row] = f;
                     if (f) atomicOr(status, IMPACT_STATUS_UNSOUND);
                 }
@@ -752,17 +837,29 @@ namespace impact {
 
 int64_t record_stride(int n, int tsum_cap)
 {
-    return ((int64_t)32 * n + (int64_t)8 * tsum_cap + 15) / 16 * 16;
+    return ((int64_t)48 * n + (int64_t)12 * tsum_cap + 15) / 16 * 16;
 }
 
 int tree_smem_bytes(int tsum_cap, int pool_cap, bool emit)
 {
     int64_t b = kHdr + 4 * (int64_t)(3 * tsum_cap + 3 * pool_cap);
     if (emit)
-        b = (b + 15) / 16 * 16 + 32 * 16 + kSeg;
+        b = (b + 15) / 16 * 16 + kEmitStageBytes;
     else
         b += 4 * (int64_t)5 * (tsum_cap + IMPACT_MAX_DIM);
     return (int)((b + 15) / 16 * 16);
+}
+
+cudaError_t launch_prep_fp32(const ImpactDesc *d_desc, int n, int64_t row_begin, int64_t row_end,
+                             unsigned char *rec, double *sink_lo, double *sink_up, double *trunc,
+                             cudaStream_t stream)
+{
+    int64_t rows = row_end - row_begin;
+    if (rows <= 0) return cudaSuccess;
+    int g = occupancy_grid((const void *)prep_fp32, kSetupThreads, 0, rows * n, kSetupThreads);
+    prep_fp32<<<g, kSetupThreads, 0, stream>>>(d_desc, row_begin, row_end, rec, sink_lo, sink_up,
+                                               trunc);
+    return cudaGetLastError();
 }
 
 int tree_warps_per_block() { return kTreeWarps; }
