@@ -58,7 +58,7 @@ L2_FLUSH_BYTES = 512 << 20
 def parse_args(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64-plain comparison")
@@ -132,7 +132,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -184,6 +184,31 @@ def hbm_peak():
             return float(json.load(f)["hbm_gbs"]), "measured"
     except (OSError, KeyError, ValueError):
         return 6800.0, "fallback"
+
+
+def emit_traffic(alg_bytes):
+    """DRAM bytes of one emit launch, from the committed ncu summary.
+
+    The summary records the DRAM traffic per algorithmic byte of the emit
+    kernel and the hash of the source it was captured on; the figure is used
+    only while that source is unchanged (None otherwise)."""
+    import hashlib
+    prof = os.path.join(ROOT, "profiles", "room5d_fp32_tree_kernels_ncu.txt")
+    src = os.path.join(ROOT, "paper_2401_03555_gb300", "csrc", "tree_fp32.cu")
+    try:
+        text = open(prof).read()
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    want, ratio = None, None
+    for line in text.splitlines():
+        if "sha256 prefix" in line:
+            want = line.split("sha256 prefix")[1].strip().rstrip(".").split()[0]
+        if line.strip().startswith("traffic_bytes_per_algorithmic_byte:"):
+            ratio = float(line.split(":")[1])
+    if want is None or ratio is None or not digest.startswith(want):
+        return None
+    return int(ratio * alg_bytes)
 
 
 # --------------------------------------------------------------------------
@@ -291,8 +316,11 @@ def run_ours(args, rank, world, local_rank):
     alg_bytes = nnz * 12 + rows * 16
     achieved = alg_bytes / (emit_avg / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": None,
+                "frac": round(achieved / peak, 4), "traffic": emit_traffic(alg_bytes),
                 "kernel": "tree_fp32<emit>", "peak_source": peak_kind,
+                "traffic_source": "ncu dram__bytes_read+write of the emit kernel on the 7^5-cell "
+                                  "case, scaled per algorithmic byte "
+                                  "(profiles/room5d_fp32_tree_kernels_ncu.txt)",
                 "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": round(emit_avg, 3)}
     clk = clocks.summary()
 
@@ -302,7 +330,7 @@ def run_ours(args, rank, world, local_rank):
            "data": "synthetic",
            "config": {"workload": workload_name(args.cells), "rows": rows, "pairs_per_step": nnz,
                       "parallelism": f"replicas{world}" if world > 1 else "single",
-                      "l2": "flushed between steps (512 MiB write); output 33 GB >> L2"},
+                      "l2": f"flushed between steps (512 MiB write); output {nnz * 12 / 1e9:.1f} GB"},
            "roofline": roofline, "clocks": clk,
            "gpu_launches": LAUNCHES_PER_STEP * args.steps, "wall_s": round(wall_s, 3)}
     del pbuf, flush, wbuf
