@@ -6,7 +6,7 @@ holds none of the method's arithmetic (no images, no Gaussian factors, no
 bounds) and imports nothing else from the package, so tests can load it on a
 machine without a GPU.
 
-The shapes follow the paper's case studies (Sec. 6): the 2-D robot, the 3-D
+The shapes follow the paper's case studies (Sec. 8): the 2-D robot, the 3-D
 vehicle (here a unicycle), the 5-D room-temperature model and the 7-D
 building model, plus a seeded family of random linear systems.
 """
@@ -92,7 +92,7 @@ def input_points(lb, ub, eta):
 
 def robot_2d(cells_per_dim: int = 21) -> Problem:
     """2-D robot, x+ = x + u + w on [-10,10]^2, inputs {-1,0,1}^2, sigma 0.75,
-    dense (cutoff 0). Shape of the paper's 2-D robot case study (Sec. 6.1)."""
+    dense (cutoff 0). Shape of the paper's 2-D robot case study (Sec. 8.1)."""
     return Problem(
         name=f"robot2d-{cells_per_dim}x{cells_per_dim}",
         kind=AFFINE,
@@ -106,7 +106,7 @@ def robot_2d(cells_per_dim: int = 21) -> Problem:
 def unicycle_3d(nx: int = 51, ny: int = 51, nth: int = 25, cutoff: float = 1e-8) -> Problem:
     """3-D unicycle on [-5,5]^2 x [-pi,pi]: x+ = x + v cos th, y+ = y + v sin th,
     th+ = th + om; v in {0.25,...,1}, om in {-0.4,...,0.4}; sigma (0.3,0.3,0.2).
-    Shaped like the paper's 3-D vehicle (Sec. 6.2)."""
+    Shaped like the paper's 3-D vehicle (Sec. 8.2)."""
     v = np.array([0.25, 0.5, 0.75, 1.0])
     om = np.array([-0.4, -0.2, 0.0, 0.2, 0.4])
     V, O = np.meshgrid(v, om, indexing="ij")
@@ -121,7 +121,7 @@ def unicycle_3d(nx: int = 51, ny: int = 51, nth: int = 25, cutoff: float = 1e-8)
 
 def room_5d_matrices():
     """A = 0.85 I + 0.03 on ring neighbours (i+-1 mod 5); heater u1 drives
-    rooms 1,3,5 and u2 rooms 2,4 with gain 0.5; offset 1.8 (Sec. 6.3 shape)."""
+    rooms 1,3,5 and u2 rooms 2,4 with gain 0.5; offset 1.8 (Sec. 8.3 shape)."""
     n = 5
     A = 0.85 * np.eye(n)
     for i in range(n):
@@ -152,7 +152,7 @@ def building_7d(cells_per_dim: int = 6, cutoff: float = 1e-8) -> Problem:
     """7-D building model: A = 0.9 I + 0.02 chain couplings (no wrap),
     u1 heats room 1 and u2 room 2 with gain 0.1, inputs {0,1}^2, sigma 0.15,
     domain [-3,3]^7 (cell width 1 at 6 cells per dim). Shaped like the
-    paper's 7-D building automation benchmark (Sec. 6.4)."""
+    paper's 7-D building automation benchmark (Sec. 8.4)."""
     n = 7
     A = 0.9 * np.eye(n)
     for i in range(n - 1):
@@ -238,7 +238,7 @@ def sample_rows(prob: Problem, count: int, seed: int = 0, include_boundary: bool
 
 
 def bas_4d(eta_scale: float = 1.0) -> Problem:
-    """The paper's 4-D building automation system (Sec. 6.4): the printed A, B,
+    """The paper's 4-D building automation system (Sec. 8.4): the printed A, B,
     offset and diagonal covariance (variances, so sigma = sqrt), state
     [19,21]^2 x [30,36]^2 with eta (0.5,0.5,1,1) scaled by ``eta_scale``,
     input [17,20] with eta 1 (points 17,18,19,20)."""
