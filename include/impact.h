@@ -205,6 +205,98 @@ impact_status impact_emit(const impact_system *sys, const impact_grid *grid,
                           const impact_inputs *inputs, const double *sigma, double cutoff,
                           impact_precision precision, impact_csr *out, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Batches: several independent builds in one set of launches. Rows of the
+ * batch are the builds' rows concatenated in request order; build q owns the
+ * global rows [row_offsets[q], row_offsets[q+1]) of one impact_csr and its
+ * column ids are target cells of its own grid. Each kernel of the FP32 path
+ * runs once for the whole batch (persistent launch: warps take rows of any
+ * build from one counter). There is no counterpart in the paper, which builds
+ * one abstraction per call (Alg. 2); the per-row arithmetic is the same.
+ * ------------------------------------------------------------------------ */
+
+/* One build of a batch: the arguments of impact_build (host pointers). */
+typedef struct {
+    const impact_system *sys;
+    const impact_grid *grid;
+    const impact_inputs *inputs;
+    const double *sigma;
+    double cutoff;
+} impact_request;
+
+/*
+ * Launch shapes of the FP32-sound prefix-tree walk (impact_batch_tune picks
+ * them). Zero fields take the defaults: 4 warps per block, 10240 bytes of
+ * shared memory per warp for the node rings, count_k chosen per build.
+ *   count_warps, emit_warps              warps per block, 1..8
+ *   count_smem_target, emit_smem_target  bytes per warp, 2048..49152
+ *   count_k                              count pass: dimensions a lane walks
+ *                                        serially at the end (1, 2; 0 auto)
+ * Shapes change speed only: results are bitwise identical for every shape.
+ */
+typedef struct {
+    int count_warps;
+    int emit_warps;
+    int count_smem_target;
+    int emit_smem_target;
+    int count_k;
+} impact_tuning;
+
+/*
+ * impact_batch_plan -- host-only sizing of a batch of `count` (1..65536)
+ * builds. Writes row_offsets[count+1] (host array, may be NULL), the summed
+ * nnz bound and the workspace bytes of the batch. `tuning` may be NULL.
+ * Errors: IMPACT_ERR_ARG (the message names the failing request).
+ */
+impact_status impact_batch_plan(const impact_request *reqs, int count, impact_precision precision,
+                                const impact_tuning *tuning, int64_t *row_offsets,
+                                int64_t *nnz_upper_bound, int64_t *workspace_bytes);
+
+/* impact_count / impact_emit / impact_build for a batch: the same contracts
+ * with `out` covering every row of the batch (out->rows = total rows). */
+impact_status impact_batch_count(const impact_request *reqs, int count,
+                                 impact_precision precision, const impact_tuning *tuning,
+                                 impact_csr *out, void *stream);
+impact_status impact_batch_emit(const impact_request *reqs, int count,
+                                impact_precision precision, const impact_tuning *tuning,
+                                impact_csr *out, void *stream);
+impact_status impact_batch_build(const impact_request *reqs, int count,
+                                 impact_precision precision, const impact_tuning *tuning,
+                                 impact_csr *out, void *stream);
+
+/*
+ * CUDA graph of a batch's whole pipeline (count, scan, emit) into fixed
+ * caller-owned arrays: out->col/lo/up with capacity out->nnz and the row
+ * arrays, all DEVICE memory that must outlive the graph. The descriptors and
+ * tables are uploaded once here (into out->workspace when given, else into
+ * scratch the graph owns); each impact_graph_launch replays the build
+ * asynchronously on `stream`. After synchronizing that stream,
+ * impact_graph_result returns the launch's status and nnz (IMPACT_ERR_CAPACITY
+ * when the capacity was short: then col/lo/up are untouched). The request
+ * arguments are read during impact_graph_create only.
+ */
+typedef struct impact_graph impact_graph;
+impact_status impact_graph_create(const impact_request *reqs, int count,
+                                  impact_precision precision, const impact_tuning *tuning,
+                                  const impact_csr *out, void *stream, impact_graph **graph);
+impact_status impact_graph_launch(impact_graph *graph, void *stream);
+impact_status impact_graph_result(impact_graph *graph, int64_t *nnz);
+impact_status impact_graph_destroy(impact_graph *graph);
+
+/*
+ * impact_batch_tune -- the autotuner: times the FP32 count pass over warps
+ * per block {2,4,8} x shared-memory targets {6144,10240,16384} x count_k
+ * {1,2}, then the emit pass over warps x targets with the best count shape,
+ * each the best of `reps` runs, on this batch, and writes the fastest shape
+ * to *best and its count + emit milliseconds to *best_ms (may be NULL).
+ * `out` as for impact_batch_emit with the capacity of a previous count
+ * (col == NULL tunes the count pass only). Synchronizes `stream`; its own
+ * scratch is allocated and freed stream-ordered. FP32_SOUND only.
+ */
+impact_status impact_batch_tune(const impact_request *reqs, int count,
+                                impact_precision precision, impact_csr *out, int reps,
+                                void *stream, impact_tuning *best, double *best_ms);
+
 /* Release library-owned arrays of a result (no-op for caller-owned ones). */
 impact_status impact_free(impact_csr *out);
 

@@ -1,10 +1,10 @@
-// api.cu -- host planner and the C ABI entry points (include/impact.h).
-//
-// The planner validates the arguments, computes every per-build constant in
-// FP64 on the host (grid edges, per-term image tables, input offsets, window
-// margins, plateau and out-of-domain constants), packs them with the
-// descriptor into one device allocation, and runs the count -> scan -> emit
-// pipeline on the caller's stream.
+// api.cu -- the C ABI entry points (include/impact.h). A call works on a
+// batch of builds (a single build is a batch of one): the planner (plan.cu)
+// makes each build's descriptor and tables, this file lays them out with the
+// batch index, the scan scratch and the per-row records in one device
+// workspace, and runs the count -> scan -> emit pipeline on the caller's
+// stream, directly or as a captured CUDA graph. It also holds the launch-shape
+// autotuner of the FP32 walk.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -19,16 +19,24 @@
 #include "../../include/impact.h"
 #include "impact_desc.h"
 #include "kernels.h"
+#include "plan.h"
 
 namespace {
-
 thread_local std::string g_last_error;
+}  // namespace
 
+namespace impact {
 impact_status fail(impact_status s, const std::string &msg)
 {
     g_last_error = msg;
     return s;
 }
+void set_last_error(const std::string &msg) { g_last_error = msg; }
+}  // namespace impact
+
+using impact::fail;
+using impact::Plan;
+using impact::Tuning;
 
 #define CK(expr)                                                                              \
     do {                                                                                      \
@@ -39,499 +47,156 @@ impact_status fail(impact_status s, const std::string &msg)
         }                                                                                     \
     } while (0)
 
-double next_down(double x) { return nextafter(x, -INFINITY); }
-double next_up(double x) { return nextafter(x, INFINITY); }
+namespace {
 
-// Smallest float >= x (x finite, representable range).
-float f32_up(double x)
-{
-    float f = (float)x;
-    if ((double)f < x) f = nextafterf(f, INFINITY);
-    return f;
-}
+constexpr int kBatchMax = 1 << 16;   // builds per batch
 
-float f32_down(double x)
+uint64_t mix(uint64_t h, uint64_t v)
 {
-    float f = (float)x;
-    if ((double)f > x) f = nextafterf(f, -INFINITY);
-    return f;
-}
-
-// Range of cos / sin over [a, b]: endpoint values, widened to +-1 where an
-// extremum (k pi for cos, pi/2 + k pi for sin) lies inside. `slack` > 0 widens
-// the interval used for the extremum test and the endpoint values (outward).
-void trig_range(bool is_cos, double a, double b, double slack, double &lo, double &hi)
-{
-    double fa = is_cos ? cos(a) : sin(a);
-    double fb = is_cos ? cos(b) : sin(b);
-    lo = fa < fb ? fa : fb;
-    hi = fa < fb ? fb : fa;
-    double shift = is_cos ? 0.0 : M_PI_2;
-    double a2 = a - slack, b2 = b + slack;
-    for (long k = (long)ceil((a2 - shift) / M_PI); shift + (double)k * M_PI <= b2; ++k) {
-        if (k % 2 == 0) hi = 1.0; else lo = -1.0;
-    }
-    if (slack > 0.0) {
-        lo = std::max(-1.0, lo - 8.0 * 2.220446049250313e-16);
-        hi = std::min(1.0, hi + 8.0 * 2.220446049250313e-16);
-    }
-}
-
-// Fast division by N for x < 2^31: q = (umulhi(x, m) + x) >> s.
-void div_magic(uint32_t N, uint32_t &m, int &s)
-{
-    int l = 0;
-    while (((uint64_t)1 << l) < N) ++l;
-    m = (uint32_t)(((((uint64_t)1 << l) - N) << 32) / N + 1);
-    s = l;
-}
-
-float2 pair_of(double v)
-{
-    float hi = (float)v;
-    float lo = (float)(v - (double)hi);
-    return make_float2(hi, lo);
-}
-
-uint64_t fnv(uint64_t h, const void *p, size_t bytes)
-{
-    const unsigned char *c = (const unsigned char *)p;
-    for (size_t i = 0; i < bytes; ++i) h = (h ^ c[i]) * 1099511628211ull;
+    for (int i = 0; i < 8; ++i) h = (h ^ ((v >> (8 * i)) & 0xff)) * 1099511628211ull;
     return h;
 }
 
-struct Plan {
-    ImpactDesc desc;
-    std::vector<double> edges, term_rn, term_dn, term_up, off_rn, off_dn, off_up, uni_rn,
-        uni_sd, inputs;
-    // FP32-sound table path
-    std::vector<float2> ea, ta_lo, ta_hi, oa, ua, oma;
-    std::vector<float> mu_lo, mu_hi, mo, um, omm;
-    int64_t rows = 0;
-    int64_t nnz_bound = 0;
-    int table_need = 0;   // upper bound of the staged entries per row (-1: unknown)
-    uint64_t hash = 0;    // identifies the arguments (workspace reuse check)
-};
-
-// Offsets (in bytes, 256-aligned) of the arrays in the device blob.
-struct BlobLayout {
-    size_t desc, edges, term_rn, term_dn, term_up, off_rn, off_dn, off_up, uni_rn, uni_sd,
-        inputs, ea, ta_lo, ta_hi, oa, ua, oma, mu_lo, mu_hi, mo, um, omm, status, scan, rec,
-        total;
-};
-
-size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
-
-BlobLayout layout_of(const Plan &p)
+impact_status tuning_of(const impact_tuning *t, Tuning &T)
 {
-    BlobLayout L;
+    T = Tuning();
+    if (!t) return IMPACT_OK;
+    if (t->count_warps) T.count_warps = t->count_warps;
+    if (t->emit_warps) T.emit_warps = t->emit_warps;
+    if (t->count_smem_target) T.count_smem = t->count_smem_target;
+    if (t->emit_smem_target) T.emit_smem = t->emit_smem_target;
+    T.count_k = t->count_k;
+    if (T.count_warps < 1 || T.count_warps > IMPACT_TREE_WARPS_MAX || T.emit_warps < 1 ||
+        T.emit_warps > IMPACT_TREE_WARPS_MAX)
+        return fail(IMPACT_ERR_ARG, "tuning: warps per block must be in [1, 8]");
+    if (T.count_smem < 2048 || T.count_smem > 48 * 1024 || T.emit_smem < 2048 ||
+        T.emit_smem > 48 * 1024)
+        return fail(IMPACT_ERR_ARG, "tuning: shared-memory target must be in [2048, 49152]");
+    if (T.count_k < 0 || T.count_k > 2)
+        return fail(IMPACT_ERR_ARG, "tuning: count_k must be 0, 1 or 2");
+    return IMPACT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batches
+// ---------------------------------------------------------------------------
+
+struct Batch {
+    std::vector<Plan> plans;
+    std::vector<const double *> images;   // per build: device images (IMAGES kind)
+    std::vector<int64_t> row_begin;       // [count + 1] first global row of each build
+    std::vector<int64_t> item_begin;      // [count + 1] first (row, dim) item
+    int64_t rows = 0, items = 0, nnz_bound = 0;
+    int prec = 0;
+    int smem_count = 0, smem_emit = 0;    // largest per-warp bytes of the walk
+    Tuning tune;
+    uint64_t hash = 0;
+    int count() const { return (int)plans.size(); }
+};
+
+impact_status make_batch(const impact_request *reqs, int count, impact_precision precision,
+                         const impact_tuning *tuning, Batch &B)
+{
+    if (!reqs) return fail(IMPACT_ERR_ARG, "null request array");
+    if (count < 1 || count > kBatchMax)
+        return fail(IMPACT_ERR_ARG, "request count must be in [1, 65536]");
+    impact_status s = tuning_of(tuning, B.tune);
+    if (s != IMPACT_OK) return s;
+    B.plans.assign(count, Plan());
+    B.images.assign(count, nullptr);
+    B.row_begin.assign(count + 1, 0);
+    B.item_begin.assign(count + 1, 0);
+    B.prec = precision;
+    uint64_t h = 1469598103934665603ull;
+    for (int q = 0; q < count; ++q) {
+        const impact_request &r = reqs[q];
+        s = impact::make_plan(r.sys, r.grid, r.inputs, r.sigma, r.cutoff, precision, B.tune,
+                              B.plans[q]);
+        if (s != IMPACT_OK) {
+            if (count > 1) g_last_error = "request " + std::to_string(q) + ": " + g_last_error;
+            return s;
+        }
+        const Plan &P = B.plans[q];
+        B.images[q] = r.sys->dev_images;
+        B.row_begin[q + 1] = B.row_begin[q] + P.rows;
+        B.item_begin[q + 1] = B.item_begin[q] + P.rows * P.desc.n;
+        B.nnz_bound = (B.nnz_bound > INT64_MAX - P.nnz_bound) ? INT64_MAX
+                                                              : B.nnz_bound + P.nnz_bound;
+        B.smem_count = std::max(B.smem_count, P.desc.tree_smem_count);
+        B.smem_emit = std::max(B.smem_emit, P.desc.tree_smem_emit);
+        h = mix(h, P.hash);
+    }
+    B.rows = B.row_begin[count];
+    B.items = B.item_begin[count];
+    h = mix(h, (uint64_t)B.tune.count_warps | ((uint64_t)B.tune.emit_warps << 8) |
+                   ((uint64_t)B.tune.count_k << 16));
+    h = mix(h, (uint64_t)B.tune.count_smem | ((uint64_t)B.tune.emit_smem << 32));
+    B.hash = h;
+    return IMPACT_OK;
+}
+
+// Offsets (bytes, 256-aligned) of everything in the device workspace.
+struct BatchLayout {
+    size_t index = 0, row_begin = 0, item_begin = 0, descs = 0, recs = 0;
+    std::vector<size_t> tables;            // per build: its descriptor and tables
+    std::vector<impact::TableLayout> tl;
+    size_t upload_end = 0;                 // [0, upload_end) is copied from the host
+    size_t status = 0, counter = 0, scan = 0;
+    std::vector<size_t> rec;               // per build: FP32 per-row records
+    size_t total = 0;
+};
+
+BatchLayout batch_layout(const Batch &B)
+{
+    BatchLayout L;
     size_t o = 0;
     auto put = [&](size_t bytes) {
         size_t at = o;
-        o = align256(o + bytes);
+        o = impact::align256(o + bytes);
         return at;
     };
-    L.desc = put(sizeof(ImpactDesc));
-    L.edges = put(p.edges.size() * 8);
-    L.term_rn = put(p.term_rn.size() * 8);
-    L.term_dn = put(p.term_dn.size() * 8);
-    L.term_up = put(p.term_up.size() * 8);
-    L.off_rn = put(p.off_rn.size() * 8);
-    L.off_dn = put(p.off_dn.size() * 8);
-    L.off_up = put(p.off_up.size() * 8);
-    L.uni_rn = put(p.uni_rn.size() * 8);
-    L.uni_sd = put(p.uni_sd.size() * 8);
-    L.inputs = put(p.inputs.size() * 8);
-    L.ea = put(p.ea.size() * 8);
-    L.ta_lo = put(p.ta_lo.size() * 8);
-    L.ta_hi = put(p.ta_hi.size() * 8);
-    L.oa = put(p.oa.size() * 8);
-    L.ua = put(p.ua.size() * 8);
-    L.oma = put(p.oma.size() * 8);
-    L.mu_lo = put(p.mu_lo.size() * 4);
-    L.mu_hi = put(p.mu_hi.size() * 4);
-    L.mo = put(p.mo.size() * 4);
-    L.um = put(p.um.size() * 4);
-    L.omm = put(p.omm.size() * 4);
+    const int count = B.count();
+    L.index = put(sizeof(BatchIndex));
+    L.row_begin = put((size_t)(count + 1) * 8);
+    L.item_begin = put((size_t)(count + 1) * 8);
+    L.descs = put((size_t)count * 8);
+    L.recs = put((size_t)count * 8);
+    L.tables.resize(count);
+    L.tl.resize(count);
+    for (int q = 0; q < count; ++q) {
+        L.tl[q] = impact::table_layout(B.plans[q]);
+        L.tables[q] = put(L.tl[q].total);
+    }
+    L.upload_end = o;
     L.status = put(64);
-    L.scan = put((size_t)impact::scan_scratch_elems(p.rows) * 8);
-    L.rec = put(p.desc.prec == PREC_FP32_SOUND ? (size_t)p.rows * p.desc.rec_stride : 0);
+    L.counter = put(64);
+    L.scan = put((size_t)impact::scan_scratch_elems(B.rows) * 8);
+    L.rec.resize(count);
+    for (int q = 0; q < count; ++q) {
+        const Plan &P = B.plans[q];
+        L.rec[q] = put(B.prec == PREC_FP32_SOUND ? (size_t)P.rows * P.desc.rec_stride : 0);
+    }
     L.total = o;
     return L;
 }
 
-// The uploaded part of the workspace (descriptor and tables) ends here.
-size_t upload_bytes(const BlobLayout &L) { return L.status; }
-
-// z with P(Z >= z) = erfc(z/sqrt2)/2 <= p for a standard normal Z (bisection).
-double normal_quantile_upper(double p)
-{
-    double lo = 0.0, hi = 40.0;
-    for (int it = 0; it < 200; ++it) {
-        double mid = 0.5 * (lo + hi);
-        if (0.5 * erfc(mid * M_SQRT1_2) <= p) hi = mid; else lo = mid;
-    }
-    return hi;
-}
-
-impact_status make_plan(const impact_system *sys, const impact_grid *grid,
-                        const impact_inputs *inputs, const double *sigma, double cutoff,
-                        impact_precision precision, Plan &P)
-{
-    if (!sys || !grid || !inputs || !sigma) return fail(IMPACT_ERR_ARG, "null argument");
-    const int n = grid->n;
-    if (n < 1 || n > IMPACT_MAX_DIM) return fail(IMPACT_ERR_ARG, "grid.n must be in [1, 8]");
-    if (sys->n != n) return fail(IMPACT_ERR_ARG, "system.n != grid.n");
-    if (!grid->lo || !grid->hi || !grid->cells) return fail(IMPACT_ERR_ARG, "null grid array");
-    if (sys->kind < IMPACT_AFFINE || sys->kind > IMPACT_IMAGES)
-        return fail(IMPACT_ERR_ARG, "unknown system kind");
-    if (precision != IMPACT_FP64_PLAIN && precision != IMPACT_FP32_SOUND)
-        return fail(IMPACT_ERR_ARG, "unknown precision");
-    if (!(cutoff >= 0.0 && cutoff < 1.0)) return fail(IMPACT_ERR_ARG, "cutoff must be in [0, 1)");
-    if (sys->params) return fail(IMPACT_ERR_ARG, "system.params is reserved and must be NULL");
-    const int m = inputs->m;
-    if (inputs->count < 1) return fail(IMPACT_ERR_ARG, "inputs.count must be >= 1");
-    if (m < 0 || m > IMPACT_MAX_M) return fail(IMPACT_ERR_ARG, "inputs.m must be in [0, 8]");
-    if (m > 0 && !inputs->points) return fail(IMPACT_ERR_ARG, "null input points");
-    if (sys->kind == IMPACT_AFFINE) {
-        if (!sys->A) return fail(IMPACT_ERR_ARG, "affine system needs A");
-        if (sys->m != m) return fail(IMPACT_ERR_ARG, "system.m != inputs.m");
-        if (m > 0 && !sys->B) return fail(IMPACT_ERR_ARG, "affine system with inputs needs B");
-    } else if (sys->kind == IMPACT_UNICYCLE) {
-        if (n != 3 || m != 2) return fail(IMPACT_ERR_ARG, "unicycle needs n = 3, m = 2");
-    } else {
-        if (!sys->dev_images) return fail(IMPACT_ERR_ARG, "images system needs dev_images");
-    }
-    int64_t cells = 1;
-    for (int d = 0; d < n; ++d) {
-        if (grid->cells[d] < 1) return fail(IMPACT_ERR_ARG, "cells must be >= 1");
-        if (!(grid->lo[d] < grid->hi[d]) || !isfinite(grid->lo[d]) || !isfinite(grid->hi[d]))
-            return fail(IMPACT_ERR_ARG, "grid needs finite lo < hi");
-        if (!(sigma[d] > 0.0) || !isfinite(sigma[d]))
-            return fail(IMPACT_ERR_ARG, "sigma must be finite and > 0");
-        cells *= grid->cells[d];
-        if (cells >= ((int64_t)1 << 31)) return fail(IMPACT_ERR_ARG, "more than 2^31-1 cells");
-    }
-    const int n_inputs = inputs->count;
-    const int64_t rows = cells * n_inputs;
-
-    ImpactDesc &D = P.desc;
-    memset(&D, 0, sizeof(D));
-    D.n = n;
-    D.m = m;
-    D.kind = sys->kind;
-    D.prec = precision;
-    D.n_inputs = n_inputs;
-    D.n_in_split_min = 24;
-    D.rows = rows;
-    D.cells = cells;
-    D.cutoff = cutoff;
-    D.cutoff32 = f32_up(cutoff);
-    D.table_max = IMPACT_TABLE_MAX;
-    P.rows = rows;
-
-    // grid edges (E_i = lo + i*h, E_N = hi), per-dimension constants
-    int nmax = 0;
-    int64_t stride = 1;
-    for (int d = n - 1; d >= 0; --d) {
-        D.dim[d].stride = (int)stride;
-        stride *= grid->cells[d];
-    }
-    const double zc = cutoff > 0.0 ? normal_quantile_upper(0.5 * cutoff) : INFINITY;
-    for (int d = 0; d < n; ++d) {
-        ImpactDim &g = D.dim[d];
-        const int N = grid->cells[d];
-        nmax = std::max(nmax, N);
-        g.lo = grid->lo[d];
-        g.hi = grid->hi[d];
-        g.N = N;
-        g.h = (g.hi - g.lo) / (double)N;
-        g.inv_h = 1.0 / g.h;
-        g.sigma = sigma[d];
-        g.inv_s = 1.0 / (sigma[d] * M_SQRT2);
-        g.kappa = g.h * g.inv_s;
-        g.kappa_hi = (float)g.kappa;
-        g.kappa_lo = (float)(g.kappa - (double)g.kappa_hi);
-        g.delta = isfinite(zc) ? sigma[d] * zc * (1.0 + 1e-9) : INFINITY;
-        g.edge_off = (int)P.edges.size();
-        double hmax = 0.0;
-        for (int i = 0; i <= N; ++i) {
-            double e = (i == N) ? g.hi : g.lo + (double)i * g.h;
-            P.edges.push_back(e);
-            if (i > 0) hmax = std::max(hmax, e - P.edges[P.edges.size() - 2]);
-        }
-        double mag = std::max(fabs(g.lo), fabs(g.hi));
-        double dev = ldexp(mag + fabs(g.hi - g.lo), -51) + fabs(g.hi - (g.lo + (double)N * g.h)) +
-                     ldexp(fabs(g.hi), -50);
-        g.edge_err = f32_up(dev * g.inv_s * (1.0 + 1e-9) + 1e-300);
-        double xp = hmax * g.inv_s * 0.5 * (1.0 + 1e-12);
-        g.plateau_hi = std::min(1.0f, f32_up(erf(xp) + 4e-16));
-        double xq = (g.hi - g.lo) * g.inv_s * 0.5 * (1.0 + 1e-12);
-        g.qmin_lo = f32_down(erfc(xq) * (1.0 - 1e-13));
-    }
-    D.n_max = nmax;
-
-    // inputs
-    for (int j = 0; j < n_inputs; ++j)
-        for (int k = 0; k < m; ++k) P.inputs.push_back(inputs->points[(int64_t)j * m + k]);
-
-    // per-dimension window width bound -> nnz bound and staging need
-    std::vector<double> width(n, 0.0);
-    if (sys->kind == IMPACT_AFFINE) {
-        const double *A = sys->A;
-        // image terms: per (d, k, cell i of dim k) the range of A_dk * x_k
-        P.term_rn.assign((size_t)n * n * nmax * 2, 0.0);
-        P.term_dn.assign((size_t)n * n * nmax, 0.0);
-        P.term_up.assign((size_t)n * n * nmax, 0.0);
-        for (int d = 0; d < n; ++d) {
-            for (int k = 0; k < n; ++k) {
-                const double a = A[d * n + k];
-                if (!isfinite(a)) return fail(IMPACT_ERR_ARG, "A must be finite");
-                const ImpactDim &gk = D.dim[k];
-                for (int i = 0; i < gk.N; ++i) {
-                    double x0 = P.edges[gk.edge_off + i], x1 = P.edges[gk.edge_off + i + 1];
-                    double p0 = a * x0, p1 = a * x1;
-                    size_t t = ((size_t)(d * n + k) * nmax + i);
-                    P.term_rn[2 * t] = p0 < p1 ? p0 : p1;
-                    P.term_rn[2 * t + 1] = p0 < p1 ? p1 : p0;
-                    // the rounded products are within half an ulp of the exact ones
-                    P.term_dn[t] = std::min(next_down(p0), next_down(p1));
-                    P.term_up[t] = std::max(next_up(p0), next_up(p1));
-                }
-                width[d] += fabs(a) * gk.h;
-            }
-        }
-        // input offsets c_d + sum_k B_dk u_k, in the definition's order, and a bracket
-        P.off_rn.assign((size_t)n_inputs * n, 0.0);
-        P.off_dn.assign((size_t)n_inputs * n, 0.0);
-        P.off_up.assign((size_t)n_inputs * n, 0.0);
-        for (int j = 0; j < n_inputs; ++j) {
-            const double *u = inputs->points ? inputs->points + (int64_t)j * m : nullptr;
-            for (int d = 0; d < n; ++d) {
-                double off = sys->c ? sys->c[d] : 0.0;
-                double mag = fabs(off);
-                for (int k = 0; k < m; ++k) {
-                    double t = sys->B[d * m + k] * u[k];
-                    off += t;
-                    mag += fabs(t);
-                }
-                if (!isfinite(off)) return fail(IMPACT_ERR_ARG, "B, c and inputs must be finite");
-                double err = ldexp(mag, -50) * (double)(m + 2) + 1e-300;
-                P.off_rn[(size_t)j * n + d] = off;
-                P.off_dn[(size_t)j * n + d] = next_down(off - err);
-                P.off_up[(size_t)j * n + d] = next_up(off + err);
-            }
-        }
-    } else if (sys->kind == IMPACT_UNICYCLE) {
-        const ImpactDim &gt = D.dim[2];
-        P.uni_rn.assign((size_t)gt.N * n_inputs * 4, 0.0);
-        P.uni_sd.assign((size_t)gt.N * n_inputs * 4, 0.0);
-        double vmax = 0.0;
-        for (int i = 0; i < gt.N; ++i) {
-            double a = P.edges[gt.edge_off + i], b = P.edges[gt.edge_off + i + 1];
-            double cl, ch, sl, sh, cls, chs, sls, shs;
-            trig_range(true, a, b, 0.0, cl, ch);
-            trig_range(false, a, b, 0.0, sl, sh);
-            trig_range(true, a, b, 1e-12, cls, chs);
-            trig_range(false, a, b, 1e-12, sls, shs);
-            for (int j = 0; j < n_inputs; ++j) {
-                double v = inputs->points[(int64_t)j * m + 0];
-                vmax = std::max(vmax, fabs(v));
-                double *r = &P.uni_rn[((size_t)i * n_inputs + j) * 4];
-                double *s = &P.uni_sd[((size_t)i * n_inputs + j) * 4];
-                double c1 = v * cl, c2 = v * ch, s1 = v * sl, s2 = v * sh;
-                r[0] = c1 < c2 ? c1 : c2;
-                r[1] = c1 < c2 ? c2 : c1;
-                r[2] = s1 < s2 ? s1 : s2;
-                r[3] = s1 < s2 ? s2 : s1;
-                double c3 = v * cls, c4 = v * chs, s3 = v * sls, s4 = v * shs;
-                s[0] = next_down(std::min(c3, c4));
-                s[1] = next_up(std::max(c3, c4));
-                s[2] = next_down(std::min(s3, s4));
-                s[3] = next_up(std::max(s3, s4));
-            }
-        }
-        width[0] = D.dim[0].h + 2.0 * vmax;
-        width[1] = D.dim[1].h + 2.0 * vmax;
-        width[2] = D.dim[2].h;
-    }
-    // window widths: image width + 2 delta, plus the 2-cell slack and rounding
-    int64_t box = 1;
-    int need = 0;
-    int tsum = 0;
-    for (int d = 0; d < n; ++d) {
-        ImpactDim &g = D.dim[d];
-        int64_t w = g.N;
-        if (sys->kind != IMPACT_IMAGES && isfinite(g.delta)) {
-            double cw = ceil((width[d] + 2.0 * g.delta) * g.inv_h) + 4.0;
-            if (cw < (double)g.N) w = (int64_t)cw;
-        }
-        box *= w;
-        need += (int)w;
-        g.wcap = (int)std::min<int64_t>(w, IMPACT_WINDOW_MAX);
-        g.delta_cells = isfinite(g.delta) ? (float)(g.delta * g.inv_h) : INFINITY;
-        div_magic((uint32_t)g.N, g.div_m, g.div_s);
-        if (precision == IMPACT_FP32_SOUND && sys->kind != IMPACT_IMAGES && w > IMPACT_WINDOW_MAX)
-            return fail(IMPACT_ERR_ARG,
-                        "dimension " + std::to_string(d) + " needs a window of " +
-                            std::to_string(w) + " cells (FP32 limit " +
-                            std::to_string(IMPACT_WINDOW_MAX) +
-                            "): raise the cutoff or use fewer cells");
-        tsum += g.wcap;
-    }
-    div_magic((uint32_t)n_inputs, D.inp_div_m, D.inp_div_s);
-    P.table_need = (sys->kind == IMPACT_IMAGES) ? -1 : need;
-    if (box > cells) box = cells;
-    P.nnz_bound = box * rows;
-    if (precision == IMPACT_FP64_PLAIN && P.table_need > IMPACT_TABLE_MAX)
-        return fail(IMPACT_ERR_ARG,
-                    "the per-row windows need " + std::to_string(P.table_need) +
-                        " staged factors (limit " + std::to_string(IMPACT_TABLE_MAX) +
-                        "): raise the cutoff or use fewer cells");
-    if (precision == IMPACT_FP32_SOUND) {
-        if (tsum > IMPACT_TSUM_MAX)
-            return fail(IMPACT_ERR_ARG,
-                        "the per-row windows need " + std::to_string(tsum) +
-                            " staged factors (FP32 limit " + std::to_string(IMPACT_TSUM_MAX) +
-                            "): raise the cutoff or use fewer cells");
-        D.tsum_cap = tsum;
-        D.rec_stride = (int)impact::record_stride(n, tsum);
-        int ro = 0;
-        for (int d = 0; d < n; ++d) {
-            D.dim[d].rec_off = ro;
-            ro += D.dim[d].wcap;
-        }
-        // prefix-tree walk. Each lane finally enumerates the last K dimensions
-        // of one parent: count pass K = 2 when the last window is narrow (a
-        // lane's serial work stays short), else 1; emit pass K = 1 (pairs are
-        // spread over the lanes for coalesced stores). Levels 0..Lp (Lp =
-        // n - 1 - K) keep a ring of nodes each, a power of two: level 0 holds
-        // the root's children, the deepest level room for a full batch plus
-        // one parent's children; rings shrink from the largest while a warp's
-        // shared memory exceeds the target.
-        D.tree_k = (n >= 3 && D.dim[n - 1].wcap <= 16) ? 2 : 1;
-        int worst = 0;
-        for (int pass = 0; pass < 2; ++pass) {
-            const int K = pass == 0 ? D.tree_k : 1;
-            const int Lp = n - 1 - K;
-            int lg[IMPACT_MAX_DIM] = {0}, lmin[IMPACT_MAX_DIM] = {0};
-            auto log2_ceil = [](int v) {
-                int l = 0;
-                while ((1 << l) < v) ++l;
-                return l;
-            };
-            for (int k = 0; k <= Lp; ++k) {
-                const int w = D.dim[k].wcap;
-                const int need = (k == Lp) ? 32 + w : w;
-                lmin[k] = log2_ceil(need);
-                lg[k] = (k == 0 && k < Lp) ? lmin[k] : std::max(lmin[k], log2_ceil(k == Lp ? 128 : 64));
-            }
-            auto bytes = [&]() {
-                int pool = 0;
-                for (int k = 0; k <= Lp; ++k) pool += 1 << lg[k];
-                return impact::tree_smem_bytes(tsum, std::max(pool, 1), pass == 1);
-            };
-            while (bytes() > IMPACT_TREE_SMEM_TARGET) {
-                int big = -1;
-                for (int k = 0; k <= Lp; ++k)
-                    if (lg[k] > lmin[k] && (big < 0 || lg[k] > lg[big])) big = k;
-                if (big < 0) break;
-                --lg[big];
-            }
-            int pool = 0;
-            for (int k = 0; k < IMPACT_MAX_DIM; ++k) {
-                D.ring_log2[pass][k] = k <= Lp ? lg[k] : 0;
-                D.ring_off[pass][k] = pool;
-                if (k <= Lp) pool += 1 << lg[k];
-            }
-            D.pool_cap[pass] = std::max(pool, 1);
-            worst = std::max(worst, bytes());
-        }
-        D.tree_smem_count = impact::tree_smem_bytes(tsum, D.pool_cap[0], false);
-        D.tree_smem_emit = impact::tree_smem_bytes(tsum, D.pool_cap[1], true);
-        if ((int64_t)worst * impact::tree_warps_per_block() > 200 * 1024)
-            return fail(IMPACT_ERR_ARG, "the per-row windows are too wide for the FP32 tree walk");
-        // tables in erf units (x / (sigma sqrt2)) as FP32 pairs, and in cells
-        for (int d = 0; d < n; ++d) {
-            const ImpactDim &g = D.dim[d];
-            for (int i = 0; i <= g.N; ++i) P.ea.push_back(pair_of(P.edges[g.edge_off + i] * g.inv_s));
-        }
-        if (sys->kind == IMPACT_AFFINE) {
-            P.ta_lo.resize((size_t)n * n * nmax);
-            P.ta_hi.resize((size_t)n * n * nmax);
-            P.mu_lo.resize((size_t)n * n * nmax);
-            P.mu_hi.resize((size_t)n * n * nmax);
-            for (int d = 0; d < n; ++d) {
-                const ImpactDim &g = D.dim[d];
-                for (int k = 0; k < n; ++k)
-                    for (int i = 0; i < D.dim[k].N; ++i) {
-                        size_t t = (size_t)(d * n + k) * nmax + i;
-                        P.ta_lo[t] = pair_of(P.term_rn[2 * t] * g.inv_s);
-                        P.ta_hi[t] = pair_of(P.term_rn[2 * t + 1] * g.inv_s);
-                        P.mu_lo[t] = (float)(P.term_rn[2 * t] * g.inv_h);
-                        P.mu_hi[t] = (float)(P.term_rn[2 * t + 1] * g.inv_h);
-                    }
-            }
-            P.oa.resize((size_t)n_inputs * n);
-            P.mo.resize((size_t)n_inputs * n);
-            for (int j = 0; j < n_inputs; ++j)
-                for (int d = 0; d < n; ++d) {
-                    const ImpactDim &g = D.dim[d];
-                    double off = P.off_rn[(size_t)j * n + d];
-                    P.oa[(size_t)j * n + d] = pair_of(off * g.inv_s);
-                    P.mo[(size_t)j * n + d] = (float)((off - g.lo) * g.inv_h);
-                }
-        } else if (sys->kind == IMPACT_UNICYCLE) {
-            const ImpactDim &gx = D.dim[0], &gy = D.dim[1], &gt = D.dim[2];
-            size_t cnt = (size_t)gt.N * n_inputs * 4;
-            P.ua.resize(cnt);
-            P.um.resize(cnt);
-            for (size_t t = 0; t < cnt; ++t) {
-                const ImpactDim &g = (t % 4) < 2 ? gx : gy;
-                P.ua[t] = pair_of(P.uni_sd[t] * g.inv_s);
-                P.um[t] = (float)(P.uni_sd[t] * g.inv_h);
-            }
-            for (int j = 0; j < n_inputs; ++j) {
-                double om = inputs->points[(int64_t)j * m + 1];
-                P.oma.push_back(pair_of(om * gt.inv_s));
-                P.omm.push_back((float)(om * gt.inv_h));
-            }
-        }
-    }
-    // identity of the arguments, for reusing a caller's workspace
-    uint64_t h = 1469598103934665603ull;
-    int hdr[5] = {sys->kind, n, m, (int)precision, n_inputs};
-    h = fnv(h, hdr, sizeof(hdr));
-    h = fnv(h, &cutoff, 8);
-    h = fnv(h, grid->lo, 8 * n);
-    h = fnv(h, grid->hi, 8 * n);
-    h = fnv(h, grid->cells, 4 * n);
-    h = fnv(h, sigma, 8 * n);
-    if (sys->kind == IMPACT_AFFINE) {
-        h = fnv(h, sys->A, 8 * n * n);
-        if (m > 0) h = fnv(h, sys->B, 8 * n * m);
-        if (sys->c) h = fnv(h, sys->c, 8 * n);
-    }
-    if (m > 0) h = fnv(h, inputs->points, 8 * (size_t)n_inputs * m);
-    h = fnv(h, &sys->dev_images, sizeof(void *));
-    P.hash = h;
-    return IMPACT_OK;
-}
-
-// The device workspace of one build: descriptor and tables (uploaded), the
-// status word, the scan partial sums and (FP32) the per-row records.
+// The device workspace of one call.
 struct Work {
     unsigned char *base = nullptr;
-    BlobLayout L;
+    BatchLayout L;
     bool owned = false;
-    ImpactDesc *desc() const { return (ImpactDesc *)(base + L.desc); }
+    const BatchIndex *index() const { return (const BatchIndex *)(base + L.index); }
     uint32_t *status() const { return (uint32_t *)(base + L.status); }
+    unsigned long long *counter() const { return (unsigned long long *)(base + L.counter); }
     int64_t *scan() const { return (int64_t *)(base + L.scan); }
-    unsigned char *rec() const { return base + L.rec; }
+    const ImpactDesc *desc(int q) const
+    {
+        return (const ImpactDesc *)(base + L.tables[q] + L.tl[q].desc);
+    }
 };
 
 std::mutex g_ws_mu;
-std::unordered_map<const void *, uint64_t> g_ws_tag;   // caller workspace -> filled for plan
+std::unordered_map<const void *, uint64_t> g_ws_tag;   // caller workspace -> batch it holds
 
 void ws_tag(const void *ws, uint64_t h)
 {
@@ -546,9 +211,9 @@ bool ws_has(const void *ws, uint64_t h)
     return it != g_ws_tag.end() && it->second == h;
 }
 
-impact_status get_work(const Plan &P, const impact_csr *out, cudaStream_t st, Work &W)
+impact_status get_work(const Batch &B, const impact_csr *out, cudaStream_t st, Work &W)
 {
-    W.L = layout_of(P);
+    W.L = batch_layout(B);
     if (out && out->workspace) {
         if (out->workspace_bytes < (int64_t)W.L.total)
             return fail(IMPACT_ERR_ARG, "workspace too small: " +
@@ -572,61 +237,33 @@ impact_status release(Work &W, cudaStream_t st)
     return IMPACT_OK;
 }
 
-impact_status upload(Plan &P, Work &W, cudaStream_t st, const double *dev_images)
+// Copies the batch index, the descriptors and the tables into the workspace.
+impact_status upload(const Batch &B, Work &W, cudaStream_t st)
 {
-    const BlobLayout &L = W.L;
-    std::vector<unsigned char> host(upload_bytes(L), 0);
-    ImpactDesc D = P.desc;
-    auto dp = [&](size_t off, size_t count) -> const void * {
-        return count == 0 ? nullptr : (const void *)(W.base + off);
-    };
-    D.edges = (const double *)dp(L.edges, P.edges.size());
-    D.term_rn = (const double *)dp(L.term_rn, P.term_rn.size());
-    D.term_dn = (const double *)dp(L.term_dn, P.term_dn.size());
-    D.term_up = (const double *)dp(L.term_up, P.term_up.size());
-    D.off_rn = (const double *)dp(L.off_rn, P.off_rn.size());
-    D.off_dn = (const double *)dp(L.off_dn, P.off_dn.size());
-    D.off_up = (const double *)dp(L.off_up, P.off_up.size());
-    D.uni_rn = (const double *)dp(L.uni_rn, P.uni_rn.size());
-    D.uni_sd = (const double *)dp(L.uni_sd, P.uni_sd.size());
-    D.inputs = (const double *)dp(L.inputs, P.inputs.size());
-    D.ea = (const float2 *)dp(L.ea, P.ea.size());
-    D.ta_lo = (const float2 *)dp(L.ta_lo, P.ta_lo.size());
-    D.ta_hi = (const float2 *)dp(L.ta_hi, P.ta_hi.size());
-    D.oa = (const float2 *)dp(L.oa, P.oa.size());
-    D.ua = (const float2 *)dp(L.ua, P.ua.size());
-    D.oma = (const float2 *)dp(L.oma, P.oma.size());
-    D.mu_lo = (const float *)dp(L.mu_lo, P.mu_lo.size());
-    D.mu_hi = (const float *)dp(L.mu_hi, P.mu_hi.size());
-    D.mo = (const float *)dp(L.mo, P.mo.size());
-    D.um = (const float *)dp(L.um, P.um.size());
-    D.omm = (const float *)dp(L.omm, P.omm.size());
-    D.images = dev_images;
-    memcpy(host.data() + L.desc, &D, sizeof(D));
-    auto put = [&](size_t off, const void *src, size_t bytes) {
-        if (bytes) memcpy(host.data() + off, src, bytes);
-    };
-    put(L.edges, P.edges.data(), P.edges.size() * 8);
-    put(L.term_rn, P.term_rn.data(), P.term_rn.size() * 8);
-    put(L.term_dn, P.term_dn.data(), P.term_dn.size() * 8);
-    put(L.term_up, P.term_up.data(), P.term_up.size() * 8);
-    put(L.off_rn, P.off_rn.data(), P.off_rn.size() * 8);
-    put(L.off_dn, P.off_dn.data(), P.off_dn.size() * 8);
-    put(L.off_up, P.off_up.data(), P.off_up.size() * 8);
-    put(L.uni_rn, P.uni_rn.data(), P.uni_rn.size() * 8);
-    put(L.uni_sd, P.uni_sd.data(), P.uni_sd.size() * 8);
-    put(L.inputs, P.inputs.data(), P.inputs.size() * 8);
-    put(L.ea, P.ea.data(), P.ea.size() * 8);
-    put(L.ta_lo, P.ta_lo.data(), P.ta_lo.size() * 8);
-    put(L.ta_hi, P.ta_hi.data(), P.ta_hi.size() * 8);
-    put(L.oa, P.oa.data(), P.oa.size() * 8);
-    put(L.ua, P.ua.data(), P.ua.size() * 8);
-    put(L.oma, P.oma.data(), P.oma.size() * 8);
-    put(L.mu_lo, P.mu_lo.data(), P.mu_lo.size() * 4);
-    put(L.mu_hi, P.mu_hi.data(), P.mu_hi.size() * 4);
-    put(L.mo, P.mo.data(), P.mo.size() * 4);
-    put(L.um, P.um.data(), P.um.size() * 4);
-    put(L.omm, P.omm.data(), P.omm.size() * 4);
+    const BatchLayout &L = W.L;
+    const int count = B.count();
+    std::vector<unsigned char> host(L.upload_end, 0);
+    BatchIndex bi;
+    memset(&bi, 0, sizeof(bi));
+    bi.count = count;
+    bi.rows = B.rows;
+    bi.items = B.items;
+    bi.row_begin = (const int64_t *)(W.base + L.row_begin);
+    bi.item_begin = (const int64_t *)(W.base + L.item_begin);
+    bi.desc = (const ImpactDesc *const *)(W.base + L.descs);
+    bi.rec = (unsigned char *const *)(W.base + L.recs);
+    bi.next_row = W.counter();
+    memcpy(host.data() + L.index, &bi, sizeof(bi));
+    memcpy(host.data() + L.row_begin, B.row_begin.data(), (size_t)(count + 1) * 8);
+    memcpy(host.data() + L.item_begin, B.item_begin.data(), (size_t)(count + 1) * 8);
+    for (int q = 0; q < count; ++q) {
+        const ImpactDesc *d = W.desc(q);
+        unsigned char *r = B.prec == PREC_FP32_SOUND ? W.base + L.rec[q] : nullptr;
+        memcpy(host.data() + L.descs + 8 * (size_t)q, &d, 8);
+        memcpy(host.data() + L.recs + 8 * (size_t)q, &r, 8);
+        impact::pack_tables(B.plans[q], host.data() + L.tables[q], W.base + L.tables[q],
+                            B.images[q]);
+    }
     // pageable source: returns once the bytes are staged, so `host` may go
     CK(cudaMemcpyAsync(W.base, host.data(), host.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(W.status(), 0, 64, st));
@@ -657,42 +294,6 @@ bool is_device_ptr(const void *p)
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-// count pass + scan: row_ptr, sink_lo, sink_up, trunc, row_flags
-impact_status run_count(const Plan &P, const Work &W, impact_csr *out, cudaStream_t st)
-{
-    impact::RowOutputs o{out->row_ptr, nullptr, nullptr, nullptr, out->sink_lo, out->sink_up,
-                         out->trunc, out->row_flags, W.status(), -1, P.rows};
-    if (P.desc.prec == PREC_FP32_SOUND) {
-        CK(impact::launch_setup_fp32(W.desc(), P.desc.n, 0, P.rows, W.rec(), W.status(), st));
-        CK(impact::launch_prep_fp32(W.desc(), P.desc.n, 0, P.rows, W.rec(), out->sink_lo,
-                                    out->sink_up, out->trunc, st));
-        CK(impact::launch_tree_fp32(W.desc(), P.desc.tree_smem_count, false, 0, P.rows, W.rec(), o, st));
-    } else {
-        CK(impact::launch_rows(W.desc(), P.desc.prec, false, 0, P.rows, o, st));
-    }
-    CK(impact::launch_scan(out->row_ptr, P.rows, W.scan(), st));
-    return IMPACT_OK;
-}
-
-// emit pass; `tables_ready`: the FP32 records in W are valid for P
-impact_status run_emit(const Plan &P, const Work &W, impact_csr *out, int64_t capacity,
-                       bool tables_ready, cudaStream_t st)
-{
-    impact::RowOutputs o{out->row_ptr, out->col, out->lo, out->up, nullptr, nullptr, nullptr,
-                         nullptr, W.status(), capacity, P.rows};
-    if (P.desc.prec == PREC_FP32_SOUND) {
-        if (!tables_ready) {   // rebuild the records; the row outputs stay as counted
-            CK(impact::launch_setup_fp32(W.desc(), P.desc.n, 0, P.rows, W.rec(), W.status(), st));
-            CK(impact::launch_prep_fp32(W.desc(), P.desc.n, 0, P.rows, W.rec(), nullptr, nullptr,
-                                        nullptr, st));
-        }
-        CK(impact::launch_tree_fp32(W.desc(), P.desc.tree_smem_emit, true, 0, P.rows, W.rec(), o, st));
-    } else {
-        CK(impact::launch_rows(W.desc(), P.desc.prec, true, 0, P.rows, o, st));
-    }
-    return IMPACT_OK;
-}
-
 impact_status check_row_arrays(const impact_csr *out)
 {
     if (!is_device_ptr(out->row_ptr) || !is_device_ptr(out->sink_lo) ||
@@ -715,11 +316,210 @@ impact_status status_result(uint32_t status)
     return IMPACT_OK;
 }
 
+// Row outputs of build q with row-indexed arrays shifted to its first row
+// (the FP64 kernels index rows from 0 within a build).
+impact::RowOutputs shifted(const impact::RowOutputs &o, int64_t rb, int64_t rows_total)
+{
+    impact::RowOutputs s = o;
+    s.row_ptr = o.row_ptr + rb;
+    if (o.sink_lo) s.sink_lo = o.sink_lo + rb;
+    if (o.sink_up) s.sink_up = o.sink_up + rb;
+    if (o.trunc) s.trunc = o.trunc + rb;
+    if (o.flags) s.flags = o.flags + rb;
+    s.total_at = rows_total - rb;
+    return s;
+}
+
+// count pass + scan: row_ptr, sink_lo, sink_up, trunc, row_flags
+impact_status run_count(const Batch &B, const Work &W, const impact_csr *out, cudaStream_t st)
+{
+    CK(cudaMemsetAsync(W.status(), 0, 64, st));
+    impact::RowOutputs o{out->row_ptr, nullptr, nullptr, nullptr, out->sink_lo, out->sink_up,
+                         out->trunc, out->row_flags, W.status(), -1, B.rows};
+    if (B.prec == PREC_FP32_SOUND) {
+        CK(cudaMemsetAsync(W.counter(), 0, 16, st));
+        CK(impact::launch_setup_fp32(W.index(), B.items, W.status(), st));
+        CK(impact::launch_prep_fp32(W.index(), B.items, out->sink_lo, out->sink_up, out->trunc,
+                                    st));
+        CK(impact::launch_tree_fp32(W.index(), B.rows, B.smem_count, B.tune.count_warps, false, o,
+                                    st));
+    } else {
+        for (int q = 0; q < B.count(); ++q)
+            CK(impact::launch_rows(W.desc(q), B.prec, false, 0, B.plans[q].rows,
+                                   shifted(o, B.row_begin[q], B.rows), st));
+    }
+    CK(impact::launch_scan(out->row_ptr, B.rows, W.scan(), st));
+    return IMPACT_OK;
+}
+
+// emit pass; `tables_ready`: the FP32 records in W are valid for B
+impact_status run_emit(const Batch &B, const Work &W, const impact_csr *out, int64_t capacity,
+                       bool tables_ready, cudaStream_t st)
+{
+    impact::RowOutputs o{out->row_ptr, out->col, out->lo, out->up, nullptr, nullptr, nullptr,
+                         nullptr, W.status(), capacity, B.rows};
+    if (B.prec == PREC_FP32_SOUND) {
+        if (!tables_ready) {   // rebuild the records; the row outputs stay as counted
+            CK(impact::launch_setup_fp32(W.index(), B.items, W.status(), st));
+            CK(impact::launch_prep_fp32(W.index(), B.items, nullptr, nullptr, nullptr, st));
+        }
+        CK(cudaMemsetAsync(W.counter() + 1, 0, 8, st));
+        CK(impact::launch_tree_fp32(W.index(), B.rows, B.smem_emit, B.tune.emit_warps, true, o,
+                                    st));
+    } else {
+        for (int q = 0; q < B.count(); ++q)
+            CK(impact::launch_rows(W.desc(q), B.prec, true, 0, B.plans[q].rows,
+                                   shifted(o, B.row_begin[q], B.rows), st));
+    }
+    return IMPACT_OK;
+}
+
+impact_status check_pair_arrays(const impact_csr *out)
+{
+    if (out->nnz > 0 &&
+        (!is_device_ptr(out->col) || !is_device_ptr(out->lo) || !is_device_ptr(out->up)))
+        return fail(IMPACT_ERR_ARG, "col, lo and up must be device arrays");
+    return IMPACT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// the three phases behind the entry points
+// ---------------------------------------------------------------------------
+
+impact_status do_count(const Batch &B, impact_csr *out, cudaStream_t st)
+{
+    impact_status s;
+    if ((s = check_row_arrays(out)) != IMPACT_OK) return s;
+    configure_pool_once();
+    Work W;
+    if ((s = get_work(B, out, st, W)) != IMPACT_OK) return s;
+    if (!W.owned) ws_tag(W.base, 0);
+    if ((s = upload(B, W, st)) != IMPACT_OK) return s;
+    if ((s = run_count(B, W, out, st)) != IMPACT_OK) return s;
+    int64_t nnz = 0;
+    uint32_t status = 0;
+    CK(cudaMemcpyAsync(&nnz, out->row_ptr + B.rows, 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&status, W.status(), 4, cudaMemcpyDeviceToHost, st));
+    if ((s = release(W, st)) != IMPACT_OK) return s;
+    CK(cudaStreamSynchronize(st));
+    out->rows = B.rows;
+    out->nnz = nnz;
+    s = status_result(status);
+    if (!W.owned && (s == IMPACT_OK || s == IMPACT_ERR_UNSOUND)) ws_tag(out->workspace, B.hash);
+    return s;
+}
+
+impact_status do_emit(const Batch &B, impact_csr *out, cudaStream_t st)
+{
+    impact_status s;
+    if (!is_device_ptr(out->row_ptr)) return fail(IMPACT_ERR_ARG, "row_ptr must be a device array");
+    if ((s = check_pair_arrays(out)) != IMPACT_OK) return s;
+    configure_pool_once();
+    bool ready = false;
+    if (out->workspace) {
+        if (!ws_has(out->workspace, B.hash))
+            return fail(IMPACT_ERR_ARG,
+                        "workspace was not filled by impact_count for these arguments");
+        ready = true;
+    }
+    Work W;
+    if ((s = get_work(B, out, st, W)) != IMPACT_OK) return s;
+    if (!ready) {
+        if ((s = upload(B, W, st)) != IMPACT_OK) return s;
+    } else {
+        CK(cudaMemsetAsync(W.status(), 0, 64, st));
+    }
+    if ((s = run_emit(B, W, out, out->nnz, ready, st)) != IMPACT_OK) return s;
+    if ((s = release(W, st)) != IMPACT_OK) return s;
+    out->rows = B.rows;
+    return IMPACT_OK;
+}
+
+impact_status do_build(const Batch &B, impact_csr *out, cudaStream_t st)
+{
+    impact_status s;
+    configure_pool_once();
+    const bool lib_owned = (out->col == nullptr);
+    const size_t vbytes = B.prec == PREC_FP32_SOUND ? 4 : 8;
+    if (lib_owned) {
+        void *ws = out->workspace;
+        int64_t wsb = out->workspace_bytes;
+        memset(out, 0, sizeof(*out));
+        out->workspace = ws;
+        out->workspace_bytes = wsb;
+        CK(cudaMallocAsync((void **)&out->row_ptr, (B.rows + 1) * 8, st));
+        CK(cudaMallocAsync((void **)&out->sink_lo, B.rows * 8, st));
+        CK(cudaMallocAsync((void **)&out->sink_up, B.rows * 8, st));
+        CK(cudaMallocAsync((void **)&out->trunc, B.rows * 8, st));
+        CK(cudaMallocAsync((void **)&out->row_flags, B.rows * 4, st));
+        out->owned = 1;
+    } else {
+        if ((s = check_row_arrays(out)) != IMPACT_OK) return s;
+        if ((s = check_pair_arrays(out)) != IMPACT_OK) return s;
+    }
+    Work W;
+    if ((s = get_work(B, out, st, W)) != IMPACT_OK) return s;
+    if (!W.owned) ws_tag(W.base, 0);
+    if ((s = upload(B, W, st)) != IMPACT_OK) return s;
+    if ((s = run_count(B, W, out, st)) != IMPACT_OK) return s;
+    int64_t capacity = out->nnz;
+    if (lib_owned) {
+        int64_t nnz = 0;
+        CK(cudaMemcpyAsync(&nnz, out->row_ptr + B.rows, 8, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        size_t k = (size_t)std::max<int64_t>(nnz, 1);
+        CK(cudaMallocAsync((void **)&out->col, k * 4, st));
+        CK(cudaMallocAsync(&out->lo, k * vbytes, st));
+        CK(cudaMallocAsync(&out->up, k * vbytes, st));
+        capacity = nnz;
+    }
+    if ((s = run_emit(B, W, out, capacity, true, st)) != IMPACT_OK) return s;
+    int64_t nnz = 0;
+    uint32_t status = 0;
+    CK(cudaMemcpyAsync(&nnz, out->row_ptr + B.rows, 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&status, W.status(), 4, cudaMemcpyDeviceToHost, st));
+    if ((s = release(W, st)) != IMPACT_OK) return s;
+    CK(cudaStreamSynchronize(st));
+    out->rows = B.rows;
+    out->nnz = nnz;
+    if (status & IMPACT_STATUS_CAPACITY)
+        return fail(IMPACT_ERR_CAPACITY, "output capacity " + std::to_string(capacity) +
+                                             " < needed pairs " + std::to_string(nnz));
+    return status_result(status);
+}
+
+impact_request single(const impact_system *sys, const impact_grid *grid,
+                      const impact_inputs *inputs, const double *sigma, double cutoff)
+{
+    impact_request r;
+    r.sys = sys;
+    r.grid = grid;
+    r.inputs = inputs;
+    r.sigma = sigma;
+    r.cutoff = cutoff;
+    return r;
+}
+
+impact_status check_request_ptrs(const impact_request *reqs, int count)
+{
+    if (!reqs) return fail(IMPACT_ERR_ARG, "null request array");
+    for (int q = 0; q < count; ++q)
+        if (!reqs[q].sys || !reqs[q].grid || !reqs[q].inputs || !reqs[q].sigma)
+            return fail(IMPACT_ERR_ARG, "request " + std::to_string(q) + ": null argument");
+    return IMPACT_OK;
+}
+
 }  // namespace
 
-namespace impact {
-void set_last_error(const std::string &msg) { g_last_error = msg; }
-}  // namespace impact
+// A captured pipeline: count, scan and emit of one batch into fixed caller
+// buffers, replayed by impact_graph_launch.
+struct impact_graph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int64_t *h_result = nullptr;   // pinned: [0] nnz, [1] status
+    unsigned char *own_ws = nullptr;
+    int64_t rows = 0, capacity = 0;
+};
 
 extern "C" {
 
@@ -728,15 +528,16 @@ impact_status impact_plan(const impact_system *sys, const impact_grid *grid,
                           impact_precision precision, int64_t *rows, int64_t *nnz_upper_bound,
                           int64_t *bytes_upper_bound)
 {
-    Plan P;
-    impact_status s = make_plan(sys, grid, inputs, sigma, cutoff, precision, P);
+    impact_request r = single(sys, grid, inputs, sigma, cutoff);
+    Batch B;
+    impact_status s = make_batch(&r, 1, precision, nullptr, B);
     if (s != IMPACT_OK) return s;
-    if (rows) *rows = P.rows;
-    if (nnz_upper_bound) *nnz_upper_bound = P.nnz_bound;
+    if (rows) *rows = B.rows;
+    if (nnz_upper_bound) *nnz_upper_bound = B.nnz_bound;
     if (bytes_upper_bound) {
         int64_t per_pair = precision == IMPACT_FP32_SOUND ? 12 : 20;
-        *bytes_upper_bound = P.nnz_bound * per_pair + (P.rows + 1) * 8 + P.rows * (3 * 8 + 4) +
-                             (int64_t)layout_of(P).total;
+        *bytes_upper_bound = B.nnz_bound * per_pair + (B.rows + 1) * 8 + B.rows * (3 * 8 + 4) +
+                             (int64_t)batch_layout(B).total;
     }
     return IMPACT_OK;
 }
@@ -745,10 +546,11 @@ impact_status impact_workspace_bytes(const impact_system *sys, const impact_grid
                                      const impact_inputs *inputs, const double *sigma,
                                      double cutoff, impact_precision precision, int64_t *bytes)
 {
-    Plan P;
-    impact_status s = make_plan(sys, grid, inputs, sigma, cutoff, precision, P);
+    impact_request r = single(sys, grid, inputs, sigma, cutoff);
+    Batch B;
+    impact_status s = make_batch(&r, 1, precision, nullptr, B);
     if (s != IMPACT_OK) return s;
-    if (bytes) *bytes = (int64_t)layout_of(P).total;
+    if (bytes) *bytes = (int64_t)batch_layout(B).total;
     return IMPACT_OK;
 }
 
@@ -757,28 +559,11 @@ impact_status impact_count(const impact_system *sys, const impact_grid *grid,
                            impact_precision precision, impact_csr *out, void *stream)
 {
     if (!out) return fail(IMPACT_ERR_ARG, "null output");
-    Plan P;
-    impact_status s = make_plan(sys, grid, inputs, sigma, cutoff, precision, P);
+    impact_request r = single(sys, grid, inputs, sigma, cutoff);
+    Batch B;
+    impact_status s = make_batch(&r, 1, precision, nullptr, B);
     if (s != IMPACT_OK) return s;
-    if ((s = check_row_arrays(out)) != IMPACT_OK) return s;
-    configure_pool_once();
-    cudaStream_t st = (cudaStream_t)stream;
-    Work W;
-    if ((s = get_work(P, out, st, W)) != IMPACT_OK) return s;
-    if (!W.owned) ws_tag(W.base, 0);
-    if ((s = upload(P, W, st, sys->dev_images)) != IMPACT_OK) return s;
-    if ((s = run_count(P, W, out, st)) != IMPACT_OK) return s;
-    int64_t nnz = 0;
-    uint32_t status = 0;
-    CK(cudaMemcpyAsync(&nnz, out->row_ptr + P.rows, 8, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(&status, W.status(), 4, cudaMemcpyDeviceToHost, st));
-    if ((s = release(W, st)) != IMPACT_OK) return s;
-    CK(cudaStreamSynchronize(st));
-    out->rows = P.rows;
-    out->nnz = nnz;
-    s = status_result(status);
-    if (!W.owned && (s == IMPACT_OK || s == IMPACT_ERR_UNSOUND)) ws_tag(out->workspace, P.hash);
-    return s;
+    return do_count(B, out, (cudaStream_t)stream);
 }
 
 impact_status impact_emit(const impact_system *sys, const impact_grid *grid,
@@ -786,33 +571,11 @@ impact_status impact_emit(const impact_system *sys, const impact_grid *grid,
                           impact_precision precision, impact_csr *out, void *stream)
 {
     if (!out) return fail(IMPACT_ERR_ARG, "null output");
-    Plan P;
-    impact_status s = make_plan(sys, grid, inputs, sigma, cutoff, precision, P);
+    impact_request r = single(sys, grid, inputs, sigma, cutoff);
+    Batch B;
+    impact_status s = make_batch(&r, 1, precision, nullptr, B);
     if (s != IMPACT_OK) return s;
-    if (!is_device_ptr(out->row_ptr)) return fail(IMPACT_ERR_ARG, "row_ptr must be a device array");
-    if (out->nnz > 0 && (!is_device_ptr(out->col) || !is_device_ptr(out->lo) ||
-                         !is_device_ptr(out->up)))
-        return fail(IMPACT_ERR_ARG, "col, lo and up must be device arrays");
-    configure_pool_once();
-    cudaStream_t st = (cudaStream_t)stream;
-    bool ready = false;
-    if (out->workspace) {
-        if (!ws_has(out->workspace, P.hash))
-            return fail(IMPACT_ERR_ARG,
-                        "workspace was not filled by impact_count for these arguments");
-        ready = true;
-    }
-    Work W;
-    if ((s = get_work(P, out, st, W)) != IMPACT_OK) return s;
-    if (!ready) {
-        if ((s = upload(P, W, st, sys->dev_images)) != IMPACT_OK) return s;
-    } else {
-        CK(cudaMemsetAsync(W.status(), 0, 64, st));
-    }
-    if ((s = run_emit(P, W, out, out->nnz, ready, st)) != IMPACT_OK) return s;
-    if ((s = release(W, st)) != IMPACT_OK) return s;
-    out->rows = P.rows;
-    return IMPACT_OK;
+    return do_emit(B, out, (cudaStream_t)stream);
 }
 
 impact_status impact_build(const impact_system *sys, const impact_grid *grid,
@@ -820,60 +583,260 @@ impact_status impact_build(const impact_system *sys, const impact_grid *grid,
                            impact_precision precision, impact_csr *out, void *stream)
 {
     if (!out) return fail(IMPACT_ERR_ARG, "null output");
-    Plan P;
-    impact_status s = make_plan(sys, grid, inputs, sigma, cutoff, precision, P);
+    impact_request r = single(sys, grid, inputs, sigma, cutoff);
+    Batch B;
+    impact_status s = make_batch(&r, 1, precision, nullptr, B);
     if (s != IMPACT_OK) return s;
-    configure_pool_once();
+    return do_build(B, out, (cudaStream_t)stream);
+}
+
+impact_status impact_batch_plan(const impact_request *reqs, int count, impact_precision precision,
+                                const impact_tuning *tuning, int64_t *row_offsets,
+                                int64_t *nnz_upper_bound, int64_t *workspace_bytes)
+{
+    impact_status s = check_request_ptrs(reqs, count);
+    if (s != IMPACT_OK) return s;
+    Batch B;
+    if ((s = make_batch(reqs, count, precision, tuning, B)) != IMPACT_OK) return s;
+    if (row_offsets) memcpy(row_offsets, B.row_begin.data(), (size_t)(count + 1) * 8);
+    if (nnz_upper_bound) *nnz_upper_bound = B.nnz_bound;
+    if (workspace_bytes) *workspace_bytes = (int64_t)batch_layout(B).total;
+    return IMPACT_OK;
+}
+
+impact_status impact_batch_count(const impact_request *reqs, int count,
+                                 impact_precision precision, const impact_tuning *tuning,
+                                 impact_csr *out, void *stream)
+{
+    if (!out) return fail(IMPACT_ERR_ARG, "null output");
+    impact_status s = check_request_ptrs(reqs, count);
+    if (s != IMPACT_OK) return s;
+    Batch B;
+    if ((s = make_batch(reqs, count, precision, tuning, B)) != IMPACT_OK) return s;
+    return do_count(B, out, (cudaStream_t)stream);
+}
+
+impact_status impact_batch_emit(const impact_request *reqs, int count,
+                                impact_precision precision, const impact_tuning *tuning,
+                                impact_csr *out, void *stream)
+{
+    if (!out) return fail(IMPACT_ERR_ARG, "null output");
+    impact_status s = check_request_ptrs(reqs, count);
+    if (s != IMPACT_OK) return s;
+    Batch B;
+    if ((s = make_batch(reqs, count, precision, tuning, B)) != IMPACT_OK) return s;
+    return do_emit(B, out, (cudaStream_t)stream);
+}
+
+impact_status impact_batch_build(const impact_request *reqs, int count,
+                                 impact_precision precision, const impact_tuning *tuning,
+                                 impact_csr *out, void *stream)
+{
+    if (!out) return fail(IMPACT_ERR_ARG, "null output");
+    impact_status s = check_request_ptrs(reqs, count);
+    if (s != IMPACT_OK) return s;
+    Batch B;
+    if ((s = make_batch(reqs, count, precision, tuning, B)) != IMPACT_OK) return s;
+    return do_build(B, out, (cudaStream_t)stream);
+}
+
+impact_status impact_graph_create(const impact_request *reqs, int count,
+                                  impact_precision precision, const impact_tuning *tuning,
+                                  const impact_csr *out, void *stream, impact_graph **graph)
+{
+    if (!out || !graph) return fail(IMPACT_ERR_ARG, "null output or graph handle");
+    *graph = nullptr;
+    impact_status s = check_request_ptrs(reqs, count);
+    if (s != IMPACT_OK) return s;
+    Batch B;
+    if ((s = make_batch(reqs, count, precision, tuning, B)) != IMPACT_OK) return s;
+    if ((s = check_row_arrays(out)) != IMPACT_OK) return s;
+    if (!out->col) return fail(IMPACT_ERR_ARG, "a graph writes into caller-owned col/lo/up");
+    if ((s = check_pair_arrays(out)) != IMPACT_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
-    const bool lib_owned = (out->col == nullptr);
-    const size_t vbytes = precision == IMPACT_FP32_SOUND ? 4 : 8;
-    if (lib_owned) {
-        void *ws = out->workspace;
-        int64_t wsb = out->workspace_bytes;
-        memset(out, 0, sizeof(*out));
-        out->workspace = ws;
-        out->workspace_bytes = wsb;
-        CK(cudaMallocAsync((void **)&out->row_ptr, (P.rows + 1) * 8, st));
-        CK(cudaMallocAsync((void **)&out->sink_lo, P.rows * 8, st));
-        CK(cudaMallocAsync((void **)&out->sink_up, P.rows * 8, st));
-        CK(cudaMallocAsync((void **)&out->trunc, P.rows * 8, st));
-        CK(cudaMallocAsync((void **)&out->row_flags, P.rows * 4, st));
-        out->owned = 1;
-    } else {
-        if ((s = check_row_arrays(out)) != IMPACT_OK) return s;
-        if (out->nnz > 0 && (!is_device_ptr(out->col) || !is_device_ptr(out->lo) ||
-                             !is_device_ptr(out->up)))
-            return fail(IMPACT_ERR_ARG, "col, lo and up must be device arrays");
-    }
+    impact_graph *g = new impact_graph();
+    g->rows = B.rows;
+    g->capacity = out->nnz;
     Work W;
-    if ((s = get_work(P, out, st, W)) != IMPACT_OK) return s;
-    if (!W.owned) ws_tag(W.base, 0);
-    if ((s = upload(P, W, st, sys->dev_images)) != IMPACT_OK) return s;
-    if ((s = run_count(P, W, out, st)) != IMPACT_OK) return s;
-    int64_t capacity = out->nnz;
-    if (lib_owned) {
-        int64_t nnz = 0;
-        CK(cudaMemcpyAsync(&nnz, out->row_ptr + P.rows, 8, cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        size_t k = (size_t)std::max<int64_t>(nnz, 1);
-        CK(cudaMallocAsync((void **)&out->col, k * 4, st));
-        CK(cudaMallocAsync(&out->lo, k * vbytes, st));
-        CK(cudaMallocAsync(&out->up, k * vbytes, st));
-        capacity = nnz;
+    W.L = batch_layout(B);
+    auto cleanup = [&](impact_status r) {
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        if (g->graph) cudaGraphDestroy(g->graph);
+        if (g->h_result) cudaFreeHost(g->h_result);
+        if (g->own_ws) cudaFree(g->own_ws);
+        delete g;
+        return r;
+    };
+    if (out->workspace) {
+        if (out->workspace_bytes < (int64_t)W.L.total || ((uintptr_t)out->workspace & 255))
+            return cleanup(fail(IMPACT_ERR_ARG, "workspace too small or not 256-byte aligned"));
+        W.base = (unsigned char *)out->workspace;
+        ws_tag(W.base, 0);
+    } else {
+        cudaError_t e = cudaMalloc((void **)&g->own_ws, W.L.total);
+        if (e != cudaSuccess) return cleanup(fail(IMPACT_ERR_OOM, cudaGetErrorString(e)));
+        W.base = g->own_ws;
     }
-    if ((s = run_emit(P, W, out, capacity, true, st)) != IMPACT_OK) return s;
-    int64_t nnz = 0;
-    uint32_t status = 0;
-    CK(cudaMemcpyAsync(&nnz, out->row_ptr + P.rows, 8, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(&status, W.status(), 4, cudaMemcpyDeviceToHost, st));
-    if ((s = release(W, st)) != IMPACT_OK) return s;
-    CK(cudaStreamSynchronize(st));
-    out->rows = P.rows;
-    out->nnz = nnz;
+    if (cudaMallocHost((void **)&g->h_result, 16) != cudaSuccess)
+        return cleanup(fail(IMPACT_ERR_OOM, "pinned result word"));
+    if ((s = upload(B, W, st)) != IMPACT_OK) return cleanup(s);
+    if (cudaStreamSynchronize(st) != cudaSuccess)
+        return cleanup(fail(IMPACT_ERR_CUDA, "upload before capture failed"));
+    // capture on a private stream: the caller's may be the legacy default one
+    cudaStream_t cs = nullptr;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess)
+        return cleanup(fail(IMPACT_ERR_CUDA, "capture stream"));
+    impact_csr o = *out;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+        s = run_count(B, W, &o, cs);
+        if (s == IMPACT_OK) s = run_emit(B, W, &o, g->capacity, true, cs);
+        if (s == IMPACT_OK) {
+            cudaMemcpyAsync(g->h_result, o.row_ptr + B.rows, 8, cudaMemcpyDeviceToHost, cs);
+            cudaMemcpyAsync(g->h_result + 1, W.status(), 4, cudaMemcpyDeviceToHost, cs);
+        }
+        cudaError_t e2 = cudaStreamEndCapture(cs, &g->graph);
+        if (s == IMPACT_OK && e2 != cudaSuccess) s = fail(IMPACT_ERR_CUDA, cudaGetErrorString(e2));
+    } else {
+        s = fail(IMPACT_ERR_CUDA, cudaGetErrorString(e));
+    }
+    cudaStreamDestroy(cs);
+    if (s != IMPACT_OK) return cleanup(s);
+    e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+    if (e != cudaSuccess) return cleanup(fail(IMPACT_ERR_CUDA, cudaGetErrorString(e)));
+    *graph = g;
+    return IMPACT_OK;
+}
+
+impact_status impact_graph_launch(impact_graph *graph, void *stream)
+{
+    if (!graph || !graph->exec) return fail(IMPACT_ERR_ARG, "null graph");
+    graph->h_result[0] = -1;
+    graph->h_result[1] = 0;
+    CK(cudaGraphLaunch(graph->exec, (cudaStream_t)stream));
+    return IMPACT_OK;
+}
+
+impact_status impact_graph_result(impact_graph *graph, int64_t *nnz)
+{
+    if (!graph) return fail(IMPACT_ERR_ARG, "null graph");
+    const int64_t got = graph->h_result[0];
+    const uint32_t status = (uint32_t)graph->h_result[1];
+    if (nnz) *nnz = got;
+    if (got < 0) return fail(IMPACT_ERR_ARG, "no finished launch: synchronize the stream first");
     if (status & IMPACT_STATUS_CAPACITY)
-        return fail(IMPACT_ERR_CAPACITY, "output capacity " + std::to_string(capacity) +
-                                             " < needed pairs " + std::to_string(nnz));
+        return fail(IMPACT_ERR_CAPACITY, "output capacity " + std::to_string(graph->capacity) +
+                                             " < needed pairs " + std::to_string(got));
     return status_result(status);
+}
+
+impact_status impact_graph_destroy(impact_graph *graph)
+{
+    if (!graph) return IMPACT_OK;
+    if (graph->exec) cudaGraphExecDestroy(graph->exec);
+    if (graph->graph) cudaGraphDestroy(graph->graph);
+    if (graph->h_result) cudaFreeHost(graph->h_result);
+    if (graph->own_ws) cudaFree(graph->own_ws);
+    delete graph;
+    return IMPACT_OK;
+}
+
+impact_status impact_batch_tune(const impact_request *reqs, int count,
+                                impact_precision precision, impact_csr *out, int reps,
+                                void *stream, impact_tuning *best, double *best_ms)
+{
+    if (!out || !best) return fail(IMPACT_ERR_ARG, "null output or result");
+    if (precision != IMPACT_FP32_SOUND)
+        return fail(IMPACT_ERR_ARG, "the autotuner tunes the FP32-sound walk");
+    impact_status s = check_request_ptrs(reqs, count);
+    if (s != IMPACT_OK) return s;
+    if ((s = check_row_arrays(out)) != IMPACT_OK) return s;
+    if ((s = check_pair_arrays(out)) != IMPACT_OK) return s;
+    reps = std::max(1, std::min(reps, 50));
+    cudaStream_t st = (cudaStream_t)stream;
+    configure_pool_once();
+    Batch B0;
+    if ((s = make_batch(reqs, count, precision, nullptr, B0)) != IMPACT_OK) return s;
+    bool any3 = false;
+    for (const Plan &P : B0.plans) any3 |= P.desc.n >= 3;
+    Work W;
+    impact_csr wout = *out;
+    wout.workspace = nullptr;   // the tuner keeps its own scratch
+    if ((s = get_work(B0, &wout, st, W)) != IMPACT_OK) return s;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    auto timed = [&](const impact_tuning &t, bool emit, double &ms) -> impact_status {
+        Batch B;
+        impact_status r = make_batch(reqs, count, precision, &t, B);
+        if (r != IMPACT_OK) return r;
+        if ((r = upload(B, W, st)) != IMPACT_OK) return r;
+        if ((r = run_count(B, W, out, st)) != IMPACT_OK) return r;
+        ms = 1e30;
+        for (int i = 0; i < reps; ++i) {
+            CK(cudaEventRecord(e0, st));
+            r = emit ? run_emit(B, W, out, out->nnz, true, st) : run_count(B, W, out, st);
+            if (r != IMPACT_OK) return r;
+            CK(cudaEventRecord(e1, st));
+            CK(cudaEventSynchronize(e1));
+            float f = 0.0f;
+            CK(cudaEventElapsedTime(&f, e0, e1));
+            ms = std::min(ms, (double)f);
+        }
+        uint32_t status = 0;
+        CK(cudaMemcpy(&status, W.status(), 4, cudaMemcpyDeviceToHost));
+        if (status & ~IMPACT_STATUS_UNSOUND) ms = 1e30;   // a shape that cannot run this batch
+        return IMPACT_OK;
+    };
+    const int warps[3] = {2, 4, 8};
+    const int smem[3] = {6144, 10240, 16384};
+    impact_tuning cur;
+    memset(&cur, 0, sizeof(cur));
+    double best_count = 1e30, best_emit = 1e30;
+    impact_tuning tb = cur;
+    for (int k = (any3 ? 1 : 0); k <= (any3 ? 2 : 0) && s == IMPACT_OK; ++k)
+        for (int w : warps)
+            for (int m : smem) {
+                impact_tuning t = cur;
+                t.count_warps = w;
+                t.count_smem_target = m;
+                t.count_k = k;
+                double ms;
+                s = timed(t, false, ms);
+                if (s != IMPACT_OK) break;
+                if (ms < best_count) {
+                    best_count = ms;
+                    tb = t;
+                }
+            }
+    const bool can_emit = out->col != nullptr;
+    if (s == IMPACT_OK && can_emit) {
+        impact_tuning base = tb;
+        for (int w : warps)
+            for (int m : smem) {
+                impact_tuning t = base;
+                t.emit_warps = w;
+                t.emit_smem_target = m;
+                double ms;
+                s = timed(t, true, ms);
+                if (s != IMPACT_OK) break;
+                if (ms < best_emit) {
+                    best_emit = ms;
+                    tb = t;
+                }
+            }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    impact_status r2 = release(W, st);
+    if (s != IMPACT_OK) return s;
+    if (r2 != IMPACT_OK) return r2;
+    if (best_count >= 1e30) return fail(IMPACT_ERR_ARG, "no launch shape ran this batch");
+    if (tb.emit_warps == 0) tb.emit_warps = IMPACT_TREE_WARPS;
+    if (tb.emit_smem_target == 0) tb.emit_smem_target = IMPACT_TREE_SMEM_TARGET;
+    *best = tb;
+    if (best_ms) *best_ms = best_count + (can_emit ? best_emit : 0.0);
+    return IMPACT_OK;
 }
 
 impact_status impact_free(impact_csr *out)
@@ -894,6 +857,6 @@ impact_status impact_free(impact_csr *out)
 
 const char *impact_last_error(void) { return g_last_error.c_str(); }
 
-int impact_version(void) { return 200; }
+int impact_version(void) { return 300; }
 
 }  // extern "C"

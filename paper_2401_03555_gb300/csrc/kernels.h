@@ -12,7 +12,9 @@
 #define IMPACT_TSUM_MAX 256               // FP32 path: factor entries per row record
 #define IMPACT_TREE_SEG 512               // FP32 path: pairs staged per leaf batch
 #define IMPACT_TREE_HDR 256               // FP32 path: per-row scalars per warp (bytes)
-#define IMPACT_TREE_SMEM_TARGET 10240     // FP32 path: per-warp shared memory aimed for
+#define IMPACT_TREE_SMEM_TARGET 10240     // FP32 path: per-warp shared memory aimed for (default)
+#define IMPACT_TREE_WARPS 4               // FP32 path: warps per block of the walk (default)
+#define IMPACT_TREE_WARPS_MAX 8
 #define IMPACT_STATUS_TABLE_OVERFLOW 0x1u // some row's windows exceeded IMPACT_TABLE_MAX
 #define IMPACT_STATUS_UNSOUND 0x2u        // some row check proved a violation
 #define IMPACT_STATUS_CAPACITY 0x4u       // emit skipped: output capacity too small
@@ -42,19 +44,17 @@ int64_t scan_scratch_elems(int64_t n);
 // Sets the message impact_last_error() returns on this host thread.
 void set_last_error(const std::string &msg);
 
-// FP32-sound table path (tree_fp32.cu).
+// FP32-sound table path (tree_fp32.cu), every launch over a whole batch.
 int64_t record_stride(int n, int tsum_cap);
 int tree_smem_bytes(int tsum_cap, int pool_cap, bool emit);
-cudaError_t launch_prep_fp32(const ImpactDesc *d_desc, int n, int64_t row_begin, int64_t row_end,
-                             unsigned char *rec, double *sink_lo, double *sink_up, double *trunc,
-                             cudaStream_t stream);
-int tree_warps_per_block();
-cudaError_t launch_setup_fp32(const ImpactDesc *d_desc, int n, int64_t row_begin,
-                              int64_t row_end, unsigned char *rec, uint32_t *status,
+cudaError_t launch_setup_fp32(const BatchIndex *d_index, int64_t items, uint32_t *status,
                               cudaStream_t stream);
-cudaError_t launch_tree_fp32(const ImpactDesc *d_desc, int tree_smem, bool emit,
-                             int64_t row_begin, int64_t row_end, const unsigned char *rec,
-                             const RowOutputs &o, cudaStream_t stream);
+cudaError_t launch_prep_fp32(const BatchIndex *d_index, int64_t items, double *sink_lo,
+                             double *sink_up, double *trunc, cudaStream_t stream);
+// `warp_smem`: shared-memory bytes of one warp (the largest of the batch);
+// `warps`: warps per block (1..8).
+cudaError_t launch_tree_fp32(const BatchIndex *d_index, int64_t rows, int warp_smem, int warps,
+                             bool emit, const RowOutputs &o, cudaStream_t stream);
 cudaError_t launch_scan(int64_t *row_ptr, int64_t n, int64_t *scratch, cudaStream_t stream);
 
 }  // namespace impact

@@ -42,8 +42,7 @@
 namespace {
 
 constexpr int kSetupThreads = 256;
-constexpr int kTreeWarps = 4;
-constexpr int kTreeThreads = kTreeWarps * 32;
+constexpr int kTreeThreadsMax = IMPACT_TREE_WARPS_MAX * 32;
 constexpr int kSeg = IMPACT_TREE_SEG;      // pairs staged per leaf batch
 constexpr int kHdr = IMPACT_TREE_HDR;      // bytes of per-row scalars per warp
 constexpr float kTwoM44 = 5.6843419e-14f;  // 2^-44
@@ -74,6 +73,20 @@ __device__ __forceinline__ void sub_pair(float2 a, float bh, float bl, float &rh
     rl = __fadd_rn(__fsub_rn(a.y, bl), e);
 }
 
+// Row sums of the count pass are accumulated in fixed point (units of 2^-56,
+// each term rounded outward), so the totals do not depend on which lane took
+// which node nor on the order: every launch shape gives the same bits.
+constexpr float kFix = 72057594037927936.0f;         // 2^56
+constexpr double kUnfix = 1.3877787807814457e-17;    // 2^-56
+__device__ __forceinline__ unsigned long long fix_up(float x)
+{
+    return __float2ull_ru(__fmul_ru(x, kFix));
+}
+__device__ __forceinline__ unsigned long long fix_dn(float x)
+{
+    return __float2ull_rd(__fmul_rd(x, kFix));
+}
+
 __device__ __forceinline__ float fpred(float x) { return nextafterf(x, 0.0f); }
 __device__ __forceinline__ float fsucc(float x) { return nextafterf(x, INFINITY); }
 
@@ -84,6 +97,18 @@ __device__ __forceinline__ float threshold(float c, float r)
 {
     if (!(r > 0.0f)) return INFINITY;
     return fsucc(__fdiv_rd(fpred(c), r));
+}
+
+// Problem of a batch that owns global index x: begin[q] <= x < begin[q + 1].
+__device__ __forceinline__ int find_problem(const int64_t *__restrict__ begin, int count,
+                                            int64_t x)
+{
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (begin[mid] <= x) lo = mid; else hi = mid - 1;
+    }
+    return lo;
 }
 
 // Edge point: alpha = (E - m)/(sigma sqrt2) at one image end, and its tails.
@@ -114,18 +139,19 @@ __device__ __forceinline__ bool mid_above(const EdgePt &c, const EdgePt &e)
 }
 
 __global__ void __launch_bounds__(kSetupThreads)
-setup_fp32(const ImpactDesc *__restrict__ Dp, int64_t row_begin, int64_t row_end,
-           unsigned char *__restrict__ rec, uint32_t *__restrict__ status)
+setup_fp32(const BatchIndex *__restrict__ B, uint32_t *__restrict__ status)
 {
-    const ImpactDesc &D = *Dp;
-    const int n = D.n;
-    const float cut = D.cutoff32;
-    const int64_t total = (row_end - row_begin) * n;
+    const int64_t total = B->items;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total; p += stride) {
-        const int64_t rl = p / n;
-        const int d = (int)(p - rl * n);
-        const int64_t row = row_begin + rl;
+        const int q = find_problem(B->item_begin, B->count, p);
+        const ImpactDesc &D = *B->desc[q];
+        const int n = D.n;
+        const float cut = D.cutoff32;
+        const int64_t local = p - B->item_begin[q];
+        const int64_t rl = local / n;
+        const int d = (int)(local - rl * n);
+        const int64_t row = rl;   // row id within its problem
         // row -> (cell digits, input)
         int64_t cell;
         int j;
@@ -219,7 +245,7 @@ setup_fp32(const ImpactDesc *__restrict__ Dp, int64_t row_begin, int64_t row_end
         xb = fminf(fmaxf(xb, 0.0f), top);
         const int a = (int)xa;
         const int W = max((int)xb - a + 1, 1);
-        unsigned char *rr = rec + rl * (int64_t)D.rec_stride;
+        unsigned char *rr = B->rec[q] + rl * (int64_t)D.rec_stride;
         if (W > g.wcap) {
             reinterpret_cast<int4 *>(rr)[3 * d] = make_int4(a, 0, 0, 0);
             reinterpret_cast<float4 *>(rr)[3 * d + 1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
@@ -341,19 +367,20 @@ setup_fp32(const ImpactDesc *__restrict__ Dp, int64_t row_begin, int64_t row_end
 // of the targets outside the window box (FP64, outward rounding), unless the
 // row outputs are null (records rebuilt for an emit pass).
 __global__ void __launch_bounds__(kSetupThreads)
-prep_fp32(const ImpactDesc *__restrict__ Dp, int64_t row_begin, int64_t row_end,
-          unsigned char *__restrict__ rec, double *__restrict__ sink_lo,
+prep_fp32(const BatchIndex *__restrict__ B, double *__restrict__ sink_lo,
           double *__restrict__ sink_up, double *__restrict__ trunc)
 {
-    const ImpactDesc &D = *Dp;
-    const int n = D.n;
-    const float cut = D.cutoff32;
-    const int64_t total = (row_end - row_begin) * n;
+    const int64_t total = B->items;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total; p += stride) {
-        const int64_t rl = p / n;
-        const int d = (int)(p - rl * n);
-        unsigned char *rr = rec + rl * (int64_t)D.rec_stride;
+        const int q = find_problem(B->item_begin, B->count, p);
+        const ImpactDesc &D = *B->desc[q];
+        const int n = D.n;
+        const float cut = D.cutoff32;
+        const int64_t local = p - B->item_begin[q];
+        const int64_t rl = local / n;
+        const int d = (int)(local - rl * n);
+        unsigned char *rr = B->rec[q] + rl * (int64_t)D.rec_stride;
         const int4 *hi = reinterpret_cast<const int4 *>(rr);
         const float4 *hf = reinterpret_cast<const float4 *>(rr);
         float R = 1.0f, SR = 1.0f;
@@ -390,7 +417,7 @@ prep_fp32(const ImpactDesc *__restrict__ Dp, int64_t row_begin, int64_t row_end,
                 outside += pre * (double)b.y * suf;
                 suf *= (double)b.x + (double)b.y;
             }
-            const int64_t row = row_begin + rl;
+            const int64_t row = B->row_begin[q] + rl;   // global row
             sink_lo[row] = fmax(__dsub_rd(1.0, pin_up), 0.0);
             sink_up[row] = fmin(__dsub_ru(1.0, pin_dn), 1.0);
             trunc[row] = outside * (1.0 + 1e-12);
@@ -493,34 +520,39 @@ __device__ __forceinline__ float outside_sum(const Smem &S, int dim, int l, int 
 }
 
 template <bool EMIT>
-__global__ void __launch_bounds__(kTreeThreads)
-tree_fp32(const ImpactDesc *__restrict__ Dp, int64_t row_begin, int64_t row_end,
-          const unsigned char *__restrict__ rec, int64_t *__restrict__ row_ptr,
+__global__ void __launch_bounds__(kTreeThreadsMax)
+tree_fp32(const BatchIndex *__restrict__ B, int warp_smem, int64_t *__restrict__ row_ptr,
           int32_t *__restrict__ out_col, float *__restrict__ out_lo, float *__restrict__ out_up,
           double *__restrict__ sink_lo, double *__restrict__ sink_up,
           double *__restrict__ trunc, uint32_t *__restrict__ flags, uint32_t *__restrict__ status,
           int64_t capacity, int64_t total_at)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const ImpactDesc &D = *Dp;
     const int lane = threadIdx.x & 31;
-    const int n = D.n;
-    const int tcap = D.tsum_cap;
-    const int wsm = EMIT ? D.tree_smem_emit : D.tree_smem_count;
-    const int pool = D.pool_cap[EMIT ? 1 : 0];
-    const Smem S = carve<EMIT>(smem_raw + (size_t)(threadIdx.x >> 5) * wsm, tcap, pool);
-    Hdr &H = *S.h;
-    const int K = EMIT ? 1 : D.tree_k;   // dimensions a lane enumerates at the end
-    const int Lp = n - 1 - K;         // level of the block parents (-1: the root)
-    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned char *const smem_warp = smem_raw + (size_t)(threadIdx.x >> 5) * warp_smem;
     if (EMIT && capacity >= 0 && row_ptr[total_at] > capacity) {
         if (threadIdx.x == 0 && blockIdx.x == 0) atomicOr(status, IMPACT_STATUS_CAPACITY);
         return;
     }
+    unsigned long long *const next_row = B->next_row + (EMIT ? 1 : 0);
 
-    for (int64_t row = row_begin + warp0; row < row_end; row += nwarps) {
-        const unsigned char *rr = rec + (row - row_begin) * (int64_t)D.rec_stride;
+    // persistent: each warp takes the next row of the batch until none is left
+    while (true) {
+        unsigned long long taken = 0;
+        if (lane == 0) taken = atomicAdd(next_row, 1ull);
+        taken = __shfl_sync(0xffffffffu, taken, 0);
+        if (taken >= (unsigned long long)B->rows) break;
+        const int64_t row = (int64_t)taken;   // global row of the batch
+        const int q = find_problem(B->row_begin, B->count, row);
+        const ImpactDesc &D = *B->desc[q];
+        const int n = D.n;
+        const int tcap = D.tsum_cap;
+        const int pool = D.pool_cap[EMIT ? 1 : 0];
+        const Smem S = carve<EMIT>(smem_warp, tcap, pool);
+        Hdr &H = *S.h;
+        const int K = EMIT ? 1 : D.tree_k;   // dimensions a lane enumerates at the end
+        const int Lp = n - 1 - K;             // level of the block parents (-1: the root)
+        const unsigned char *rr = B->rec[q] + (row - B->row_begin[q]) * (int64_t)D.rec_stride;
         // 1. the row record: per-dimension scalars, then the trimmed tables
         if (lane < n) {
             const int4 hi = reinterpret_cast<const int4 *>(rr)[3 * lane];
@@ -581,7 +613,7 @@ tree_fp32(const ImpactDesc *__restrict__ Dp, int64_t row_begin, int64_t row_end,
         }
         __syncwarp();
 
-        float drop = 0.0f, sup = 0.0f, slo = 0.0f;   // count pass, per lane
+        unsigned long long drop = 0, sup = 0, slo = 0;   // count pass, per lane (fixed point)
         int cnt = 0;
         int64_t out_base = 0, out_end = 0, written = 0;
         if (EMIT) {
@@ -595,10 +627,10 @@ tree_fp32(const ImpactDesc *__restrict__ Dp, int64_t row_begin, int64_t row_end,
             if (c > 0) {
                 float su = fmaxf(__fsub_ru(S.pu_up[po + l + c], S.pu_dn[po + l]), 0.0f);
                 float sl = fmaxf(__fsub_rd(S.pl_dn[po + l + c], S.pl_up[po + l]), 0.0f);
-                sup = __fadd_ru(sup, __fmul_ru(P, su));
-                slo = __fadd_rd(slo, __fmul_rd(Pl, sl));
+                sup += fix_up(__fmul_ru(P, su));
+                slo += fix_dn(__fmul_rd(Pl, sl));
             }
-            drop = __fadd_ru(drop, __fmul_ru(P, outside_sum(S, dl, l, c)));
+            drop += fix_up(__fmul_ru(P, outside_sum(S, dl, l, c)));
         };
 
         // K = 1: each active lane's parent (P, Pl, cb) owns one run of the
@@ -642,8 +674,7 @@ tree_fp32(const ImpactDesc *__restrict__ Dp, int64_t row_begin, int64_t row_end,
             int lm = 0, cm = 0;
             if (act) run_of(S, dm, P, lm, cm);
             if (act) {
-                drop = __fadd_ru(drop, __fmul_ru(__fmul_ru(P, outside_sum(S, dm, lm, cm)),
-                                                 H.swr[dm]));
+                drop += fix_up(__fmul_ru(__fmul_ru(P, outside_sum(S, dm, lm, cm)), H.swr[dm]));
                 for (int i = 0; i < cm; ++i) {
                     const int m = lm + i;
                     const float P2 = __fmul_ru(P, S.U[offm + m]);
@@ -768,8 +799,8 @@ tree_fp32(const ImpactDesc *__restrict__ Dp, int64_t row_begin, int64_t row_end,
                         S.ncol[ix] = cb + (ta + t) * st;
                     }
                     if (!EMIT)
-                        drop = __fadd_ru(drop, __fmul_ru(__fmul_ru(P, outside_sum(S, dim, l, c)),
-                                                         H.swr[dim]));
+                        drop += fix_up(__fmul_ru(__fmul_ru(P, outside_sum(S, dim, l, c)),
+                                                 H.swr[dim]));
                 }
                 // children appended: the sum of the taken lanes' runs
                 int added = take ? c : 0;
@@ -788,7 +819,7 @@ tree_fp32(const ImpactDesc *__restrict__ Dp, int64_t row_begin, int64_t row_end,
             if (lane == 0 && out_base + written != out_end)
                 atomicOr(status, IMPACT_STATUS_EMIT_MISMATCH);
         } else {
-            double dsum = (double)drop, usum = (double)sup, lsum = (double)slo;
+            unsigned long long dsum = drop, usum = sup, lsum = slo;
             long long csum = cnt;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
@@ -798,14 +829,14 @@ tree_fp32(const ImpactDesc *__restrict__ Dp, int64_t row_begin, int64_t row_end,
                 csum += __shfl_xor_sync(0xffffffffu, csum, o);
             }
             if (lane == 0) {
-                const double tr = trunc[row] + dsum * (1.0 + 1e-12);
+                const double tr = __dadd_ru(trunc[row], __ull2double_ru(dsum) * kUnfix);
                 row_ptr[row] = csum;
                 trunc[row] = tr;
                 if (flags) {
                     // the emitted values are RU / RD products of the factors:
                     // widen the run sums by their rounding before testing
-                    const double lo_sum = lsum * (1.0 - 1e-6);
-                    const double up_sum = usum * (1.0 + 1e-6);
+                    const double lo_sum = __ull2double_rd(lsum) * kUnfix * (1.0 - 1e-6);
+                    const double up_sum = __ull2double_ru(usum) * kUnfix * (1.0 + 1e-6);
                     uint32_t f = 0;
                     if (__dadd_rd(lo_sum, sink_lo[row]) > 1.0) f |= 0x1u;
                     if (__dadd_ru(__dadd_ru(up_sum, sink_up[row]), tr) < 1.0) f |= 0x2u;
@@ -850,50 +881,44 @@ int tree_smem_bytes(int tsum_cap, int pool_cap, bool emit)
     return (int)((b + 15) / 16 * 16);
 }
 
-cudaError_t launch_prep_fp32(const ImpactDesc *d_desc, int n, int64_t row_begin, int64_t row_end,
-                             unsigned char *rec, double *sink_lo, double *sink_up, double *trunc,
-                             cudaStream_t stream)
-{
-    int64_t rows = row_end - row_begin;
-    if (rows <= 0) return cudaSuccess;
-    int g = occupancy_grid((const void *)prep_fp32, kSetupThreads, 0, rows * n, kSetupThreads);
-    prep_fp32<<<g, kSetupThreads, 0, stream>>>(d_desc, row_begin, row_end, rec, sink_lo, sink_up,
-                                               trunc);
-    return cudaGetLastError();
-}
-
-int tree_warps_per_block() { return kTreeWarps; }
-
-cudaError_t launch_setup_fp32(const ImpactDesc *d_desc, int n, int64_t row_begin,
-                              int64_t row_end, unsigned char *rec, uint32_t *status,
+cudaError_t launch_setup_fp32(const BatchIndex *d_index, int64_t items, uint32_t *status,
                               cudaStream_t stream)
 {
-    int64_t rows = row_end - row_begin;
-    if (rows <= 0) return cudaSuccess;
-    int g = occupancy_grid((const void *)setup_fp32, kSetupThreads, 0, rows * n, kSetupThreads);
-    setup_fp32<<<g, kSetupThreads, 0, stream>>>(d_desc, row_begin, row_end, rec, status);
+    if (items <= 0) return cudaSuccess;
+    int g = occupancy_grid((const void *)setup_fp32, kSetupThreads, 0, items, kSetupThreads);
+    setup_fp32<<<g, kSetupThreads, 0, stream>>>(d_index, status);
     return cudaGetLastError();
 }
 
-cudaError_t launch_tree_fp32(const ImpactDesc *d_desc, int tree_smem, bool emit,
-                             int64_t row_begin, int64_t row_end, const unsigned char *rec,
-                             const RowOutputs &o, cudaStream_t stream)
+cudaError_t launch_prep_fp32(const BatchIndex *d_index, int64_t items, double *sink_lo,
+                             double *sink_up, double *trunc, cudaStream_t stream)
 {
-    int64_t rows = row_end - row_begin;
+    if (items <= 0) return cudaSuccess;
+    int g = occupancy_grid((const void *)prep_fp32, kSetupThreads, 0, items, kSetupThreads);
+    prep_fp32<<<g, kSetupThreads, 0, stream>>>(d_index, sink_lo, sink_up, trunc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tree_fp32(const BatchIndex *d_index, int64_t rows, int warp_smem, int warps,
+                             bool emit, const RowOutputs &o, cudaStream_t stream)
+{
     if (rows <= 0) return cudaSuccess;
-    const size_t smem = (size_t)tree_smem * kTreeWarps;
+    warps = std::max(1, std::min(warps, IMPACT_TREE_WARPS_MAX));
+    const int threads = warps * 32;
+    const size_t smem = (size_t)warp_smem * warps;
     const void *k = emit ? (const void *)tree_fp32<true> : (const void *)tree_fp32<false>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    int g = occupancy_grid(k, kTreeThreads, smem, rows, kTreeWarps);
+    // persistent grid: as many blocks as fit at once (rows are taken dynamically)
+    int g = occupancy_grid(k, threads, smem, rows, warps);
     if (emit)
-        tree_fp32<true><<<g, kTreeThreads, smem, stream>>>(
-            d_desc, row_begin, row_end, rec, o.row_ptr, o.col, (float *)o.lo, (float *)o.up,
-            o.sink_lo, o.sink_up, o.trunc, o.flags, o.status, o.capacity, o.total_at);
+        tree_fp32<true><<<g, threads, smem, stream>>>(
+            d_index, warp_smem, o.row_ptr, o.col, (float *)o.lo, (float *)o.up, o.sink_lo,
+            o.sink_up, o.trunc, o.flags, o.status, o.capacity, o.total_at);
     else
-        tree_fp32<false><<<g, kTreeThreads, smem, stream>>>(
-            d_desc, row_begin, row_end, rec, o.row_ptr, o.col, (float *)o.lo, (float *)o.up,
-            o.sink_lo, o.sink_up, o.trunc, o.flags, o.status, o.capacity, o.total_at);
+        tree_fp32<false><<<g, threads, smem, stream>>>(
+            d_index, warp_smem, o.row_ptr, o.col, (float *)o.lo, (float *)o.up, o.sink_lo,
+            o.sink_up, o.trunc, o.flags, o.status, o.capacity, o.total_at);
     return cudaGetLastError();
 }
 

@@ -29,7 +29,10 @@ _PREC = {"fp64": FP64_PLAIN, "fp32": FP32_SOUND, FP64_PLAIN: FP64_PLAIN, FP32_SO
 
 ENTRY_POINTS = ("impact_plan", "impact_workspace_bytes", "impact_build", "impact_count",
                 "impact_emit", "impact_free", "impact_last_error", "impact_version",
-                "impact_scan_rows_static")
+                "impact_scan_rows_static", "impact_batch_plan", "impact_batch_count",
+                "impact_batch_emit", "impact_batch_build", "impact_graph_create",
+                "impact_graph_launch", "impact_graph_result", "impact_graph_destroy",
+                "impact_batch_tune")
 
 
 class ImpactError(RuntimeError):
@@ -61,6 +64,20 @@ class _CSR(ctypes.Structure):
                 ("trunc", ctypes.c_void_p), ("row_flags", ctypes.c_void_p),
                 ("owned", ctypes.c_int), ("workspace", ctypes.c_void_p),
                 ("workspace_bytes", ctypes.c_int64)]
+
+
+class _Request(ctypes.Structure):
+    _fields_ = [("sys", ctypes.c_void_p), ("grid", ctypes.c_void_p), ("inputs", ctypes.c_void_p),
+                ("sigma", ctypes.c_void_p), ("cutoff", ctypes.c_double)]
+
+
+class _Tuning(ctypes.Structure):
+    _fields_ = [("count_warps", ctypes.c_int), ("emit_warps", ctypes.c_int),
+                ("count_smem_target", ctypes.c_int), ("emit_smem_target", ctypes.c_int),
+                ("count_k", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
 
 
 _lib = None
@@ -101,6 +118,27 @@ def load(build_if_missing: bool = True):
         lib.impact_version.argtypes = []
         lib.impact_scan_rows_static.restype = ctypes.c_int
         lib.impact_scan_rows_static.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
+        breq = [ctypes.POINTER(_Request), ctypes.c_int, ctypes.c_int, ctypes.POINTER(_Tuning)]
+        lib.impact_batch_plan.restype = ctypes.c_int
+        lib.impact_batch_plan.argtypes = breq + [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_int64)] * 2
+        for name in ("impact_batch_count", "impact_batch_emit", "impact_batch_build"):
+            f = getattr(lib, name)
+            f.restype = ctypes.c_int
+            f.argtypes = breq + [ctypes.POINTER(_CSR), ctypes.c_void_p]
+        lib.impact_graph_create.restype = ctypes.c_int
+        lib.impact_graph_create.argtypes = breq + [ctypes.POINTER(_CSR), ctypes.c_void_p,
+                                                   ctypes.POINTER(ctypes.c_void_p)]
+        lib.impact_graph_launch.restype = ctypes.c_int
+        lib.impact_graph_launch.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+        lib.impact_graph_result.restype = ctypes.c_int
+        lib.impact_graph_result.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]
+        lib.impact_graph_destroy.restype = ctypes.c_int
+        lib.impact_graph_destroy.argtypes = [ctypes.c_void_p]
+        lib.impact_batch_tune.restype = ctypes.c_int
+        lib.impact_batch_tune.argtypes = [ctypes.POINTER(_Request), ctypes.c_int, ctypes.c_int,
+                                          ctypes.POINTER(_CSR), ctypes.c_int, ctypes.c_void_p,
+                                          ctypes.POINTER(_Tuning),
+                                          ctypes.POINTER(ctypes.c_double)]
         _lib = lib
         return lib
 
@@ -322,3 +360,149 @@ def scan_rows_static(row_ptr: torch.Tensor, rows: int, stream=None) -> None:
 
 def version() -> int:
     return int(load().impact_version())
+
+
+# --------------------------------------------------------------------------
+# batches: several builds per launch (impact_batch_*), CUDA graphs, autotuner
+# --------------------------------------------------------------------------
+
+def tuning(count_warps=0, emit_warps=0, count_smem_target=0, emit_smem_target=0, count_k=0):
+    """An impact_tuning (zero fields take the library defaults)."""
+    return _Tuning(count_warps, emit_warps, count_smem_target, emit_smem_target, count_k)
+
+
+@dataclass
+class BatchCSR:
+    """Device result of a batch: one CSR over the concatenated rows."""
+    csr: CSR
+    row_offsets: np.ndarray   # int64 [count+1], host
+
+    @property
+    def count(self) -> int:
+        return int(self.row_offsets.shape[0]) - 1
+
+    def part(self, q: int) -> CSR:
+        """Build q as its own CSR (views; row_ptr rebased to start at 0)."""
+        r0, r1 = int(self.row_offsets[q]), int(self.row_offsets[q + 1])
+        c = self.csr
+        rp = c.row_ptr[r0:r1 + 1]
+        base = int(rp[0].item())
+        end = int(rp[-1].item())
+        return CSR(c.precision, rp - base, c.col[base:end], c.lo[base:end], c.up[base:end],
+                   c.sink_lo[r0:r1], c.sink_up[r0:r1], c.trunc[r0:r1], c.row_flags[r0:r1])
+
+
+class Batch:
+    """Several builds handled by one launch of each kernel (impact_batch_*).
+
+    Holds the marshalled arguments of every problem; `plan`, `count`, `emit`,
+    `build`, `tune` and `graph` call the C ABI."""
+
+    def __init__(self, problems, precision="fp32", tune=None):
+        self.problems = list(problems)
+        self.precision = precision
+        self.prec = _PREC[precision]
+        self.args = [_Args(p) for p in self.problems]
+        n = len(self.args)
+        self.reqs = (_Request * n)()
+        for q, a in enumerate(self.args):
+            self.reqs[q] = _Request(ctypes.addressof(a.sys), ctypes.addressof(a.grid),
+                                    ctypes.addressof(a.inp), a.sigma_ptr, a.cutoff)
+        self.tuning = tune
+        self.row_offsets, self.nnz_bound, self.ws_bytes = self.plan()
+        self.rows = int(self.row_offsets[-1])
+
+    def _tp(self):
+        return None if self.tuning is None else ctypes.byref(self.tuning)
+
+    def plan(self):
+        n = len(self.args)
+        offs = np.zeros(n + 1, dtype=np.int64)
+        nnz, ws = ctypes.c_int64(), ctypes.c_int64()
+        _check(load().impact_batch_plan(self.reqs, n, self.prec, self._tp(), offs.ctypes.data,
+                                        ctypes.byref(nnz), ctypes.byref(ws)))
+        return offs, nnz.value, ws.value
+
+    def alloc_workspace(self, device=None):
+        dev = device or torch.device("cuda")
+        return torch.empty(max(self.ws_bytes, 256), dtype=torch.uint8, device=dev)
+
+    def count(self, rows_buf, workspace=None, stream=None, check_unsound=True) -> int:
+        c = _csr_struct(rows_buf, workspace=workspace)
+        st = load().impact_batch_count(self.reqs, len(self.args), self.prec, self._tp(),
+                                       ctypes.byref(c), ctypes.c_void_p(_stream_handle(stream)))
+        if st != IMPACT_OK and not (st == IMPACT_ERR_UNSOUND and not check_unsound):
+            _check(st)
+        return int(c.nnz)
+
+    def emit(self, rows_buf, pairs_buf, capacity, workspace=None, stream=None):
+        c = _csr_struct(rows_buf, pairs_buf, capacity=capacity, workspace=workspace)
+        _check(load().impact_batch_emit(self.reqs, len(self.args), self.prec, self._tp(),
+                                        ctypes.byref(c), ctypes.c_void_p(_stream_handle(stream))))
+
+    def build(self, stream=None) -> BatchCSR:
+        """count, allocate exactly, emit (shared workspace)."""
+        rb = alloc_rows(self.rows)
+        ws = self.alloc_workspace()
+        nnz = self.count(rb, ws, stream)
+        pb = alloc_pairs(nnz, self.precision)
+        self.emit(rb, pb, nnz, ws, stream)
+        csr = CSR("fp32" if self.prec == FP32_SOUND else "fp64", rb["row_ptr"], pb["col"][:nnz],
+                  pb["lo"][:nnz], pb["up"][:nnz], rb["sink_lo"], rb["sink_up"], rb["trunc"],
+                  rb["row_flags"])
+        return BatchCSR(csr, self.row_offsets.copy())
+
+    def build_into(self, rows_buf, pairs_buf, capacity, workspace=None, stream=None) -> int:
+        """impact_batch_build into caller buffers; returns nnz."""
+        c = _csr_struct(rows_buf, pairs_buf, capacity=capacity, workspace=workspace)
+        _check(load().impact_batch_build(self.reqs, len(self.args), self.prec, self._tp(),
+                                         ctypes.byref(c), ctypes.c_void_p(_stream_handle(stream))))
+        return int(c.nnz)
+
+    def tune(self, rows_buf, pairs_buf=None, capacity=0, reps=3, stream=None):
+        """Run the autotuner; stores and returns (tuning, count+emit ms)."""
+        c = _csr_struct(rows_buf, pairs_buf, capacity=capacity)
+        best = _Tuning()
+        ms = ctypes.c_double()
+        _check(load().impact_batch_tune(self.reqs, len(self.args), self.prec, ctypes.byref(c),
+                                        int(reps), ctypes.c_void_p(_stream_handle(stream)),
+                                        ctypes.byref(best), ctypes.byref(ms)))
+        self.tuning = best
+        return best, ms.value
+
+    def graph(self, rows_buf, pairs_buf, capacity, workspace=None, stream=None) -> "Graph":
+        return Graph(self, rows_buf, pairs_buf, capacity, workspace, stream)
+
+
+class Graph:
+    """A captured CUDA graph of one batch's whole pipeline (impact_graph_*)."""
+
+    def __init__(self, batch: Batch, rows_buf, pairs_buf, capacity, workspace=None, stream=None):
+        self.batch = batch
+        self.bufs = (rows_buf, pairs_buf, workspace)   # kept alive with the graph
+        c = _csr_struct(rows_buf, pairs_buf, capacity=capacity, workspace=workspace)
+        h = ctypes.c_void_p()
+        _check(load().impact_graph_create(batch.reqs, len(batch.args), batch.prec, batch._tp(),
+                                          ctypes.byref(c), ctypes.c_void_p(_stream_handle(stream)),
+                                          ctypes.byref(h)))
+        self.handle = h
+
+    def launch(self, stream=None):
+        _check(load().impact_graph_launch(self.handle, ctypes.c_void_p(_stream_handle(stream))))
+
+    def result(self) -> int:
+        """Status and nnz of the last launch (synchronize its stream first)."""
+        nnz = ctypes.c_int64()
+        _check(load().impact_graph_result(self.handle, ctypes.byref(nnz)))
+        return int(nnz.value)
+
+    def close(self):
+        if self.handle:
+            load().impact_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

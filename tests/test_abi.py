@@ -37,7 +37,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_version(lib):
-    assert impact.version() == 200
+    assert impact.version() == 300
 
 
 @pytest.mark.parametrize("make", [W.robot_2d, W.room_5d, W.unicycle_3d, W.building_7d])
@@ -95,3 +95,30 @@ def test_fast_division_constants_are_exact():
         xs = xs[(xs >= 0) & (xs < 2**31)]
         q = ((xs * m) >> 32) + xs >> l
         assert np.array_equal(q, xs // N), N
+
+
+def test_batch_plan_concatenates_rows_and_bounds(lib):
+    probs = [W.robot_2d(cells_per_dim=7), W.room_5d(cells_per_dim=4),
+             W.random_linear(3, min_cells=300, max_cells=3000)]
+    b = impact.Batch(probs, "fp32")
+    want = np.concatenate([[0], np.cumsum([p.rows for p in probs])])
+    assert np.array_equal(b.row_offsets, want)
+    bounds = [impact.plan(p, "fp32")[1] for p in probs]
+    assert b.nnz_bound == sum(bounds)
+    assert b.ws_bytes >= sum(impact.workspace_bytes(p, "fp32") for p in probs) // 2
+
+
+def test_batch_plan_names_the_failing_request(lib):
+    bad = W.room_5d(cells_per_dim=4)
+    bad.sigma = np.array([0.2, 0.2, -1.0, 0.2, 0.2])
+    with pytest.raises(impact.ImpactError, match="request 1"):
+        impact.Batch([W.robot_2d(cells_per_dim=5), bad], "fp32")
+
+
+@pytest.mark.parametrize("field,value,msg", [("count_warps", 9, "warps"),
+                                              ("emit_smem_target", 100, "shared-memory"),
+                                              ("count_k", 3, "count_k")])
+def test_batch_plan_rejects_bad_tuning(lib, field, value, msg):
+    t = impact.tuning(**{field: value})
+    with pytest.raises(impact.ImpactError, match=msg):
+        impact.Batch([W.robot_2d(cells_per_dim=5)], "fp32", tune=t)
