@@ -64,6 +64,10 @@ def parse_args(argv=None):
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64-plain comparison")
     p.add_argument("--no-e2e", action="store_true", help="skip the end-to-end measurement")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    p.add_argument("--no-serve", action="store_true",
+                   help="skip the served stream (Poisson arrivals, continuous batching)")
+    p.add_argument("--no-batched", action="store_true",
+                   help="skip the batched workload (256 seeded systems, graphs, autotuner)")
     p.add_argument("--cpu-rows", type=int, default=0, help="oracle sample size (0: auto)")
     p.add_argument("--cells", type=int, default=11,
                    help="cells per dimension (11 = the benchmark workload; smaller values "
@@ -351,6 +355,20 @@ def run_ours(args, rank, world, local_rank):
         del c64
         torch.cuda.empty_cache()
 
+    if not args.no_batched and rank == 0:
+        try:
+            out["batched"] = run_batched(dev, stream)
+        except Exception as exc:
+            out["batched"] = {"value": None, "error": str(exc)[:300]}
+        torch.cuda.empty_cache()
+
+    if not args.no_serve and rank == 0:
+        try:
+            out["served"] = run_serving()
+        except Exception as exc:
+            out["served"] = {"value": None, "error": str(exc)[:300]}
+        torch.cuda.empty_cache()
+
     # end to end through the public API with the CSR read back to pinned host memory
     if not args.no_e2e:
         out["e2e"] = run_e2e(prob, nnz, dev, stream, world, steps=max(1, min(args.steps, 3)))
@@ -364,23 +382,199 @@ def run_ours(args, rank, world, local_rank):
     return out
 
 
-def run_e2e(prob, nnz, dev, stream, world, steps=3):
+BATCHED_WORKLOAD = ("256 seeded linear systems x+ = A x + B u + w (seeds 0..255): n in 2..5, "
+                    "A = 0.9 Q D Q^T, B ~ N(0, 0.3^2), 1e3..1e5 cells log-uniform on [-1,1]^n, "
+                    "2-3 input dims x 2-3 points, sigma 0.1..1 cell widths, cutoff 1e-8, "
+                    "FP32-sound")
+
+
+def run_batched(dev, stream, reps=2, cap_pairs=8_000_000_000):
+    """The batched workload: all 256 systems counted in one batch, then built
+    as groups of consecutive systems that fit `cap_pairs` of output, each group
+    one persistent launch per kernel replayed from a captured CUDA graph, with
+    launch shapes from the autotuner (timed against the default shapes)."""
+    import torch
+    from paper_2401_03555_gb300 import impact, workloads as W
+    probs = W.batched_family(256)
+    full = impact.Batch(probs, "fp32")
+    rb = impact.alloc_rows(full.rows, dev)
+    ws = full.alloc_workspace(dev)
+    t0 = time.perf_counter()
+    total = full.count(rb, ws, stream)
+    count_all_s = time.perf_counter() - t0
+    offs = torch.as_tensor(full.row_offsets, device=dev)
+    rp = rb["row_ptr"]
+    per = (rp[offs[1:]] - rp[offs[:-1]]).cpu().numpy()
+    del ws, rb, rp
+    torch.cuda.empty_cache()
+    groups, cur, acc = [], [], 0
+    for q, k in enumerate(per):
+        if cur and acc + k > cap_pairs:
+            groups.append(cur)
+            cur, acc = [], 0
+        cur.append(q)
+        acc += int(k)
+    groups.append(cur)
+    gnnz = [int(sum(per[q] for q in g)) for g in groups]
+    grows = [sum(probs[q].rows for q in g) for g in groups]
+    pb = impact.alloc_pairs(max(gnnz), "fp32", dev)
+    rbuf = impact.alloc_rows(max(grows), dev)
+
+    def make_graphs(tune):
+        batches = [impact.Batch([probs[q] for q in g], "fp32", tune=tune) for g in groups]
+        wss = [b.alloc_workspace(dev) for b in batches]
+        return [b.graph(rbuf, pb, k, w, stream) for b, k, w in zip(batches, gnnz, wss)], wss
+
+    def timed(graphs):
+        for g in graphs:                       # warm-up pass
+            g.launch(stream)
+        torch.cuda.synchronize(dev)
+        ms = []
+        for _ in range(reps):
+            s = torch.cuda.Event(enable_timing=True)
+            e = torch.cuda.Event(enable_timing=True)
+            s.record(stream)
+            for g in graphs:
+                g.launch(stream)
+            e.record(stream)
+            e.synchronize()
+            ms.append(s.elapsed_time(e))
+        for g, k in zip(graphs, gnnz):         # every group built completely
+            assert g.result() == k
+        return min(ms)
+
+    graphs, wss = make_graphs(None)
+    ms_default = timed(graphs)
+    for g in graphs:
+        g.close()
+    del graphs, wss
+    torch.cuda.empty_cache()
+    g0 = impact.Batch([probs[q] for q in groups[0]], "fp32")
+    t0 = time.perf_counter()
+    best, _ = g0.tune(rbuf, pb, gnnz[0], reps=2, stream=stream)
+    tune_s = time.perf_counter() - t0
+    graphs, wss = make_graphs(best)
+    ms_tuned = timed(graphs)
+    for g in graphs:
+        g.close()
+    del graphs, wss, pb, rbuf
+    ms = min(ms_tuned, ms_default)
+    return {"workload": BATCHED_WORKLOAD, "systems": len(probs), "rows": int(full.rows),
+            "pairs": int(total), "groups": len(groups), "group_sizes": [len(g) for g in groups],
+            "value": total / (ms_tuned / 1e3), "unit": UNIT, "ms_per_pass": ms_tuned,
+            "ms_per_pass_default_shapes": ms_default, "tuning": best.as_dict(),
+            "tune_s": round(tune_s, 2), "count_all_s": round(count_all_s, 3),
+            "gpu_launches_per_pass": 7 * len(groups),
+            "path": "impact_graph_launch per group (count + scan + emit, one persistent "
+                    "launch per kernel over every system of the group)"}
+
+
+SERVED_WORKLOAD = ("Poisson stream of 500 requests (seed 1): 7-D building (6^7 cells, inputs "
+                   "{0,1}^2, sigma 0.15, cutoff 1e-8) with probability 1/8, else a seeded "
+                   "linear system of the batched workload; arrivals at 70% of the measured "
+                   "service rate; FP32-sound, results kept on device until the client "
+                   "releases them")
+
+
+def served_requests(count=500, seed=1):
+    from paper_2401_03555_gb300 import workloads as W
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        if rng.random() < 0.125:
+            out.append(W.building_7d())
+        else:
+            out.append(W.random_linear(int(rng.integers(256))))
+    return out
+
+
+def serve_stream(srv, probs, gaps):
+    """Submit probs after the given gaps (seconds) from a client thread while a
+    collector waits for each in order and releases it; returns latencies (ms),
+    pairs and the wall time from the first submission to the last completion."""
+    import threading
+    tickets = [None] * len(probs)
+    ready = [threading.Event() for _ in probs]
+    lat = [None] * len(probs)
+    t_start = time.perf_counter()
+
+    def client():
+        t = time.perf_counter()
+        for i, (p, g) in enumerate(zip(probs, gaps)):
+            t += g
+            d = t - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            tickets[i] = srv.submit(p)
+            ready[i].set()
+
+    th = threading.Thread(target=client)
+    th.start()
+    for i in range(len(probs)):
+        ready[i].wait()
+        _, lat[i] = srv.poll(tickets[i], wait=True)
+        srv.release(tickets[i])
+    th.join()
+    wall = time.perf_counter() - t_start
+    return np.array(lat), wall
+
+
+def run_serving(count=500, seed=1, load=0.7):
+    from paper_2401_03555_gb300 import impact
+    probs = served_requests(count, seed)
+    with impact.Server("fp32", timeout_s=120.0) as srv:
+        # service rate: the same requests submitted at once (closed burst)
+        lat_b, wall_b = serve_stream(srv, probs, [0.0] * len(probs))
+        st = srv.stats()
+        pairs = st["pairs"]
+        service_s = wall_b / len(probs)
+        rate = load / service_s
+        gaps = np.random.default_rng(seed + 1000).exponential(1.0 / rate, size=len(probs))
+        gaps[0] = 0.0
+        lat, wall = serve_stream(srv, probs, gaps.tolist())
+        st2 = srv.stats()
+    pairs_stream = st2["pairs"] - pairs
+    return {"workload": SERVED_WORKLOAD, "requests": len(probs),
+            "building_requests": int(sum(1 for p in probs if p.n == 7)),
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "max_ms": float(lat.max()),
+            "value": pairs_stream / wall, "unit": UNIT, "wall_s": round(wall, 3),
+            "arrival_rate_per_s": round(rate, 2),
+            "burst": {"pairs_per_s": pairs / wall_b, "wall_s": round(wall_b, 3),
+                      "p50_ms": float(np.percentile(lat_b, 50)),
+                      "p99_ms": float(np.percentile(lat_b, 99))},
+            "groups": st2["groups"], "budget_bytes": st2["budget"],
+            "path": "impact_server_submit / impact_server_poll / impact_server_release "
+                    "(continuous batching, admission by device-memory footprint)"}
+
+
+def run_e2e(prob, nnz, dev, stream, world, steps=3, copy_streams=4, chunk_bytes=256 << 20):
+    """impact_build through the C ABI, then every output array copied into
+    pinned host memory in chunks spread over several copy streams."""
     import torch
     from paper_2401_03555_gb300 import impact
     b = impact.Builder(prob, "fp32", capacity=nnz)
     rb, pb = b.rows_buf, b.pairs_buf
-    host = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in
-            list(rb.items()) + list(pb.items())}
-    d2h = sum(v.numel() * v.element_size() for v in host.values())
+    arrays = list(rb.items()) + [(k, v[:nnz]) for k, v in pb.items()]
+    host = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in arrays}
+    chunks = []
+    for k, v in arrays:
+        step = max(1, chunk_bytes // v.element_size())
+        for a in range(0, v.numel(), step):
+            chunks.append((v[a:a + step], host[k][a:a + step]))
+    cs = [torch.cuda.Stream(dev) for _ in range(copy_streams)]
+    d2h = sum(v.numel() * v.element_size() for _, v in arrays)
     h2d = impact_blob_bytes(prob)
     times = []
     for it in range(steps + 1):
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        got = b.run(stream)
-        for k, v in list(rb.items()) + list(pb.items()):
-            host[k].copy_(v, non_blocking=True)
-        torch.cuda.current_stream(dev).synchronize()
+        got = b.run(stream)                   # synchronizes its stream at the end
+        for i, (src, dst) in enumerate(chunks):
+            with torch.cuda.stream(cs[i % copy_streams]):
+                dst.copy_(src, non_blocking=True)
+        for c in cs:
+            c.synchronize()
         dt = time.perf_counter() - t0
         if it > 0:
             times.append(dt)
@@ -388,16 +582,15 @@ def run_e2e(prob, nnz, dev, stream, world, steps=3):
     total = sum_over_ranks(float(got), world, dev)
     return {"value": total / t, "unit": UNIT, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "ms_per_step": t * 1e3,
-            "path": "impact_build (C ABI) + cudaMemcpy of row_ptr/col/lo/up/sink/trunc/flags "
-                    "into pinned host buffers, synchronized"}
+            "path": "impact_build (C ABI, tables uploaded per call) + device-to-host copies "
+                    f"of row_ptr/col/lo/up/sink/trunc/flags into pinned host memory in "
+                    f"{chunk_bytes >> 20} MiB chunks over {copy_streams} streams, synchronized"}
 
 
 def impact_blob_bytes(prob):
-    """Bytes the planner uploads per build (descriptor + tables), from impact_plan."""
+    """Bytes one build copies host -> device (descriptor and tables)."""
     from paper_2401_03555_gb300 import impact
-    rows, bound, nbytes = impact.plan(prob, "fp32")
-    per_pair = 12
-    return int(nbytes - bound * per_pair - (rows + 1) * 8 - rows * 28)
+    return int(impact.Batch([prob], "fp32").upload_bytes)
 
 
 # --------------------------------------------------------------------------

@@ -245,12 +245,15 @@ typedef struct {
 /*
  * impact_batch_plan -- host-only sizing of a batch of `count` (1..65536)
  * builds. Writes row_offsets[count+1] (host array, may be NULL), the summed
- * nnz bound and the workspace bytes of the batch. `tuning` may be NULL.
+ * nnz bound, the workspace bytes of the batch and the bytes each count or
+ * build call copies host -> device (descriptors and tables). `tuning` may be
+ * NULL; so may every output pointer.
  * Errors: IMPACT_ERR_ARG (the message names the failing request).
  */
 impact_status impact_batch_plan(const impact_request *reqs, int count, impact_precision precision,
                                 const impact_tuning *tuning, int64_t *row_offsets,
-                                int64_t *nnz_upper_bound, int64_t *workspace_bytes);
+                                int64_t *nnz_upper_bound, int64_t *workspace_bytes,
+                                int64_t *upload_bytes);
 
 /* impact_count / impact_emit / impact_build for a batch: the same contracts
  * with `out` covering every row of the batch (out->rows = total rows). */
@@ -296,6 +299,71 @@ impact_status impact_graph_destroy(impact_graph *graph);
 impact_status impact_batch_tune(const impact_request *reqs, int count,
                                 impact_precision precision, impact_csr *out, int reps,
                                 void *stream, impact_tuning *best, double *best_ms);
+
+/* ------------------------------------------------------------------------
+ * Serving: a request loop with continuous batching. Builds are submitted from
+ * any host thread and run asynchronously: a scheduler thread admits waiting
+ * requests in arrival order while their workspace and row arrays fit the
+ * device-memory budget, runs them together as one batch count, emits each
+ * counted group as soon as its exact output fits the budget, and overlaps
+ * groups on a pool of streams, so requests that arrive while others are on
+ * the device join the next group. Results stay on the device until released.
+ * Each result is bitwise the same alone and in any mix (same kernels and
+ * launch shapes per row). The paper has no counterpart (it builds one
+ * abstraction per program run).
+ * ------------------------------------------------------------------------ */
+
+typedef struct {
+    int64_t memory_budget;       /* device bytes for requests in flight and kept
+                                    results (0: 80% of free memory at creation) */
+    int max_batch;               /* builds per group (0: 64)                  */
+    int64_t max_group_rows;      /* rows per group, past its first build
+                                    (0: 2^22)                                 */
+    int streams;                 /* streams groups overlap on, 0..8 (0: 2)    */
+    impact_precision precision;
+} impact_server_config;
+
+typedef struct {
+    int64_t completed;           /* requests finished                          */
+    int64_t pairs;               /* pairs of the finished requests             */
+    int64_t groups;              /* groups launched                            */
+    int64_t waiting;             /* requests not yet admitted                  */
+    int64_t bytes_in_use;        /* device bytes held now                      */
+    int64_t budget;              /* the memory budget in force                 */
+} impact_server_stats_t;
+
+typedef struct impact_server impact_server;
+
+/* Starts the scheduler thread on the current device. */
+impact_status impact_server_create(const impact_server_config *config, impact_server **server);
+
+/* Checks the request (host only), copies its host arrays and queues it;
+ * *ticket identifies it. Errors: IMPACT_ERR_ARG. */
+impact_status impact_server_submit(impact_server *server, const impact_request *request,
+                                   int64_t *ticket);
+
+/*
+ * impact_server_poll -- *done = 1 once the request finished. wait_ms > 0
+ * waits up to that many milliseconds for it (< 0: without limit, 0: not at
+ * all); *done = 0 when it is still in flight. Once done, *latency_ms (may be
+ * NULL) is the time from submission to completion, and *result (may be NULL) describes the device result: rows,
+ * nnz, row_ptr (rows+1 entries whose values index col/lo/up directly; the
+ * first is not necessarily 0), col/lo/up, sink_lo/sink_up/trunc/row_flags.
+ * The arrays belong to the server (owned = 0) and stay valid until
+ * impact_server_release. Returns the request's status (IMPACT_ERR_OOM when it
+ * can never fit the budget).
+ */
+impact_status impact_server_poll(impact_server *server, int64_t ticket, int wait_ms, int *done,
+                                 impact_csr *result, double *latency_ms);
+
+/* Frees a finished request's result (its group's memory goes once every
+ * request of the group is released). Errors: IMPACT_ERR_ARG when in flight. */
+impact_status impact_server_release(impact_server *server, int64_t ticket);
+
+impact_status impact_server_stats(impact_server *server, impact_server_stats_t *stats);
+
+/* Waits for every submitted request, then frees everything. */
+impact_status impact_server_destroy(impact_server *server);
 
 /* Release library-owned arrays of a result (no-op for caller-owned ones). */
 impact_status impact_free(impact_csr *out);

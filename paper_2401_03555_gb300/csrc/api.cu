@@ -19,6 +19,7 @@
 #include "../../include/impact.h"
 #include "impact_desc.h"
 #include "kernels.h"
+#include "pipeline.h"
 #include "plan.h"
 
 namespace {
@@ -34,9 +35,6 @@ impact_status fail(impact_status s, const std::string &msg)
 void set_last_error(const std::string &msg) { g_last_error = msg; }
 }  // namespace impact
 
-using impact::fail;
-using impact::Plan;
-using impact::Tuning;
 
 #define CK(expr)                                                                              \
     do {                                                                                      \
@@ -47,7 +45,7 @@ using impact::Tuning;
         }                                                                                     \
     } while (0)
 
-namespace {
+namespace impact {
 
 constexpr int kBatchMax = 1 << 16;   // builds per batch
 
@@ -81,18 +79,6 @@ impact_status tuning_of(const impact_tuning *t, Tuning &T)
 // batches
 // ---------------------------------------------------------------------------
 
-struct Batch {
-    std::vector<Plan> plans;
-    std::vector<const double *> images;   // per build: device images (IMAGES kind)
-    std::vector<int64_t> row_begin;       // [count + 1] first global row of each build
-    std::vector<int64_t> item_begin;      // [count + 1] first (row, dim) item
-    int64_t rows = 0, items = 0, nnz_bound = 0;
-    int prec = 0;
-    int smem_count = 0, smem_emit = 0;    // largest per-warp bytes of the walk
-    Tuning tune;
-    uint64_t hash = 0;
-    int count() const { return (int)plans.size(); }
-};
 
 impact_status make_batch(const impact_request *reqs, int count, impact_precision precision,
                          const impact_tuning *tuning, Batch &B)
@@ -135,16 +121,6 @@ impact_status make_batch(const impact_request *reqs, int count, impact_precision
     return IMPACT_OK;
 }
 
-// Offsets (bytes, 256-aligned) of everything in the device workspace.
-struct BatchLayout {
-    size_t index = 0, row_begin = 0, item_begin = 0, descs = 0, recs = 0;
-    std::vector<size_t> tables;            // per build: its descriptor and tables
-    std::vector<impact::TableLayout> tl;
-    size_t upload_end = 0;                 // [0, upload_end) is copied from the host
-    size_t status = 0, counter = 0, scan = 0;
-    std::vector<size_t> rec;               // per build: FP32 per-row records
-    size_t total = 0;
-};
 
 BatchLayout batch_layout(const Batch &B)
 {
@@ -180,20 +156,6 @@ BatchLayout batch_layout(const Batch &B)
     return L;
 }
 
-// The device workspace of one call.
-struct Work {
-    unsigned char *base = nullptr;
-    BatchLayout L;
-    bool owned = false;
-    const BatchIndex *index() const { return (const BatchIndex *)(base + L.index); }
-    uint32_t *status() const { return (uint32_t *)(base + L.status); }
-    unsigned long long *counter() const { return (unsigned long long *)(base + L.counter); }
-    int64_t *scan() const { return (int64_t *)(base + L.scan); }
-    const ImpactDesc *desc(int q) const
-    {
-        return (const ImpactDesc *)(base + L.tables[q] + L.tl[q].desc);
-    }
-};
 
 std::mutex g_ws_mu;
 std::unordered_map<const void *, uint64_t> g_ws_tag;   // caller workspace -> batch it holds
@@ -509,7 +471,9 @@ impact_status check_request_ptrs(const impact_request *reqs, int count)
     return IMPACT_OK;
 }
 
-}  // namespace
+}  // namespace impact
+
+using namespace impact;
 
 // A captured pipeline: count, scan and emit of one batch into fixed caller
 // buffers, replayed by impact_graph_launch.
@@ -592,7 +556,8 @@ impact_status impact_build(const impact_system *sys, const impact_grid *grid,
 
 impact_status impact_batch_plan(const impact_request *reqs, int count, impact_precision precision,
                                 const impact_tuning *tuning, int64_t *row_offsets,
-                                int64_t *nnz_upper_bound, int64_t *workspace_bytes)
+                                int64_t *nnz_upper_bound, int64_t *workspace_bytes,
+                                int64_t *upload_bytes)
 {
     impact_status s = check_request_ptrs(reqs, count);
     if (s != IMPACT_OK) return s;
@@ -600,7 +565,11 @@ impact_status impact_batch_plan(const impact_request *reqs, int count, impact_pr
     if ((s = make_batch(reqs, count, precision, tuning, B)) != IMPACT_OK) return s;
     if (row_offsets) memcpy(row_offsets, B.row_begin.data(), (size_t)(count + 1) * 8);
     if (nnz_upper_bound) *nnz_upper_bound = B.nnz_bound;
-    if (workspace_bytes) *workspace_bytes = (int64_t)batch_layout(B).total;
+    if (workspace_bytes || upload_bytes) {
+        const BatchLayout L = batch_layout(B);
+        if (workspace_bytes) *workspace_bytes = (int64_t)L.total;
+        if (upload_bytes) *upload_bytes = (int64_t)L.upload_end;
+    }
     return IMPACT_OK;
 }
 

@@ -1,0 +1,72 @@
+// pipeline.h -- a batch of builds, its device workspace and the count /
+// emit pipeline (api.cu), shared with the serving runtime (server.cu);
+// internal.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/impact.h"
+#include "impact_desc.h"
+#include "kernels.h"
+#include "plan.h"
+
+namespace impact {
+
+struct Batch {
+    std::vector<Plan> plans;
+    std::vector<const double *> images;   // per build: device images (IMAGES kind)
+    std::vector<int64_t> row_begin;       // [count + 1] first global row of each build
+    std::vector<int64_t> item_begin;      // [count + 1] first (row, dim) item
+    int64_t rows = 0, items = 0, nnz_bound = 0;
+    int prec = 0;
+    int smem_count = 0, smem_emit = 0;    // largest per-warp bytes of the walk
+    Tuning tune;
+    uint64_t hash = 0;
+    int count() const { return (int)plans.size(); }
+};
+
+impact_status make_batch(const impact_request *reqs, int count, impact_precision precision,
+                         const impact_tuning *tuning, Batch &B);
+
+// Offsets (bytes, 256-aligned) of everything in the device workspace.
+struct BatchLayout {
+    size_t index = 0, row_begin = 0, item_begin = 0, descs = 0, recs = 0;
+    std::vector<size_t> tables;            // per build: its descriptor and tables
+    std::vector<impact::TableLayout> tl;
+    size_t upload_end = 0;                 // [0, upload_end) is copied from the host
+    size_t status = 0, counter = 0, scan = 0;
+    std::vector<size_t> rec;               // per build: FP32 per-row records
+    size_t total = 0;
+};
+
+BatchLayout batch_layout(const Batch &B);
+
+// The device workspace of one call.
+struct Work {
+    unsigned char *base = nullptr;
+    BatchLayout L;
+    bool owned = false;
+    const BatchIndex *index() const { return (const BatchIndex *)(base + L.index); }
+    uint32_t *status() const { return (uint32_t *)(base + L.status); }
+    unsigned long long *counter() const { return (unsigned long long *)(base + L.counter); }
+    int64_t *scan() const { return (int64_t *)(base + L.scan); }
+    const ImpactDesc *desc(int q) const
+    {
+        return (const ImpactDesc *)(base + L.tables[q] + L.tl[q].desc);
+    }
+};
+
+// Copies the batch index, the descriptors and the tables into W (stream-ordered).
+impact_status upload(const Batch &B, Work &W, cudaStream_t st);
+// count pass + row-pointer scan into out's row arrays.
+impact_status run_count(const Batch &B, const Work &W, const impact_csr *out, cudaStream_t st);
+// emit pass into out's pair arrays (`tables_ready`: W holds B's FP32 records).
+impact_status run_emit(const Batch &B, const Work &W, const impact_csr *out, int64_t capacity,
+                       bool tables_ready, cudaStream_t st);
+// Maps the device status word of a finished pipeline to a status code.
+impact_status status_result(uint32_t status);
+void configure_pool_once();
+
+}  // namespace impact

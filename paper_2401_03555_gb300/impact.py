@@ -32,7 +32,9 @@ ENTRY_POINTS = ("impact_plan", "impact_workspace_bytes", "impact_build", "impact
                 "impact_scan_rows_static", "impact_batch_plan", "impact_batch_count",
                 "impact_batch_emit", "impact_batch_build", "impact_graph_create",
                 "impact_graph_launch", "impact_graph_result", "impact_graph_destroy",
-                "impact_batch_tune")
+                "impact_batch_tune", "impact_server_create", "impact_server_submit",
+                "impact_server_poll", "impact_server_release", "impact_server_stats",
+                "impact_server_destroy")
 
 
 class ImpactError(RuntimeError):
@@ -80,6 +82,18 @@ class _Tuning(ctypes.Structure):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
 
 
+class _ServerConfig(ctypes.Structure):
+    _fields_ = [("memory_budget", ctypes.c_int64), ("max_batch", ctypes.c_int),
+                ("max_group_rows", ctypes.c_int64), ("streams", ctypes.c_int),
+                ("precision", ctypes.c_int)]
+
+
+class _ServerStats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_int64), ("pairs", ctypes.c_int64),
+                ("groups", ctypes.c_int64), ("waiting", ctypes.c_int64),
+                ("bytes_in_use", ctypes.c_int64), ("budget", ctypes.c_int64)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -120,7 +134,7 @@ def load(build_if_missing: bool = True):
         lib.impact_scan_rows_static.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
         breq = [ctypes.POINTER(_Request), ctypes.c_int, ctypes.c_int, ctypes.POINTER(_Tuning)]
         lib.impact_batch_plan.restype = ctypes.c_int
-        lib.impact_batch_plan.argtypes = breq + [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_int64)] * 2
+        lib.impact_batch_plan.argtypes = breq + [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_int64)] * 3
         for name in ("impact_batch_count", "impact_batch_emit", "impact_batch_build"):
             f = getattr(lib, name)
             f.restype = ctypes.c_int
@@ -139,6 +153,22 @@ def load(build_if_missing: bool = True):
                                           ctypes.POINTER(_CSR), ctypes.c_int, ctypes.c_void_p,
                                           ctypes.POINTER(_Tuning),
                                           ctypes.POINTER(ctypes.c_double)]
+        lib.impact_server_create.restype = ctypes.c_int
+        lib.impact_server_create.argtypes = [ctypes.POINTER(_ServerConfig),
+                                             ctypes.POINTER(ctypes.c_void_p)]
+        lib.impact_server_submit.restype = ctypes.c_int
+        lib.impact_server_submit.argtypes = [ctypes.c_void_p, ctypes.POINTER(_Request),
+                                             ctypes.POINTER(ctypes.c_int64)]
+        lib.impact_server_poll.restype = ctypes.c_int
+        lib.impact_server_poll.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
+                                           ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_CSR),
+                                           ctypes.POINTER(ctypes.c_double)]
+        lib.impact_server_release.restype = ctypes.c_int
+        lib.impact_server_release.argtypes = [ctypes.c_void_p, ctypes.c_int64]
+        lib.impact_server_stats.restype = ctypes.c_int
+        lib.impact_server_stats.argtypes = [ctypes.c_void_p, ctypes.POINTER(_ServerStats)]
+        lib.impact_server_destroy.restype = ctypes.c_int
+        lib.impact_server_destroy.argtypes = [ctypes.c_void_p]
         _lib = lib
         return lib
 
@@ -409,7 +439,7 @@ class Batch:
             self.reqs[q] = _Request(ctypes.addressof(a.sys), ctypes.addressof(a.grid),
                                     ctypes.addressof(a.inp), a.sigma_ptr, a.cutoff)
         self.tuning = tune
-        self.row_offsets, self.nnz_bound, self.ws_bytes = self.plan()
+        self.row_offsets, self.nnz_bound, self.ws_bytes, self.upload_bytes = self.plan()
         self.rows = int(self.row_offsets[-1])
 
     def _tp(self):
@@ -418,10 +448,10 @@ class Batch:
     def plan(self):
         n = len(self.args)
         offs = np.zeros(n + 1, dtype=np.int64)
-        nnz, ws = ctypes.c_int64(), ctypes.c_int64()
+        nnz, ws, up = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
         _check(load().impact_batch_plan(self.reqs, n, self.prec, self._tp(), offs.ctypes.data,
-                                        ctypes.byref(nnz), ctypes.byref(ws)))
-        return offs, nnz.value, ws.value
+                                        ctypes.byref(nnz), ctypes.byref(ws), ctypes.byref(up)))
+        return offs, nnz.value, ws.value, up.value
 
     def alloc_workspace(self, device=None):
         dev = device or torch.device("cuda")
@@ -506,3 +536,110 @@ class Graph:
             self.close()
         except Exception:
             pass
+
+
+# --------------------------------------------------------------------------
+# serving (impact_server_*)
+# --------------------------------------------------------------------------
+
+class _DeviceArray:
+    """A zero-copy view of server-owned device memory (CUDA array interface)."""
+
+    def __init__(self, ptr, count, typestr):
+        self.__cuda_array_interface__ = {"shape": (int(count),), "typestr": typestr,
+                                         "data": (int(ptr) if count else 0, False),
+                                         "version": 3, "strides": None}
+
+
+def _view(ptr, count, dtype):
+    typestr = {torch.int64: "<i8", torch.int32: "<i4", torch.float32: "<f4",
+               torch.float64: "<f8"}[dtype]
+    if count == 0:
+        return torch.empty(0, dtype=dtype, device="cuda")
+    return torch.as_tensor(_DeviceArray(ptr, count, typestr), device="cuda")
+
+
+class Server:
+    """Continuous-batching request loop (impact_server_*): submit builds as
+    they arrive, poll for their device results, release them when done."""
+
+    def __init__(self, precision="fp32", memory_budget=0, max_batch=0, streams=0,
+                 max_group_rows=0, timeout_s=600.0):
+        self.precision = precision
+        self.prec = _PREC[precision]
+        self.timeout_ms = int(timeout_s * 1000)
+        cfg = _ServerConfig(int(memory_budget), int(max_batch), int(max_group_rows), int(streams),
+                            self.prec)
+        h = ctypes.c_void_p()
+        _check(load().impact_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self.handle = h
+        self._args = {}
+
+    def submit(self, prob) -> int:
+        a = _Args(prob)
+        req = _Request(ctypes.addressof(a.sys), ctypes.addressof(a.grid), ctypes.addressof(a.inp),
+                       a.sigma_ptr, a.cutoff)
+        t = ctypes.c_int64()
+        _check(load().impact_server_submit(self.handle, ctypes.byref(req), ctypes.byref(t)))
+        if prob.kind == 2:
+            self._args[t.value] = a   # device images must outlive the request
+        return int(t.value)
+
+    def poll(self, ticket: int, wait: bool = False):
+        """(done, latency_ms); raises if the request failed, TimeoutError if
+        `wait` and it did not finish within the server's timeout."""
+        done = ctypes.c_int()
+        lat = ctypes.c_double()
+        _check(load().impact_server_poll(self.handle, int(ticket),
+                                         self.timeout_ms if wait else 0, ctypes.byref(done),
+                                         None, ctypes.byref(lat)))
+        if wait and not done.value:
+            raise TimeoutError(f"request {ticket} still in flight after {self.timeout_ms} ms")
+        return bool(done.value), (lat.value if done.value else None)
+
+    def result(self, ticket: int) -> CSR:
+        """Zero-copy views of a finished request's device result (row_ptr
+        rebased to 0 as a new tensor); valid until release(ticket)."""
+        done = ctypes.c_int()
+        c = _CSR()
+        _check(load().impact_server_poll(self.handle, int(ticket), self.timeout_ms,
+                                         ctypes.byref(done), ctypes.byref(c), None))
+        if not done.value:
+            raise TimeoutError(f"request {ticket} still in flight after {self.timeout_ms} ms")
+        rows, nnz = int(c.rows), int(c.nnz)
+        vt = torch.float32 if self.prec == FP32_SOUND else torch.float64
+        rp = _view(c.row_ptr, rows + 1, torch.int64)
+        base = int(rp[0].item())
+        col_all = _view(c.col, base + nnz, torch.int32)
+        lo_all = _view(c.lo, base + nnz, vt)
+        up_all = _view(c.up, base + nnz, vt)
+        return CSR(self.precision, rp - base, col_all[base:], lo_all[base:], up_all[base:],
+                   _view(c.sink_lo, rows, torch.float64), _view(c.sink_up, rows, torch.float64),
+                   _view(c.trunc, rows, torch.float64), _view(c.row_flags, rows, torch.int32))
+
+    def release(self, ticket: int):
+        _check(load().impact_server_release(self.handle, int(ticket)))
+        self._args.pop(int(ticket), None)
+
+    def stats(self) -> dict:
+        st = _ServerStats()
+        _check(load().impact_server_stats(self.handle, ctypes.byref(st)))
+        return {k: int(getattr(st, k)) for k, _ in st._fields_}
+
+    def close(self):
+        if self.handle:
+            load().impact_server_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
