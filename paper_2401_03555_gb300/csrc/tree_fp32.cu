@@ -510,6 +510,22 @@ __device__ __forceinline__ void run_of(const Smem &S, int dim, float P, int &l, 
     l = pk + 1 - cl;
 }
 
+// The same run, moved from the previous run [l, r) of the dimension under
+// another product: the boundaries only step outwards while they still pass
+// and inwards while they fail (T is monotone on each side of the peak), so a
+// sequence of products that rises and falls costs O(window) steps in all.
+// An empty run is l = r = pk + 1.
+__device__ __forceinline__ void run_step(const Smem &S, int dim, float P, int &l, int &r)
+{
+    const int off = S.h->toff[dim], pk = S.h->pk[dim], tw = S.h->tw[dim];
+    const float *T = S.T + off;
+    while (l > 0 && T[l - 1] <= P) --l;
+    while (l <= pk && T[l] > P) ++l;
+    while (r < tw && T[r] <= P) ++r;
+    while (r > pk + 1 && T[r - 1] > P) --r;
+    if (l > pk) r = pk + 1;
+}
+
 // Upper bound of the sum of U over the window of `dim` outside [l, l + c):
 // a prefix sum plus a suffix sum, both rounded up (no cancellation).
 __device__ __forceinline__ float outside_sum(const Smem &S, int dim, int l, int c)
@@ -675,13 +691,15 @@ tree_fp32(const BatchIndex *__restrict__ B, int warp_smem, int64_t *__restrict__
             if (act) run_of(S, dm, P, lm, cm);
             if (act) {
                 drop += fix_up(__fmul_ru(__fmul_ru(P, outside_sum(S, dm, lm, cm)), H.swr[dm]));
+                // the middle run's products rise to its peak and fall after it:
+                // the leaf runs follow them incrementally
+                int l1 = H.pk[dl] + 1, r1 = l1;
                 for (int i = 0; i < cm; ++i) {
                     const int m = lm + i;
                     const float P2 = __fmul_ru(P, S.U[offm + m]);
                     const float Pl2 = __fmul_rd(Pl, S.L[offm + m]);
-                    int l1, c1;
-                    run_of(S, dl, P2, l1, c1);
-                    leaf_sums(dl, P2, Pl2, l1, c1);
+                    run_step(S, dl, P2, l1, r1);
+                    leaf_sums(dl, P2, Pl2, l1, r1 - l1);
                 }
             }
         };

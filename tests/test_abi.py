@@ -90,8 +90,10 @@ def test_fast_division_constants_are_exact():
         while (1 << l) < N:
             l += 1
         m = ((((1 << l) - N) << 32) // N + 1) & 0xffffffff
-        xs = np.concatenate([rng.integers(0, 2**31, 2000), np.arange(0, 3 * N + 5),
-                             [2**31 - 1, 2**31 - N, (2**31 - 1) // N * N]]).astype(np.int64)
+        ks = np.unique(np.concatenate([np.arange(0, 64), rng.integers(0, (2**31 - 1) // N + 1, 64)]))
+        near = (ks[:, None] * N + np.arange(-2, 3)[None, :]).ravel()   # around multiples of N
+        xs = np.concatenate([rng.integers(0, 2**31, 2000), np.arange(0, min(3 * N + 5, 4096)),
+                             near, [2**31 - 1, 2**31 - N, (2**31 - 1) // N * N]]).astype(np.int64)
         xs = xs[(xs >= 0) & (xs < 2**31)]
         q = ((xs * m) >> 32) + xs >> l
         assert np.array_equal(q, xs // N), N
