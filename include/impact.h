@@ -226,8 +226,9 @@ typedef struct {
 
 /*
  * Launch shapes of the FP32-sound prefix-tree walk (impact_batch_tune picks
- * them). Zero fields take the defaults: 4 warps per block, 10240 bytes of
- * shared memory per warp for the node rings, count_k chosen per build.
+ * them). Zero fields take the defaults: 4 warps per block, 6144 (count) and
+ * 8192 (emit) bytes of shared memory per warp for the node rings, count_k
+ * chosen per build.
  *   count_warps, emit_warps              warps per block, 1..8
  *   count_smem_target, emit_smem_target  bytes per warp, 2048..49152
  *   count_k                              count pass: dimensions a lane walks
@@ -288,7 +289,7 @@ impact_status impact_graph_destroy(impact_graph *graph);
 
 /*
  * impact_batch_tune -- the autotuner: times the FP32 count pass over warps
- * per block {2,4,8} x shared-memory targets {6144,10240,16384} x count_k
+ * per block {2,4,8} x shared-memory targets {4096,6144,8192,12288} x count_k
  * {1,2}, then the emit pass over warps x targets with the best count shape,
  * each the best of `reps` runs, on this batch, and writes the fastest shape
  * to *best and its count + emit milliseconds to *best_ms (may be NULL).

@@ -758,7 +758,7 @@ impact_status impact_batch_tune(const impact_request *reqs, int count,
         return IMPACT_OK;
     };
     const int warps[3] = {2, 4, 8};
-    const int smem[3] = {6144, 10240, 16384};
+    const int smem[4] = {4096, 6144, 8192, 12288};
     impact_tuning cur;
     memset(&cur, 0, sizeof(cur));
     double best_count = 1e30, best_emit = 1e30;
@@ -802,7 +802,7 @@ impact_status impact_batch_tune(const impact_request *reqs, int count,
     if (r2 != IMPACT_OK) return r2;
     if (best_count >= 1e30) return fail(IMPACT_ERR_ARG, "no launch shape ran this batch");
     if (tb.emit_warps == 0) tb.emit_warps = IMPACT_TREE_WARPS;
-    if (tb.emit_smem_target == 0) tb.emit_smem_target = IMPACT_TREE_SMEM_TARGET;
+    if (tb.emit_smem_target == 0) tb.emit_smem_target = IMPACT_TREE_SMEM_EMIT;
     *best = tb;
     if (best_ms) *best_ms = best_count + (can_emit ? best_emit : 0.0);
     return IMPACT_OK;

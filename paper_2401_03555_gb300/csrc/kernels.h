@@ -12,7 +12,8 @@
 #define IMPACT_TSUM_MAX 256               // FP32 path: factor entries per row record
 #define IMPACT_TREE_SEG 512               // FP32 path: pairs staged per leaf batch
 #define IMPACT_TREE_HDR 256               // FP32 path: per-row scalars per warp (bytes)
-#define IMPACT_TREE_SMEM_TARGET 10240     // FP32 path: per-warp shared memory aimed for (default)
+#define IMPACT_TREE_SMEM_COUNT 6144       // FP32 path: per-warp shared memory aimed for, count (default)
+#define IMPACT_TREE_SMEM_EMIT 8192        // FP32 path: per-warp shared memory aimed for, emit (default)
 #define IMPACT_TREE_WARPS 4               // FP32 path: warps per block of the walk (default)
 #define IMPACT_TREE_WARPS_MAX 8
 #define IMPACT_STATUS_TABLE_OVERFLOW 0x1u // some row's windows exceeded IMPACT_TABLE_MAX

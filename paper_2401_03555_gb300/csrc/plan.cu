@@ -366,8 +366,9 @@ impact_status make_plan(const impact_system *sys, const impact_grid *grid,
         // spread over the lanes for coalesced stores). Levels 0..Lp (Lp =
         // n - 1 - K) keep a ring of nodes each, a power of two: level 0 holds
         // the root's children, the deepest level room for a full batch plus
-        // one parent's children; rings shrink from the largest while a warp's
-        // shared memory exceeds the target.
+        // one parent's children; rings start large (fewer, fuller steps) and
+        // shrink from the largest while a warp's shared memory exceeds the
+        // target (more warps per SM).
         D.tree_k = T.count_k == 1 || T.count_k == 2
                        ? (n >= 3 ? T.count_k : 1)
                        : ((n >= 3 && D.dim[n - 1].wcap <= 16) ? 2 : 1);
@@ -385,7 +386,8 @@ impact_status make_plan(const impact_system *sys, const impact_grid *grid,
                 const int w = D.dim[k].wcap;
                 const int need = (k == Lp) ? 32 + w : w;
                 lmin[k] = log2_ceil(need);
-                lg[k] = (k == 0 && k < Lp) ? lmin[k] : std::max(lmin[k], log2_ceil(k == Lp ? 128 : 64));
+                lg[k] = (k == 0 && k < Lp) ? lmin[k]
+                                           : std::max(lmin[k], log2_ceil(k == Lp ? 1024 : 512));
             }
             auto bytes = [&]() {
                 int pool = 0;

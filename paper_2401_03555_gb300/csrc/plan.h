@@ -20,8 +20,8 @@ impact_status fail(impact_status s, const std::string &msg);
 struct Tuning {
     int count_warps = IMPACT_TREE_WARPS;
     int emit_warps = IMPACT_TREE_WARPS;
-    int count_smem = IMPACT_TREE_SMEM_TARGET;
-    int emit_smem = IMPACT_TREE_SMEM_TARGET;
+    int count_smem = IMPACT_TREE_SMEM_COUNT;
+    int emit_smem = IMPACT_TREE_SMEM_EMIT;
     int count_k = 0;   // 0: chosen per problem
 };
 

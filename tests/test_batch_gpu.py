@@ -119,8 +119,8 @@ def test_autotuner_returns_a_listed_shape():
     best, ms = b.tune(rb, pb, nnz, reps=2)
     d = best.as_dict()
     assert d["count_warps"] in (2, 4, 8) and d["emit_warps"] in (2, 4, 8)
-    assert d["count_smem_target"] in (6144, 10240, 16384)
-    assert d["emit_smem_target"] in (6144, 10240, 16384)
+    assert d["count_smem_target"] in (4096, 6144, 8192, 12288)
+    assert d["emit_smem_target"] in (4096, 6144, 8192, 12288)
     assert d["count_k"] in (1, 2) and ms > 0
     assert_same(impact.Batch(probs, "fp32", tune=best).build().csr, ref.csr, "tuned shape")
 
