@@ -91,7 +91,7 @@ impact_status make_batch(const impact_request *reqs, int count, impact_precision
     B.plans.assign(count, Plan());
     B.images.assign(count, nullptr);
     B.row_begin.assign(count + 1, 0);
-    B.item_begin.assign(count + 1, 0);
+    B.unit_begin.assign(count + 1, 0);
     B.prec = precision;
     uint64_t h = 1469598103934665603ull;
     for (int q = 0; q < count; ++q) {
@@ -105,7 +105,8 @@ impact_status make_batch(const impact_request *reqs, int count, impact_precision
         const Plan &P = B.plans[q];
         B.images[q] = r.sys->dev_images;
         B.row_begin[q + 1] = B.row_begin[q] + P.rows;
-        B.item_begin[q + 1] = B.item_begin[q] + P.rows * P.desc.n;
+        const int64_t rpw = 32 / P.desc.n;
+        B.unit_begin[q + 1] = B.unit_begin[q] + (P.rows + rpw - 1) / rpw;
         B.nnz_bound = (B.nnz_bound > INT64_MAX - P.nnz_bound) ? INT64_MAX
                                                               : B.nnz_bound + P.nnz_bound;
         B.smem_count = std::max(B.smem_count, P.desc.tree_smem_count);
@@ -113,7 +114,7 @@ impact_status make_batch(const impact_request *reqs, int count, impact_precision
         h = mix(h, P.hash);
     }
     B.rows = B.row_begin[count];
-    B.items = B.item_begin[count];
+    B.units = B.unit_begin[count];
     h = mix(h, (uint64_t)B.tune.count_warps | ((uint64_t)B.tune.emit_warps << 8) |
                    ((uint64_t)B.tune.count_k << 16));
     h = mix(h, (uint64_t)B.tune.count_smem | ((uint64_t)B.tune.emit_smem << 32));
@@ -134,7 +135,7 @@ BatchLayout batch_layout(const Batch &B)
     const int count = B.count();
     L.index = put(sizeof(BatchIndex));
     L.row_begin = put((size_t)(count + 1) * 8);
-    L.item_begin = put((size_t)(count + 1) * 8);
+    L.unit_begin = put((size_t)(count + 1) * 8);
     L.descs = put((size_t)count * 8);
     L.recs = put((size_t)count * 8);
     L.tables.resize(count);
@@ -209,15 +210,15 @@ impact_status upload(const Batch &B, Work &W, cudaStream_t st)
     memset(&bi, 0, sizeof(bi));
     bi.count = count;
     bi.rows = B.rows;
-    bi.items = B.items;
+    bi.units = B.units;
     bi.row_begin = (const int64_t *)(W.base + L.row_begin);
-    bi.item_begin = (const int64_t *)(W.base + L.item_begin);
+    bi.unit_begin = (const int64_t *)(W.base + L.unit_begin);
     bi.desc = (const ImpactDesc *const *)(W.base + L.descs);
     bi.rec = (unsigned char *const *)(W.base + L.recs);
     bi.next_row = W.counter();
     memcpy(host.data() + L.index, &bi, sizeof(bi));
     memcpy(host.data() + L.row_begin, B.row_begin.data(), (size_t)(count + 1) * 8);
-    memcpy(host.data() + L.item_begin, B.item_begin.data(), (size_t)(count + 1) * 8);
+    memcpy(host.data() + L.unit_begin, B.unit_begin.data(), (size_t)(count + 1) * 8);
     for (int q = 0; q < count; ++q) {
         const ImpactDesc *d = W.desc(q);
         unsigned char *r = B.prec == PREC_FP32_SOUND ? W.base + L.rec[q] : nullptr;
@@ -300,9 +301,8 @@ impact_status run_count(const Batch &B, const Work &W, const impact_csr *out, cu
                          out->trunc, out->row_flags, W.status(), -1, B.rows};
     if (B.prec == PREC_FP32_SOUND) {
         CK(cudaMemsetAsync(W.counter(), 0, 16, st));
-        CK(impact::launch_setup_fp32(W.index(), B.items, W.status(), st));
-        CK(impact::launch_prep_fp32(W.index(), B.items, out->sink_lo, out->sink_up, out->trunc,
-                                    st));
+        CK(impact::launch_setup_fp32(W.index(), B.units, W.status(), out->sink_lo, out->sink_up,
+                                     out->trunc, st));
         CK(impact::launch_tree_fp32(W.index(), B.rows, B.smem_count, B.tune.count_warps, false, o,
                                     st));
     } else {
@@ -322,8 +322,8 @@ impact_status run_emit(const Batch &B, const Work &W, const impact_csr *out, int
                          nullptr, W.status(), capacity, B.rows};
     if (B.prec == PREC_FP32_SOUND) {
         if (!tables_ready) {   // rebuild the records; the row outputs stay as counted
-            CK(impact::launch_setup_fp32(W.index(), B.items, W.status(), st));
-            CK(impact::launch_prep_fp32(W.index(), B.items, nullptr, nullptr, nullptr, st));
+            CK(impact::launch_setup_fp32(W.index(), B.units, W.status(), nullptr, nullptr, nullptr,
+                                         st));
         }
         CK(cudaMemsetAsync(W.counter() + 1, 0, 8, st));
         CK(impact::launch_tree_fp32(W.index(), B.rows, B.smem_emit, B.tune.emit_warps, true, o,

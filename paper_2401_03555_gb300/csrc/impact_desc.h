@@ -100,14 +100,14 @@ struct ImpactDesc {
 
 // Several builds handled by one launch of each FP32 kernel: problem q owns the
 // global rows [row_begin[q], row_begin[q+1]) of the concatenated output and
-// the (row, dimension) items [item_begin[q], item_begin[q+1]); a single build
-// is a batch of one.
+// the setup units [unit_begin[q], unit_begin[q+1]) (a unit is the 32/n rows
+// one warp prepares); a single build is a batch of one.
 struct BatchIndex {
     int count;                          // problems
     int64_t rows;                       // total rows
-    int64_t items;                      // total (row, dimension) items
+    int64_t units;                      // setup work units: 32/n rows of one problem
     const int64_t *row_begin;           // [count + 1]
-    const int64_t *item_begin;          // [count + 1]
+    const int64_t *unit_begin;          // [count + 1]
     const ImpactDesc *const *desc;      // [count] device descriptors
     unsigned char *const *rec;          // [count] FP32 per-row records
     unsigned long long *next_row;       // [2] row counters of the count / emit walk

@@ -48,10 +48,10 @@ void set_last_error(const std::string &msg);
 // FP32-sound table path (tree_fp32.cu), every launch over a whole batch.
 int64_t record_stride(int n, int tsum_cap);
 int tree_smem_bytes(int tsum_cap, int pool_cap, bool emit);
-cudaError_t launch_setup_fp32(const BatchIndex *d_index, int64_t items, uint32_t *status,
-                              cudaStream_t stream);
-cudaError_t launch_prep_fp32(const BatchIndex *d_index, int64_t items, double *sink_lo,
-                             double *sink_up, double *trunc, cudaStream_t stream);
+// `units`: warp units of the batch (BatchIndex::units); the row outputs may
+// be null (records rebuilt for an emit pass).
+cudaError_t launch_setup_fp32(const BatchIndex *d_index, int64_t units, uint32_t *status,
+                              double *sink_lo, double *sink_up, double *trunc, cudaStream_t stream);
 // `warp_smem`: shared-memory bytes of one warp (the largest of the batch);
 // `warps`: warps per block (1..8).
 cudaError_t launch_tree_fp32(const BatchIndex *d_index, int64_t rows, int warp_smem, int warps,

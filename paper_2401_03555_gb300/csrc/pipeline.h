@@ -18,8 +18,8 @@ struct Batch {
     std::vector<Plan> plans;
     std::vector<const double *> images;   // per build: device images (IMAGES kind)
     std::vector<int64_t> row_begin;       // [count + 1] first global row of each build
-    std::vector<int64_t> item_begin;      // [count + 1] first (row, dim) item
-    int64_t rows = 0, items = 0, nnz_bound = 0;
+    std::vector<int64_t> unit_begin;      // [count + 1] first setup unit (32/n rows)
+    int64_t rows = 0, units = 0, nnz_bound = 0;
     int prec = 0;
     int smem_count = 0, smem_emit = 0;    // largest per-warp bytes of the walk
     Tuning tune;
@@ -32,7 +32,7 @@ impact_status make_batch(const impact_request *reqs, int count, impact_precision
 
 // Offsets (bytes, 256-aligned) of everything in the device workspace.
 struct BatchLayout {
-    size_t index = 0, row_begin = 0, item_begin = 0, descs = 0, recs = 0;
+    size_t index = 0, row_begin = 0, unit_begin = 0, descs = 0, recs = 0;
     std::vector<size_t> tables;            // per build: its descriptor and tables
     std::vector<impact::TableLayout> tl;
     size_t upload_end = 0;                 // [0, upload_end) is copied from the host

@@ -1,21 +1,19 @@
 // tree_fp32.cu -- FP32-sound construction (Def. 3.1 with outward rounding,
-// Sec. 4.4 cutoff, Remark 4.1 sink) in three kernels plus the row scan:
+// Sec. 4.4 cutoff, Remark 4.1 sink) in two kernels plus the row scan:
 //
-//   setup_fp32  one thread per (row, dimension). From the interval image of
-//               the cell it finds the window of target cells that can pass
-//               the cutoff and the factor table of the window: U[t], an upper
-//               bound of the largest Gaussian mass of target t over the image
-//               (T_max of Def. 3.1, relaxed to the image box) and L[t], a
-//               lower bound of the smallest (T_min). Each window edge needs
-//               one erf/erfc evaluation at the image's lower end and one at
-//               its upper end; neighbouring targets share them. It trims the
-//               window to the targets that pass on their own, makes U
-//               unimodal there (a running maximum from each end towards the
-//               peak: only raises upper bounds) and stores the mass outside
-//               the trimmed window and the out-of-domain bounds.
-//   prep_fp32   one thread per (row, dimension) once all tables exist: the
-//               exact pruning thresholds of the dimension, and per row the
-//               sink bounds and the mass of the targets outside the window box.
+//   setup_fp32  one lane per (row, dimension), the rows of a warp aligned to
+//               it. From the interval image of the cell each lane finds the
+//               window of target cells that can pass the cutoff and the factor
+//               table of the window: U[t], an upper bound of the largest
+//               Gaussian mass of target t over the image (T_max of Def. 3.1,
+//               relaxed to the image box) and L[t], a lower bound of the
+//               smallest (T_min). Each window edge needs one erf/erfc
+//               evaluation at the image's lower end and one at its upper end;
+//               neighbouring targets share them. The lanes of a row then
+//               exchange their window maxima and sums by shuffles: each turns
+//               its table into exact pruning thresholds, and the lane of the
+//               first dimension writes the row's sink bounds and the mass of
+//               the targets outside the window box.
 //   tree_fp32   one warp per row. It walks the prefix tree of target cells in
 //               C order: a node at depth d is a prefix (t_0..t_d) with the
 //               RU-rounded running product P of its upper factors, and its
@@ -138,289 +136,305 @@ __device__ __forceinline__ bool mid_above(const EdgePt &c, const EdgePt &e)
     return __fadd_rd(__fsub_rd(c.a, c.da), __fsub_rd(e.a, e.da)) >= 0.0f;
 }
 
-__global__ void __launch_bounds__(kSetupThreads)
-setup_fp32(const BatchIndex *__restrict__ B, uint32_t *__restrict__ status)
+// Everything of one (row, dimension) that needs no other dimension: the
+// window and its factor tables U, L (written to the row record, trimmed to
+// the targets that pass on their own, U made unimodal there: a running
+// maximum from each end towards the peak, which only raises upper bounds),
+// the mass outside the trimmed window and the out-of-domain bounds.
+struct DimOut {
+    int a = 0;          // first window cell
+    int tw = 0, f0 = 0, pk = 0;   // trimmed width, its first index, peak index
+    float M = 0.0f;     // largest U
+    float SW = 0.0f;    // sum of U over the trimmed window (rounded up)
+    float O = 0.0f;     // mass outside the trimmed window (rounded up)
+    float qlo = 0.0f, qhi = 0.0f;   // out-of-domain mass bounds
+};
+
+__device__ DimOut dim_table(const ImpactDesc &D, unsigned char *rr, int64_t row, int d,
+                            uint32_t *status)
 {
-    const int64_t total = B->items;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total; p += stride) {
-        const int q = find_problem(B->item_begin, B->count, p);
-        const ImpactDesc &D = *B->desc[q];
-        const int n = D.n;
-        const float cut = D.cutoff32;
-        const int64_t local = p - B->item_begin[q];
-        const int64_t rl = local / n;
-        const int d = (int)(local - rl * n);
-        const int64_t row = rl;   // row id within its problem
-        // row -> (cell digits, input)
-        int64_t cell;
-        int j;
-        if (row < ((int64_t)1 << 31)) {
-            uint32_t c = fastdiv((uint32_t)row, D.inp_div_m, D.inp_div_s);
-            cell = c;
-            j = (int)((uint32_t)row - c * (uint32_t)D.n_inputs);
-        } else {
-            cell = row / D.n_inputs;
-            j = (int)(row - cell * D.n_inputs);
-        }
-        int idx[IMPACT_MAX_DIM];
-        {
-            uint32_t c = (uint32_t)cell;
-#pragma unroll
-            for (int k = IMPACT_MAX_DIM - 1; k >= 0; --k) {
-                if (k < n) {
-                    uint32_t q = fastdiv(c, D.dim[k].div_m, D.dim[k].div_s);
-                    idx[k] = (int)(c - q * (uint32_t)D.dim[k].N);
-                    c = q;
-                }
-            }
-        }
-        int my_idx = 0;
-#pragma unroll
-        for (int k = 0; k < IMPACT_MAX_DIM; ++k)
-            if (k == d) my_idx = idx[k];
-        const ImpactDim &g = D.dim[d];
-
-        // image of dimension d: window estimate (cells) and, in erf units,
-        // rho = (E_a - m)/(sigma sqrt2) at m_lo and m_hi as FP32 pairs
-        float mulo = 0.0f, muhi = 0.0f;
-        float m0h = 0.0f, m0l = 0.0f, m1h = 0.0f, m1l = 0.0f, mag = 0.0f;
-        double dmlo = 0.0, dmhi = 0.0;
-        if (D.kind == KIND_AFFINE) {
-#pragma unroll
-            for (int k = 0; k < IMPACT_MAX_DIM; ++k) {
-                if (k < n) {
-                    int t = (d * n + k) * D.n_max + idx[k];
-                    mulo += D.mu_lo[t];
-                    muhi += D.mu_hi[t];
-                    float2 pl = D.ta_lo[t], ph = D.ta_hi[t];
-                    acc_pair(m0h, m0l, pl);
-                    acc_pair(m1h, m1l, ph);
-                    mag += fabsf(pl.x) + fabsf(ph.x);
-                }
-            }
-            float2 o = D.oa[j * n + d];
-            acc_pair(m0h, m0l, o);
-            acc_pair(m1h, m1l, o);
-            mag += 2.0f * fabsf(o.x);
-            float mo = D.mo[j * n + d];
-            mulo += mo;
-            muhi += mo;
-        } else if (D.kind == KIND_UNICYCLE) {
-            const float2 *ea = D.ea + g.edge_off;
-            float2 xlo = ea[my_idx], xhi = ea[my_idx + 1];
-            acc_pair(m0h, m0l, xlo);
-            acc_pair(m1h, m1l, xhi);
-            float2 vl, vh;
-            float cl, ch;
-            if (d == 2) {
-                vl = vh = D.oma[j];
-                cl = ch = D.omm[j];
-            } else {
-                int t = (idx[2] * D.n_inputs + j) * 4 + 2 * d;
-                vl = D.ua[t];
-                vh = D.ua[t + 1];
-                cl = D.um[t];
-                ch = D.um[t + 1];
-            }
-            acc_pair(m0h, m0l, vl);
-            acc_pair(m1h, m1l, vh);
-            mag += fabsf(xlo.x) + fabsf(xhi.x) + fabsf(vl.x) + fabsf(vh.x);
-            mulo = (float)my_idx + cl;
-            muhi = (float)(my_idx + 1) + ch;
-        } else {
-            const double *im = D.images + (row * n + d) * 2;
-            dmlo = im[0];
-            dmhi = im[1];
-            mulo = (float)((dmlo - g.lo) * g.inv_h);
-            muhi = (float)((dmhi - g.lo) * g.inv_h);
-        }
-        // conservative window [a, a + W): every target outside has U below
-        // the cutoff (its cell lies more than delta beyond the image)
-        const float dc = g.delta_cells;
-        float xa = floorf(mulo - dc - 1e-3f - 1e-5f * fabsf(mulo));
-        float xb = floorf(muhi + dc + 1e-3f + 1e-5f * fabsf(muhi));
-        const float top = (float)(g.N - 1);
-        xa = fminf(fmaxf(xa, 0.0f), top);
-        xb = fminf(fmaxf(xb, 0.0f), top);
-        const int a = (int)xa;
-        const int W = max((int)xb - a + 1, 1);
-        unsigned char *rr = B->rec[q] + rl * (int64_t)D.rec_stride;
-        if (W > g.wcap) {
-            reinterpret_cast<int4 *>(rr)[3 * d] = make_int4(a, 0, 0, 0);
-            reinterpret_cast<float4 *>(rr)[3 * d + 1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            reinterpret_cast<float4 *>(rr)[3 * d + 2] = make_float4(0.0f, 0.0f, 1.0f, 0.0f);
-            atomicOr(status, IMPACT_STATUS_TABLE_OVERFLOW);
-            continue;
-        }
-        RhoPair R0, R1;
-        {
-            float2 ea = D.ea[g.edge_off + a];
-            if (D.kind == KIND_IMAGES) {
-                const double Ea = D.edges[g.edge_off + a];
-                sound::split_pair((Ea - dmlo) * g.inv_s, R0.rh, R0.rl);
-                sound::split_pair((Ea - dmhi) * g.inv_s, R1.rh, R1.rl);
-                mag = (float)((fabs(Ea) + fabs(dmlo) + fabs(dmhi)) * g.inv_s);
-            } else {
-                sub_pair(ea, m0h, m0l, R0.rh, R0.rl);
-                sub_pair(ea, m1h, m1l, R1.rh, R1.rl);
-                mag += fabsf(ea.x);
-            }
-            R0.kh = R1.kh = g.kappa_hi;
-            R0.kl = R1.kl = g.kappa_lo;
-            R0.err = R1.err = __fadd_ru(g.edge_err, __fmul_ru(__fmul_ru(mag, 4.0f), kTwoM44));
-        }
-
-        // factor table of the window: U[k], L[k] for target a + k
-        float *RU = reinterpret_cast<float *>(rr + 48 * n) + g.rec_off;
-        float *RL = RU + D.tsum_cap;
-        EdgePt c0 = R0.at(0), c1 = R1.at(0);
-        const EdgePt w0 = c0;   // edge a at m_lo (left tail below)
-        int first = -1, last = -1;
-        float pre = 0.0f, mid = 0.0f, post = 0.0f;
-        for (int k = 0; k < W; ++k) {
-            EdgePt e0 = R0.at(k + 1), e1 = R1.at(k + 1);
-            float U, L;
-            if (mid_below(c0, e0)) {            // target midpoint <= m_lo
-                U = sound::cell_hi(c0.a, c0.t, e0.a, e0.t);
-                L = sound::cell_lo(c1.a, c1.t, e1.a, e1.t);
-            } else if (mid_above(c1, e1)) {     // target midpoint >= m_hi
-                U = sound::cell_hi(c1.a, c1.t, e1.a, e1.t);
-                L = sound::cell_lo(c0.a, c0.t, e0.a, e0.t);
-            } else {                            // midpoint may be inside
-                U = g.plateau_hi;
-                L = fminf(sound::cell_lo(c0.a, c0.t, e0.a, e0.t),
-                          sound::cell_lo(c1.a, c1.t, e1.a, e1.t));
-            }
-            RU[k] = U;
-            RL[k] = L;
-            if (U >= cut) {
-                if (first < 0) {
-                    first = k;
-                    mid = U;
-                } else {
-                    mid = __fadd_ru(mid, __fadd_ru(post, U));
-                    post = 0.0f;
-                }
-                last = k;
-            } else if (first < 0) {
-                pre = __fadd_ru(pre, U);
-            } else {
-                post = __fadd_ru(post, U);
-            }
-            c0 = e0;
-            c1 = e1;
-        }
-        // c1 is now edge a + W at m_hi
-        float O = __fadd_ru(pre, post);
-        const EdgePt lo0 = R0.at(-a), hi0 = R0.at(g.N - a);   // domain edges at m_lo
-        const EdgePt lo1 = R1.at(-a), hi1 = R1.at(g.N - a);   // domain edges at m_hi
-        if (a > 0)   // cells 0..a-1 lie left of the image: their mass at m_lo
-            O = __fadd_ru(O, sound::cell_hi(lo0.a, lo0.t, w0.a, w0.t));
-        if (a + W < g.N)   // cells right of the window: their mass at m_hi
-            O = __fadd_ru(O, sound::cell_hi(c1.a, c1.t, hi1.a, hi1.t));
-        // out-of-domain mass Q(m) = T(-alpha(lo_D)) + T(alpha(hi_D))
-        float q0 = __fadd_ru(lo0.t.m_hi, hi0.t.p_hi);
-        float q1 = __fadd_ru(lo1.t.m_hi, hi1.t.p_hi);
-        float qhi = fminf(fmaxf(q0, q1), 1.0f);
-        float qlo;
-        if (mid_below(lo0, hi0))
-            qlo = __fadd_rd(lo0.t.m_lo, hi0.t.p_lo);
-        else if (mid_above(lo1, hi1))
-            qlo = __fadd_rd(lo1.t.m_lo, hi1.t.p_lo);
-        else
-            qlo = g.qmin_lo;
-        qlo = fminf(qlo, 1.0f);
-        const int tw = first >= 0 ? last - first + 1 : 0;
-        const int f0 = first >= 0 ? first : 0;
-        // unimodal envelope of U on the trimmed window (running maximum from
-        // each end towards the peak); raw U is unimodal up to rounding, so
-        // this rarely changes a value, and it only raises upper bounds
-        int pk = 0;
-        float M = 0.0f;
-        if (tw > 0) {
-            float *u = RU + f0;
-            for (int t = 0; t < tw; ++t)
-                if (u[t] > M) { M = u[t]; pk = t; }
-            float run = u[0];
-            for (int t = 1; t < pk; ++t) {
-                float v = u[t];
-                if (v < run) u[t] = run; else run = v;
-            }
-            run = u[tw - 1];
-            for (int t = tw - 2; t > pk; --t) {
-                float v = u[t];
-                if (v < run) u[t] = run; else run = v;
-            }
-        }
-        reinterpret_cast<int4 *>(rr)[3 * d] = make_int4(a + f0, tw, f0, pk);
-        reinterpret_cast<float4 *>(rr)[3 * d + 1] = make_float4(mid, O, qlo, qhi);
-        reinterpret_cast<float4 *>(rr)[3 * d + 2] = make_float4(M, 0.0f, 1.0f, 0.0f);
+    DimOut o;
+    const int n = D.n;
+    const float cut = D.cutoff32;
+    // row -> (cell digits, input)
+    int64_t cell;
+    int j;
+    if (row < ((int64_t)1 << 31)) {
+        uint32_t c = fastdiv((uint32_t)row, D.inp_div_m, D.inp_div_s);
+        cell = c;
+        j = (int)((uint32_t)row - c * (uint32_t)D.n_inputs);
+    } else {
+        cell = row / D.n_inputs;
+        j = (int)(row - cell * D.n_inputs);
     }
+    int idx[IMPACT_MAX_DIM];
+    {
+        uint32_t c = (uint32_t)cell;
+#pragma unroll
+        for (int k = IMPACT_MAX_DIM - 1; k >= 0; --k) {
+            if (k < n) {
+                uint32_t q = fastdiv(c, D.dim[k].div_m, D.dim[k].div_s);
+                idx[k] = (int)(c - q * (uint32_t)D.dim[k].N);
+                c = q;
+            }
+        }
+    }
+    int my_idx = 0;
+#pragma unroll
+    for (int k = 0; k < IMPACT_MAX_DIM; ++k)
+        if (k == d) my_idx = idx[k];
+    const ImpactDim &g = D.dim[d];
+
+    // image of dimension d: window estimate (cells) and, in erf units,
+    // rho = (E_a - m)/(sigma sqrt2) at m_lo and m_hi as FP32 pairs
+    float mulo = 0.0f, muhi = 0.0f;
+    float m0h = 0.0f, m0l = 0.0f, m1h = 0.0f, m1l = 0.0f, mag = 0.0f;
+    double dmlo = 0.0, dmhi = 0.0;
+    if (D.kind == KIND_AFFINE) {
+#pragma unroll
+        for (int k = 0; k < IMPACT_MAX_DIM; ++k) {
+            if (k < n) {
+                int t = (d * n + k) * D.n_max + idx[k];
+                mulo += D.mu_lo[t];
+                muhi += D.mu_hi[t];
+                float2 pl = D.ta_lo[t], ph = D.ta_hi[t];
+                acc_pair(m0h, m0l, pl);
+                acc_pair(m1h, m1l, ph);
+                mag += fabsf(pl.x) + fabsf(ph.x);
+            }
+        }
+        float2 o = D.oa[j * n + d];
+        acc_pair(m0h, m0l, o);
+        acc_pair(m1h, m1l, o);
+        mag += 2.0f * fabsf(o.x);
+        float mo = D.mo[j * n + d];
+        mulo += mo;
+        muhi += mo;
+    } else if (D.kind == KIND_UNICYCLE) {
+        const float2 *ea = D.ea + g.edge_off;
+        float2 xlo = ea[my_idx], xhi = ea[my_idx + 1];
+        acc_pair(m0h, m0l, xlo);
+        acc_pair(m1h, m1l, xhi);
+        float2 vl, vh;
+        float cl, ch;
+        if (d == 2) {
+            vl = vh = D.oma[j];
+            cl = ch = D.omm[j];
+        } else {
+            int t = (idx[2] * D.n_inputs + j) * 4 + 2 * d;
+            vl = D.ua[t];
+            vh = D.ua[t + 1];
+            cl = D.um[t];
+            ch = D.um[t + 1];
+        }
+        acc_pair(m0h, m0l, vl);
+        acc_pair(m1h, m1l, vh);
+        mag += fabsf(xlo.x) + fabsf(xhi.x) + fabsf(vl.x) + fabsf(vh.x);
+        mulo = (float)my_idx + cl;
+        muhi = (float)(my_idx + 1) + ch;
+    } else {
+        const double *im = D.images + (row * n + d) * 2;
+        dmlo = im[0];
+        dmhi = im[1];
+        mulo = (float)((dmlo - g.lo) * g.inv_h);
+        muhi = (float)((dmhi - g.lo) * g.inv_h);
+    }
+    // conservative window [a, a + W): every target outside has U below
+    // the cutoff (its cell lies more than delta beyond the image)
+    const float dc = g.delta_cells;
+    float xa = floorf(mulo - dc - 1e-3f - 1e-5f * fabsf(mulo));
+    float xb = floorf(muhi + dc + 1e-3f + 1e-5f * fabsf(muhi));
+    const float top = (float)(g.N - 1);
+    xa = fminf(fmaxf(xa, 0.0f), top);
+    xb = fminf(fmaxf(xb, 0.0f), top);
+    const int a = (int)xa;
+    const int W = max((int)xb - a + 1, 1);
+    o.a = a;
+    if (W > g.wcap) {
+        atomicOr(status, IMPACT_STATUS_TABLE_OVERFLOW);
+        return o;
+    }
+    RhoPair R0, R1;
+    {
+        float2 ea = D.ea[g.edge_off + a];
+        if (D.kind == KIND_IMAGES) {
+            const double Ea = D.edges[g.edge_off + a];
+            sound::split_pair((Ea - dmlo) * g.inv_s, R0.rh, R0.rl);
+            sound::split_pair((Ea - dmhi) * g.inv_s, R1.rh, R1.rl);
+            mag = (float)((fabs(Ea) + fabs(dmlo) + fabs(dmhi)) * g.inv_s);
+        } else {
+            sub_pair(ea, m0h, m0l, R0.rh, R0.rl);
+            sub_pair(ea, m1h, m1l, R1.rh, R1.rl);
+            mag += fabsf(ea.x);
+        }
+        R0.kh = R1.kh = g.kappa_hi;
+        R0.kl = R1.kl = g.kappa_lo;
+        R0.err = R1.err = __fadd_ru(g.edge_err, __fmul_ru(__fmul_ru(mag, 4.0f), kTwoM44));
+    }
+
+    // factor table of the window: U[k], L[k] for target a + k
+    float *RU = reinterpret_cast<float *>(rr + 48 * n) + g.rec_off;
+    float *RL = RU + D.tsum_cap;
+    EdgePt c0 = R0.at(0), c1 = R1.at(0);
+    const EdgePt w0 = c0;   // edge a at m_lo (left tail below)
+    int first = -1, last = -1;
+    float pre = 0.0f, mid = 0.0f, post = 0.0f;
+    for (int k = 0; k < W; ++k) {
+        EdgePt e0 = R0.at(k + 1), e1 = R1.at(k + 1);
+        float U, L;
+        if (mid_below(c0, e0)) {            // target midpoint <= m_lo
+            U = sound::cell_hi(c0.a, c0.t, e0.a, e0.t);
+            L = sound::cell_lo(c1.a, c1.t, e1.a, e1.t);
+        } else if (mid_above(c1, e1)) {     // target midpoint >= m_hi
+            U = sound::cell_hi(c1.a, c1.t, e1.a, e1.t);
+            L = sound::cell_lo(c0.a, c0.t, e0.a, e0.t);
+        } else {                            // midpoint may be inside
+            U = g.plateau_hi;
+            L = fminf(sound::cell_lo(c0.a, c0.t, e0.a, e0.t),
+                      sound::cell_lo(c1.a, c1.t, e1.a, e1.t));
+        }
+        RU[k] = U;
+        RL[k] = L;
+        if (U >= cut) {
+            if (first < 0) {
+                first = k;
+                mid = U;
+            } else {
+                mid = __fadd_ru(mid, __fadd_ru(post, U));
+                post = 0.0f;
+            }
+            last = k;
+        } else if (first < 0) {
+            pre = __fadd_ru(pre, U);
+        } else {
+            post = __fadd_ru(post, U);
+        }
+        c0 = e0;
+        c1 = e1;
+    }
+    // c1 is now edge a + W at m_hi
+    float O = __fadd_ru(pre, post);
+    const EdgePt lo0 = R0.at(-a), hi0 = R0.at(g.N - a);   // domain edges at m_lo
+    const EdgePt lo1 = R1.at(-a), hi1 = R1.at(g.N - a);   // domain edges at m_hi
+    if (a > 0)   // cells 0..a-1 lie left of the image: their mass at m_lo
+        O = __fadd_ru(O, sound::cell_hi(lo0.a, lo0.t, w0.a, w0.t));
+    if (a + W < g.N)   // cells right of the window: their mass at m_hi
+        O = __fadd_ru(O, sound::cell_hi(c1.a, c1.t, hi1.a, hi1.t));
+    // out-of-domain mass Q(m) = T(-alpha(lo_D)) + T(alpha(hi_D))
+    float q0 = __fadd_ru(lo0.t.m_hi, hi0.t.p_hi);
+    float q1 = __fadd_ru(lo1.t.m_hi, hi1.t.p_hi);
+    float qhi = fminf(fmaxf(q0, q1), 1.0f);
+    float qlo;
+    if (mid_below(lo0, hi0))
+        qlo = __fadd_rd(lo0.t.m_lo, hi0.t.p_lo);
+    else if (mid_above(lo1, hi1))
+        qlo = __fadd_rd(lo1.t.m_lo, hi1.t.p_lo);
+    else
+        qlo = g.qmin_lo;
+    qlo = fminf(qlo, 1.0f);
+    const int tw = first >= 0 ? last - first + 1 : 0;
+    const int f0 = first >= 0 ? first : 0;
+    // unimodal envelope of U on the trimmed window (running maximum from
+    // each end towards the peak); raw U is unimodal up to rounding, so
+    // this rarely changes a value, and it only raises upper bounds
+    int pk = 0;
+    float M = 0.0f;
+    if (tw > 0) {
+        float *u = RU + f0;
+        for (int t = 0; t < tw; ++t)
+            if (u[t] > M) { M = u[t]; pk = t; }
+        float run = u[0];
+        for (int t = 1; t < pk; ++t) {
+            float v = u[t];
+            if (v < run) u[t] = run; else run = v;
+        }
+        run = u[tw - 1];
+        for (int t = tw - 2; t > pk; --t) {
+            float v = u[t];
+            if (v < run) u[t] = run; else run = v;
+        }
+    }
+    o.tw = tw;
+    o.f0 = f0;
+    o.pk = pk;
+    o.M = M;
+    o.SW = mid;
+    o.O = O;
+    o.qlo = qlo;
+    o.qhi = qhi;
+    return o;
 }
 
-// prep_fp32: one thread per (row, dimension) once every dimension's table
-// exists. Pruning thresholds of this dimension: a child t of a node with
+// setup_fp32: one warp per 32/n rows of one build, one lane per (row,
+// dimension). Each lane builds its dimension's tables (dim_table); the lanes
+// of a row then exchange their maxima and window sums by shuffles and each
+// finishes its dimension: the pruning thresholds (a child t of a node with
 // product P survives iff RU(RU(P U_d[t]) R') >= cutoff, R' bounding the
-// product of the later dimensions' largest factors; TH_d[t] is the least
-// such P. Thread 0 of a row also finishes the row's sink bounds and the mass
-// of the targets outside the window box (FP64, outward rounding), unless the
-// row outputs are null (records rebuilt for an emit pass).
+// product of the later dimensions' largest factors; TH_d[t] is the least such
+// P) and the header. The lane of dimension 0 also writes the row's sink
+// bounds and the mass of the targets outside the window box (FP64, outward
+// rounding), unless the row outputs are null (records rebuilt for an emit).
 __global__ void __launch_bounds__(kSetupThreads)
-prep_fp32(const BatchIndex *__restrict__ B, double *__restrict__ sink_lo,
-          double *__restrict__ sink_up, double *__restrict__ trunc)
+setup_fp32(const BatchIndex *__restrict__ B, uint32_t *__restrict__ status,
+           double *__restrict__ sink_lo, double *__restrict__ sink_up, double *__restrict__ trunc)
 {
-    const int64_t total = B->items;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total; p += stride) {
-        const int q = find_problem(B->item_begin, B->count, p);
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t u = warp0; u < B->units; u += nwarps) {
+        const int q = find_problem(B->unit_begin, B->count, u);
         const ImpactDesc &D = *B->desc[q];
         const int n = D.n;
-        const float cut = D.cutoff32;
-        const int64_t local = p - B->item_begin[q];
-        const int64_t rl = local / n;
-        const int d = (int)(local - rl * n);
-        unsigned char *rr = B->rec[q] + rl * (int64_t)D.rec_stride;
-        const int4 *hi = reinterpret_cast<const int4 *>(rr);
-        const float4 *hf = reinterpret_cast<const float4 *>(rr);
+        const int rpw = 32 / n;
+        const int slot = lane / n, d = lane - slot * n;
+        const int64_t rows_q = B->row_begin[q + 1] - B->row_begin[q];
+        const int64_t rl = (u - B->unit_begin[q]) * rpw + slot;
+        const bool act = slot < rpw && rl < rows_q;
+        unsigned char *rr = act ? B->rec[q] + rl * (int64_t)D.rec_stride : nullptr;
+        DimOut o;
+        if (act) o = dim_table(D, rr, rl, d, status);
+        // the row's other dimensions, in order k = 0..n-1 (lanes base + k)
+        const int base = slot * n;
         float R = 1.0f, SR = 1.0f;
-        for (int k = d + 1; k < n; ++k) {
-            R = __fmul_ru(R, hf[3 * k + 2].x);
-            SR = __fmul_ru(SR, hf[3 * k + 1].x);
+        double pin_up = 1.0, pin_dn = 1.0, acc = 0.0, pre = 1.0;
+#pragma unroll
+        for (int k = 0; k < IMPACT_MAX_DIM; ++k) {
+            if (k < n) {   // n is the same for the whole warp
+                const int src = (base + k) & 31;
+                const float Mk = __shfl_sync(0xffffffffu, o.M, src);
+                const float SWk = __shfl_sync(0xffffffffu, o.SW, src);
+                const float Ok = __shfl_sync(0xffffffffu, o.O, src);
+                const float qlk = __shfl_sync(0xffffffffu, o.qlo, src);
+                const float qhk = __shfl_sync(0xffffffffu, o.qhi, src);
+                if (k > d) {
+                    R = __fmul_ru(R, Mk);
+                    SR = __fmul_ru(SR, SWk);
+                }
+                // sink: 1 - prod_k (1 - Q_k)
+                pin_up = __dmul_ru(pin_up, __dsub_ru(1.0, (double)qlk));
+                pin_dn = __dmul_rd(pin_dn, __dsub_rd(1.0, (double)qhk));
+                // mass outside the window box, partitioned by the first
+                // dimension that leaves its window:
+                // sum_k prod_{i<k} SW_i * O_k * prod_{i>k} (SW_i + O_i)
+                acc = acc * ((double)SWk + (double)Ok) + pre * (double)Ok;
+                pre *= (double)SWk;
+            }
         }
+        if (!act) continue;
+        const float cut = D.cutoff32;
         float cp = 0.0f;
         if (cut > 0.0f) cp = (d == n - 1) ? cut : threshold(cut, __fmul_ru(R, kGrow18));
-        const int4 h = hi[3 * d];
-        float4 c = hf[3 * d + 2];
-        c.y = cp;
-        c.z = SR;
-        reinterpret_cast<float4 *>(rr)[3 * d + 2] = c;
-        const float *RU = reinterpret_cast<const float *>(rr + 48 * n) + D.dim[d].rec_off + h.z;
-        float *RT = reinterpret_cast<float *>(rr + 48 * n) + 2 * D.tsum_cap + D.dim[d].rec_off + h.z;
-        for (int t = 0; t < h.y; ++t) RT[t] = cp > 0.0f ? threshold(cp, RU[t]) : 0.0f;
+        const float *RUt = reinterpret_cast<const float *>(rr + 48 * n) + D.dim[d].rec_off + o.f0;
+        float *RT = reinterpret_cast<float *>(rr + 48 * n) + 2 * D.tsum_cap + D.dim[d].rec_off + o.f0;
+        for (int t = 0; t < o.tw; ++t) RT[t] = cp > 0.0f ? threshold(cp, RUt[t]) : 0.0f;
+        reinterpret_cast<int4 *>(rr)[3 * d] = make_int4(o.a + o.f0, o.tw, o.f0, o.pk);
+        reinterpret_cast<float4 *>(rr)[3 * d + 1] = make_float4(o.SW, o.O, o.qlo, o.qhi);
+        reinterpret_cast<float4 *>(rr)[3 * d + 2] = make_float4(o.M, cp, SR, 0.0f);
         if (d == 0 && trunc) {
-            // sink bounds: 1 - prod_d (1 - Q_d)
-            double pin_up = 1.0, pin_dn = 1.0;
-            for (int k = 0; k < n; ++k) {
-                const float4 b = hf[3 * k + 1];
-                pin_up = __dmul_ru(pin_up, __dsub_ru(1.0, (double)b.z));
-                pin_dn = __dmul_rd(pin_dn, __dsub_rd(1.0, (double)b.w));
-            }
-            // mass of the targets outside the window box, partitioned by the
-            // first dimension whose index leaves the window:
-            // prod_{k<d} SW_k * O_d * prod_{k>d} (SW_k + O_k)
-            double suf = 1.0, outside = 0.0;
-            for (int k = n - 1; k >= 0; --k) {
-                double pre = 1.0;
-                for (int q = 0; q < k; ++q) pre *= (double)hf[3 * q + 1].x;
-                const float4 b = hf[3 * k + 1];
-                outside += pre * (double)b.y * suf;
-                suf *= (double)b.x + (double)b.y;
-            }
             const int64_t row = B->row_begin[q] + rl;   // global row
             sink_lo[row] = fmax(__dsub_rd(1.0, pin_up), 0.0);
             sink_up[row] = fmin(__dsub_ru(1.0, pin_dn), 1.0);
-            trunc[row] = outside * (1.0 + 1e-12);
+            trunc[row] = acc * (1.0 + 1e-12);
         }
     }
 }
@@ -899,21 +913,12 @@ int tree_smem_bytes(int tsum_cap, int pool_cap, bool emit)
     return (int)((b + 15) / 16 * 16);
 }
 
-cudaError_t launch_setup_fp32(const BatchIndex *d_index, int64_t items, uint32_t *status,
-                              cudaStream_t stream)
+cudaError_t launch_setup_fp32(const BatchIndex *d_index, int64_t units, uint32_t *status,
+                              double *sink_lo, double *sink_up, double *trunc, cudaStream_t stream)
 {
-    if (items <= 0) return cudaSuccess;
-    int g = occupancy_grid((const void *)setup_fp32, kSetupThreads, 0, items, kSetupThreads);
-    setup_fp32<<<g, kSetupThreads, 0, stream>>>(d_index, status);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_prep_fp32(const BatchIndex *d_index, int64_t items, double *sink_lo,
-                             double *sink_up, double *trunc, cudaStream_t stream)
-{
-    if (items <= 0) return cudaSuccess;
-    int g = occupancy_grid((const void *)prep_fp32, kSetupThreads, 0, items, kSetupThreads);
-    prep_fp32<<<g, kSetupThreads, 0, stream>>>(d_index, sink_lo, sink_up, trunc);
+    if (units <= 0) return cudaSuccess;
+    int g = occupancy_grid((const void *)setup_fp32, kSetupThreads, 0, units, kSetupThreads / 32);
+    setup_fp32<<<g, kSetupThreads, 0, stream>>>(d_index, status, sink_lo, sink_up, trunc);
     return cudaGetLastError();
 }
 
