@@ -71,18 +71,27 @@ __device__ __forceinline__ void sub_pair(float2 a, float bh, float bl, float &rh
     rl = __fadd_rn(__fsub_rn(a.y, bl), e);
 }
 
-// Row sums of the count pass are accumulated in fixed point (units of 2^-56,
+// Row sums of the count pass are accumulated in fixed point (units of 2^-44,
 // each term rounded outward), so the totals do not depend on which lane took
-// which node nor on the order: every launch shape gives the same bits.
-constexpr float kFix = 72057594037927936.0f;         // 2^56
-constexpr double kUnfix = 1.3877787807814457e-17;    // 2^-56
+// which node nor on the order: every launch shape gives the same bits. Terms
+// are capped at 2^18 and sums saturate at 2^62 (2^18 in value): the sums
+// bound probability masses (at most 1) or only ever prove a row sum too
+// small, so a capped value keeps every use sound.
+constexpr float kFix = 17592186044416.0f;            // 2^44
+constexpr double kUnfix = 5.684341886080802e-14;     // 2^-44
+constexpr float kTermCap = 262144.0f;                // 2^18
+constexpr unsigned long long kFixMax = 1ull << 62;
 __device__ __forceinline__ unsigned long long fix_up(float x)
 {
-    return __float2ull_ru(__fmul_ru(x, kFix));
+    return __float2ull_ru(__fmul_ru(fminf(x, kTermCap), kFix));
 }
 __device__ __forceinline__ unsigned long long fix_dn(float x)
 {
-    return __float2ull_rd(__fmul_rd(x, kFix));
+    return __float2ull_rd(__fmul_rd(fminf(x, kTermCap), kFix));
+}
+__device__ __forceinline__ void fix_add(unsigned long long &s, unsigned long long t)
+{
+    s = (s > kFixMax - t) ? kFixMax : s + t;
 }
 
 __device__ __forceinline__ float fpred(float x) { return nextafterf(x, 0.0f); }
@@ -657,10 +666,10 @@ tree_fp32(const BatchIndex *__restrict__ B, int warp_smem, int64_t *__restrict__
             if (c > 0) {
                 float su = fmaxf(__fsub_ru(S.pu_up[po + l + c], S.pu_dn[po + l]), 0.0f);
                 float sl = fmaxf(__fsub_rd(S.pl_dn[po + l + c], S.pl_up[po + l]), 0.0f);
-                sup += fix_up(__fmul_ru(P, su));
-                slo += fix_dn(__fmul_rd(Pl, sl));
+                fix_add(sup, fix_up(__fmul_ru(P, su)));
+                fix_add(slo, fix_dn(__fmul_rd(Pl, sl)));
             }
-            drop += fix_up(__fmul_ru(P, outside_sum(S, dl, l, c)));
+            fix_add(drop, fix_up(__fmul_ru(P, outside_sum(S, dl, l, c))));
         };
 
         // K = 1: each active lane's parent (P, Pl, cb) owns one run of the
@@ -704,7 +713,7 @@ tree_fp32(const BatchIndex *__restrict__ B, int warp_smem, int64_t *__restrict__
             int lm = 0, cm = 0;
             if (act) run_of(S, dm, P, lm, cm);
             if (act) {
-                drop += fix_up(__fmul_ru(__fmul_ru(P, outside_sum(S, dm, lm, cm)), H.swr[dm]));
+                fix_add(drop, fix_up(__fmul_ru(__fmul_ru(P, outside_sum(S, dm, lm, cm)), H.swr[dm])));
                 // the middle run's products rise to its peak and fall after it:
                 // the leaf runs follow them incrementally
                 int l1 = H.pk[dl] + 1, r1 = l1;
@@ -831,8 +840,8 @@ tree_fp32(const BatchIndex *__restrict__ B, int warp_smem, int64_t *__restrict__
                         S.ncol[ix] = cb + (ta + t) * st;
                     }
                     if (!EMIT)
-                        drop += fix_up(__fmul_ru(__fmul_ru(P, outside_sum(S, dim, l, c)),
-                                                 H.swr[dim]));
+                        fix_add(drop, fix_up(__fmul_ru(__fmul_ru(P, outside_sum(S, dim, l, c)),
+                                                       H.swr[dim])));
                 }
                 // children appended: the sum of the taken lanes' runs
                 int added = take ? c : 0;
@@ -855,9 +864,9 @@ tree_fp32(const BatchIndex *__restrict__ B, int warp_smem, int64_t *__restrict__
             long long csum = cnt;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
-                dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
-                usum += __shfl_xor_sync(0xffffffffu, usum, o);
-                lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+                fix_add(dsum, __shfl_xor_sync(0xffffffffu, dsum, o));
+                fix_add(usum, __shfl_xor_sync(0xffffffffu, usum, o));
+                fix_add(lsum, __shfl_xor_sync(0xffffffffu, lsum, o));
                 csum += __shfl_xor_sync(0xffffffffu, csum, o);
             }
             if (lane == 0) {
