@@ -109,7 +109,10 @@ typedef struct {
 
 /*
  * The result, a CSR matrix with one row per (cell, input) and int32 target
- * cell ids in ascending order within each row. All arrays are DEVICE memory.
+ * cell ids in ascending order within each row. All arrays are DEVICE memory,
+ * except that caller-owned col/lo/up may also be pinned host memory the
+ * device can address (cudaHostAlloc / cudaHostRegister): the emit pass then
+ * writes the pairs straight into host memory over the host link.
  *   rows            out: number of rows
  *   nnz             in: capacity of col/lo/up when the caller owns them;
  *                   out: number of stored pairs

@@ -336,11 +336,27 @@ impact_status run_emit(const Batch &B, const Work &W, const impact_csr *out, int
     return IMPACT_OK;
 }
 
-impact_status check_pair_arrays(const impact_csr *out)
+// col/lo/up may be device memory or pinned host memory the device can
+// address (the emit pass then writes the pairs straight to host memory over
+// the host link); `v` is `out` with device-visible addresses.
+impact_status pair_view(const impact_csr *out, impact_csr &v)
 {
-    if (out->nnz > 0 &&
-        (!is_device_ptr(out->col) || !is_device_ptr(out->lo) || !is_device_ptr(out->up)))
-        return fail(IMPACT_ERR_ARG, "col, lo and up must be device arrays");
+    v = *out;
+    if (out->nnz <= 0) return IMPACT_OK;
+    void **ps[3] = {(void **)&v.col, &v.lo, &v.up};
+    for (void **pp : ps) {
+        cudaPointerAttributes a;
+        if (!*pp || cudaPointerGetAttributes(&a, *pp) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(IMPACT_ERR_ARG, "col, lo and up must be device or pinned host arrays");
+        }
+        if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) continue;
+        if (a.type == cudaMemoryTypeHost && a.devicePointer) {
+            *pp = a.devicePointer;
+            continue;
+        }
+        return fail(IMPACT_ERR_ARG, "col, lo and up must be device or pinned host arrays");
+    }
     return IMPACT_OK;
 }
 
@@ -375,7 +391,8 @@ impact_status do_emit(const Batch &B, impact_csr *out, cudaStream_t st)
 {
     impact_status s;
     if (!is_device_ptr(out->row_ptr)) return fail(IMPACT_ERR_ARG, "row_ptr must be a device array");
-    if ((s = check_pair_arrays(out)) != IMPACT_OK) return s;
+    impact_csr view;
+    if ((s = pair_view(out, view)) != IMPACT_OK) return s;
     configure_pool_once();
     bool ready = false;
     if (out->workspace) {
@@ -391,7 +408,7 @@ impact_status do_emit(const Batch &B, impact_csr *out, cudaStream_t st)
     } else {
         CK(cudaMemsetAsync(W.status(), 0, 64, st));
     }
-    if ((s = run_emit(B, W, out, out->nnz, ready, st)) != IMPACT_OK) return s;
+    if ((s = run_emit(B, W, &view, out->nnz, ready, st)) != IMPACT_OK) return s;
     if ((s = release(W, st)) != IMPACT_OK) return s;
     out->rows = B.rows;
     return IMPACT_OK;
@@ -417,7 +434,6 @@ impact_status do_build(const Batch &B, impact_csr *out, cudaStream_t st)
         out->owned = 1;
     } else {
         if ((s = check_row_arrays(out)) != IMPACT_OK) return s;
-        if ((s = check_pair_arrays(out)) != IMPACT_OK) return s;
     }
     Work W;
     if ((s = get_work(B, out, st, W)) != IMPACT_OK) return s;
@@ -435,7 +451,9 @@ impact_status do_build(const Batch &B, impact_csr *out, cudaStream_t st)
         CK(cudaMallocAsync(&out->up, k * vbytes, st));
         capacity = nnz;
     }
-    if ((s = run_emit(B, W, out, capacity, true, st)) != IMPACT_OK) return s;
+    impact_csr view;
+    if ((s = pair_view(out, view)) != IMPACT_OK) return s;
+    if ((s = run_emit(B, W, &view, capacity, true, st)) != IMPACT_OK) return s;
     int64_t nnz = 0;
     uint32_t status = 0;
     CK(cudaMemcpyAsync(&nnz, out->row_ptr + B.rows, 8, cudaMemcpyDeviceToHost, st));
@@ -621,7 +639,8 @@ impact_status impact_graph_create(const impact_request *reqs, int count,
     if ((s = make_batch(reqs, count, precision, tuning, B)) != IMPACT_OK) return s;
     if ((s = check_row_arrays(out)) != IMPACT_OK) return s;
     if (!out->col) return fail(IMPACT_ERR_ARG, "a graph writes into caller-owned col/lo/up");
-    if ((s = check_pair_arrays(out)) != IMPACT_OK) return s;
+    impact_csr view;
+    if ((s = pair_view(out, view)) != IMPACT_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     impact_graph *g = new impact_graph();
     g->rows = B.rows;
@@ -655,7 +674,7 @@ impact_status impact_graph_create(const impact_request *reqs, int count,
     cudaStream_t cs = nullptr;
     if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess)
         return cleanup(fail(IMPACT_ERR_CUDA, "capture stream"));
-    impact_csr o = *out;
+    impact_csr o = view;
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
     if (e == cudaSuccess) {
         s = run_count(B, W, &o, cs);
@@ -720,7 +739,9 @@ impact_status impact_batch_tune(const impact_request *reqs, int count,
     impact_status s = check_request_ptrs(reqs, count);
     if (s != IMPACT_OK) return s;
     if ((s = check_row_arrays(out)) != IMPACT_OK) return s;
-    if ((s = check_pair_arrays(out)) != IMPACT_OK) return s;
+    impact_csr view;
+    if ((s = pair_view(out, view)) != IMPACT_OK) return s;
+    out = &view;
     reps = std::max(1, std::min(reps, 50));
     cudaStream_t st = (cudaStream_t)stream;
     configure_pool_once();

@@ -279,12 +279,17 @@ def alloc_rows(rows: int, device=None):
                 row_flags=torch.empty(rows, dtype=torch.int32, device=dev))
 
 
-def alloc_pairs(nnz: int, precision="fp32", device=None):
-    dev = device or torch.device("cuda")
+def alloc_pairs(nnz: int, precision="fp32", device=None, host: bool = False):
+    """col/lo/up buffers for `nnz` pairs: device memory, or (host=True) pinned
+    host memory that the emit kernel writes directly."""
     vt = torch.float32 if _PREC[precision] == FP32_SOUND else torch.float64
     k = max(int(nnz), 1)
-    return dict(col=torch.empty(k, dtype=torch.int32, device=dev),
-                lo=torch.empty(k, dtype=vt, device=dev), up=torch.empty(k, dtype=vt, device=dev))
+    if host:
+        mk = lambda dt: torch.empty(k, dtype=dt, pin_memory=True)
+    else:
+        dev = device or torch.device("cuda")
+        mk = lambda dt: torch.empty(k, dtype=dt, device=dev)
+    return dict(col=mk(torch.int32), lo=mk(vt), up=mk(vt))
 
 
 def _csr_struct(rows_buf, pairs_buf=None, capacity=0, workspace=None):
@@ -334,7 +339,8 @@ class Builder:
     """Repeated builds of one problem into preallocated device buffers through
     the single-call entry point impact_build (caller-owned arrays)."""
 
-    def __init__(self, prob, precision="fp32", capacity: Optional[int] = None, images=None):
+    def __init__(self, prob, precision="fp32", capacity: Optional[int] = None, images=None,
+                 pairs_on_host: bool = False):
         self.prob = prob
         self.precision = precision
         self.prec = _PREC[precision]
@@ -343,7 +349,7 @@ class Builder:
         if capacity is None:
             capacity = build(prob, precision).nnz
         self.capacity = int(capacity)
-        self.pairs_buf = alloc_pairs(self.capacity, precision)
+        self.pairs_buf = alloc_pairs(self.capacity, precision, host=pairs_on_host)
         self.workspace = alloc_workspace(prob, precision)
         self.nnz = 0
 

@@ -175,3 +175,20 @@ def test_capacity_too_small_reports_needed_pairs():
         b.run()
     assert e.value.status == impact.IMPACT_ERR_CAPACITY
     assert str(need) in str(e.value)
+
+
+def test_pairs_written_straight_to_pinned_host_memory():
+    """col/lo/up in pinned host memory: the emit kernel writes them over the
+    host link; the result equals the device build bit for bit."""
+    prob = W.room_5d(cells_per_dim=5)
+    ref = impact.build(prob, "fp32")
+    b = impact.Builder(prob, "fp32", capacity=ref.nnz, pairs_on_host=True)
+    assert not b.pairs_buf["col"].is_cuda
+    assert b.run() == ref.nnz
+    torch.cuda.synchronize()
+    got = b.result()
+    for name in ("col", "lo", "up"):
+        x = getattr(got, name).numpy()
+        y = getattr(ref, name).cpu().numpy()
+        assert np.array_equal(x.view(np.uint8), y.view(np.uint8)), name
+    assert torch.equal(got.row_ptr.cpu(), ref.row_ptr.cpu())
