@@ -234,8 +234,11 @@ typedef struct {
  * chosen per build.
  *   count_warps, emit_warps              warps per block, 1..8
  *   count_smem_target, emit_smem_target  bytes per warp, 2048..49152
- *   count_k                              count pass: dimensions a lane walks
- *                                        serially at the end (1, 2; 0 auto)
+ *   count_k, emit_k                      how the walk handles the last
+ *                                        dimensions: 1 leaf batches, 2 (count
+ *                                        only) the last two dimensions serially
+ *                                        per lane, 3 the last two dimensions
+ *                                        lane-parallel (0: chosen per build)
  * Shapes change speed only: results are bitwise identical for every shape.
  */
 typedef struct {
@@ -244,6 +247,7 @@ typedef struct {
     int count_smem_target;
     int emit_smem_target;
     int count_k;
+    int emit_k;
 } impact_tuning;
 
 /*
@@ -292,8 +296,9 @@ impact_status impact_graph_destroy(impact_graph *graph);
 
 /*
  * impact_batch_tune -- the autotuner: times the FP32 count pass over warps
- * per block {2,4,8} x shared-memory targets {4096,6144,8192,12288} x count_k
- * {1,2}, then the emit pass over warps x targets with the best count shape,
+ * per block {4,8} x shared-memory targets {4096,6144,8192,12288} x count_k
+ * {1,2,3}, then the emit pass over warps x targets x emit_k {1,3} with the
+ * best count shape,
  * each the best of `reps` runs, on this batch, and writes the fastest shape
  * to *best and its count + emit milliseconds to *best_ms (may be NULL).
  * `out` as for impact_batch_emit with the capacity of a previous count

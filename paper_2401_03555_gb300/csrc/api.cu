@@ -64,14 +64,17 @@ impact_status tuning_of(const impact_tuning *t, Tuning &T)
     if (t->count_smem_target) T.count_smem = t->count_smem_target;
     if (t->emit_smem_target) T.emit_smem = t->emit_smem_target;
     T.count_k = t->count_k;
+    T.emit_k = t->emit_k;
     if (T.count_warps < 1 || T.count_warps > IMPACT_TREE_WARPS_MAX || T.emit_warps < 1 ||
         T.emit_warps > IMPACT_TREE_WARPS_MAX)
         return fail(IMPACT_ERR_ARG, "tuning: warps per block must be in [1, 8]");
     if (T.count_smem < 2048 || T.count_smem > 48 * 1024 || T.emit_smem < 2048 ||
         T.emit_smem > 48 * 1024)
         return fail(IMPACT_ERR_ARG, "tuning: shared-memory target must be in [2048, 49152]");
-    if (T.count_k < 0 || T.count_k > 2)
-        return fail(IMPACT_ERR_ARG, "tuning: count_k must be 0, 1 or 2");
+    if (T.count_k < 0 || T.count_k > 3)
+        return fail(IMPACT_ERR_ARG, "tuning: count_k must be 0, 1, 2 or 3");
+    if (T.emit_k != 0 && T.emit_k != 1 && T.emit_k != 3)
+        return fail(IMPACT_ERR_ARG, "tuning: emit_k must be 0, 1 or 3");
     return IMPACT_OK;
 }
 
@@ -116,7 +119,7 @@ impact_status make_batch(const impact_request *reqs, int count, impact_precision
     B.rows = B.row_begin[count];
     B.units = B.unit_begin[count];
     h = mix(h, (uint64_t)B.tune.count_warps | ((uint64_t)B.tune.emit_warps << 8) |
-                   ((uint64_t)B.tune.count_k << 16));
+                   ((uint64_t)B.tune.count_k << 16) | ((uint64_t)B.tune.emit_k << 24));
     h = mix(h, (uint64_t)B.tune.count_smem | ((uint64_t)B.tune.emit_smem << 32));
     B.hash = h;
     return IMPACT_OK;
@@ -778,13 +781,13 @@ impact_status impact_batch_tune(const impact_request *reqs, int count,
         if (status & ~IMPACT_STATUS_UNSOUND) ms = 1e30;   // a shape that cannot run this batch
         return IMPACT_OK;
     };
-    const int warps[3] = {2, 4, 8};
+    const int warps[2] = {4, 8};
     const int smem[4] = {4096, 6144, 8192, 12288};
     impact_tuning cur;
     memset(&cur, 0, sizeof(cur));
     double best_count = 1e30, best_emit = 1e30;
     impact_tuning tb = cur;
-    for (int k = (any3 ? 1 : 0); k <= (any3 ? 2 : 0) && s == IMPACT_OK; ++k)
+    for (int k = (any3 ? 1 : 0); k <= (any3 ? 3 : 0) && s == IMPACT_OK; ++k)
         for (int w : warps)
             for (int m : smem) {
                 impact_tuning t = cur;
@@ -801,20 +804,22 @@ impact_status impact_batch_tune(const impact_request *reqs, int count,
             }
     const bool can_emit = out->col != nullptr;
     if (s == IMPACT_OK && can_emit) {
-        impact_tuning base = tb;
-        for (int w : warps)
-            for (int m : smem) {
-                impact_tuning t = base;
-                t.emit_warps = w;
-                t.emit_smem_target = m;
-                double ms;
-                s = timed(t, true, ms);
-                if (s != IMPACT_OK) break;
-                if (ms < best_emit) {
-                    best_emit = ms;
-                    tb = t;
+        const impact_tuning base = tb;
+        for (int k = (any3 ? 1 : 0); k <= (any3 ? 3 : 0) && s == IMPACT_OK; k += 2)
+            for (int w : warps)
+                for (int m : smem) {
+                    impact_tuning t = base;
+                    t.emit_warps = w;
+                    t.emit_smem_target = m;
+                    t.emit_k = k;
+                    double ms;
+                    s = timed(t, true, ms);
+                    if (s != IMPACT_OK) break;
+                    if (ms < best_emit) {
+                        best_emit = ms;
+                        tb = t;
+                    }
                 }
-            }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

@@ -77,8 +77,10 @@ struct ImpactDesc {
     int inp_div_s;
     int rec_stride;           // bytes per row record in the workspace
     int tsum_cap;             // factor entries a row record holds (all dims)
-    int tree_k;               // prefix-tree walk, count pass: dimensions a lane enumerates
-                              // at the end (1 or 2; the emit pass always 1)
+    int tree_k[2];            // prefix-tree walk, [0] count pass, [1] emit pass: how the
+                              // last dimensions are walked: 1 leaf batches, 2 two
+                              // dimensions serially per lane (count), 3 two dimensions
+                              // lane-parallel
     int ring_log2[2][IMPACT_MAX_DIM];   // prefix-tree walk: log2 capacity of the node ring
                                         // of each level, [0] count pass, [1] emit pass
     int ring_off[2][IMPACT_MAX_DIM];    // prefix-tree walk: first node of each ring

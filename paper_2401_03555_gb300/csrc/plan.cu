@@ -360,22 +360,26 @@ impact_status make_plan(const impact_system *sys, const impact_grid *grid,
             D.dim[d].rec_off = ro;
             ro += D.dim[d].wcap;
         }
-        // prefix-tree walk. Each lane finally enumerates the last K dimensions
-        // of one parent: count pass K = 2 when the last window is narrow (a
-        // lane's serial work stays short), else 1; emit pass K = 1 (pairs are
-        // spread over the lanes for coalesced stores). Levels 0..Lp (Lp =
-        // n - 1 - K) keep a ring of nodes each, a power of two: level 0 holds
-        // the root's children, the deepest level room for a full batch plus
-        // one parent's children; rings start large (fewer, fuller steps) and
-        // shrink from the largest while a warp's shared memory exceeds the
-        // target (more warps per SM).
-        D.tree_k = T.count_k == 1 || T.count_k == 2
-                       ? (n >= 3 ? T.count_k : 1)
-                       : ((n >= 3 && D.dim[n - 1].wcap <= 16) ? 2 : 1);
+        // prefix-tree walk. The last dimensions: K = 1 leaf batches under the
+        // nodes of level n - 2; K = 2 (count pass) each lane walks the last two
+        // dimensions of a level n - 3 node serially (no stores to coalesce);
+        // K = 3 the last two dimensions lane-parallel (middle nodes numbered
+        // across the warp, leaf batches of them). Defaults from measurements
+        // on the 5-D, 7-D and unicycle workloads: count 2 for n >= 4 with a
+        // narrow last window, else 3; emit 3. Levels 0..Lp keep a ring of
+        // nodes each, a power of two: level 0 holds the root's children, the
+        // deepest level room for a full batch plus one parent's children; rings
+        // start large (fewer, fuller steps) and shrink from the largest while a
+        // warp's shared memory exceeds the target (more warps per SM).
+        D.tree_k[0] = n < 3 ? 1
+                      : (T.count_k >= 1 && T.count_k <= 3)
+                          ? T.count_k
+                          : ((n >= 4 && D.dim[n - 1].wcap <= 16) ? 2 : 3);
+        D.tree_k[1] = n < 3 ? 1 : (T.emit_k == 1 || T.emit_k == 3 ? T.emit_k : 3);
         int worst = 0;
         for (int pass = 0; pass < 2; ++pass) {
-            const int K = pass == 0 ? D.tree_k : 1;
-            const int Lp = n - 1 - K;
+            const int K = D.tree_k[pass];
+            const int Lp = n - 1 - (K == 1 ? 1 : 2);
             int lg[IMPACT_MAX_DIM] = {0}, lmin[IMPACT_MAX_DIM] = {0};
             auto log2_ceil = [](int v) {
                 int l = 0;

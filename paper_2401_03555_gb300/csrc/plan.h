@@ -22,7 +22,8 @@ struct Tuning {
     int emit_warps = IMPACT_TREE_WARPS;
     int count_smem = IMPACT_TREE_SMEM_COUNT;
     int emit_smem = IMPACT_TREE_SMEM_EMIT;
-    int count_k = 0;   // 0: chosen per problem
+    int count_k = 0;   // 0: chosen per problem (1, 2, 3: see ImpactDesc::tree_k)
+    int emit_k = 0;    // 0: chosen per problem (1 or 3)
 };
 
 struct Plan {

@@ -589,8 +589,10 @@ tree_fp32(const BatchIndex *__restrict__ B, int warp_smem, int64_t *__restrict__
         const int pool = D.pool_cap[EMIT ? 1 : 0];
         const Smem S = carve<EMIT>(smem_warp, tcap, pool);
         Hdr &H = *S.h;
-        const int K = EMIT ? 1 : D.tree_k;   // dimensions a lane enumerates at the end
-        const int Lp = n - 1 - K;             // level of the block parents (-1: the root)
+        // the last dimensions: 1 leaf batches, 2 two dimensions serially per
+        // lane (count pass), 3 two dimensions lane-parallel
+        const int K = D.tree_k[EMIT ? 1 : 0];
+        const int Lp = n - 1 - (K == 1 ? 1 : 2);   // level of the batch parents (-1: the root)
         const unsigned char *rr = B->rec[q] + (row - B->row_begin[q]) * (int64_t)D.rec_stride;
         // 1. the row record: per-dimension scalars, then the trimmed tables
         if (lane < n) {
@@ -727,6 +729,47 @@ tree_fp32(const BatchIndex *__restrict__ B, int warp_smem, int64_t *__restrict__
             }
         };
 
+        // K = 3: the last two dimensions lane-parallel. Each active lane's
+        // parent owns a run of the middle dimension; the runs' nodes are
+        // numbered across the warp and taken in groups of one per lane (the
+        // owner of node e is the last lane whose first node is at or before
+        // e), and each group is a leaf batch. Same terms as K = 1, without
+        // queueing the middle nodes in a ring.
+        auto pair_batch = [&](bool act, float P, float Pl, int cb, int LB) {
+            const int dm = n - 2;
+            const int offm = H.toff[dm], stm = D.dim[dm].stride, tam = H.ta[dm];
+            int lm = 0, cm = 0;
+            if (act) run_of(S, dm, P, lm, cm);
+            if (!EMIT && act)
+                fix_add(drop, fix_up(__fmul_ru(__fmul_ru(P, outside_sum(S, dm, lm, cm)), H.swr[dm])));
+            int C1;
+            const int o = warp_excl_scan(cm, C1);
+            for (int base = 0; base < C1; base += LB) {
+                const int e = base + lane;
+                const bool a2 = lane < LB && e < C1;
+                int owner = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const int oc = __shfl_sync(0xffffffffu, o, owner + step);
+                    if (oc <= e) owner += step;
+                }
+                const float Po = __shfl_sync(0xffffffffu, P, owner);
+                const float Plo = __shfl_sync(0xffffffffu, Pl, owner);
+                const int cbo = __shfl_sync(0xffffffffu, cb, owner);
+                const int lmo = __shfl_sync(0xffffffffu, lm, owner);
+                const int oo = __shfl_sync(0xffffffffu, o, owner);
+                float P2 = 0.0f, Pl2 = 0.0f;
+                int cb2 = 0;
+                if (a2) {
+                    const int m = lmo + (e - oo);
+                    P2 = __fmul_ru(Po, S.U[offm + m]);
+                    Pl2 = __fmul_rd(Plo, S.L[offm + m]);
+                    cb2 = cbo + (tam + m) * stm;
+                }
+                leaf_batch(a2, P2, Pl2, cb2);
+            }
+        };
+
         // The walk keeps one ring buffer of nodes per level 0..Lp (level k
         // holds prefixes of k + 1 dimensions, in C order). Lane k keeps the
         // head and size of ring k. A step either consumes a batch of the
@@ -738,7 +781,7 @@ tree_fp32(const BatchIndex *__restrict__ B, int warp_smem, int64_t *__restrict__
         int my_head = 0, my_size = 0;   // ring `lane`
         const int my_cap = lane < n ? (1 << D.ring_log2[pass][lane]) : 0;
         const int my_off = lane < n ? D.ring_off[pass][lane] : 0;
-        const int LB = (K == 1 && EMIT) ? min(32, kSeg / max(H.tw[n - 1], 1)) : 32;
+        const int LB = EMIT ? min(32, kSeg / max(H.tw[n - 1], 1)) : 32;
         if (!empty) {
             // every step takes at least one node off a ring (or is the root
             // step), so the nodes of levels 0..Lp bound the steps; the guard
@@ -775,6 +818,8 @@ tree_fp32(const BatchIndex *__restrict__ B, int warp_smem, int64_t *__restrict__
                     const int cb = act ? S.ncol[ix] : 0;
                     if (K == 1)
                         leaf_batch(act, P, Pl, cb);
+                    else if (K == 3)
+                        pair_batch(act, P, Pl, cb, LB);
                     else
                         block_batch(act, P, Pl);
                     if (lane == Lp) {
@@ -796,6 +841,8 @@ tree_fp32(const BatchIndex *__restrict__ B, int warp_smem, int64_t *__restrict__
                 if (dim > Lp) {   // Lp < 0: the root is the only parent
                     if (K == 1)
                         leaf_batch(lane == 0, 1.0f, 1.0f, 0);
+                    else if (K == 3)
+                        pair_batch(lane == 0, 1.0f, 1.0f, 0, LB);
                     else
                         block_batch(lane == 0, 1.0f, 1.0f);
                     continue;

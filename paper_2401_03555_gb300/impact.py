@@ -76,7 +76,7 @@ class _Request(ctypes.Structure):
 class _Tuning(ctypes.Structure):
     _fields_ = [("count_warps", ctypes.c_int), ("emit_warps", ctypes.c_int),
                 ("count_smem_target", ctypes.c_int), ("emit_smem_target", ctypes.c_int),
-                ("count_k", ctypes.c_int)]
+                ("count_k", ctypes.c_int), ("emit_k", ctypes.c_int)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -402,9 +402,10 @@ def version() -> int:
 # batches: several builds per launch (impact_batch_*), CUDA graphs, autotuner
 # --------------------------------------------------------------------------
 
-def tuning(count_warps=0, emit_warps=0, count_smem_target=0, emit_smem_target=0, count_k=0):
+def tuning(count_warps=0, emit_warps=0, count_smem_target=0, emit_smem_target=0, count_k=0,
+           emit_k=0):
     """An impact_tuning (zero fields take the library defaults)."""
-    return _Tuning(count_warps, emit_warps, count_smem_target, emit_smem_target, count_k)
+    return _Tuning(count_warps, emit_warps, count_smem_target, emit_smem_target, count_k, emit_k)
 
 
 @dataclass

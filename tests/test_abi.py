@@ -119,7 +119,8 @@ def test_batch_plan_names_the_failing_request(lib):
 
 @pytest.mark.parametrize("field,value,msg", [("count_warps", 9, "warps"),
                                               ("emit_smem_target", 100, "shared-memory"),
-                                              ("count_k", 3, "count_k")])
+                                              ("count_k", 4, "count_k"),
+                                              ("emit_k", 2, "emit_k")])
 def test_batch_plan_rejects_bad_tuning(lib, field, value, msg):
     t = impact.tuning(**{field: value})
     with pytest.raises(impact.ImpactError, match=msg):
