@@ -522,15 +522,22 @@ __device__ __forceinline__ int warp_excl_scan(int v, int &total)
 
 // Run of dimension `dim` kept under a node with product P: [l, l + c).
 // TH is non-increasing up to the peak and non-decreasing after it.
+// Both ends by binary lifting (the trip counts depend on the row only, so the
+// lanes stay converged): the left end is the first t <= pk with T[t] <= P, the
+// right end the last t > pk with T[t] <= P.
 __device__ __forceinline__ void run_of(const Smem &S, int dim, float P, int &l, int &c)
 {
     const int off = S.h->toff[dim], pk = S.h->pk[dim], tw = S.h->tw[dim];
     const float *T = S.T + off;
-    int cl = 0, cr = 0;
-    for (int t = 0; t <= pk; ++t) cl += (T[t] <= P) ? 1 : 0;
-    for (int t = pk + 1; t < tw; ++t) cr += (T[t] <= P) ? 1 : 0;
-    c = cl > 0 ? cl + cr : 0;
-    l = pk + 1 - cl;
+    int a = pk + 1;
+    for (int st = 1 << (31 - __clz(pk + 1)); st > 0; st >>= 1)
+        if (a - st >= 0 && T[a - st] <= P) a -= st;
+    int b = pk;
+    if (tw - pk - 1 > 0)
+        for (int st = 1 << (31 - __clz(tw - pk - 1)); st > 0; st >>= 1)
+            if (b + st < tw && T[b + st] <= P) b += st;
+    c = a <= pk ? b - a + 1 : 0;
+    l = a;
 }
 
 // The same run, moved from the previous run [l, r) of the dimension under
