@@ -383,7 +383,7 @@ __device__ DimOut dim_table(const ImpactDesc &D, unsigned char *rr, int64_t row,
 // P) and the header. The lane of dimension 0 also writes the row's sink
 // bounds and the mass of the targets outside the window box (FP64, outward
 // rounding), unless the row outputs are null (records rebuilt for an emit).
-__global__ void __launch_bounds__(kSetupThreads)
+__global__ void __launch_bounds__(kSetupThreads, 3)
 setup_fp32(const BatchIndex *__restrict__ B, uint32_t *__restrict__ status,
            double *__restrict__ sink_lo, double *__restrict__ sink_up, double *__restrict__ trunc)
 {
