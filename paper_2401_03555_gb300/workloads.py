@@ -256,3 +256,31 @@ def bas_4d(eta_scale: float = 1.0) -> Problem:
         kind=AFFINE, lo=lo, hi=hi, cells=cells,
         inputs=input_points([17], [20], [1]),
         sigma=np.sqrt(var), cutoff=0.0, A=A, B=B, c=c)
+
+
+def region_labels(prob: Problem, target=None, avoid=None) -> np.ndarray:
+    """Per-cell labels for synthesis: 1 if the cell's centre lies in a target
+    box, 2 if in an avoid box (avoid wins), else 0. Boxes are (lo, hi) pairs
+    of coordinate lists; `target` / `avoid` are one box or a list of them."""
+    cells = np.asarray(prob.cells, dtype=np.int64)
+    lo = np.asarray(prob.lo, np.float64)
+    hi = np.asarray(prob.hi, np.float64)
+    h = (hi - lo) / cells
+    axes = [lo[d] + (np.arange(cells[d]) + 0.5) * h[d] for d in range(len(cells))]
+    mesh = np.meshgrid(*axes, indexing="ij")
+    centres = np.stack([m.reshape(-1) for m in mesh], axis=1)
+    labels = np.zeros(centres.shape[0], np.uint8)
+
+    def boxes(b):
+        if b is None:
+            return []
+        if len(b) == 2 and np.ndim(b[0]) == 1:
+            return [b]
+        return list(b)
+
+    for code, spec in ((1, target), (2, avoid)):
+        for blo, bhi in boxes(spec):
+            inside = np.all((centres >= np.asarray(blo)) & (centres <= np.asarray(bhi)), axis=1)
+            labels[inside] = code
+    return labels
+
