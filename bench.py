@@ -69,6 +69,8 @@ def parse_args(argv=None):
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     p.add_argument("--no-serve", action="store_true",
                    help="skip the served stream (Poisson arrivals, continuous batching)")
+    p.add_argument("--no-synth", action="store_true",
+                   help="skip the controller-synthesis measurement (interval iteration)")
     p.add_argument("--no-batched", action="store_true",
                    help="skip the batched workload (256 seeded systems, graphs, autotuner)")
     p.add_argument("--cpu-rows", type=int, default=0, help="oracle sample size (0: auto)")
@@ -365,6 +367,13 @@ def run_ours(args, rank, world, local_rank):
             out["batched"] = {"value": None, "error": str(exc)[:300]}
         torch.cuda.empty_cache()
 
+    if not args.no_synth and rank == 0:
+        try:
+            out["synthesis"] = run_synthesis()
+        except Exception as exc:
+            out["synthesis"] = {"value": None, "error": str(exc)[:300]}
+        torch.cuda.empty_cache()
+
     if not args.no_serve and rank == 0:
         try:
             out["served"] = run_serving()
@@ -471,6 +480,49 @@ def run_batched(dev, stream, reps=2, cap_pairs=8_000_000_000):
             "gpu_launches_per_pass": LAUNCHES_PER_STEP * len(groups),
             "path": "impact_graph_launch per group (count + scan + emit, one persistent "
                     "launch per kernel over every system of the group)"}
+
+
+SYNTH_WORKLOAD = ("reach-avoid controller for the 2-D robot (21^2 cells, 9 inputs, dense "
+                  "FP64 IMDP, 1.75e6 pairs): target [3,7]^2, avoid [-7,-3]^2 and the "
+                  "out-of-domain sink; interval iteration to eps 1e-6, both phases")
+
+
+def run_synthesis(eps=1e-6, oracle_iters=2):
+    """impact_synthesize on the robot abstraction; the oracle's interval
+    iteration timed on the same IMDP for a bounded number of iterations."""
+    import torch
+    from paper_2401_03555_gb300 import impact, workloads as W
+    prob = W.robot_2d()
+    labels = W.region_labels(prob, target=([3, 3], [7, 7]), avoid=([-7, -7], [-3, -3]))
+    csr = impact.build(prob, "fp64")
+    impact.synthesize(csr, prob, labels, eps=eps)          # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g = impact.synthesize(csr, prob, labels, eps=eps)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    its = sum(g.iterations)
+    # one iteration = both vectors' Bellman update over every row
+    row_lps = 2 * prob.rows * its
+    out = {"workload": SYNTH_WORKLOAD, "iterations": list(g.iterations), "ms": dt * 1e3,
+           "ms_per_iteration": dt * 1e3 / its, "value": row_lps / dt, "unit": "row LPs/s",
+           "p_min_max": float(g.p_min.max().item()),
+           "path": "impact_synthesize (sorting-method LP by warp bisection, one warp per cell)"}
+    try:
+        import oracle
+        from oracle import synthesis as SY
+        ocsr = oracle.build_rows(prob)
+        t0 = time.perf_counter()
+        SY.interval_iteration(ocsr, labels, prob.n_inputs, SY.REACH_AVOID, eps=eps,
+                              max_iters=oracle_iters)
+        odt = time.perf_counter() - t0
+        # the oracle runs both phases for `oracle_iters` iterations each
+        out["cpu_baseline"] = {"value": 2 * prob.rows * 2 * oracle_iters / odt,
+                               "unit": "row LPs/s", "cores": 1, "kind": "oracle",
+                               "sample": f"{oracle_iters} iterations of each phase"}
+    except Exception as exc:
+        out["cpu_baseline"] = {"value": None, "error": str(exc)[:200]}
+    return out
 
 
 SERVED_WORKLOAD = ("Poisson stream of 500 requests (seed 1): 7-D building (6^7 cells, inputs "

@@ -374,6 +374,40 @@ impact_status impact_server_stats(impact_server *server, impact_server_stats_t *
 /* Waits for every submitted request, then frees everything. */
 impact_status impact_server_destroy(impact_server *server);
 
+/* ------------------------------------------------------------------------
+ * Controller synthesis on a built IMDP (paper: Sec. 5 and Alg. 3/4, the LP of
+ * Sec. 5 solved by the sorting method of Sec. 6.2), pessimistic policy.
+ * ------------------------------------------------------------------------ */
+
+typedef enum {
+    IMPACT_REACH_AVOID = 0,   /* reach a target cell, never an avoid cell or the sink */
+    IMPACT_SAFETY = 1         /* never reach an avoid cell or the sink             */
+} impact_spec;
+
+/*
+ * impact_synthesize -- interval iteration on the IMDP `imdp` (a result of
+ * impact_build for one build: rows = cells * n_inputs, all arrays on the
+ * device; FP32 or FP64 values per `precision`). labels: DEVICE uint8[cells],
+ * 0 free, 1 target, 2 avoid. The successors of a row are its kept targets
+ * [lo, up], the sink [sink_lo, sink_up] and the truncated mass [0, trunc]
+ * (valued at its worst end: 0 in a min LP, 1 in a max LP). Phase 1 iterates
+ * V0 (from 0) and V1 (from 1) with the best input per cell (reach-avoid:
+ * max over inputs of the min LP; safety: min over inputs of the max LP of
+ * reaching an avoid cell or the sink) until max |V1 - V0| <= eps, and fixes
+ * that input as the policy; phase 2 iterates the opposite LP under the policy.
+ * Writes p_min, p_max (DEVICE double[cells]: reach-avoid V0 of phase 1 and V1
+ * of phase 2; safety 1 - V1 of phase 1 and 1 - V0 of phase 2) and policy
+ * (DEVICE int32[cells], input index; 0 on labelled cells), and the iterations
+ * of each phase to iterations[2] (host, may be NULL). A phase that reaches
+ * max_iters stops there (its interval is then wider than eps). Synchronizes
+ * `stream` once per iteration. Errors: IMPACT_ERR_ARG, IMPACT_ERR_OOM,
+ * IMPACT_ERR_CUDA.
+ */
+impact_status impact_synthesize(const impact_csr *imdp, impact_precision precision,
+                                int64_t cells, int n_inputs, const uint8_t *labels, int spec,
+                                double eps, int max_iters, double *p_min, double *p_max,
+                                int32_t *policy, int *iterations, void *stream);
+
 /* Release library-owned arrays of a result (no-op for caller-owned ones). */
 impact_status impact_free(impact_csr *out);
 

@@ -34,7 +34,7 @@ ENTRY_POINTS = ("impact_plan", "impact_workspace_bytes", "impact_build", "impact
                 "impact_graph_launch", "impact_graph_result", "impact_graph_destroy",
                 "impact_batch_tune", "impact_server_create", "impact_server_submit",
                 "impact_server_poll", "impact_server_release", "impact_server_stats",
-                "impact_server_destroy")
+                "impact_server_destroy", "impact_synthesize")
 
 
 class ImpactError(RuntimeError):
@@ -169,6 +169,12 @@ def load(build_if_missing: bool = True):
         lib.impact_server_stats.argtypes = [ctypes.c_void_p, ctypes.POINTER(_ServerStats)]
         lib.impact_server_destroy.restype = ctypes.c_int
         lib.impact_server_destroy.argtypes = [ctypes.c_void_p]
+        lib.impact_synthesize.restype = ctypes.c_int
+        lib.impact_synthesize.argtypes = [ctypes.POINTER(_CSR), ctypes.c_int, ctypes.c_int64,
+                                          ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                          ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]
         _lib = lib
         return lib
 
@@ -649,4 +655,42 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+# --------------------------------------------------------------------------
+# controller synthesis (impact_synthesize)
+# --------------------------------------------------------------------------
+
+REACH_AVOID, SAFETY = 0, 1
+
+
+@dataclass
+class Controller:
+    p_min: torch.Tensor     # float64 [cells]
+    p_max: torch.Tensor     # float64 [cells]
+    policy: torch.Tensor    # int32 [cells]
+    iterations: tuple
+
+
+def synthesize(csr: CSR, prob, labels, spec=REACH_AVOID, eps=1e-6, max_iters=10000,
+               stream=None) -> Controller:
+    """Interval iteration on a device IMDP built for `prob` (impact_synthesize)."""
+    cells = int(prob.total_cells)
+    lab = torch.as_tensor(np.asarray(labels, np.uint8)).cuda()
+    dev = lab.device
+    p_min = torch.empty(cells, dtype=torch.float64, device=dev)
+    p_max = torch.empty(cells, dtype=torch.float64, device=dev)
+    pol = torch.empty(cells, dtype=torch.int32, device=dev)
+    c = _CSR()
+    c.rows = csr.rows
+    c.nnz = csr.nnz
+    p = lambda t: t.data_ptr()
+    c.row_ptr, c.col, c.lo, c.up = p(csr.row_ptr), p(csr.col), p(csr.lo), p(csr.up)
+    c.sink_lo, c.sink_up, c.trunc = p(csr.sink_lo), p(csr.sink_up), p(csr.trunc)
+    its = (ctypes.c_int * 2)()
+    _check(load().impact_synthesize(ctypes.byref(c), _PREC[csr.precision], cells,
+                                    int(prob.n_inputs), p(lab), int(spec), float(eps),
+                                    int(max_iters), p(p_min), p(p_max), p(pol), its,
+                                    ctypes.c_void_p(_stream_handle(stream))))
+    return Controller(p_min, p_max, pol, (int(its[0]), int(its[1])))
 
