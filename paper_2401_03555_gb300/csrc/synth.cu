@@ -16,9 +16,10 @@
 // the upper end otherwise, so V0 stays below and V1 above their exact values.
 // The max LP is the min LP of the values 1 - v.
 //
-// One warp per free cell walks the cell's rows (one per input), keeps the best
-// input, and writes the cell's next V0 and V1; the largest |V1 - V0| is
-// gathered with an atomic max on the bits of a non-negative double.
+// One warp per row computes the row's LP for both vectors; one thread per cell
+// then keeps the best input (or the policy's) and writes the cell's next V0
+// and V1; the largest |V1 - V0| is gathered with an atomic max on the bits of
+// a non-negative double.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -35,6 +36,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kBisect = 52;   // bracket width 2^-52 of [0, 1]
+constexpr int kCache = 16;    // successors per lane kept in registers (rows <= 512)
 
 #define CK(expr)                                                                              \
     do {                                                                                      \
@@ -109,6 +111,48 @@ __device__ double row_lp(const RowRef &R, const int32_t *__restrict__ col,
     double res;
     if (rest <= 0.0) {
         res = slov;
+    } else if (R.b - R.a <= 32 * kCache) {
+        // short rows: each lane keeps its successors' values and widths in
+        // registers for the whole bisection
+        double cv[kCache], cw[kCache];
+#pragma unroll
+        for (int k = 0; k < kCache; ++k) {
+            const int64_t i = R.a + lane + 32 * k;
+            const bool in = i < R.b;
+            cv[k] = in ? val(V[col[i]]) : 2.0;   // 2: never <= x
+            cw[k] = in ? (double)up[i] - (double)lo[i] : 0.0;
+        }
+        auto Gc = [&](double x, double &gv) {
+            double g = 0.0, v2 = 0.0;
+#pragma unroll
+            for (int k = 0; k < kCache; ++k)
+                if (cv[k] <= x) {
+                    g += cw[k];
+                    v2 += cw[k] * cv[k];
+                }
+            g = warp_sum(g);
+            v2 = warp_sum(v2);
+            if (sv <= x) {
+                g += R.sink_up - R.sink_lo;
+                v2 += (R.sink_up - R.sink_lo) * sv;
+            }
+            if (tv <= x) {
+                g += R.trunc;
+                v2 += R.trunc * tv;
+            }
+            gv = v2;
+            return g;
+        };
+        double xl = -1.0, xh = 1.0;
+        for (int it = 0; it < kBisect; ++it) {
+            const double xm = 0.5 * (xl + xh);
+            double gv;
+            if (Gc(xm, gv) >= rest) xh = xm; else xl = xm;
+        }
+        double gv;
+        const double g = Gc(xl, gv);
+        const double x = maximize ? (high ? xl : xh) : (high ? xh : xl);
+        res = slov + gv + (rest - g) * fmax(x, 0.0);
     } else {
         double xl = -1.0, xh = 1.0;   // G(xl) = 0 < rest; G(1) >= rest by the row invariants
         for (int it = 0; it < kBisect; ++it) {
@@ -130,54 +174,85 @@ struct Phase {
     bool maximize;    // the LP direction
 };
 
+// The LP of every row the phase needs (all inputs in phase 1, the policy's in
+// phase 2), one warp per row, for both vectors.
 template <typename VT>
 __global__ void __launch_bounds__(kThreads)
-bellman(Phase ph, int64_t cells, int n_inputs, const uint8_t *__restrict__ labels,
-        const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
-        const VT *__restrict__ lo, const VT *__restrict__ up, const double *__restrict__ sink_lo,
-        const double *__restrict__ sink_up, const double *__restrict__ trunc,
-        const double *__restrict__ V0, const double *__restrict__ V1, double *__restrict__ N0,
-        double *__restrict__ N1, int32_t *__restrict__ policy, unsigned long long *__restrict__ diff)
+row_values(Phase ph, int64_t rows, int n_inputs, const uint8_t *__restrict__ labels,
+           const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
+           const VT *__restrict__ lo, const VT *__restrict__ up,
+           const double *__restrict__ sink_lo, const double *__restrict__ sink_up,
+           const double *__restrict__ trunc, const double *__restrict__ V0,
+           const double *__restrict__ V1, const int32_t *__restrict__ policy,
+           double *__restrict__ R0, double *__restrict__ R1)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const double sink_v = ph.spec == IMPACT_REACH_AVOID ? 0.0 : 1.0;
+    for (int64_t r = warp0; r < rows; r += nwarps) {
+        const int64_t c = r / n_inputs;
+        const int j = (int)(r - c * n_inputs);
+        if (labels[c] != 0 || (!ph.choose && j != policy[c])) continue;
+        RowRef R{row_ptr[r], row_ptr[r + 1], sink_lo[r], sink_up[r], trunc[r]};
+        // V0 never rises above, V1 never falls below the exact update
+        const double a = row_lp(R, col, lo, up, V0, ph.maximize, sink_v, false);
+        const double b = row_lp(R, col, lo, up, V1, ph.maximize, sink_v, true);
+        if (lane == 0) {
+            R0[r] = a;
+            R1[r] = b;
+        }
+    }
+}
+
+// Per cell: the best input (phase 1) or the policy's row (phase 2), the next
+// V0 and V1, and the largest |V1 - V0|.
+__global__ void __launch_bounds__(kThreads)
+cell_update(Phase ph, int64_t cells, int n_inputs, const uint8_t *__restrict__ labels,
+            const double *__restrict__ R0, const double *__restrict__ R1,
+            double *__restrict__ N0, double *__restrict__ N1, int32_t *__restrict__ policy,
+            unsigned long long *__restrict__ diff)
+{
     const bool reach = ph.spec == IMPACT_REACH_AVOID;
-    const double sink_v = reach ? 0.0 : 1.0;
     // reach-avoid phase 1: max over inputs of the min LP; safety: min of max
     const bool pick_max = reach;
-    for (int64_t c = warp0; c < cells; c += nwarps) {
+    double dmax = 0.0;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < cells;
+         c += (int64_t)gridDim.x * blockDim.x) {
         const uint8_t lab = labels[c];
         double n0, n1;
-        int32_t arg = ph.choose ? 0 : policy[c];
         if (lab != 0) {   // absorbing: target (reach) or avoid (safety) has value 1
             n0 = n1 = (reach ? lab == 1 : lab == 2) ? 1.0 : 0.0;
-        } else {
-            const int j0 = ph.choose ? 0 : arg, j1 = ph.choose ? n_inputs : arg + 1;
+            if (ph.choose) policy[c] = 0;
+        } else if (ph.choose) {
             double b0 = 0.0, b1 = 0.0;
-            for (int j = j0; j < j1; ++j) {
-                const int64_t r = c * n_inputs + j;
-                RowRef R{row_ptr[r], row_ptr[r + 1], sink_lo[r], sink_up[r], trunc[r]};
-                // V0 never rises above, V1 never falls below the exact update
-                const double a = row_lp(R, col, lo, up, V0, ph.maximize, sink_v, false);
-                const double b = row_lp(R, col, lo, up, V1, ph.maximize, sink_v, true);
-                if (j == j0 || (pick_max ? a > b0 : a < b0)) {
+            int arg = 0;
+            for (int j = 0; j < n_inputs; ++j) {
+                const double a = R0[c * n_inputs + j], b = R1[c * n_inputs + j];
+                if (j == 0 || (pick_max ? a > b0 : a < b0)) {
                     b0 = a;
                     arg = j;
                 }
-                if (j == j0 || (pick_max ? b > b1 : b < b1)) b1 = b;
+                if (j == 0 || (pick_max ? b > b1 : b < b1)) b1 = b;
             }
-            n0 = fmin(fmax(b0, 0.0), 1.0);
-            n1 = fmin(fmax(b1, 0.0), 1.0);
+            policy[c] = arg;
+            n0 = b0;
+            n1 = b1;
+        } else {
+            const int64_t r = c * n_inputs + policy[c];
+            n0 = R0[r];
+            n1 = R1[r];
         }
-        if (lane == 0) {
-            N0[c] = n0;
-            N1[c] = n1;
-            if (ph.choose) policy[c] = arg;
-            const double d = fabs(n1 - n0);
-            atomicMax(diff, (unsigned long long)__double_as_longlong(d));
-        }
+        n0 = fmin(fmax(n0, 0.0), 1.0);
+        n1 = fmin(fmax(n1, 0.0), 1.0);
+        N0[c] = n0;
+        N1[c] = n1;
+        dmax = fmax(dmax, fabs(n1 - n0));
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    if ((threadIdx.x & 31) == 0 && dmax > 0.0)
+        atomicMax(diff, (unsigned long long)__double_as_longlong(dmax));
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -250,14 +325,16 @@ extern "C" impact_status impact_synthesize(const impact_csr *imdp, impact_precis
                            !device_array(imdp->up))))
         return fail(IMPACT_ERR_ARG, "the IMDP, labels and outputs must be device arrays");
     cudaStream_t st = (cudaStream_t)stream;
-    double *buf = nullptr;
+    double *buf = nullptr, *rbuf = nullptr;
     unsigned long long *d_diff = nullptr, *h_diff = nullptr;
+    const int64_t rows = cells * n_inputs;
     CK(cudaMallocAsync((void **)&buf, (size_t)cells * 4 * sizeof(double), st));
+    CK(cudaMallocAsync((void **)&rbuf, (size_t)rows * 2 * sizeof(double), st));
     CK(cudaMallocAsync((void **)&d_diff, sizeof(unsigned long long), st));
     CK(cudaMallocHost((void **)&h_diff, sizeof(unsigned long long)));
     const bool reach = spec == IMPACT_REACH_AVOID;
     const int g_cells = grid_of(cells, kThreads);
-    const int g_warps = grid_of(cells, kThreads / 32);
+    const int g_rows = grid_of(rows, kThreads / 32);
     impact_status status = IMPACT_OK;
     int its[2] = {0, 0};
     for (int phase = 0; phase < 2 && status == IMPACT_OK; ++phase) {
@@ -271,16 +348,19 @@ extern "C" impact_status impact_synthesize(const impact_csr *imdp, impact_precis
         int it = 0;
         while (it < max_iters) {
             cudaMemsetAsync(d_diff, 0, sizeof(unsigned long long), st);
+            double *R0 = rbuf, *R1 = rbuf + rows;
             if (precision == IMPACT_FP32_SOUND)
-                bellman<float><<<g_warps, kThreads, 0, st>>>(
-                    ph, cells, n_inputs, labels, imdp->row_ptr, imdp->col,
+                row_values<float><<<g_rows, kThreads, 0, st>>>(
+                    ph, rows, n_inputs, labels, imdp->row_ptr, imdp->col,
                     (const float *)imdp->lo, (const float *)imdp->up, imdp->sink_lo,
-                    imdp->sink_up, imdp->trunc, V0, V1, N0, N1, policy, d_diff);
+                    imdp->sink_up, imdp->trunc, V0, V1, policy, R0, R1);
             else
-                bellman<double><<<g_warps, kThreads, 0, st>>>(
-                    ph, cells, n_inputs, labels, imdp->row_ptr, imdp->col,
+                row_values<double><<<g_rows, kThreads, 0, st>>>(
+                    ph, rows, n_inputs, labels, imdp->row_ptr, imdp->col,
                     (const double *)imdp->lo, (const double *)imdp->up, imdp->sink_lo,
-                    imdp->sink_up, imdp->trunc, V0, V1, N0, N1, policy, d_diff);
+                    imdp->sink_up, imdp->trunc, V0, V1, policy, R0, R1);
+            cell_update<<<g_cells, kThreads, 0, st>>>(ph, cells, n_inputs, labels, R0, R1, N0, N1,
+                                                      policy, d_diff);
             cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) {
                 status = fail(IMPACT_ERR_CUDA, cudaGetErrorString(e));
@@ -308,6 +388,7 @@ extern "C" impact_status impact_synthesize(const impact_csr *imdp, impact_precis
         finish<<<g_cells, kThreads, 0, st>>>(spec, cells, src, !reach, dst);
     }
     cudaFreeAsync(buf, st);
+    cudaFreeAsync(rbuf, st);
     cudaFreeAsync(d_diff, st);
     cudaStreamSynchronize(st);
     cudaFreeHost(h_diff);
