@@ -13,6 +13,12 @@ A *problem* is any object with the attributes ``kind`` (0 affine, 1 unicycle,
 ``None``). Rows are numbered ``cell * n_inputs + j`` with the cell id in C
 order (last dimension fastest).
 
+Regions (Sec. 3.1, Alg. 1, Remark 4.1): cells are labelled target / avoid
+when their centre lies in a target / avoid box; the per-row vectors R and A
+are either the paper's sums of the per-cell bounds over the labelled cells
+or one box relaxation per region box (the box's cells taken as one big
+target), the sink added to A.
+
 Parity pins: every function here is pinned by ``tests/test_oracle_pins.py``
 (library CDF, telescoping identity, 1-D closed form, brute-force argmax for
 separable systems, Monte-Carlo containment, noise sampling, invariants,
@@ -100,6 +106,17 @@ class Oracle:
         lib.oracle_release.argtypes = [ctypes.c_void_p]
         lib.oracle_max_threads.restype = ctypes.c_int
         lib.oracle_max_threads.argtypes = []
+        lib.oracle_box_cells.restype = ctypes.c_int
+        lib.oracle_box_cells.argtypes = [P] + [ctypes.c_void_p] * 4
+        lib.oracle_labels.restype = None
+        lib.oracle_labels.argtypes = [P, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p]
+        lib.oracle_region_rows.restype = None
+        lib.oracle_region_rows.argtypes = [P, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
+                                           ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_void_p]
         self.lib = lib
         self.path = lib_path
 
@@ -163,6 +180,52 @@ class Oracle:
         """OpenMP threads the oracle uses by default."""
         return int(self.lib.oracle_max_threads())
 
+    def box_cells(self, prob, box):
+        """Index range (first, last) per dimension of the cells whose centre
+        lies in the closed box ``(lo, hi)``, or None when there is none."""
+        mp = _Marshalled(prob)
+        lo, hi = (_f64(b).reshape(mp.n) for b in box)
+        first = np.zeros(mp.n, np.int32)
+        last = np.zeros(mp.n, np.int32)
+        ok = self.lib.oracle_box_cells(ctypes.byref(mp.struct), lo.ctypes.data, hi.ctypes.data,
+                                       first.ctypes.data, last.ctypes.data)
+        return (first, last) if ok else None
+
+    def region_labels(self, prob, target=(), avoid=()) -> np.ndarray:
+        """uint8 label per cell: 0 free, 1 target, 2 avoid (avoid wins)."""
+        mp = _Marshalled(prob)
+        (tl, th), (al, ah) = _box_arrays(target, mp.n), _box_arrays(avoid, mp.n)
+        out = np.zeros(mp.total_cells, np.uint8)
+        self.lib.oracle_labels(ctypes.byref(mp.struct), len(target), tl.ctypes.data,
+                               th.ctypes.data, len(avoid), al.ctypes.data, ah.ctypes.data,
+                               out.ctypes.data)
+        return out
+
+    def region_vectors(self, prob, rows=None, target=(), avoid=(), mode: str = "box"):
+        """(R_min, R_max, A_min, A_max) per row; mode "box" (one relaxation
+        per region box) or "cells" (the paper's sums of per-cell bounds)."""
+        mp = _Marshalled(prob)
+        if rows is None:
+            rows = np.arange(mp.rows, dtype=np.int64)
+        rows = np.ascontiguousarray(np.asarray(rows, dtype=np.int64))
+        if mode == "box":
+            spans = [self.box_cells(prob, b) for b in list(target) + list(avoid)]
+            spans = [s for s in spans if s is not None]
+            for i in range(len(spans)):
+                for k in range(i):
+                    (f1, l1), (f2, l2) = spans[i], spans[k]
+                    if np.all(np.maximum(f1, f2) <= np.minimum(l1, l2)):
+                        raise ValueError("region boxes share cells")
+        (tl, th), (al, ah) = _box_arrays(target, mp.n), _box_arrays(avoid, mp.n)
+        labels = self.region_labels(prob, target, avoid)
+        out = np.zeros((rows.shape[0], 4))
+        self.lib.oracle_region_rows(ctypes.byref(mp.struct), rows.ctypes.data,
+                                    int(rows.shape[0]), 0 if mode == "box" else 1,
+                                    labels.ctypes.data, len(target), tl.ctypes.data,
+                                    th.ctypes.data, len(avoid), al.ctypes.data, ah.ctypes.data,
+                                    out.ctypes.data)
+        return out[:, 0].copy(), out[:, 1].copy(), out[:, 2].copy(), out[:, 3].copy()
+
 
 def default() -> Oracle:
     """The oracle compiled from ``impact_oracle.c`` (built on first use)."""
@@ -192,6 +255,16 @@ def source_text() -> str:
 
 def _f64(x):
     return None if x is None else np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+
+
+def _box_arrays(boxes, n):
+    """[(lo, hi), ...] -> two contiguous [count][n] arrays (at least one row)."""
+    lo = np.zeros((max(len(boxes), 1), n))
+    hi = np.zeros((max(len(boxes), 1), n))
+    for k, (a, b) in enumerate(boxes):
+        lo[k] = np.asarray(a, np.float64).reshape(n)
+        hi[k] = np.asarray(b, np.float64).reshape(n)
+    return np.ascontiguousarray(lo), np.ascontiguousarray(hi)
 
 
 class _Marshalled:
@@ -277,3 +350,11 @@ def build_rows(prob, rows=None, threads: int = 0) -> OracleCSR:
 
 def max_threads() -> int:
     return default().max_threads()
+
+
+def region_labels(prob, target=(), avoid=()):
+    return default().region_labels(prob, target, avoid)
+
+
+def region_vectors(prob, rows=None, target=(), avoid=(), mode="box"):
+    return default().region_vectors(prob, rows, target, avoid, mode)

@@ -351,3 +351,137 @@ int oracle_max_threads(void)
     return 1;
 #endif
 }
+
+/* ---- target / avoid regions (Sec. 3.1, Alg. 1, Remark 4.1) --------------- */
+
+enum { ORACLE_FREE = 0, ORACLE_TARGET = 1, ORACLE_AVOID = 2 };
+
+/* Centre of cell i of dimension d. */
+static double cell_centre(const oracle_problem *p, int d, int i)
+{
+    return 0.5 * (oracle_edge(p, d, i) + oracle_edge(p, d, i + 1));
+}
+
+/*
+ * Cells of one region box: in every dimension the cells whose centre lies in
+ * the closed interval [box_lo_d, box_hi_d] (a contiguous index range). Writes
+ * the first and last index per dimension; returns 0 when no cell qualifies.
+ */
+int oracle_box_cells(const oracle_problem *p, const double *box_lo, const double *box_hi,
+                     int *first, int *last)
+{
+    for (int d = 0; d < p->n; ++d) {
+        first[d] = -1;
+        last[d] = -2;
+        for (int i = 0; i < p->cells[d]; ++i) {
+            double c = cell_centre(p, d, i);
+            if (c >= box_lo[d] && c <= box_hi[d]) {
+                if (first[d] < 0) first[d] = i;
+                last[d] = i;
+            }
+        }
+        if (first[d] < 0) return 0;
+    }
+    return 1;
+}
+
+/*
+ * Labels of every cell (Sec. 3.1: target and avoid states are absorbing): a
+ * cell is avoid if its centre lies in an avoid box, else target if it lies in
+ * a target box, else free. Boxes: [count][n] lower and upper corners.
+ */
+void oracle_labels(const oracle_problem *p, int n_target, const double *t_lo, const double *t_hi,
+                   int n_avoid, const double *a_lo, const double *a_hi, uint8_t *labels)
+{
+    int64_t T = total_cells(p);
+    for (int64_t t = 0; t < T; ++t) {
+        uint8_t lab = ORACLE_FREE;
+        for (int k = 0; k < n_target + n_avoid; ++k) {
+            int avoid = k >= n_target;
+            const double *lo = avoid ? a_lo + (k - n_target) * p->n : t_lo + k * p->n;
+            const double *hi = avoid ? a_hi + (k - n_target) * p->n : t_hi + k * p->n;
+            int in = 1;
+            for (int d = 0; d < p->n && in; ++d) {
+                double c = cell_centre(p, d, cell_digit(p, t, d));
+                in = c >= lo[d] && c <= hi[d];
+            }
+            if (in && avoid) lab = ORACLE_AVOID;
+            else if (in && lab == ORACLE_FREE) lab = ORACLE_TARGET;
+        }
+        labels[t] = lab;
+    }
+}
+
+/*
+ * Region vectors of one row: out = (R_min, R_max, A_min, A_max).
+ *   mode 1 (the paper's sums, Alg. 1): R = sum over the target-labelled
+ *     cells of the per-cell bounds [lo_t, up_t] (every cell, no cutoff);
+ *     A = the same over the avoid cells plus the sink bounds (Remark 4.1).
+ *   mode 0 (one relaxation per region box): each box is replaced by the
+ *     union of its cells, [edge first_d, edge last_d + 1] per dimension, and
+ *     bounded like one big target cell: up = prod_d g_d(clamp(mid_d)),
+ *     lo = prod_d min(g_d(m_lo_d), g_d(m_hi_d)); R and A sum their boxes,
+ *     A adds the sink.
+ * `labels` (mode 1) comes from oracle_labels; the boxes (mode 0) must cover
+ * pairwise disjoint sets of cells (checked by the caller).
+ */
+void oracle_region_row(const oracle_problem *p, int64_t row, int mode, const uint8_t *labels,
+                       int n_target, const double *t_lo, const double *t_hi, int n_avoid,
+                       const double *a_lo, const double *a_hi, double *out)
+{
+    int n = p->n;
+    int64_t T = total_cells(p);
+    double *up = (double *)malloc(sizeof(double) * (size_t)T);
+    double *lo = (double *)malloc(sizeof(double) * (size_t)T);
+    double sl, su;
+    oracle_row_dense(p, row, up, lo, &sl, &su);
+    double r_lo = 0.0, r_up = 0.0, x_lo = 0.0, x_up = 0.0;
+    if (mode == 1) {
+        for (int64_t t = 0; t < T; ++t) {
+            if (labels[t] == ORACLE_TARGET) { r_lo += lo[t]; r_up += up[t]; }
+            if (labels[t] == ORACLE_AVOID) { x_lo += lo[t]; x_up += up[t]; }
+        }
+    } else {
+        double m_lo[ORACLE_MAX_DIM], m_hi[ORACLE_MAX_DIM];
+        oracle_image(p, row, m_lo, m_hi);
+        for (int k = 0; k < n_target + n_avoid; ++k) {
+            int avoid = k >= n_target;
+            const double *blo = avoid ? a_lo + (k - n_target) * n : t_lo + k * n;
+            const double *bhi = avoid ? a_hi + (k - n_target) * n : t_hi + k * n;
+            int first[ORACLE_MAX_DIM], last[ORACLE_MAX_DIM];
+            if (!oracle_box_cells(p, blo, bhi, first, last)) continue;
+            double b_up = 1.0, b_lo = 1.0;
+            for (int d = 0; d < n; ++d) {
+                double left = oracle_edge(p, d, first[d]);
+                double right = oracle_edge(p, d, last[d] + 1);
+                double sd = p->sigma[d];
+                double centre = 0.5 * (left + right);
+                double r_max = oracle_phi_diff(left, right, clamp(centre, m_lo[d], m_hi[d]), sd);
+                double r_a = oracle_phi_diff(left, right, m_lo[d], sd);
+                double r_b = oracle_phi_diff(left, right, m_hi[d], sd);
+                b_up *= r_max;
+                b_lo *= r_a < r_b ? r_a : r_b;
+            }
+            if (avoid) { x_lo += b_lo; x_up += b_up; }
+            else { r_lo += b_lo; r_up += b_up; }
+        }
+    }
+    out[0] = r_lo;
+    out[1] = r_up;
+    out[2] = sl + x_lo;
+    out[3] = su + x_up;
+    free(up);
+    free(lo);
+}
+
+/* oracle_region_row over a list of rows (OpenMP), out: [nrows][4]. */
+void oracle_region_rows(const oracle_problem *p, const int64_t *rows, int64_t nrows, int mode,
+                        const uint8_t *labels, int n_target, const double *t_lo,
+                        const double *t_hi, int n_avoid, const double *a_lo, const double *a_hi,
+                        double *out)
+{
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t k = 0; k < nrows; ++k)
+        oracle_region_row(p, rows[k], mode, labels, n_target, t_lo, t_hi, n_avoid, a_lo, a_hi,
+                          out + 4 * k);
+}

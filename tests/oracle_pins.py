@@ -376,3 +376,124 @@ def coupled_cases():
     return [(room, W.sample_rows(room, 4, seed=1)), (bas, W.sample_rows(bas, 4, seed=2)),
             (uni, W.sample_rows(uni, 6, seed=3)), (lin, W.sample_rows(lin, 4, seed=4)),
             (b7, W.sample_rows(b7, 2, seed=5, include_boundary=False))]
+
+
+# --------------------------------------------------------------------------
+# regions (Sec. 3.1, Alg. 1, Remark 4.1)
+# --------------------------------------------------------------------------
+
+
+def region_cases():
+    """(problem, target boxes, avoid boxes, rows): regions away from cell
+    centres (the labels do not hinge on a rounding), rows near and far."""
+    robot = W.robot_2d(cells_per_dim=9)
+    room = W.room_5d(cells_per_dim=4)
+    uni = W.unicycle_3d(nx=6, ny=6, nth=5)
+    b7 = W.building_7d(cells_per_dim=3)
+    return [
+        (robot, [([3.1, 3.1], [7.2, 7.2])],
+         [([-7.2, -7.2], [-3.1, -3.1]), ([-9.6, 4.1], [-5.9, 9.3])],
+         [0, 40, 120, 301, 365, 601, 700]),
+        (room, [([18.4] * 5, [21.6] * 5)], [([17.0] * 5, [18.1, 23, 23, 23, 23])],
+         W.sample_rows(room, 4, seed=21)),
+        (uni, [([1.0, 1.0, -4.0], [5.0, 5.0, 4.0])], [([-5.0, -1.0, -4.0], [-1.2, 1.0, 4.0])],
+         W.sample_rows(uni, 4, seed=22)),
+        (b7, [([-3.0] * 7, [-0.5] + [3.0] * 6)], [([0.5] + [-3.0] * 6, [3.0] * 7)],
+         W.sample_rows(b7, 2, seed=23, include_boundary=False)),
+    ]
+
+
+def pin_region_labels(orc):
+    """The oracle's labels against the generator module's own restatement
+    (cell centres on a mesh), and avoid winning where boxes overlap."""
+    for prob, tb, ab, _ in region_cases():
+        got = orc.region_labels(prob, tb, ab)
+        assert np.array_equal(got, W.region_labels(prob, target=tb, avoid=ab)), prob.name
+    robot = W.robot_2d(cells_per_dim=9)
+    big, small = ([-8.0, -8.0], [8.0, 8.0]), ([-1.0, -1.0], [1.0, 1.0])
+    lab = orc.region_labels(robot, [big], [small]).reshape(9, 9)
+    assert lab[4, 4] == 2 and lab[3, 3] == 1 and lab[0, 0] == 0
+    assert np.array_equal(orc.region_labels(robot, [small], [big]) == 2,
+                          orc.region_labels(robot, [], [big]) == 2)
+
+
+def pin_region_containment(orc, samples=24, seed=7):
+    """For points x of the source cell the exact probability of landing in
+    the labelled cells (a sum of library-CDF products over every labelled
+    cell) lies in [R_min, R_max]; the probability of an avoid cell or of
+    leaving the domain in [A_min, A_max]. Both modes."""
+    rng = np.random.default_rng(seed)
+    for prob, tb, ab, rows in region_cases():
+        labels = W.region_labels(prob, target=tb, avoid=ab)
+        for mode in ("box", "cells"):
+            r_lo, r_up, a_lo, a_up = orc.region_vectors(prob, rows, tb, ab, mode)
+            for k, row in enumerate(rows):
+                cell, j = divmod(int(row), prob.n_inputs)
+                bl, bh = cell_box(prob, cell)
+                xs = bl + (bh - bl) * rng.random((samples, prob.n))
+                corners = np.array([[bh[d] if (c >> d) & 1 else bl[d] for d in range(prob.n)]
+                                    for c in range(1 << prob.n)])
+                for mu in dynamics(prob, np.concatenate([xs, corners]), prob.inputs[j]):
+                    P, out = exact_probs(prob, mu)
+                    pr = float(np.sum(P[labels == 1]))
+                    pa = float(np.sum(P[labels == 2])) + out
+                    assert r_lo[k] - 1e-13 <= pr <= r_up[k] + 1e-13, (prob.name, mode, row, pr)
+                    assert a_lo[k] - 1e-13 <= pa <= a_up[k] + 1e-13, (prob.name, mode, row, pa)
+
+
+def pin_region_box_exact_separable(orc):
+    """Separable 2-D system: the box relaxation of a region is the exact
+    min / max over the cell of the probability of landing in it (the min at
+    a corner, the max the product of numerically maximised 1-D factors)."""
+    prob, tb, ab, rows = region_cases()[0]
+    labels = W.region_labels(prob, target=tb, avoid=ab).reshape(9, 9)
+    ii = np.nonzero(labels == 1)
+    span = [(ii[d].min(), ii[d].max()) for d in range(2)]
+    r_lo, r_up, _, _ = orc.region_vectors(prob, rows, tb, ab, "box")
+    for k, row in enumerate(rows):
+        cell, j = divmod(int(row), prob.n_inputs)
+        u = prob.inputs[j]
+        bl, bh = cell_box(prob, cell)
+        mass = []
+        for d in range(2):
+            e = grid_edges(prob, d)
+            a, b = e[span[d][0]], e[span[d][1] + 1]
+            mass.append((lambda x, a=a, b=b, d=d: float(interval_mass(a, b, x + u[d],
+                                                                      prob.sigma[d]))))
+        corners = [(x0, x1) for x0 in (bl[0], bh[0]) for x1 in (bl[1], bh[1])]
+        lo_ref = min(mass[0](x0) * mass[1](x1) for x0, x1 in corners)
+        up_ref = (_max_over_interval(mass[0], bl[0], bh[0])
+                  * _max_over_interval(mass[1], bl[1], bh[1]))
+        assert abs(r_lo[k] - lo_ref) <= 1e-14 + 1e-12 * lo_ref, (row, r_lo[k], lo_ref)
+        assert r_up[k] >= up_ref - 1e-14 and r_up[k] - up_ref < 1e-9, (row, r_up[k], up_ref)
+
+
+def pin_region_reductions(orc):
+    """One-cell regions equal that cell's own bounds in both modes; the box
+    bounds lie inside the paper's sums of per-cell bounds; a region covering
+    the whole domain is the complement of the sink."""
+    prob = W.robot_2d(cells_per_dim=9)
+    rows = [0, 40, 77, 300, 555]
+    e0 = grid_edges(prob, 0)
+    t = (5, 6)                                           # the cell, as (i0, i1)
+    box = ([e0[t[0]] + 0.3, e0[t[1]] + 0.3], [e0[t[0] + 1] - 0.3, e0[t[1] + 1] - 0.3])
+    tcell = t[0] * 9 + t[1]
+    for mode in ("box", "cells"):
+        r_lo, r_up, a_lo, a_up = orc.region_vectors(prob, rows, [box], [], mode)
+        for k, row in enumerate(rows):
+            up, lo, sl, su = orc.row_dense(prob, row)
+            assert abs(r_lo[k] - lo[tcell]) <= 1e-15 * max(1.0, lo[tcell]), (mode, row)
+            assert abs(r_up[k] - up[tcell]) <= 1e-15 * max(1.0, up[tcell]), (mode, row)
+            assert a_lo[k] == sl and a_up[k] == su
+    for prob, tb, ab, rows in region_cases():
+        B = orc.region_vectors(prob, rows, tb, ab, "box")
+        C = orc.region_vectors(prob, rows, tb, ab, "cells")
+        for lo_i, up_i in ((0, 1), (2, 3)):
+            assert np.all(C[lo_i] <= B[lo_i] + 1e-15), prob.name
+            assert np.all(B[up_i] <= C[up_i] + 1e-15), prob.name
+            assert np.all(B[lo_i] <= B[up_i] + 1e-15), prob.name
+        whole = (prob.lo, prob.hi)
+        r_lo, r_up, _, _ = orc.region_vectors(prob, rows, [whole], [], "box")
+        csr = orc.build_rows(prob, rows)
+        assert np.all(np.abs(r_lo - (1.0 - csr.sink_up)) < 1e-15), prob.name
+        assert np.all(np.abs(r_up - (1.0 - csr.sink_lo)) < 1e-15), prob.name

@@ -51,6 +51,18 @@ MUTANTS = {
                             ("*sink_up = 1.0 - in_min;", "*sink_up = 1.0 - in_max;")],
     "trunc sums lo": [("else neumaier_add(&s, &comp, up[t]);",
                        "else neumaier_add(&s, &comp, lo[t]);")],
+    "region lo takes max": [("b_lo *= r_a < r_b ? r_a : r_b;", "b_lo *= r_a < r_b ? r_b : r_a;")],
+    "region box one cell short": [("double right = oracle_edge(p, d, last[d] + 1);",
+                                   "double right = oracle_edge(p, d, last[d]);")],
+    "region centre not clamped": [("clamp(centre, m_lo[d], m_hi[d])", "centre")],
+    "sink left out of A": [("out[2] = sl + x_lo;", "out[2] = x_lo;"),
+                           ("out[3] = su + x_up;", "out[3] = x_up;")],
+    "region sums take up for lo": [("{ r_lo += lo[t]; r_up += up[t]; }",
+                                    "{ r_lo += up[t]; r_up += up[t]; }")],
+    "labels: target wins": [("if (in && avoid) lab = ORACLE_AVOID;\n            else if (in && lab == ORACLE_FREE) lab = ORACLE_TARGET;",
+                             "if (in && !avoid) lab = ORACLE_TARGET;\n            else if (in && lab == ORACLE_FREE) lab = ORACLE_AVOID;")],
+    "cell centre off by half": [("return 0.5 * (oracle_edge(p, d, i) + oracle_edge(p, d, i + 1));",
+                                 "return oracle_edge(p, d, i);")],
     "ties dropped": [("if (up[t] >= p->cutoff) ++cnt;", "if (up[t] > p->cutoff) ++cnt;"),
                      ("if (up[t] >= p->cutoff) {", "if (up[t] > p->cutoff) {")],
 }
@@ -79,6 +91,10 @@ try:
     for prob in (W.bas_4d(eta_scale=2.0), W.unicycle_3d(nx=8, ny=8, nth=6)):
         P.pin_noise_sampling(orc, prob, W.sample_rows(prob, 1, seed=9, include_boundary=False)[0],
                              draws=60000)
+    P.pin_region_labels(orc)
+    P.pin_region_containment(orc, samples=6)
+    P.pin_region_box_exact_separable(orc)
+    P.pin_region_reductions(orc)
 except AssertionError as e:
     print("CAUGHT", repr(e)[:200])
     sys.exit(3)

@@ -73,6 +73,28 @@ def test_sum_of_uppers_is_product_of_axis_sums(orc, case):
     P.pin_separable_sum(orc, prob, rows)
 
 
+def test_region_labels(orc):
+    P.pin_region_labels(orc)
+
+
+def test_region_vectors_contain_the_exact_probabilities(orc):
+    P.pin_region_containment(orc)
+
+
+def test_region_box_is_exact_for_separable_dynamics(orc):
+    P.pin_region_box_exact_separable(orc)
+
+
+def test_region_vectors_reduce_to_cells_and_sink(orc):
+    P.pin_region_reductions(orc)
+
+
+def test_overlapping_region_boxes_are_refused(orc):
+    prob = W.robot_2d(cells_per_dim=9)
+    with pytest.raises(ValueError):
+        orc.region_vectors(prob, [0], [([0, 0], [5, 5])], [([4, 4], [8, 8])], "box")
+
+
 def test_ties_with_cutoff_are_kept(orc):
     P.pin_tie_kept(orc)
 
