@@ -376,7 +376,9 @@ impact_status impact_server_destroy(impact_server *server);
 
 /* ------------------------------------------------------------------------
  * Controller synthesis on a built IMDP (paper: Sec. 5 and Alg. 3/4, the LP of
- * Sec. 5 solved by the sorting method of Sec. 6.2), pessimistic policy.
+ * Sec. 5 solved by the sorting method of Sec. 6.2); impact_synthesize_ex
+ * (below) adds the optimistic policy, a finite horizon, disturbances and
+ * region vectors.
  * ------------------------------------------------------------------------ */
 
 typedef enum {
@@ -400,13 +402,126 @@ typedef enum {
  * (DEVICE int32[cells], input index; 0 on labelled cells), and the iterations
  * of each phase to iterations[2] (host, may be NULL). A phase that reaches
  * max_iters stops there (its interval is then wider than eps). Synchronizes
- * `stream` once per iteration. Errors: IMPACT_ERR_ARG, IMPACT_ERR_OOM,
- * IMPACT_ERR_CUDA.
+ * `stream` once per iteration. Same as impact_synthesize_ex with a
+ * pessimistic policy, no horizon, one disturbance point and no region
+ * vectors. Errors: IMPACT_ERR_ARG, IMPACT_ERR_OOM, IMPACT_ERR_CUDA.
  */
 impact_status impact_synthesize(const impact_csr *imdp, impact_precision precision,
                                 int64_t cells, int n_inputs, const uint8_t *labels, int spec,
                                 double eps, int max_iters, double *p_min, double *p_max,
                                 int32_t *policy, int *iterations, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Target and avoid regions (paper: Sec. 3.1 and Alg. 1 for the labels and
+ * the vectors R and A, Remark 4.1 for the sink inside A).
+ * ------------------------------------------------------------------------ */
+
+#define IMPACT_REGION_MAX_BOXES 16
+
+typedef enum {
+    IMPACT_LABEL_FREE = 0,
+    IMPACT_LABEL_TARGET = 1,
+    IMPACT_LABEL_AVOID = 2
+} impact_label;
+
+typedef enum {
+    IMPACT_REGION_BOX = 0,        /* one relaxation per region box (tighter)          */
+    IMPACT_REGION_CELL_SUM = 1    /* the paper's sums of per-cell bounds (Alg. 1)     */
+} impact_region_mode;
+
+/*
+ * Regions as axis-aligned boxes in state coordinates: HOST arrays of
+ * [count][n] lower and upper corners (lo <= hi, finite). A box labels the
+ * cells whose centre (the midpoint of the cell's two edges, edges as in
+ * impact_grid) lies in the closed box, so every box stands for a block of
+ * whole cells. n_target + n_avoid <= IMPACT_REGION_MAX_BOXES; a box that
+ * contains no centre is ignored.
+ */
+typedef struct {
+    int n_target;
+    int n_avoid;
+    const double *target_lo, *target_hi;   /* host [n_target][n] */
+    const double *avoid_lo, *avoid_hi;     /* host [n_avoid][n]  */
+} impact_regions;
+
+/*
+ * impact_label_cells -- labels of every cell (Alg. 1, labelling step):
+ * IMPACT_LABEL_AVOID if the cell's centre lies in an avoid box, else
+ * IMPACT_LABEL_TARGET if it lies in a target box, else IMPACT_LABEL_FREE
+ * (boxes may overlap; avoid wins). labels: DEVICE uint8[total cells], C
+ * order, written stream-ordered on `stream`. Errors: IMPACT_ERR_ARG.
+ */
+impact_status impact_label_cells(const impact_grid *grid, const impact_regions *regions,
+                                 uint8_t *labels, void *stream);
+
+/*
+ * impact_region_vectors -- per row r = cell * n_inputs + j the bounds
+ * [R_min, R_max] of the probability of landing in the target cells and
+ * [A_min, A_max] of landing in an avoid cell or outside the domain.
+ *   IMPACT_REGION_CELL_SUM: the paper's vectors, sums of the per-cell
+ *     bounds of impact_build (Def. 3.1 relaxation, every cell, no cutoff)
+ *     over the labelled cells;
+ *   IMPACT_REGION_BOX: each box, as the block of its cells, bounded like one
+ *     large target cell (clamped-midpoint maximum, endpoint minimum per
+ *     dimension), summed over the boxes. Lies inside the cell sums.
+ * Both add the sink bounds of the row to A. The boxes must cover pairwise
+ * disjoint sets of cells (IMPACT_ERR_ARG otherwise). IMPACT_FP64_PLAIN
+ * evaluates in round-to-nearest FP64; IMPACT_FP32_SOUND uses the outward
+ * image and widens every factor by its error bound, with directed rounding,
+ * so the vectors enclose the exact ones. r_lo, r_up, a_lo, a_up: DEVICE
+ * double[rows], written stream-ordered on `stream`. Errors: IMPACT_ERR_ARG,
+ * IMPACT_ERR_OOM, IMPACT_ERR_CUDA.
+ */
+impact_status impact_region_vectors(const impact_system *sys, const impact_grid *grid,
+                                    const impact_inputs *inputs, const double *sigma,
+                                    const impact_regions *regions, impact_region_mode mode,
+                                    impact_precision precision, double *r_lo, double *r_up,
+                                    double *a_lo, double *a_up, void *stream);
+
+/*
+ * Options of impact_synthesize_ex.
+ *   spec        IMPACT_REACH_AVOID or IMPACT_SAFETY
+ *   optimistic  0: the policy is optimised on the lower bound P_min
+ *               (pessimistic), 1: on the upper bound P_max (optimistic); the
+ *               other bound follows with the policy fixed (Sec. 5)
+ *   horizon     0: iterate until max |V1 - V0| <= eps (or max_iters);
+ *               K > 0: exactly K steps from V0 = V1 = 0 on the free cells
+ *               (Remark 5.1; eps and max_iters are then unused)
+ *   n_disturb   disturbance points per input (>= 1): the rows are
+ *               r = (cell * n_inputs + j) * n_disturb + k, i.e. the build's
+ *               input points are the (input, disturbance) pairs with the
+ *               disturbance fastest. The disturbance is the adversary:
+ *               it minimises satisfaction, the input maximises it (Sec. 5)
+ *   r_lo..a_up  NULL (the labelled cells stay successors and the sink is
+ *               one more) or the four DEVICE double[rows] vectors of
+ *               impact_region_vectors: the labelled cells then leave every
+ *               row and the regions enter as two successors
+ */
+typedef struct {
+    int spec;
+    int optimistic;
+    int horizon;
+    int n_disturb;
+    double eps;
+    int max_iters;
+    const double *r_lo, *r_up, *a_lo, *a_up;
+} impact_synth_options;
+
+/*
+ * impact_synthesize_ex -- impact_synthesize with the options above. The
+ * reported ends: reach-avoid P_min = V0 of the min-LP phase and P_max = V1
+ * of the max-LP phase; safety P_min = 1 - V1 of the max-LP phase and
+ * P_max = 1 - V0 of the min-LP phase. The policy is phase 1's choice on the
+ * vector whose end phase 1 reports (ties: the lowest input index).
+ * rows of imdp must equal cells * n_inputs * n_disturb. Synchronizes
+ * `stream` once per iteration (once per phase with a horizon). Errors:
+ * IMPACT_ERR_ARG, IMPACT_ERR_OOM, IMPACT_ERR_CUDA.
+ */
+impact_status impact_synthesize_ex(const impact_csr *imdp, impact_precision precision,
+                                   int64_t cells, int n_inputs, const uint8_t *labels,
+                                   const impact_synth_options *options, double *p_min,
+                                   double *p_max, int32_t *policy, int *iterations,
+                                   void *stream);
 
 /* Release library-owned arrays of a result (no-op for caller-owned ones). */
 impact_status impact_free(impact_csr *out);

@@ -492,6 +492,75 @@ impact_status check_request_ptrs(const impact_request *reqs, int count)
     return IMPACT_OK;
 }
 
+static_assert(IMPACT_REGION_BOXES == IMPACT_REGION_MAX_BOXES, "region box limits differ");
+
+// Region boxes -> blocks of whole cells: in every dimension the cells whose
+// centre (midpoint of the cell's edges, edges as the planner makes them)
+// lies in the closed box. Boxes with no such cell are dropped; targets stay
+// first. `disjoint`: refuse boxes that share a cell.
+impact_status snap_regions(const impact_grid *grid, const impact_regions *reg, bool disjoint,
+                           RegionBoxes &B)
+{
+    if (!grid || !grid->lo || !grid->hi || !grid->cells) return fail(IMPACT_ERR_ARG, "null grid");
+    const int n = grid->n;
+    if (n < 1 || n > IMPACT_MAX_DIM) return fail(IMPACT_ERR_ARG, "grid.n must be in [1, 8]");
+    int64_t total = 1;
+    for (int d = 0; d < n; ++d) {
+        if (grid->cells[d] < 1) return fail(IMPACT_ERR_ARG, "cells must be >= 1");
+        if (!(grid->lo[d] < grid->hi[d]) || !isfinite(grid->lo[d]) || !isfinite(grid->hi[d]))
+            return fail(IMPACT_ERR_ARG, "grid needs finite lo < hi");
+        total *= grid->cells[d];
+        if (total >= ((int64_t)1 << 31)) return fail(IMPACT_ERR_ARG, "more than 2^31-1 cells");
+    }
+    if (!reg) return fail(IMPACT_ERR_ARG, "null regions");
+    const int nt = reg->n_target, na = reg->n_avoid;
+    if (nt < 0 || na < 0 || nt + na > IMPACT_REGION_MAX_BOXES)
+        return fail(IMPACT_ERR_ARG, "region boxes: 0 <= n_target + n_avoid <= 16");
+    if ((nt > 0 && (!reg->target_lo || !reg->target_hi)) ||
+        (na > 0 && (!reg->avoid_lo || !reg->avoid_hi)))
+        return fail(IMPACT_ERR_ARG, "null region box corners");
+    memset(&B, 0, sizeof(B));
+    B.n = n;
+    for (int d = 0; d < n; ++d) B.cells[d] = grid->cells[d];
+    for (int k = 0; k < nt + na; ++k) {
+        const bool avoid = k >= nt;
+        const double *lo = avoid ? reg->avoid_lo + (size_t)(k - nt) * n : reg->target_lo + (size_t)k * n;
+        const double *hi = avoid ? reg->avoid_hi + (size_t)(k - nt) * n : reg->target_hi + (size_t)k * n;
+        bool empty = false;
+        for (int d = 0; d < n; ++d) {
+            if (!isfinite(lo[d]) || !isfinite(hi[d]) || lo[d] > hi[d])
+                return fail(IMPACT_ERR_ARG, "region boxes need finite lo <= hi");
+            const int N = grid->cells[d];
+            const double h = (grid->hi[d] - grid->lo[d]) / (double)N;
+            auto edge = [&](int i) { return i >= N ? grid->hi[d] : grid->lo[d] + (double)i * h; };
+            int f = -1, l = -2;
+            for (int i = 0; i < N; ++i) {
+                const double c = 0.5 * (edge(i) + edge(i + 1));
+                if (c >= lo[d] && c <= hi[d]) {
+                    if (f < 0) f = i;
+                    l = i;
+                }
+            }
+            if (f < 0) empty = true;
+            B.first[B.count][d] = f;
+            B.last[B.count][d] = l;
+        }
+        if (empty) continue;
+        if (!avoid) ++B.n_target;
+        ++B.count;
+    }
+    if (disjoint)
+        for (int a = 0; a < B.count; ++a)
+            for (int b = 0; b < a; ++b) {
+                bool meet = true;
+                for (int d = 0; d < n; ++d)
+                    meet = meet && std::max(B.first[a][d], B.first[b][d]) <=
+                                       std::min(B.last[a][d], B.last[b][d]);
+                if (meet) return fail(IMPACT_ERR_ARG, "region boxes share cells");
+            }
+    return IMPACT_OK;
+}
+
 }  // namespace impact
 
 using namespace impact;
@@ -852,6 +921,58 @@ impact_status impact_free(impact_csr *out)
 
 const char *impact_last_error(void) { return g_last_error.c_str(); }
 
-int impact_version(void) { return 300; }
+impact_status impact_label_cells(const impact_grid *grid, const impact_regions *regions,
+                                 uint8_t *labels, void *stream)
+{
+    RegionBoxes B;
+    impact_status s = snap_regions(grid, regions, false, B);
+    if (s != IMPACT_OK) return s;
+    if (!is_device_ptr(labels)) return fail(IMPACT_ERR_ARG, "labels must be a device array");
+    int64_t total = 1;
+    for (int d = 0; d < grid->n; ++d) total *= grid->cells[d];
+    cudaError_t e = launch_labels(B, total, labels, (cudaStream_t)stream);
+    if (e != cudaSuccess) return fail(IMPACT_ERR_CUDA, cudaGetErrorString(e));
+    return IMPACT_OK;
+}
+
+impact_status impact_region_vectors(const impact_system *sys, const impact_grid *grid,
+                                    const impact_inputs *inputs, const double *sigma,
+                                    const impact_regions *regions, impact_region_mode mode,
+                                    impact_precision precision, double *r_lo, double *r_up,
+                                    double *a_lo, double *a_up, void *stream)
+{
+    if (mode != IMPACT_REGION_BOX && mode != IMPACT_REGION_CELL_SUM)
+        return fail(IMPACT_ERR_ARG, "unknown region mode");
+    if (precision != IMPACT_FP32_SOUND && precision != IMPACT_FP64_PLAIN)
+        return fail(IMPACT_ERR_ARG, "unknown precision");
+    if (!sys || !grid || !inputs || !sigma) return fail(IMPACT_ERR_ARG, "null argument");
+    RegionBoxes B;
+    impact_status s = snap_regions(grid, regions, true, B);
+    if (s != IMPACT_OK) return s;
+    if (!is_device_ptr(r_lo) || !is_device_ptr(r_up) || !is_device_ptr(a_lo) ||
+        !is_device_ptr(a_up))
+        return fail(IMPACT_ERR_ARG, "the region vectors must be device arrays");
+    configure_pool_once();
+    cudaStream_t st = (cudaStream_t)stream;
+    // the FP64 tables of the build (images in both roundings); the cutoff
+    // does not enter the vectors
+    impact_request req = single(sys, grid, inputs, sigma, 0.5);
+    Batch batch;
+    s = make_batch(&req, 1, IMPACT_FP64_PLAIN, nullptr, batch);
+    if (s != IMPACT_OK) return s;
+    Work W;
+    s = get_work(batch, nullptr, st, W);
+    if (s != IMPACT_OK) return s;
+    s = upload(batch, W, st);
+    if (s == IMPACT_OK) {
+        cudaError_t e = launch_regions(W.desc(0), batch.rows, B, mode == IMPACT_REGION_CELL_SUM,
+                                       precision == IMPACT_FP32_SOUND, r_lo, r_up, a_lo, a_up, st);
+        if (e != cudaSuccess) s = fail(IMPACT_ERR_CUDA, cudaGetErrorString(e));
+    }
+    impact_status r = release(W, st);
+    return s != IMPACT_OK ? s : r;
+}
+
+int impact_version(void) { return 301; }
 
 }  // extern "C"

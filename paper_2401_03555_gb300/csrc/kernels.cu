@@ -19,6 +19,8 @@
 // The count pass runs 1-4 without storing pairs; a scan turns the counts into
 // row pointers; the emit pass repeats 1-3 and writes the CSR pairs.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 #include <math.h>
 #include <stdint.h>
 
@@ -471,6 +473,127 @@ __global__ void __launch_bounds__(kScanThreads) scan_apply(int64_t *__restrict__
     }
 }
 
+// ---------------------------------------------------------------------------
+// target / avoid regions (Sec. 3.1, Alg. 1, Remark 4.1)
+// ---------------------------------------------------------------------------
+
+using impact::RegionBoxes;
+
+__global__ void __launch_bounds__(256)
+label_cells(RegionBoxes B, int64_t total, uint8_t *__restrict__ labels)
+{
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < total;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        int idx[IMPACT_MAX_DIM];
+        int64_t rest = c;
+        for (int d = B.n - 1; d >= 0; --d) {
+            idx[d] = (int)(rest % B.cells[d]);
+            rest /= B.cells[d];
+        }
+        uint8_t lab = 0;
+        for (int b = 0; b < B.count; ++b) {
+            bool in = true;
+            for (int d = 0; d < B.n; ++d)
+                in = in && idx[d] >= B.first[b][d] && idx[d] <= B.last[b][d];
+            if (in) lab = b >= B.n_target ? 2 : (lab == 0 ? 1 : lab);
+        }
+        labels[c] = lab;
+    }
+}
+
+// Error bound of one factor g64 (absolute): erfc within a few ulp of values
+// <= 2, the difference and its halving, and the rounded argument.
+constexpr double kFactorErr = 0x1p-48;
+
+// Upper / lower end of one factor: as computed (plain) or widened by its
+// error bound (sound).
+template <bool SOUND>
+__device__ __forceinline__ double f_up(double g)
+{
+    return SOUND ? fmin(__dadd_ru(g, kFactorErr), 1.0) : g;
+}
+template <bool SOUND>
+__device__ __forceinline__ double f_dn(double g)
+{
+    return SOUND ? fmax(__dsub_rd(g, kFactorErr), 0.0) : g;
+}
+template <bool SOUND>
+__device__ __forceinline__ double mul_up(double a, double b) { return SOUND ? __dmul_ru(a, b) : a * b; }
+template <bool SOUND>
+__device__ __forceinline__ double mul_dn(double a, double b) { return SOUND ? __dmul_rd(a, b) : a * b; }
+template <bool SOUND>
+__device__ __forceinline__ double add_up(double a, double b) { return SOUND ? __dadd_ru(a, b) : a + b; }
+template <bool SOUND>
+__device__ __forceinline__ double add_dn(double a, double b) { return SOUND ? __dadd_rd(a, b) : a + b; }
+
+// One thread per row: the interval image, the sink (the domain box, Remark
+// 4.1), then per region box the product over dimensions of either the box's
+// own factor (one relaxation per box) or the sum of the per-cell factors
+// over the box's cells (the paper's sums: sum over the cells of a product
+// of per-dimension factors equals the product of per-dimension sums).
+template <bool SOUND>
+__global__ void __launch_bounds__(128)
+region_rows(const ImpactDesc *__restrict__ Dp, int64_t rows, RegionBoxes B, bool cell_sum,
+            double *__restrict__ r_lo, double *__restrict__ r_up, double *__restrict__ a_lo,
+            double *__restrict__ a_up)
+{
+    const ImpactDesc &D = *Dp;
+    const int n = D.n;
+    for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < rows;
+         row += (int64_t)gridDim.x * blockDim.x) {
+        int idx[IMPACT_MAX_DIM];
+        int j;
+        decode_row(D, row, idx, j);
+        double mlo[IMPACT_MAX_DIM], mhi[IMPACT_MAX_DIM];
+        double in_max = 1.0, in_min = 1.0;
+        for (int d = 0; d < n; ++d) {
+            image_dim<SOUND>(D, row, idx, j, d, mlo[d], mhi[d]);
+            const ImpactDim &g = D.dim[d];
+            const double mid = 0.5 * (g.lo + g.hi);
+            in_max = mul_up<SOUND>(in_max, f_up<SOUND>(g64(g.lo, g.hi, clampd(mid, mlo[d], mhi[d]),
+                                                           g.inv_s)));
+            in_min = mul_dn<SOUND>(in_min, f_dn<SOUND>(fmin(g64(g.lo, g.hi, mlo[d], g.inv_s),
+                                                            g64(g.lo, g.hi, mhi[d], g.inv_s))));
+        }
+        double rl = 0.0, ru = 0.0;
+        double xl = SOUND ? fmax(__dsub_rd(1.0, in_max), 0.0) : 1.0 - in_max;
+        double xu = SOUND ? fmin(__dsub_ru(1.0, in_min), 1.0) : 1.0 - in_min;
+        for (int b = 0; b < B.count; ++b) {
+            double pu = 1.0, pl = 1.0;
+            for (int d = 0; d < n; ++d) {
+                const ImpactDim &g = D.dim[d];
+                const double *E = D.edges + g.edge_off;
+                double fu, fl;
+                if (cell_sum) {
+                    fu = 0.0;
+                    fl = 0.0;
+                    for (int i = B.first[b][d]; i <= B.last[b][d]; ++i) {
+                        fu = add_up<SOUND>(fu, f_up<SOUND>(up64(g, E, i, mlo[d], mhi[d])));
+                        fl = add_dn<SOUND>(fl, f_dn<SOUND>(lo64(g, E, i, mlo[d], mhi[d])));
+                    }
+                } else {
+                    const double c = E[B.first[b][d]], e = E[B.last[b][d] + 1];
+                    fu = f_up<SOUND>(g64(c, e, clampd(0.5 * (c + e), mlo[d], mhi[d]), g.inv_s));
+                    fl = f_dn<SOUND>(fmin(g64(c, e, mlo[d], g.inv_s), g64(c, e, mhi[d], g.inv_s)));
+                }
+                pu = mul_up<SOUND>(pu, fu);
+                pl = mul_dn<SOUND>(pl, fl);
+            }
+            if (b < B.n_target) {
+                rl = add_dn<SOUND>(rl, pl);
+                ru = add_up<SOUND>(ru, pu);
+            } else {
+                xl = add_dn<SOUND>(xl, pl);
+                xu = add_up<SOUND>(xu, pu);
+            }
+        }
+        r_lo[row] = rl;
+        r_up[row] = ru;
+        a_lo[row] = xl;
+        a_up[row] = xu;
+    }
+}
+
 int grid_for(const void *kernel, int64_t rows)
 {
     int dev = 0, sms = 0, occ = 0;
@@ -508,6 +631,30 @@ cudaError_t launch_rows(const ImpactDesc *d_desc, int prec, bool emit, int64_t r
                 o.sink_lo, o.sink_up, o.trunc, o.flags, o.status, o.capacity, o.total_at);
         }
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_labels(const RegionBoxes &boxes, int64_t total_cells, uint8_t *labels,
+                          cudaStream_t stream)
+{
+    if (total_cells <= 0) return cudaSuccess;
+    const int64_t g = std::min<int64_t>((total_cells + 255) / 256, 152 * 16);
+    label_cells<<<(unsigned)g, 256, 0, stream>>>(boxes, total_cells, labels);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_regions(const ImpactDesc *d_desc, int64_t rows, const RegionBoxes &boxes,
+                           bool cell_sum, bool sound, double *r_lo, double *r_up, double *a_lo,
+                           double *a_up, cudaStream_t stream)
+{
+    if (rows <= 0) return cudaSuccess;
+    const int64_t g = std::min<int64_t>((rows + 127) / 128, 152 * 32);
+    if (sound)
+        region_rows<true><<<(unsigned)g, 128, 0, stream>>>(d_desc, rows, boxes, cell_sum, r_lo,
+                                                           r_up, a_lo, a_up);
+    else
+        region_rows<false><<<(unsigned)g, 128, 0, stream>>>(d_desc, rows, boxes, cell_sum, r_lo,
+                                                            r_up, a_lo, a_up);
     return cudaGetLastError();
 }
 

@@ -45,6 +45,28 @@ int64_t scan_scratch_elems(int64_t n);
 // Sets the message impact_last_error() returns on this host thread.
 void set_last_error(const std::string &msg);
 
+// Region boxes as blocks of whole cells (impact_regions after the host has
+// found the cells whose centre lies in each box): targets first.
+#define IMPACT_REGION_BOXES 16
+struct RegionBoxes {
+    int count;                                      // boxes in use
+    int n_target;                                   // boxes [0, n_target) are targets
+    int n;                                          // dimensions
+    int cells[IMPACT_MAX_DIM];                      // grid cells per dimension
+    int first[IMPACT_REGION_BOXES][IMPACT_MAX_DIM];   // first cell index per dimension
+    int last[IMPACT_REGION_BOXES][IMPACT_MAX_DIM];    // last cell index per dimension
+};
+
+// Labels of every cell (0 free, 1 target, 2 avoid; avoid wins).
+cudaError_t launch_labels(const RegionBoxes &boxes, int64_t total_cells, uint8_t *labels,
+                          cudaStream_t stream);
+// Region vectors of rows [0, rows) of the build described by d_desc (FP64
+// tables): cell_sum selects the paper's sums of per-cell bounds, else one
+// relaxation per box; sound selects the enclosing evaluation.
+cudaError_t launch_regions(const ImpactDesc *d_desc, int64_t rows, const RegionBoxes &boxes,
+                           bool cell_sum, bool sound, double *r_lo, double *r_up, double *a_lo,
+                           double *a_up, cudaStream_t stream);
+
 // FP32-sound table path (tree_fp32.cu), every launch over a whole batch.
 int64_t record_stride(int n, int tsum_cap);
 int tree_smem_bytes(int tsum_cap, int pool_cap, bool emit);

@@ -1,11 +1,15 @@
 // synth.cu -- interval-iteration controller synthesis on a device-resident
-// IMDP (impact_synthesize, include/impact.h): the paper's Alg. 3 (safety) and
-// Alg. 4 (reach-avoid), pessimistic policy, with the linear program of Sec. 5
-// solved per row by the sorting method of Sec. 6.2.
+// IMDP (impact_synthesize / impact_synthesize_ex, include/impact.h): the
+// paper's Alg. 3 (safety) and Alg. 4 (reach-avoid), pessimistic or optimistic
+// policy (Sec. 5), infinite or finite horizon (Remark 5.1), the disturbance
+// points as an adversary, with the linear program of Sec. 5 solved per row by
+// the sorting method of Sec. 6.2.
 //
 // Per row the successors are the kept target cells t with [lo_t, up_t], the
 // out-of-domain sink with [sink_lo, sink_up] and the truncated mass as one
-// more successor with [0, trunc]. The sorting method starts every successor
+// more successor with [0, trunc]; with region vectors (Sec. 3.1) the
+// labelled cells and the sink give way to the target region [R_min, R_max]
+// and the avoid region [A_min, A_max]. The sorting method starts every successor
 // at its lower bound and raises them in ascending (min LP) or descending (max
 // LP) order of their value until the total is 1. Instead of sorting, one warp
 // finds the value threshold tau of that greedy fill by bisection: with
@@ -56,39 +60,60 @@ __device__ __forceinline__ double warp_sum(double v)
 
 struct RowRef {
     int64_t a, b;           // successor range in col/lo/up
-    double sink_lo, sink_up, trunc;
+    // three further successors: the sink and an empty one, or the two
+    // regions; then the truncated mass. Lower bounds, widths and values
+    // (before the max LP's mapping v -> 1 - v)
+    double xlo[3], xw[3], xv[3];
 };
 
 // Greedy (sorting-method) optimum of one row for the value vector V.
-// `maximize`: the max LP; `sink_v`: value of the sink; `high`: value the
-// remaining mass of the bracket at its upper end (else its lower end).
+// `maximize`: the max LP; `high`: value the remaining mass of the bracket at
+// its upper end (else its lower end); `excl`: when not null, successors t
+// with excl[t] != 0 are left out (their mass is in the region successors).
 template <typename VT>
 __device__ double row_lp(const RowRef &R, const int32_t *__restrict__ col,
                          const VT *__restrict__ lo, const VT *__restrict__ up,
-                         const double *__restrict__ V, bool maximize, double sink_v, bool high)
+                         const uint8_t *__restrict__ excl, const double *__restrict__ V,
+                         bool maximize, bool high)
 {
     const int lane = threadIdx.x & 31;
     // the value as seen by the min LP (max LP: 1 - v)
     auto val = [&](double v) { return maximize ? 1.0 - v : v; };
-    const double tv = val(maximize ? 1.0 : 0.0);   // the truncated mass: the worst end
-    const double sv = val(sink_v);
+    auto out = [&](int32_t t) { return excl != nullptr && excl[t] != 0; };
     // sums over the successors: lo, lo * v
     double slo = 0.0, slov = 0.0;
     for (int64_t i = R.a + lane; i < R.b; i += 32) {
+        const int32_t t = col[i];
+        if (out(t)) continue;
         const double l = (double)lo[i];
         slo += l;
-        slov += l * val(V[col[i]]);
+        slov += l * val(V[t]);
     }
     slo = warp_sum(slo);
     slov = warp_sum(slov);
-    slo += R.sink_lo;
-    slov += R.sink_lo * sv;
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+        slo += R.xlo[x];
+        slov += R.xlo[x] * val(R.xv[x]);
+    }
     const double rest = 1.0 - slo;
+    auto extras = [&](double x, double &g, double &v2) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const double v = val(R.xv[k]);
+            if (v <= x) {
+                g += R.xw[k];
+                v2 += R.xw[k] * v;
+            }
+        }
+    };
     // mass of the successors with value <= x, and their weighted value
     auto G = [&](double x, double &gv) {
         double g = 0.0, v2 = 0.0;
         for (int64_t i = R.a + lane; i < R.b; i += 32) {
-            const double v = val(V[col[i]]);
+            const int32_t t = col[i];
+            if (out(t)) continue;
+            const double v = val(V[t]);
             if (v <= x) {
                 const double w = (double)up[i] - (double)lo[i];
                 g += w;
@@ -97,14 +122,7 @@ __device__ double row_lp(const RowRef &R, const int32_t *__restrict__ col,
         }
         g = warp_sum(g);
         v2 = warp_sum(v2);
-        if (sv <= x) {
-            g += R.sink_up - R.sink_lo;
-            v2 += (R.sink_up - R.sink_lo) * sv;
-        }
-        if (tv <= x) {
-            g += R.trunc;
-            v2 += R.trunc * tv;
-        }
+        extras(x, g, v2);
         gv = v2;
         return g;
     };
@@ -118,7 +136,7 @@ __device__ double row_lp(const RowRef &R, const int32_t *__restrict__ col,
 #pragma unroll
         for (int k = 0; k < kCache; ++k) {
             const int64_t i = R.a + lane + 32 * k;
-            const bool in = i < R.b;
+            const bool in = i < R.b && !out(col[i]);
             cv[k] = in ? val(V[col[i]]) : 2.0;   // 2: never <= x
             cw[k] = in ? (double)up[i] - (double)lo[i] : 0.0;
         }
@@ -132,14 +150,7 @@ __device__ double row_lp(const RowRef &R, const int32_t *__restrict__ col,
                 }
             g = warp_sum(g);
             v2 = warp_sum(v2);
-            if (sv <= x) {
-                g += R.sink_up - R.sink_lo;
-                v2 += (R.sink_up - R.sink_lo) * sv;
-            }
-            if (tv <= x) {
-                g += R.trunc;
-                v2 += R.trunc * tv;
-            }
+            extras(x, g, v2);
             gv = v2;
             return g;
         };
@@ -172,6 +183,13 @@ struct Phase {
     int spec;         // IMPACT_REACH_AVOID or IMPACT_SAFETY
     bool choose;      // optimise over the inputs (phase 1) or follow the policy
     bool maximize;    // the LP direction
+    bool pol_v1;      // phase 1: the policy follows the V1 choice (else V0)
+    int n_disturb;    // disturbance points per input
+};
+
+// Region vectors of the rows (all four, or all null).
+struct Regions {
+    const double *r_lo, *r_up, *a_lo, *a_up;
 };
 
 // The LP of every row the phase needs (all inputs in phase 1, the policy's in
@@ -182,22 +200,47 @@ row_values(Phase ph, int64_t rows, int n_inputs, const uint8_t *__restrict__ lab
            const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
            const VT *__restrict__ lo, const VT *__restrict__ up,
            const double *__restrict__ sink_lo, const double *__restrict__ sink_up,
-           const double *__restrict__ trunc, const double *__restrict__ V0,
+           const double *__restrict__ trunc, Regions rg, const double *__restrict__ V0,
            const double *__restrict__ V1, const int32_t *__restrict__ policy,
            double *__restrict__ R0, double *__restrict__ R1)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const double sink_v = ph.spec == IMPACT_REACH_AVOID ? 0.0 : 1.0;
+    const bool reach = ph.spec == IMPACT_REACH_AVOID;
+    const int64_t per_cell = (int64_t)n_inputs * ph.n_disturb;
+    const uint8_t *excl = rg.r_lo ? labels : nullptr;
     for (int64_t r = warp0; r < rows; r += nwarps) {
-        const int64_t c = r / n_inputs;
-        const int j = (int)(r - c * n_inputs);
+        const int64_t c = r / per_cell;
+        const int j = (int)((r - c * per_cell) / ph.n_disturb);
         if (labels[c] != 0 || (!ph.choose && j != policy[c])) continue;
-        RowRef R{row_ptr[r], row_ptr[r + 1], sink_lo[r], sink_up[r], trunc[r]};
+        RowRef R;
+        R.a = row_ptr[r];
+        R.b = row_ptr[r + 1];
+        if (rg.r_lo) {
+            // the target region (reach: value 1) and the avoid region with
+            // the sink (safety: value 1)
+            R.xlo[0] = rg.r_lo[r];
+            R.xw[0] = rg.r_up[r] - rg.r_lo[r];
+            R.xv[0] = reach ? 1.0 : 0.0;
+            R.xlo[1] = rg.a_lo[r];
+            R.xw[1] = rg.a_up[r] - rg.a_lo[r];
+            R.xv[1] = reach ? 0.0 : 1.0;
+        } else {
+            R.xlo[0] = sink_lo[r];
+            R.xw[0] = sink_up[r] - sink_lo[r];
+            R.xv[0] = reach ? 0.0 : 1.0;
+            R.xlo[1] = 0.0;
+            R.xw[1] = 0.0;
+            R.xv[1] = 0.0;
+        }
+        // the truncated mass, at its worst end: 0 in a min LP, 1 in a max LP
+        R.xlo[2] = 0.0;
+        R.xw[2] = trunc[r];
+        R.xv[2] = ph.maximize ? 1.0 : 0.0;
         // V0 never rises above, V1 never falls below the exact update
-        const double a = row_lp(R, col, lo, up, V0, ph.maximize, sink_v, false);
-        const double b = row_lp(R, col, lo, up, V1, ph.maximize, sink_v, true);
+        const double a = row_lp(R, col, lo, up, excl, V0, ph.maximize, false);
+        const double b = row_lp(R, col, lo, up, excl, V1, ph.maximize, true);
         if (lane == 0) {
             R0[r] = a;
             R1[r] = b;
@@ -205,8 +248,20 @@ row_values(Phase ph, int64_t rows, int n_inputs, const uint8_t *__restrict__ lab
     }
 }
 
-// Per cell: the best input (phase 1) or the policy's row (phase 2), the next
-// V0 and V1, and the largest |V1 - V0|.
+// The disturbance's choice among the W rows of one input: the least
+// satisfaction (reach-avoid) or the most unsafe value (safety).
+__device__ __forceinline__ double worst(const double *__restrict__ p, int W, bool reach)
+{
+    double w = p[0];
+    for (int k = 1; k < W; ++k) w = reach ? fmin(w, p[k]) : fmax(w, p[k]);
+    return w;
+}
+
+// Per cell: for each input the disturbance's worst row, then the best input
+// (phase 1) or the policy's input (phase 2), the next V0 and V1, and the
+// largest |V1 - V0|. The values are satisfaction probabilities (reach-avoid:
+// inputs maximise, disturbances minimise) or unsafe ones (safety: inputs
+// minimise, disturbances maximise).
 __global__ void __launch_bounds__(kThreads)
 cell_update(Phase ph, int64_t cells, int n_inputs, const uint8_t *__restrict__ labels,
             const double *__restrict__ R0, const double *__restrict__ R1,
@@ -214,8 +269,7 @@ cell_update(Phase ph, int64_t cells, int n_inputs, const uint8_t *__restrict__ l
             unsigned long long *__restrict__ diff)
 {
     const bool reach = ph.spec == IMPACT_REACH_AVOID;
-    // reach-avoid phase 1: max over inputs of the min LP; safety: min of max
-    const bool pick_max = reach;
+    const int W = ph.n_disturb;
     double dmax = 0.0;
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < cells;
          c += (int64_t)gridDim.x * blockDim.x) {
@@ -226,22 +280,25 @@ cell_update(Phase ph, int64_t cells, int n_inputs, const uint8_t *__restrict__ l
             if (ph.choose) policy[c] = 0;
         } else if (ph.choose) {
             double b0 = 0.0, b1 = 0.0;
-            int arg = 0;
+            int arg0 = 0, arg1 = 0;
             for (int j = 0; j < n_inputs; ++j) {
-                const double a = R0[c * n_inputs + j], b = R1[c * n_inputs + j];
-                if (j == 0 || (pick_max ? a > b0 : a < b0)) {
+                const double a = worst(R0 + (c * n_inputs + j) * W, W, reach);
+                const double b = worst(R1 + (c * n_inputs + j) * W, W, reach);
+                if (j == 0 || (reach ? a > b0 : a < b0)) {
                     b0 = a;
-                    arg = j;
+                    arg0 = j;
                 }
-                if (j == 0 || (pick_max ? b > b1 : b < b1)) b1 = b;
+                if (j == 0 || (reach ? b > b1 : b < b1)) {
+                    b1 = b;
+                    arg1 = j;
+                }
             }
-            policy[c] = arg;
+            policy[c] = ph.pol_v1 ? arg1 : arg0;
             n0 = b0;
             n1 = b1;
         } else {
-            const int64_t r = c * n_inputs + policy[c];
-            n0 = R0[r];
-            n1 = R1[r];
+            n0 = worst(R0 + (c * n_inputs + policy[c]) * W, W, reach);
+            n1 = worst(R1 + (c * n_inputs + policy[c]) * W, W, reach);
         }
         n0 = fmin(fmax(n0, 0.0), 1.0);
         n1 = fmin(fmax(n1, 0.0), 1.0);
@@ -255,9 +312,11 @@ cell_update(Phase ph, int64_t cells, int n_inputs, const uint8_t *__restrict__ l
         atomicMax(diff, (unsigned long long)__double_as_longlong(dmax));
 }
 
+// V0 from 0 and V1 from 1 on the free cells (from 0 both, for a finite
+// horizon); the labelled cells hold their absorbing value.
 __global__ void __launch_bounds__(kThreads)
-init_values(int spec, int64_t cells, const uint8_t *__restrict__ labels, double *__restrict__ V0,
-            double *__restrict__ V1)
+init_values(int spec, bool horizon, int64_t cells, const uint8_t *__restrict__ labels,
+            double *__restrict__ V0, double *__restrict__ V1)
 {
     const bool reach = spec == IMPACT_REACH_AVOID;
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < cells;
@@ -265,7 +324,7 @@ init_values(int spec, int64_t cells, const uint8_t *__restrict__ labels, double 
         const uint8_t lab = labels[c];
         if (lab == 0) {
             V0[c] = 0.0;
-            V1[c] = 1.0;
+            V1[c] = horizon ? 0.0 : 1.0;
         } else {
             V0[c] = V1[c] = (reach ? lab == 1 : lab == 2) ? 1.0 : 0.0;
         }
@@ -303,36 +362,56 @@ bool device_array(const void *p)
 
 }  // namespace
 
-extern "C" impact_status impact_synthesize(const impact_csr *imdp, impact_precision precision,
-                                           int64_t cells, int n_inputs, const uint8_t *labels,
-                                           int spec, double eps, int max_iters, double *p_min,
-                                           double *p_max, int32_t *policy, int *iterations,
-                                           void *stream)
+extern "C" impact_status impact_synthesize_ex(const impact_csr *imdp, impact_precision precision,
+                                              int64_t cells, int n_inputs, const uint8_t *labels,
+                                              const impact_synth_options *opt, double *p_min,
+                                              double *p_max, int32_t *policy, int *iterations,
+                                              void *stream)
 {
     using impact::fail;
-    if (!imdp) return fail(IMPACT_ERR_ARG, "null IMDP");
+    if (!imdp || !opt) return fail(IMPACT_ERR_ARG, "null IMDP or options");
     if (precision != IMPACT_FP32_SOUND && precision != IMPACT_FP64_PLAIN)
         return fail(IMPACT_ERR_ARG, "unknown precision");
+    const int spec = opt->spec;
     if (spec != IMPACT_REACH_AVOID && spec != IMPACT_SAFETY)
         return fail(IMPACT_ERR_ARG, "unknown specification");
-    if (cells < 1 || n_inputs < 1 || imdp->rows != cells * n_inputs)
-        return fail(IMPACT_ERR_ARG, "the IMDP must have cells * n_inputs rows");
-    if (!(eps > 0.0) || max_iters < 1) return fail(IMPACT_ERR_ARG, "eps > 0 and max_iters >= 1");
+    if (opt->optimistic != 0 && opt->optimistic != 1)
+        return fail(IMPACT_ERR_ARG, "optimistic must be 0 or 1");
+    if (opt->horizon < 0) return fail(IMPACT_ERR_ARG, "horizon must be >= 0");
+    const int W = opt->n_disturb;
+    if (W < 1) return fail(IMPACT_ERR_ARG, "n_disturb must be >= 1");
+    if (cells < 1 || n_inputs < 1 || imdp->rows != cells * n_inputs * W)
+        return fail(IMPACT_ERR_ARG, "the IMDP must have cells * n_inputs * n_disturb rows");
+    const bool horizon = opt->horizon > 0;
+    if (!horizon && (!(opt->eps > 0.0) || opt->max_iters < 1))
+        return fail(IMPACT_ERR_ARG, "eps > 0 and max_iters >= 1");
     if (!device_array(imdp->row_ptr) || !device_array(imdp->sink_lo) ||
         !device_array(imdp->sink_up) || !device_array(imdp->trunc) || !device_array(labels) ||
         !device_array(p_min) || !device_array(p_max) || !device_array(policy) ||
         (imdp->nnz > 0 && (!device_array(imdp->col) || !device_array(imdp->lo) ||
                            !device_array(imdp->up))))
         return fail(IMPACT_ERR_ARG, "the IMDP, labels and outputs must be device arrays");
+    Regions rg{opt->r_lo, opt->r_up, opt->a_lo, opt->a_up};
+    const int given = !!rg.r_lo + !!rg.r_up + !!rg.a_lo + !!rg.a_up;
+    if (given != 0 && given != 4) return fail(IMPACT_ERR_ARG, "give all four region vectors or none");
+    if (given == 4 && (!device_array(rg.r_lo) || !device_array(rg.r_up) ||
+                       !device_array(rg.a_lo) || !device_array(rg.a_up)))
+        return fail(IMPACT_ERR_ARG, "the region vectors must be device arrays");
     cudaStream_t st = (cudaStream_t)stream;
     double *buf = nullptr, *rbuf = nullptr;
     unsigned long long *d_diff = nullptr, *h_diff = nullptr;
-    const int64_t rows = cells * n_inputs;
+    const int64_t rows = imdp->rows;
     CK(cudaMallocAsync((void **)&buf, (size_t)cells * 4 * sizeof(double), st));
     CK(cudaMallocAsync((void **)&rbuf, (size_t)rows * 2 * sizeof(double), st));
     CK(cudaMallocAsync((void **)&d_diff, sizeof(unsigned long long), st));
     CK(cudaMallocHost((void **)&h_diff, sizeof(unsigned long long)));
     const bool reach = spec == IMPACT_REACH_AVOID;
+    // the LP that bounds satisfaction from below: reach-avoid the min LP,
+    // safety the max LP of the unsafe value; phase 1 optimises the inputs on
+    // it (pessimistic) or on the other one (optimistic)
+    const bool lower_max = !reach;
+    const bool lp1_max = opt->optimistic ? !lower_max : lower_max;
+    const int limit = horizon ? opt->horizon : opt->max_iters;
     const int g_cells = grid_of(cells, kThreads);
     const int g_rows = grid_of(rows, kThreads / 32);
     impact_status status = IMPACT_OK;
@@ -342,23 +421,26 @@ extern "C" impact_status impact_synthesize(const impact_csr *imdp, impact_precis
         Phase ph;
         ph.spec = spec;
         ph.choose = phase == 0;
-        // reach-avoid: phase 1 min LP, phase 2 max LP; safety the other way
-        ph.maximize = reach ? phase == 1 : phase == 0;
-        init_values<<<g_cells, kThreads, 0, st>>>(spec, cells, labels, V0, V1);
+        ph.maximize = phase == 0 ? lp1_max : !lp1_max;
+        // the vector whose end phase 1 reports: reach min LP -> V0, reach max
+        // LP -> V1, safety max LP -> V1 (P_min = 1 - V1), min LP -> V0
+        ph.pol_v1 = lp1_max;
+        ph.n_disturb = W;
+        init_values<<<g_cells, kThreads, 0, st>>>(spec, horizon, cells, labels, V0, V1);
         int it = 0;
-        while (it < max_iters) {
+        while (it < limit) {
             cudaMemsetAsync(d_diff, 0, sizeof(unsigned long long), st);
             double *R0 = rbuf, *R1 = rbuf + rows;
             if (precision == IMPACT_FP32_SOUND)
                 row_values<float><<<g_rows, kThreads, 0, st>>>(
                     ph, rows, n_inputs, labels, imdp->row_ptr, imdp->col,
                     (const float *)imdp->lo, (const float *)imdp->up, imdp->sink_lo,
-                    imdp->sink_up, imdp->trunc, V0, V1, policy, R0, R1);
+                    imdp->sink_up, imdp->trunc, rg, V0, V1, policy, R0, R1);
             else
                 row_values<double><<<g_rows, kThreads, 0, st>>>(
                     ph, rows, n_inputs, labels, imdp->row_ptr, imdp->col,
                     (const double *)imdp->lo, (const double *)imdp->up, imdp->sink_lo,
-                    imdp->sink_up, imdp->trunc, V0, V1, policy, R0, R1);
+                    imdp->sink_up, imdp->trunc, rg, V0, V1, policy, R0, R1);
             cell_update<<<g_cells, kThreads, 0, st>>>(ph, cells, n_inputs, labels, R0, R1, N0, N1,
                                                       policy, d_diff);
             cudaError_t e = cudaGetLastError();
@@ -369,6 +451,7 @@ extern "C" impact_status impact_synthesize(const impact_csr *imdp, impact_precis
             std::swap(V0, N0);
             std::swap(V1, N1);
             ++it;
+            if (horizon) continue;   // a fixed number of steps: no stopping test
             // the stopping test of Alg. 3/4 on the vectors just computed
             cudaMemcpyAsync(h_diff, d_diff, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
             if (cudaStreamSynchronize(st) != cudaSuccess) {
@@ -377,15 +460,24 @@ extern "C" impact_status impact_synthesize(const impact_csr *imdp, impact_precis
             }
             double dmax;
             memcpy(&dmax, h_diff, sizeof(dmax));
-            if (dmax <= eps) break;
+            if (dmax <= opt->eps) break;
         }
         its[phase] = it;
         if (status != IMPACT_OK) break;
-        // reach-avoid: P_min = V0 of phase 1, P_max = V1 of phase 2;
-        // safety: P_min = 1 - V1 of phase 1, P_max = 1 - V0 of phase 2
-        double *dst = phase == 0 ? p_min : p_max;
-        const double *src = reach ? (phase == 0 ? V0 : V1) : (phase == 0 ? V1 : V0);
+        // reach-avoid: the min LP gives P_min = V0, the max LP P_max = V1;
+        // safety: the max LP gives P_min = 1 - V1, the min LP P_max = 1 - V0
+        double *dst;
+        const double *src;
+        if (reach) {
+            dst = ph.maximize ? p_max : p_min;
+            src = ph.maximize ? V1 : V0;
+        } else {
+            dst = ph.maximize ? p_min : p_max;
+            src = ph.maximize ? V1 : V0;
+        }
         finish<<<g_cells, kThreads, 0, st>>>(spec, cells, src, !reach, dst);
+        if (horizon && cudaStreamSynchronize(st) != cudaSuccess)
+            status = fail(IMPACT_ERR_CUDA, "synthesis phase failed");
     }
     cudaFreeAsync(buf, st);
     cudaFreeAsync(rbuf, st);
@@ -397,4 +489,20 @@ extern "C" impact_status impact_synthesize(const impact_csr *imdp, impact_precis
         iterations[1] = its[1];
     }
     return status;
+}
+
+extern "C" impact_status impact_synthesize(const impact_csr *imdp, impact_precision precision,
+                                           int64_t cells, int n_inputs, const uint8_t *labels,
+                                           int spec, double eps, int max_iters, double *p_min,
+                                           double *p_max, int32_t *policy, int *iterations,
+                                           void *stream)
+{
+    impact_synth_options o;
+    memset(&o, 0, sizeof(o));
+    o.spec = spec;
+    o.n_disturb = 1;
+    o.eps = eps;
+    o.max_iters = max_iters;
+    return impact_synthesize_ex(imdp, precision, cells, n_inputs, labels, &o, p_min, p_max,
+                                policy, iterations, stream);
 }

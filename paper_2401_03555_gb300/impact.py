@@ -34,7 +34,8 @@ ENTRY_POINTS = ("impact_plan", "impact_workspace_bytes", "impact_build", "impact
                 "impact_graph_launch", "impact_graph_result", "impact_graph_destroy",
                 "impact_batch_tune", "impact_server_create", "impact_server_submit",
                 "impact_server_poll", "impact_server_release", "impact_server_stats",
-                "impact_server_destroy", "impact_synthesize")
+                "impact_server_destroy", "impact_synthesize", "impact_label_cells",
+                "impact_region_vectors", "impact_synthesize_ex")
 
 
 class ImpactError(RuntimeError):
@@ -80,6 +81,19 @@ class _Tuning(ctypes.Structure):
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+class _Regions(ctypes.Structure):
+    _fields_ = [("n_target", ctypes.c_int), ("n_avoid", ctypes.c_int),
+                ("target_lo", ctypes.c_void_p), ("target_hi", ctypes.c_void_p),
+                ("avoid_lo", ctypes.c_void_p), ("avoid_hi", ctypes.c_void_p)]
+
+
+class _SynthOptions(ctypes.Structure):
+    _fields_ = [("spec", ctypes.c_int), ("optimistic", ctypes.c_int), ("horizon", ctypes.c_int),
+                ("n_disturb", ctypes.c_int), ("eps", ctypes.c_double),
+                ("max_iters", ctypes.c_int), ("r_lo", ctypes.c_void_p), ("r_up", ctypes.c_void_p),
+                ("a_lo", ctypes.c_void_p), ("a_up", ctypes.c_void_p)]
 
 
 class _ServerConfig(ctypes.Structure):
@@ -175,6 +189,21 @@ def load(build_if_missing: bool = True):
                                           ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
                                           ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]
+        lib.impact_label_cells.restype = ctypes.c_int
+        lib.impact_label_cells.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(_Regions),
+                                           ctypes.c_void_p, ctypes.c_void_p]
+        lib.impact_region_vectors.restype = ctypes.c_int
+        lib.impact_region_vectors.argtypes = [ctypes.POINTER(_System), ctypes.POINTER(_Grid),
+                                              ctypes.POINTER(_Inputs), ctypes.c_void_p,
+                                              ctypes.POINTER(_Regions), ctypes.c_int, ctypes.c_int,
+                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                              ctypes.c_void_p, ctypes.c_void_p]
+        lib.impact_synthesize_ex.restype = ctypes.c_int
+        lib.impact_synthesize_ex.argtypes = [ctypes.POINTER(_CSR), ctypes.c_int, ctypes.c_int64,
+                                             ctypes.c_int, ctypes.c_void_p,
+                                             ctypes.POINTER(_SynthOptions), ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]
         _lib = lib
         return lib
 
@@ -672,11 +701,78 @@ class Controller:
     iterations: tuple
 
 
+class _RegionArgs:
+    """impact_regions for lists of (lo, hi) boxes; keeps the arrays alive."""
+
+    def __init__(self, n, target=(), avoid=()):
+        def arr(boxes, k):
+            a = np.zeros((max(len(boxes), 1), n))
+            for i, b in enumerate(boxes):
+                a[i] = np.asarray(b[k], np.float64).reshape(n)
+            return np.ascontiguousarray(a)
+        self.t_lo, self.t_hi = arr(target, 0), arr(target, 1)
+        self.a_lo, self.a_hi = arr(avoid, 0), arr(avoid, 1)
+        self.struct = _Regions(len(target), len(avoid), self.t_lo.ctypes.data,
+                               self.t_hi.ctypes.data, self.a_lo.ctypes.data, self.a_hi.ctypes.data)
+
+
+def label_cells(prob, target=(), avoid=(), stream=None) -> torch.Tensor:
+    """uint8 label per cell on the GPU: 0 free, 1 target, 2 avoid
+    (impact_label_cells; a box labels the cells whose centre it contains)."""
+    a = _Args(prob, need_images=False)
+    r = _RegionArgs(int(a.lo.shape[0]), target, avoid)
+    out = torch.empty(int(prob.total_cells), dtype=torch.uint8, device="cuda")
+    _check(load().impact_label_cells(ctypes.byref(a.grid), ctypes.byref(r.struct),
+                                     out.data_ptr(), ctypes.c_void_p(_stream_handle(stream))))
+    return out
+
+
+@dataclass
+class RegionVectors:
+    """Per-row bounds of landing in the target cells and in an avoid cell or
+    outside the domain (float64 tensors on the GPU)."""
+    r_lo: torch.Tensor
+    r_up: torch.Tensor
+    a_lo: torch.Tensor
+    a_up: torch.Tensor
+
+
+REGION_BOX, REGION_CELL_SUM = 0, 1
+_MODE = {"box": REGION_BOX, "cells": REGION_CELL_SUM, REGION_BOX: REGION_BOX,
+         REGION_CELL_SUM: REGION_CELL_SUM}
+
+
+def region_vectors(prob, target=(), avoid=(), mode="box", precision="fp64",
+                   stream=None) -> RegionVectors:
+    """impact_region_vectors: mode "box" (one relaxation per region box) or
+    "cells" (the paper's sums of per-cell bounds)."""
+    a = _Args(prob)
+    r = _RegionArgs(int(a.lo.shape[0]), target, avoid)
+    rows = int(prob.rows)
+    v = [torch.empty(rows, dtype=torch.float64, device="cuda") for _ in range(4)]
+    _check(load().impact_region_vectors(ctypes.byref(a.sys), ctypes.byref(a.grid),
+                                        ctypes.byref(a.inp), a.sigma_ptr, ctypes.byref(r.struct),
+                                        _MODE[mode], _PREC[precision],
+                                        *[t.data_ptr() for t in v],
+                                        ctypes.c_void_p(_stream_handle(stream))))
+    return RegionVectors(*v)
+
+
 def synthesize(csr: CSR, prob, labels, spec=REACH_AVOID, eps=1e-6, max_iters=10000,
+               optimistic=False, horizon=0, n_disturb=1, regions: Optional[RegionVectors] = None,
                stream=None) -> Controller:
-    """Interval iteration on a device IMDP built for `prob` (impact_synthesize)."""
+    """Interval iteration on a device IMDP built for `prob`
+    (impact_synthesize_ex). With disturbances the build's input points are
+    the (input, disturbance) pairs, disturbance fastest: prob.n_inputs =
+    inputs * n_disturb."""
     cells = int(prob.total_cells)
-    lab = torch.as_tensor(np.asarray(labels, np.uint8)).cuda()
+    if int(prob.n_inputs) % int(n_disturb):
+        raise ValueError("the build's input count is not a multiple of n_disturb")
+    n_inputs = int(prob.n_inputs) // int(n_disturb)
+    if isinstance(labels, torch.Tensor):
+        lab = labels.to(device="cuda", dtype=torch.uint8).contiguous()
+    else:
+        lab = torch.as_tensor(np.asarray(labels, np.uint8)).cuda()
     dev = lab.device
     p_min = torch.empty(cells, dtype=torch.float64, device=dev)
     p_max = torch.empty(cells, dtype=torch.float64, device=dev)
@@ -687,10 +783,13 @@ def synthesize(csr: CSR, prob, labels, spec=REACH_AVOID, eps=1e-6, max_iters=100
     p = lambda t: t.data_ptr()
     c.row_ptr, c.col, c.lo, c.up = p(csr.row_ptr), p(csr.col), p(csr.lo), p(csr.up)
     c.sink_lo, c.sink_up, c.trunc = p(csr.sink_lo), p(csr.sink_up), p(csr.trunc)
+    o = _SynthOptions(int(spec), int(bool(optimistic)), int(horizon), int(n_disturb), float(eps),
+                      int(max_iters), None, None, None, None)
+    if regions is not None:
+        o.r_lo, o.r_up = p(regions.r_lo), p(regions.r_up)
+        o.a_lo, o.a_up = p(regions.a_lo), p(regions.a_up)
     its = (ctypes.c_int * 2)()
-    _check(load().impact_synthesize(ctypes.byref(c), _PREC[csr.precision], cells,
-                                    int(prob.n_inputs), p(lab), int(spec), float(eps),
-                                    int(max_iters), p(p_min), p(p_max), p(pol), its,
-                                    ctypes.c_void_p(_stream_handle(stream))))
+    _check(load().impact_synthesize_ex(ctypes.byref(c), _PREC[csr.precision], cells, n_inputs,
+                                       p(lab), ctypes.byref(o), p(p_min), p(p_max), p(pol), its,
+                                       ctypes.c_void_p(_stream_handle(stream))))
     return Controller(p_min, p_max, pol, (int(its[0]), int(its[1])))
-

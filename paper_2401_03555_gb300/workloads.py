@@ -209,6 +209,24 @@ def batched_family(count: int = 256, first_seed: int = 0, **kw) -> List[Problem]
     return [random_linear(first_seed + s, **kw) for s in range(count)]
 
 
+def with_disturbances(prob: Problem, Bw, w_points) -> Problem:
+    """The affine `prob` with a disturbance input: f(x, u, w) = A x + B u +
+    Bw w + c. The build's input points become the (u, w) pairs, w fastest,
+    so row r = (cell * n_u + j) * n_w + k."""
+    if prob.kind != AFFINE:
+        raise ValueError("disturbances are added to affine systems")
+    U = np.asarray(prob.inputs, np.float64)
+    if U.ndim == 1:
+        U = U.reshape(-1, 1)
+    Wp = np.asarray(w_points, np.float64)
+    if Wp.ndim == 1:
+        Wp = Wp.reshape(-1, 1)
+    Bw = np.asarray(Bw, np.float64).reshape(prob.n, Wp.shape[1])
+    pts = np.array([np.concatenate([u, w]) for u in U for w in Wp])
+    B = Bw if U.shape[1] == 0 else np.concatenate([np.asarray(prob.B, np.float64), Bw], axis=1)
+    return replace(prob, name=prob.name + f"+w{Wp.shape[0]}", inputs=pts, B=B)
+
+
 def with_images(prob: Problem, images: np.ndarray) -> Problem:
     """Same grid/inputs/noise, but with caller-supplied interval images."""
     return replace(prob, kind=IMAGES, images=_arr(images), name=prob.name + "+images")

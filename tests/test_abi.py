@@ -37,7 +37,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_version(lib):
-    assert impact.version() == 300
+    assert impact.version() == 301
 
 
 @pytest.mark.parametrize("make", [W.robot_2d, W.room_5d, W.unicycle_3d, W.building_7d])
