@@ -373,6 +373,11 @@ def run_ours(args, rank, world, local_rank):
         except Exception as exc:
             out["synthesis"] = {"value": None, "error": str(exc)[:300]}
         torch.cuda.empty_cache()
+        try:
+            out["regions"] = run_regions()
+        except Exception as exc:
+            out["regions"] = {"value": None, "error": str(exc)[:300]}
+        torch.cuda.empty_cache()
 
     if not args.no_serve and rank == 0:
         try:
@@ -493,7 +498,8 @@ def run_synthesis(eps=1e-6, oracle_iters=2):
     import torch
     from paper_2401_03555_gb300 import impact, workloads as W
     prob = W.robot_2d()
-    labels = W.region_labels(prob, target=([3, 3], [7, 7]), avoid=([-7, -7], [-3, -3]))
+    target, avoid = [([3, 3], [7, 7])], [([-7, -7], [-3, -3])]
+    labels = impact.label_cells(prob, target, avoid)
     csr = impact.build(prob, "fp64")
     impact.synthesize(csr, prob, labels, eps=eps)          # warm-up
     torch.cuda.synchronize()
@@ -507,19 +513,68 @@ def run_synthesis(eps=1e-6, oracle_iters=2):
     out = {"workload": SYNTH_WORKLOAD, "iterations": list(g.iterations), "ms": dt * 1e3,
            "ms_per_iteration": dt * 1e3 / its, "value": row_lps / dt, "unit": "row LPs/s",
            "p_min_max": float(g.p_min.max().item()),
-           "path": "impact_synthesize (sorting-method LP by warp bisection, one warp per cell)"}
+           "path": "impact_synthesize (sorting-method LP by warp bisection, one warp per row, "
+                   "then one thread per cell)"}
+    # the same controller with the region vectors (one box relaxation per region)
+    rv = impact.region_vectors(prob, target, avoid, "box", "fp64")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    gr = impact.synthesize(csr, prob, labels, eps=eps, regions=rv)
+    torch.cuda.synchronize()
+    out["with_region_boxes"] = {"iterations": list(gr.iterations),
+                                "ms": (time.perf_counter() - t0) * 1e3,
+                                "p_min_gain_max": float((gr.p_min - g.p_min).max().item())}
     try:
         import oracle
         from oracle import synthesis as SY
         ocsr = oracle.build_rows(prob)
+        olab = labels.cpu().numpy()
         t0 = time.perf_counter()
-        SY.interval_iteration(ocsr, labels, prob.n_inputs, SY.REACH_AVOID, eps=eps,
+        SY.interval_iteration(ocsr, olab, prob.n_inputs, SY.REACH_AVOID, eps=eps,
                               max_iters=oracle_iters)
         odt = time.perf_counter() - t0
         # the oracle runs both phases for `oracle_iters` iterations each
         out["cpu_baseline"] = {"value": 2 * prob.rows * 2 * oracle_iters / odt,
                                "unit": "row LPs/s", "cores": 1, "kind": "oracle",
                                "sample": f"{oracle_iters} iterations of each phase"}
+    except Exception as exc:
+        out["cpu_baseline"] = {"value": None, "error": str(exc)[:200]}
+    return out
+
+
+REGION_WORKLOAD = ("target / avoid vectors R and A of the 5-D room (11^5 cells x 9 inputs = "
+                   "1,449,459 rows): target [19,21]^5, avoid x1 in [17,17.6]; box relaxation "
+                   "and the paper's per-cell sums, FP32-sound evaluation")
+
+
+def run_regions(reps=5, oracle_rows=16):
+    """impact_region_vectors over every row of the 5-D room, both modes; the
+    oracle (dense per-cell sums) on a few sampled rows."""
+    import torch
+    from paper_2401_03555_gb300 import impact, workloads as W
+    prob = W.room_5d()
+    target = [([19.0] * 5, [21.0] * 5)]
+    avoid = [([17.0] * 5, [17.6, 23, 23, 23, 23])]
+    out = {"workload": REGION_WORKLOAD, "rows": int(prob.rows), "unit": "rows/s"}
+    for mode in ("box", "cells"):
+        impact.region_vectors(prob, target, avoid, mode, "fp32")       # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            impact.region_vectors(prob, target, avoid, mode, "fp32")
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t0) * 1e3 / reps
+        out[mode] = {"ms": ms, "value": prob.rows / (ms * 1e-3),
+                     "path": "impact_region_vectors (plan upload + one thread per row)"}
+    try:
+        import oracle
+        rows = W.sample_rows(prob, oracle_rows, seed=5, include_boundary=False)
+        t0 = time.perf_counter()
+        oracle.region_vectors(prob, rows, target, avoid, "cells")
+        odt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": len(rows) / odt, "unit": "rows/s",
+                               "cores": oracle.max_threads(), "kind": "oracle",
+                               "sample": f"{len(rows)} sampled rows, dense per-cell sums"}
     except Exception as exc:
         out["cpu_baseline"] = {"value": None, "error": str(exc)[:200]}
     return out

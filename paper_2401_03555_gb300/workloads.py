@@ -209,6 +209,14 @@ def batched_family(count: int = 256, first_seed: int = 0, **kw) -> List[Problem]
     return [random_linear(first_seed + s, **kw) for s in range(count)]
 
 
+def without_inputs(prob: Problem) -> Problem:
+    """The autonomous system f(x) = A x + c of an affine `prob`: one input
+    point of dimension 0, so the build is an interval Markov chain (IMC)."""
+    if prob.kind != AFFINE:
+        raise ValueError("only affine systems drop their inputs here")
+    return replace(prob, name=prob.name + "-imc", inputs=np.zeros((1, 0)), B=None)
+
+
 def with_disturbances(prob: Problem, Bw, w_points) -> Problem:
     """The affine `prob` with a disturbance input: f(x, u, w) = A x + B u +
     Bw w + c. The build's input points become the (u, w) pairs, w fastest,

@@ -89,6 +89,20 @@ def test_region_vectors_reduce_to_cells_and_sink(orc):
     P.pin_region_reductions(orc)
 
 
+def test_interval_markov_chain_is_the_zero_input_row(orc):
+    """Without inputs (an IMC, Sec. 6.4) the robot's rows equal its rows for
+    the input point u = 0."""
+    prob = W.robot_2d(cells_per_dim=9)
+    imc = W.without_inputs(prob)
+    j0 = int(np.nonzero(np.all(prob.inputs == 0.0, axis=1))[0][0])
+    cells = np.arange(0, 81, 7)
+    a = orc.build_rows(imc, cells)
+    b = orc.build_rows(prob, cells * prob.n_inputs + j0)
+    for x, y in ((a.row_ptr, b.row_ptr), (a.col, b.col), (a.lo, b.lo), (a.up, b.up),
+                 (a.sink_lo, b.sink_lo), (a.sink_up, b.sink_up), (a.trunc, b.trunc)):
+        assert np.array_equal(x, y)
+
+
 def test_overlapping_region_boxes_are_refused(orc):
     prob = W.robot_2d(cells_per_dim=9)
     with pytest.raises(ValueError):

@@ -174,6 +174,29 @@ def test_disturbance_adversary(spec):
     assert torch.all(got.p_min <= plain.p_min + 1e-6).item()
 
 
+@pytest.mark.parametrize("disturb", [False, True])
+def test_interval_markov_chain_verification(disturb):
+    """No inputs (an IMC): the build and the verification bounds; with
+    disturbance points the adversary still chooses."""
+    base, tb, ab = robot(7)
+    prob = W.without_inputs(base)
+    if disturb:
+        prob = W.with_disturbances(prob, np.eye(2), [[-0.5, 0.0], [0.5, 0.0]])
+    W_n = 2 if disturb else 1
+    ocsr = oracle.build_rows(prob)
+    csr = impact.build(prob, "fp64")
+    assert np.array_equal(csr.row_ptr.cpu().numpy(), ocsr.row_ptr)
+    assert np.max(np.abs(csr.up.cpu().numpy() - ocsr.up)) < 1e-12
+    olab = oracle.region_labels(prob, tb, ab)
+    for spec in (SY.REACH_AVOID, SY.SAFETY):
+        ref = SY.interval_iteration(ocsr, olab, 1, spec, eps=1e-10, max_iters=5000, n_disturb=W_n)
+        got = impact.synthesize(csr, prob, impact.label_cells(prob, tb, ab), spec=spec, eps=1e-10,
+                                max_iters=5000, n_disturb=W_n)
+        assert np.max(np.abs(got.p_min.cpu().numpy() - ref.p_min)) < 1e-8
+        assert np.max(np.abs(got.p_max.cpu().numpy() - ref.p_max)) < 1e-8
+        assert int(got.policy.abs().max()) == 0
+
+
 def test_synthesis_option_errors():
     prob, tb, ab = robot(5)
     csr = impact.build(prob, "fp64")
