@@ -26,6 +26,7 @@
 
 #include "impact_desc.h"
 #include "kernels.h"
+#include "sound_fp32.cuh"
 
 namespace {
 
@@ -501,22 +502,57 @@ label_cells(RegionBoxes B, int64_t total, uint8_t *__restrict__ labels)
     }
 }
 
-// Error bound of one factor g64 (absolute): erfc within a few ulp of values
-// <= 2, the difference and its halving, and the rounded argument.
-constexpr double kFactorErr = 0x1p-48;
+// FP32 interval of (p - m') / (sigma sqrt2) for every m' within dm of m: the
+// FP64 evaluation (relative error below 2^-49 with the rounded 1/(sigma
+// sqrt2)) widened by that error and by dm, then rounded outward to FP32.
+__device__ __forceinline__ void arg_iv(double p, double m, double dm, double inv_s, float &lo,
+                                       float &hi)
+{
+    const double x = (p - m) * inv_s;
+    const double w = dm * inv_s;
+    const double e = (fabs(x) + w) * 0x1p-49 + w;
+    lo = __double2float_rd(x - e);
+    hi = __double2float_ru(x + e);
+}
 
-// Upper / lower end of one factor: as computed (plain) or widened by its
-// error bound (sound).
+// Bounds of one factor g(c, e; m), the mass of [c, e] around a mean m known
+// to within dm: FP64 round-to-nearest (plain), or the FP32 outward bounds of
+// sound_fp32.cuh (sound).
 template <bool SOUND>
-__device__ __forceinline__ double f_up(double g)
+__device__ __forceinline__ double g_up(double c, double e, double m, double dm, double inv_s)
 {
-    return SOUND ? fmin(__dadd_ru(g, kFactorErr), 1.0) : g;
+    if (!SOUND) return g64(c, e, m, inv_s);
+    float acl, ach, ael, aeh;
+    arg_iv(c, m, dm, inv_s, acl, ach);
+    arg_iv(e, m, dm, inv_s, ael, aeh);
+    return (double)sound::mass_hi(acl, ach, ael, aeh);
 }
 template <bool SOUND>
-__device__ __forceinline__ double f_dn(double g)
+__device__ __forceinline__ double g_dn(double c, double e, double m, double inv_s)
 {
-    return SOUND ? fmax(__dsub_rd(g, kFactorErr), 0.0) : g;
+    if (!SOUND) return g64(c, e, m, inv_s);
+    float acl, ach, ael, aeh;
+    arg_iv(c, m, 0.0, inv_s, acl, ach);
+    arg_iv(e, m, 0.0, inv_s, ael, aeh);
+    return (double)sound::mass_lo(acl, ach, ael, aeh);
 }
+
+// Largest factor over m in [mlo, mhi] (at the clamped midpoint of [c, e],
+// whose rounding dm the sound bound covers) and the smallest (at an end).
+template <bool SOUND>
+__device__ __forceinline__ double f_max(double c, double e, double mlo, double mhi, double inv_s)
+{
+    const double mid = 0.5 * (c + e);
+    const double m = clampd(mid, mlo, mhi);
+    const double dm = (m == mid) ? fabs(mid) * 0x1p-52 : 0.0;
+    return g_up<SOUND>(c, e, m, dm, inv_s);
+}
+template <bool SOUND>
+__device__ __forceinline__ double f_min(double c, double e, double mlo, double mhi, double inv_s)
+{
+    return fmin(g_dn<SOUND>(c, e, mlo, inv_s), g_dn<SOUND>(c, e, mhi, inv_s));
+}
+
 template <bool SOUND>
 __device__ __forceinline__ double mul_up(double a, double b) { return SOUND ? __dmul_ru(a, b) : a * b; }
 template <bool SOUND>
@@ -549,11 +585,8 @@ region_rows(const ImpactDesc *__restrict__ Dp, int64_t rows, RegionBoxes B, bool
         for (int d = 0; d < n; ++d) {
             image_dim<SOUND>(D, row, idx, j, d, mlo[d], mhi[d]);
             const ImpactDim &g = D.dim[d];
-            const double mid = 0.5 * (g.lo + g.hi);
-            in_max = mul_up<SOUND>(in_max, f_up<SOUND>(g64(g.lo, g.hi, clampd(mid, mlo[d], mhi[d]),
-                                                           g.inv_s)));
-            in_min = mul_dn<SOUND>(in_min, f_dn<SOUND>(fmin(g64(g.lo, g.hi, mlo[d], g.inv_s),
-                                                            g64(g.lo, g.hi, mhi[d], g.inv_s))));
+            in_max = mul_up<SOUND>(in_max, f_max<SOUND>(g.lo, g.hi, mlo[d], mhi[d], g.inv_s));
+            in_min = mul_dn<SOUND>(in_min, f_min<SOUND>(g.lo, g.hi, mlo[d], mhi[d], g.inv_s));
         }
         double rl = 0.0, ru = 0.0;
         double xl = SOUND ? fmax(__dsub_rd(1.0, in_max), 0.0) : 1.0 - in_max;
@@ -568,13 +601,13 @@ region_rows(const ImpactDesc *__restrict__ Dp, int64_t rows, RegionBoxes B, bool
                     fu = 0.0;
                     fl = 0.0;
                     for (int i = B.first[b][d]; i <= B.last[b][d]; ++i) {
-                        fu = add_up<SOUND>(fu, f_up<SOUND>(up64(g, E, i, mlo[d], mhi[d])));
-                        fl = add_dn<SOUND>(fl, f_dn<SOUND>(lo64(g, E, i, mlo[d], mhi[d])));
+                        fu = add_up<SOUND>(fu, f_max<SOUND>(E[i], E[i + 1], mlo[d], mhi[d], g.inv_s));
+                        fl = add_dn<SOUND>(fl, f_min<SOUND>(E[i], E[i + 1], mlo[d], mhi[d], g.inv_s));
                     }
                 } else {
                     const double c = E[B.first[b][d]], e = E[B.last[b][d] + 1];
-                    fu = f_up<SOUND>(g64(c, e, clampd(0.5 * (c + e), mlo[d], mhi[d]), g.inv_s));
-                    fl = f_dn<SOUND>(fmin(g64(c, e, mlo[d], g.inv_s), g64(c, e, mhi[d], g.inv_s)));
+                    fu = f_max<SOUND>(c, e, mlo[d], mhi[d], g.inv_s);
+                    fl = f_min<SOUND>(c, e, mlo[d], mhi[d], g.inv_s);
                 }
                 pu = mul_up<SOUND>(pu, fu);
                 pl = mul_dn<SOUND>(pl, fl);

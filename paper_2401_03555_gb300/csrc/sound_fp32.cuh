@@ -150,7 +150,7 @@ struct TailPair {
     float m_lo, m_hi;   // T(-x)
 };
 
-__device__ __noinline__ TailPair tails(float xm, float dx)
+static __device__ __noinline__ TailPair tails(float xm, float dx)
 {
     TailPair r;
     float ax = fabsf(xm);
