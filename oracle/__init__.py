@@ -19,6 +19,11 @@ are either the paper's sums of the per-cell bounds over the labelled cells
 or one box relaxation per region box (the box's cells taken as one big
 target), the sink added to A.
 
+Sampled noise (Sec. 4.1, full covariance or a custom distribution by
+Monte-Carlo integration): given noise draws w_s, a row's up / lo for target
+t are the fractions of draws for which the image box moved by w_s meets t /
+lies inside t; the sink counts draws that leave the domain in part / whole.
+
 Parity pins: every function here is pinned by ``tests/test_oracle_pins.py``
 (library CDF, telescoping identity, 1-D closed form, brute-force argmax for
 separable systems, Monte-Carlo containment, noise sampling, invariants,
@@ -106,6 +111,11 @@ class Oracle:
         lib.oracle_release.argtypes = [ctypes.c_void_p]
         lib.oracle_max_threads.restype = ctypes.c_int
         lib.oracle_max_threads.argtypes = []
+        lib.oracle_cell_of.restype = ctypes.c_int
+        lib.oracle_cell_of.argtypes = [P, ctypes.c_int, ctypes.c_double]
+        lib.oracle_run_mc.restype = ctypes.c_void_p
+        lib.oracle_run_mc.argtypes = [P, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                      ctypes.c_int64, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]
         lib.oracle_box_cells.restype = ctypes.c_int
         lib.oracle_box_cells.argtypes = [P] + [ctypes.c_void_p] * 4
         lib.oracle_labels.restype = None
@@ -172,6 +182,43 @@ class Oracle:
             out.col = out.col[:nnz.value]
             out.lo = out.lo[:nnz.value]
             out.up = out.up[:nnz.value]
+        finally:
+            lib.oracle_release(h)
+        return out
+
+    def cell_of(self, prob, d: int, y: float) -> int:
+        """Cell of dimension d holding coordinate y (-1 below, N above)."""
+        mp = _Marshalled(prob)
+        return int(self.lib.oracle_cell_of(ctypes.byref(mp.struct), int(d), float(y)))
+
+    def build_rows_mc(self, prob, samples, rows=None, threads: int = 0) -> "OracleCSR":
+        """Rows built from sampled noise: samples is an (S, n) array of noise
+        draws; lo / up / sink are sample fractions (see oracle_mc_row)."""
+        mp = _Marshalled(prob)
+        if rows is None:
+            rows = np.arange(mp.rows, dtype=np.int64)
+        rows = np.ascontiguousarray(np.asarray(rows, dtype=np.int64))
+        W = np.ascontiguousarray(np.asarray(samples, np.float64).reshape(-1, mp.n).T)
+        S = int(W.shape[1])
+        nnz = ctypes.c_int64()
+        h = self.lib.oracle_run_mc(ctypes.byref(mp.struct), rows.ctypes.data, int(rows.shape[0]),
+                                   W.ctypes.data, S, int(threads), ctypes.byref(nnz))
+        return self._fetch(h, rows, nnz.value)
+
+    def _fetch(self, h, rows, nnz):
+        lib = self.lib
+        try:
+            R = int(rows.shape[0])
+            k = max(nnz, 1)
+            out = OracleCSR(rows=rows, row_ptr=np.empty(R + 1, np.int64),
+                            col=np.empty(k, np.int32), lo=np.empty(k), up=np.empty(k),
+                            sink_lo=np.empty(R), sink_up=np.empty(R), trunc=np.empty(R))
+            lib.oracle_fetch(h, out.row_ptr.ctypes.data, out.col.ctypes.data,
+                             out.lo.ctypes.data, out.up.ctypes.data, out.sink_lo.ctypes.data,
+                             out.sink_up.ctypes.data, out.trunc.ctypes.data)
+            out.col = out.col[:nnz]
+            out.lo = out.lo[:nnz]
+            out.up = out.up[:nnz]
         finally:
             lib.oracle_release(h)
         return out
@@ -354,6 +401,10 @@ def max_threads() -> int:
 
 def region_labels(prob, target=(), avoid=()):
     return default().region_labels(prob, target, avoid)
+
+
+def build_rows_mc(prob, samples, rows=None, threads: int = 0) -> OracleCSR:
+    return default().build_rows_mc(prob, samples, rows, threads)
 
 
 def region_vectors(prob, rows=None, target=(), avoid=(), mode="box"):

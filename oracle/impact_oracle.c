@@ -485,3 +485,130 @@ void oracle_region_rows(const oracle_problem *p, const int64_t *rows, int64_t nr
         oracle_region_row(p, rows[k], mode, labels, n_target, t_lo, t_hi, n_avoid, a_lo, a_hi,
                           out + 4 * k);
 }
+
+/* ---- sampled noise (Sec. 4.1: full covariance or a custom distribution,
+ * integrated by Monte-Carlo sampling) ------------------------------------- */
+
+/*
+ * Cell of dimension d that holds the coordinate y: -1 below the domain, N
+ * above it, else the i with edge i <= y < edge i+1 (the last cell also holds
+ * y == hi).
+ */
+int oracle_cell_of(const oracle_problem *p, int d, double y)
+{
+    int N = p->cells[d];
+    if (y < oracle_edge(p, d, 0)) return -1;
+    if (y > oracle_edge(p, d, N)) return N;
+    for (int i = 0; i < N; ++i)
+        if (y < oracle_edge(p, d, i + 1)) return i;
+    return N - 1;
+}
+
+/*
+ * Sample counts of one row. With the image box M = [m_lo, m_hi] of the row
+ * and the noise samples w_s (samples[d * S + s], dimension-major), sample s
+ * moves the box to w_s + M:
+ *   up[t]    += 1 for every target cell t the moved box meets,
+ *   lo[t]    += 1 for the one cell t that holds the whole moved box,
+ *   sink_up  += 1 when the moved box is not inside the domain,
+ *   sink_lo  += 1 when it lies entirely outside.
+ * Divided by S these estimate P(w + M meets t) >= max over m in M of
+ * P(m + w in t) and P(w + M inside t) <= the min (Def. 3.1 for a noise whose
+ * cell masses have no closed form).
+ */
+void oracle_mc_row(const oracle_problem *p, int64_t row, const double *samples, int64_t S,
+                   uint32_t *up, uint32_t *lo, int64_t *sink_lo, int64_t *sink_up)
+{
+    int n = p->n;
+    double m_lo[ORACLE_MAX_DIM], m_hi[ORACLE_MAX_DIM];
+    oracle_image(p, row, m_lo, m_hi);
+    int64_t T = total_cells(p);
+    memset(up, 0, sizeof(uint32_t) * (size_t)T);
+    memset(lo, 0, sizeof(uint32_t) * (size_t)T);
+    *sink_lo = 0;
+    *sink_up = 0;
+    for (int64_t s = 0; s < S; ++s) {
+        int a[ORACLE_MAX_DIM], b[ORACLE_MAX_DIM];
+        int inside = 1, outside = 0, single = 1;
+        for (int d = 0; d < n; ++d) {
+            double w = samples[(int64_t)d * S + s];
+            a[d] = oracle_cell_of(p, d, w + m_lo[d]);
+            b[d] = oracle_cell_of(p, d, w + m_hi[d]);
+            if (a[d] < 0 || b[d] > p->cells[d] - 1) inside = 0;
+            if (b[d] < 0 || a[d] > p->cells[d] - 1) outside = 1;
+            if (a[d] != b[d]) single = 0;
+        }
+        if (!inside) ++*sink_up;
+        if (outside) {
+            ++*sink_lo;
+            continue;
+        }
+        /* every target cell t: does the moved box meet it, hold it whole? */
+        for (int64_t t = 0; t < T; ++t) {
+            int meets = 1;
+            for (int d = 0; d < n && meets; ++d) {
+                int i = cell_digit(p, t, d);
+                meets = a[d] <= i && i <= b[d];
+            }
+            if (meets) {
+                ++up[t];
+                if (single) ++lo[t];
+            }
+        }
+    }
+}
+
+/* Build the rows listed from sampled noise (same layout and rules as
+ * oracle_run: keep t iff up_t >= cutoff, trunc = dropped up mass), values
+ * count / S. */
+void *oracle_run_mc(const oracle_problem *p, const int64_t *rows, int64_t nrows,
+                    const double *samples, int64_t S, int threads, int64_t *nnz)
+{
+    oracle_batch *b = (oracle_batch *)calloc(1, sizeof(oracle_batch));
+    b->nrows = nrows;
+    b->r = (oracle_row_result *)calloc((size_t)(nrows > 0 ? nrows : 1), sizeof(oracle_row_result));
+    int64_t T = total_cells(p);
+    const double dS = (double)S;
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+#else
+    (void)threads;
+#endif
+#pragma omp parallel
+    {
+        uint32_t *up = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)T);
+        uint32_t *lo = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)T);
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t k = 0; k < nrows; ++k) {
+            oracle_row_result *res = &b->r[k];
+            int64_t sl, su, cnt = 0, dropped = 0;
+            oracle_mc_row(p, rows[k], samples, S, up, lo, &sl, &su);
+            for (int64_t t = 0; t < T; ++t) {
+                if ((double)up[t] / dS >= p->cutoff) ++cnt;
+                else dropped += up[t];
+            }
+            res->sink_lo = (double)sl / dS;
+            res->sink_up = (double)su / dS;
+            res->trunc = (double)dropped / dS;
+            res->count = cnt;
+            res->col = (int32_t *)malloc(sizeof(int32_t) * (size_t)(cnt > 0 ? cnt : 1));
+            res->lo = (double *)malloc(sizeof(double) * (size_t)(cnt > 0 ? cnt : 1));
+            res->up = (double *)malloc(sizeof(double) * (size_t)(cnt > 0 ? cnt : 1));
+            int64_t w = 0;
+            for (int64_t t = 0; t < T; ++t) {
+                if ((double)up[t] / dS >= p->cutoff) {
+                    res->col[w] = (int32_t)t;
+                    res->lo[w] = (double)lo[t] / dS;
+                    res->up[w] = (double)up[t] / dS;
+                    ++w;
+                }
+            }
+        }
+        free(up);
+        free(lo);
+    }
+    int64_t total = 0;
+    for (int64_t k = 0; k < nrows; ++k) total += b->r[k].count;
+    *nnz = total;
+    return b;
+}

@@ -497,3 +497,162 @@ def pin_region_reductions(orc):
         csr = orc.build_rows(prob, rows)
         assert np.all(np.abs(r_lo - (1.0 - csr.sink_up)) < 1e-15), prob.name
         assert np.all(np.abs(r_up - (1.0 - csr.sink_lo)) < 1e-15), prob.name
+
+
+# --------------------------------------------------------------------------
+# sampled noise (Sec. 4.1: Monte-Carlo integration for full covariance or a
+# custom distribution)
+# --------------------------------------------------------------------------
+
+
+def _binomial_ok(est, p, S, k=5.0):
+    """|est - p| within k binomial standard deviations (plus one count)."""
+    sd = np.sqrt(np.maximum(p * (1.0 - p), 0.0) / S)
+    return np.abs(est - p) <= k * sd + 1.0 / S
+
+
+def pin_mc_cell_of(orc):
+    """Cell of a coordinate: the library's sorted search over the edges."""
+    prob = W.robot_2d(cells_per_dim=9)
+    e = grid_edges(prob, 0)
+    ys = np.concatenate([e, np.nextafter(e, -np.inf), np.nextafter(e, np.inf), [-50.0, 50.0],
+                         np.linspace(-11, 11, 97)])
+    for y in ys:
+        if y < e[0]:
+            ref = -1
+        elif y > e[-1]:
+            ref = 9
+        else:
+            ref = min(int(np.searchsorted(e, y, side="right")) - 1, 8)
+        assert orc.cell_of(prob, 0, float(y)) == ref, y
+
+
+def mc_images(prob, seed, width):
+    """Images of every row: a random centre per row and the given widths."""
+    rng = np.random.default_rng(seed)
+    n = prob.n
+    mid = prob.lo + (prob.hi - prob.lo) * rng.uniform(0.1, 0.9, (prob.rows, n))
+    im = np.stack([mid - 0.5 * np.asarray(width), mid + 0.5 * np.asarray(width)], axis=2)
+    return W.with_images(prob, im)
+
+
+def pin_mc_point_images(orc, S=20000, seed=31):
+    """Point images: up == lo for every target, and the fractions agree with
+    the closed-form Gaussian cell mass (diagonal noise, library CDF) and with
+    the library's bivariate normal CDF (full covariance) within 5 binomial
+    standard deviations."""
+    from scipy.stats import multivariate_normal
+    base = W.robot_2d(cells_per_dim=7)
+    prob = mc_images(base, seed, [0.0, 0.0])
+    rng = np.random.default_rng(seed)
+    rows = [3, 50, 200, 400]
+    sig = np.asarray(base.sigma)
+    w = rng.normal(0.0, 1.0, (S, 2)) * sig
+    csr = orc.build_rows_mc(prob, w, rows)
+    for k, row in enumerate(rows):
+        cols, lo, up = csr.row(k)
+        assert np.array_equal(lo, up)
+        mu = prob.images[row][:, 0]
+        P, out = exact_probs(base, mu)
+        assert np.all(_binomial_ok(up, P[cols], S)), row
+        missing = np.setdiff1d(np.arange(P.size), cols)
+        assert np.all(P[missing] < 6.0 / np.sqrt(S)), row
+        assert _binomial_ok(csr.sink_lo[k], out, S) and csr.sink_lo[k] == csr.sink_up[k]
+    # full covariance: w = L z
+    cov = np.array([[1.0, 0.6], [0.6, 0.8]]) * 0.6 ** 2
+    L = np.linalg.cholesky(cov)
+    w = rng.normal(0.0, 1.0, (S, 2)) @ L.T
+    csr = orc.build_rows_mc(prob, w, rows)
+    e0, e1 = grid_edges(base, 0), grid_edges(base, 1)
+    for k, row in enumerate(rows):
+        cols, lo, up = csr.row(k)
+        mu = prob.images[row][:, 0]
+        F = multivariate_normal(mean=mu, cov=cov)
+        for t, u in zip(cols[::3], up[::3]):
+            i, j = divmod(int(t), 7)
+            p = (F.cdf([e0[i + 1], e1[j + 1]]) - F.cdf([e0[i], e1[j + 1]])
+                 - F.cdf([e0[i + 1], e1[j]]) + F.cdf([e0[i], e1[j]]))
+            assert _binomial_ok(u, max(p, 0.0), S) or abs(u - p) < 2e-4, (row, t, u, p)
+
+
+def pin_mc_box_images(orc, S=20000, seed=32):
+    """Wide images, diagonal noise: the fraction of draws whose moved box
+    meets a cell / lies inside it / leaves the domain have product closed
+    forms (independent coordinates)."""
+    base = W.robot_2d(cells_per_dim=7)
+    width = [1.3, 0.4]
+    prob = mc_images(base, seed, width)
+    rng = np.random.default_rng(seed)
+    sig = np.asarray(base.sigma)
+    w = rng.normal(0.0, 1.0, (S, 2)) * sig
+    rows = [7, 99, 250, 420]
+    csr = orc.build_rows_mc(prob, w, rows)
+    E = [grid_edges(base, d) for d in range(2)]
+    for k, row in enumerate(rows):
+        mlo, mhi = prob.images[row][:, 0], prob.images[row][:, 1]
+        # P(w in [c - m_hi, e - m_lo]) = mass of [c, e + m_hi - m_lo] around m_hi
+        meet = [interval_mass(E[d][:-1], E[d][1:] + (mhi[d] - mlo[d]), mhi[d], sig[d])
+                for d in range(2)]
+        inside = [np.where(E[d][1:] - E[d][:-1] >= mhi[d] - mlo[d],
+                           interval_mass(E[d][:-1] + (mhi[d] - mlo[d]), np.maximum(
+                               E[d][1:], E[d][:-1] + (mhi[d] - mlo[d])), mhi[d], sig[d]), 0.0)
+                  for d in range(2)]
+        Pm = np.multiply.outer(meet[0], meet[1]).reshape(-1)
+        Pi = np.multiply.outer(inside[0], inside[1]).reshape(-1)
+        cols, lo, up = csr.row(k)
+        assert np.all(_binomial_ok(up, Pm[cols], S)), row
+        assert np.all(_binomial_ok(lo, Pi[cols], S)), row
+        stay = np.prod([float(interval_mass(base.lo[d] + (mhi[d] - mlo[d]), base.hi[d], mhi[d],
+                                            sig[d])) for d in range(2)])
+        touch = np.prod([float(interval_mass(base.lo[d], base.hi[d] + (mhi[d] - mlo[d]), mhi[d],
+                                             sig[d])) for d in range(2)])
+        assert _binomial_ok(csr.sink_up[k], 1.0 - stay, S), row
+        assert _binomial_ok(csr.sink_lo[k], 1.0 - touch, S), row
+
+
+def pin_mc_counting(orc, S=3000, seed=33):
+    """Exact counting identities: every draw lands in at most one lo cell or
+    the sink's lo, and meets at least one cell or the sink's up; and a brute
+    force over every cell with the edges searched by the library agrees
+    count for count."""
+    base = W.robot_2d(cells_per_dim=6)
+    prob = mc_images(base, seed, [0.9, 2.1])
+    rng = np.random.default_rng(seed)
+    w = rng.normal(0.0, 1.0, (S, 2)) * np.asarray(base.sigma) * 2.0
+    prob.cutoff = 0.02
+    rows = [0, 11, 100, 200, 323]
+    csr = orc.build_rows_mc(prob, w, rows)
+    E = [grid_edges(base, d) for d in range(2)]
+
+    def cell(d, y):
+        if y < E[d][0]:
+            return -1
+        if y > E[d][-1]:
+            return 6
+        return min(int(np.searchsorted(E[d], y, side="right")) - 1, 5)
+
+    for k, row in enumerate(rows):
+        cols, lo, up = csr.row(k)
+        mlo, mhi = prob.images[row][:, 0], prob.images[row][:, 1]
+        cu = np.zeros(36, np.int64)
+        cl = np.zeros(36, np.int64)
+        part = whole = 0
+        for s in range(S):
+            a = [cell(d, w[s, d] + mlo[d]) for d in range(2)]
+            b = [cell(d, w[s, d] + mhi[d]) for d in range(2)]
+            part += any(a[d] < 0 or b[d] > 5 for d in range(2))
+            whole += any(b[d] < 0 or a[d] > 5 for d in range(2))
+            for i in range(max(a[0], 0), min(b[0], 5) + 1):
+                for j in range(max(a[1], 0), min(b[1], 5) + 1):
+                    cu[i * 6 + j] += 1
+                    if a == b:
+                        cl[i * 6 + j] += 1
+        kept = np.nonzero(cu / S >= prob.cutoff)[0]
+        assert np.array_equal(cols, kept), row
+        assert np.array_equal(np.round(up * S).astype(np.int64), cu[kept]), row
+        assert np.array_equal(np.round(lo * S).astype(np.int64), cl[kept]), row
+        assert round(csr.trunc[k] * S) == cu.sum() - cu[kept].sum(), row
+        assert round(csr.sink_up[k] * S) == part and round(csr.sink_lo[k] * S) == whole, row
+        # every draw: at most one lo cell or the sink's lo; at least one cell
+        # met or the sink's up
+        assert cl.sum() + whole <= S and cu.sum() + part >= S

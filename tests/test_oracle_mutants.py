@@ -63,6 +63,13 @@ MUTANTS = {
                              "if (in && !avoid) lab = ORACLE_TARGET;\n            else if (in && lab == ORACLE_FREE) lab = ORACLE_AVOID;")],
     "cell centre off by half": [("return 0.5 * (oracle_edge(p, d, i) + oracle_edge(p, d, i + 1));",
                                  "return oracle_edge(p, d, i);")],
+    "cell_of closes the cell": [("if (y < oracle_edge(p, d, i + 1)) return i;",
+                                 "if (y <= oracle_edge(p, d, i + 1)) return i;")],
+    "mc box ends swapped": [("b[d] = oracle_cell_of(p, d, w + m_hi[d]);",
+                             "b[d] = oracle_cell_of(p, d, w - m_hi[d]);")],
+    "mc lo without the single test": [("if (single) ++lo[t];", "++lo[t];")],
+    "mc sink_up counts leaving whole": [("if (!inside) ++*sink_up;", "if (outside) ++*sink_up;")],
+    "mc dropped mass from lo": [("else dropped += up[t];", "else dropped += lo[t];")],
     "ties dropped": [("if (up[t] >= p->cutoff) ++cnt;", "if (up[t] > p->cutoff) ++cnt;"),
                      ("if (up[t] >= p->cutoff) {", "if (up[t] > p->cutoff) {")],
 }
@@ -95,6 +102,10 @@ try:
     P.pin_region_containment(orc, samples=6)
     P.pin_region_box_exact_separable(orc)
     P.pin_region_reductions(orc)
+    P.pin_mc_cell_of(orc)
+    P.pin_mc_point_images(orc, S=6000)
+    P.pin_mc_box_images(orc, S=6000)
+    P.pin_mc_counting(orc, S=600)
 except AssertionError as e:
     print("CAUGHT", repr(e)[:200])
     sys.exit(3)

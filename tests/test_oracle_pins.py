@@ -89,6 +89,22 @@ def test_region_vectors_reduce_to_cells_and_sink(orc):
     P.pin_region_reductions(orc)
 
 
+def test_mc_cell_of(orc):
+    P.pin_mc_cell_of(orc)
+
+
+def test_mc_point_images_match_closed_forms_and_library_cdf(orc):
+    P.pin_mc_point_images(orc)
+
+
+def test_mc_box_images_match_closed_forms(orc):
+    P.pin_mc_box_images(orc)
+
+
+def test_mc_counts_equal_brute_force(orc):
+    P.pin_mc_counting(orc)
+
+
 def test_interval_markov_chain_is_the_zero_input_row(orc):
     """Without inputs (an IMC, Sec. 6.4) the robot's rows equal its rows for
     the input point u = 0."""
