@@ -411,6 +411,34 @@ impact_status impact_synthesize(const impact_csr *imdp, impact_precision precisi
                                 double eps, int max_iters, double *p_min, double *p_max,
                                 int32_t *policy, int *iterations, void *stream);
 
+/*
+ * impact_build_mc -- impact_build for a noise given by draws instead of the
+ * diagonal Gaussian (paper: Sec. 4.1, a full covariance matrix or a custom
+ * distribution, integrated by Monte-Carlo sampling). samples: DEVICE
+ * double[n][n_samples], dimension-major (draw s of coordinate d at
+ * d * n_samples + s); for a covariance C pass L z with C = L L^T and z
+ * standard normal. The draws are the caller's: the library draws nothing.
+ * With the row's interval image M (as in impact_build) and draw w_s moving it
+ * to w_s + M, and cells half-open (edge_i <= y < edge_{i+1}, the last one
+ * closed):
+ *   up  = fraction of draws whose moved box meets the target cell,
+ *   lo  = fraction of draws whose moved box lies in the target cell,
+ *   sink_up / sink_lo = fraction that leaves the domain in part / whole,
+ * Monte-Carlo estimates of P(w + M meets t), an upper bound of the maximum
+ * over the cell, and of P(w + M inside t), a lower bound of the minimum.
+ * A target is kept iff up >= cutoff (cutoff 0: every cell); trunc is the
+ * dropped up mass. Values are count / n_samples (FP64 exactly as divided;
+ * FP32: lo rounded down, up rounded up). sys, grid and inputs as for
+ * impact_build (sigma is not used); n_samples in [1, 2^31 - 1]. The cells
+ * within reach of a row's moved boxes must number at most 12288 (IMPACT_ERR_ARG
+ * otherwise). Ownership, capacity and errors as impact_build; synchronizes
+ * `stream` once between the passes.
+ */
+impact_status impact_build_mc(const impact_system *sys, const impact_grid *grid,
+                              const impact_inputs *inputs, const double *samples,
+                              int64_t n_samples, double cutoff, impact_precision precision,
+                              impact_csr *out, void *stream);
+
 /* ------------------------------------------------------------------------
  * Target and avoid regions (paper: Sec. 3.1 and Alg. 1 for the labels and
  * the vectors R and A, Remark 4.1 for the sink inside A).

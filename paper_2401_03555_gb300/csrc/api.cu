@@ -955,8 +955,9 @@ impact_status impact_region_vectors(const impact_system *sys, const impact_grid 
     configure_pool_once();
     cudaStream_t st = (cudaStream_t)stream;
     // the FP64 tables of the build (images in both roundings); the cutoff
-    // does not enter the vectors
-    impact_request req = single(sys, grid, inputs, sigma, 0.5);
+    // does not enter the vectors, and one near 1 keeps the planner's windows
+    // small
+    impact_request req = single(sys, grid, inputs, sigma, 0.999);
     Batch batch;
     s = make_batch(&req, 1, IMPACT_FP64_PLAIN, nullptr, batch);
     if (s != IMPACT_OK) return s;

@@ -479,6 +479,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_apply(int64_t *__restrict__
 // ---------------------------------------------------------------------------
 
 using impact::RegionBoxes;
+using impact::RowOutputs;
 
 __global__ void __launch_bounds__(256)
 label_cells(RegionBoxes B, int64_t total, uint8_t *__restrict__ labels)
@@ -627,6 +628,266 @@ region_rows(const ImpactDesc *__restrict__ Dp, int64_t rows, RegionBoxes B, bool
     }
 }
 
+// ---------------------------------------------------------------------------
+// sampled noise: Monte-Carlo integration of the cell masses (Sec. 4.1)
+// ---------------------------------------------------------------------------
+
+constexpr int kMcThreads = 256;
+
+// Per-dimension least and largest draw: range[2d], range[2d + 1].
+__global__ void __launch_bounds__(kMcThreads)
+mc_range(const double *__restrict__ samples, int64_t S, double *__restrict__ range)
+{
+    __shared__ double smin[kMcThreads], smax[kMcThreads];
+    const int d = blockIdx.x;
+    double a = INFINITY, b = -INFINITY;
+    for (int64_t s = threadIdx.x; s < S; s += blockDim.x) {
+        const double w = samples[(int64_t)d * S + s];
+        a = fmin(a, w);
+        b = fmax(b, w);
+    }
+    smin[threadIdx.x] = a;
+    smax[threadIdx.x] = b;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if ((int)threadIdx.x < k) {
+            smin[threadIdx.x] = fmin(smin[threadIdx.x], smin[threadIdx.x + k]);
+            smax[threadIdx.x] = fmax(smax[threadIdx.x], smax[threadIdx.x + k]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        range[2 * d] = smin[0];
+        range[2 * d + 1] = smax[0];
+    }
+}
+
+// Cell of a coordinate: -1 below the domain, N above it, else the i with
+// E_i <= y < E_{i+1} (the last cell also holds y == E_N). A first guess from
+// the nominal width, corrected against the edges themselves.
+__device__ __forceinline__ int cell_of(const double *__restrict__ E, int N, double inv_h, double y)
+{
+    if (y < E[0]) return -1;
+    if (y > E[N]) return N;
+    int i = (int)fmin(fmax(floor((y - E[0]) * inv_h), 0.0), (double)(N - 1));
+    while (i > 0 && y < E[i]) --i;
+    while (i < N - 1 && y >= E[i + 1]) ++i;
+    return i;
+}
+
+struct McRow {
+    double mlo[IMPACT_MAX_DIM], mhi[IMPACT_MAX_DIM];
+    int o[IMPACT_MAX_DIM], e[IMPACT_MAX_DIM];   // window: first cell and extent per dimension
+    int ws[IMPACT_MAX_DIM];                      // window strides (C order)
+    int H;                                       // window cells (0: the draws all leave)
+    unsigned sink_lo, sink_up;
+    int64_t kept, dropped, base;
+    int scan[kMcThreads / 32];
+};
+
+// One block per row (grid-stride over the rows). The draws move the row's
+// image box; a block-wide histogram in shared memory counts, for every cell
+// of the row's window, the draws whose moved box meets it (hu) and lies in it
+// (hl). The count pass writes the row's kept count, sink and dropped mass;
+// the emit pass repeats the histogram and writes the kept cells in ascending
+// order (cutoff 0 keeps every cell of the grid, as the dense definition does).
+template <bool EMIT>
+__global__ void __launch_bounds__(kMcThreads)
+mc_rows(const ImpactDesc *__restrict__ Dp, int64_t rows, const double *__restrict__ samples,
+        int64_t S, const double *__restrict__ range, int hist_cap, RowOutputs o)
+{
+    extern __shared__ __align__(16) unsigned char mc_smem[];
+    __shared__ McRow R;
+    unsigned *hu = reinterpret_cast<unsigned *>(mc_smem);
+    unsigned *hl = hu + hist_cap;
+    const ImpactDesc &D = *Dp;
+    const int n = D.n;
+    const double dS = (double)S;
+    const double cut = D.cutoff;
+    const int64_t T = D.cells;
+    if (EMIT && o.capacity >= 0 && o.row_ptr[o.total_at] > o.capacity) {
+        if (threadIdx.x == 0 && blockIdx.x == 0) atomicOr(o.status, IMPACT_STATUS_CAPACITY);
+        return;
+    }
+    for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
+        if (threadIdx.x == 0) {
+            int idx[IMPACT_MAX_DIM];
+            int j;
+            decode_row(D, row, idx, j);
+            int64_t Hw = 1;
+            for (int d = 0; d < n; ++d) {
+                double lo, hi;
+                image_dim<false>(D, row, idx, j, d, lo, hi);
+                R.mlo[d] = fmin(lo, hi);   // ordered ends (caller images included)
+                R.mhi[d] = fmax(lo, hi);
+                const ImpactDim &g = D.dim[d];
+                const double *E = D.edges + g.edge_off;
+                const int a = max(cell_of(E, g.N, g.inv_h, range[2 * d] + R.mlo[d]), 0);
+                const int b = min(cell_of(E, g.N, g.inv_h, range[2 * d + 1] + R.mhi[d]), g.N - 1);
+                R.o[d] = a;
+                R.e[d] = b >= a ? b - a + 1 : 0;
+                Hw *= R.e[d];   // at most the grid's cell count
+            }
+            int H = Hw < (int64_t)hist_cap ? (int)Hw : hist_cap;
+            if (Hw > hist_cap) {
+                atomicOr(o.status, IMPACT_STATUS_MC_WINDOW);
+                H = -1;
+            }
+            int st = 1;
+            for (int d = n - 1; d >= 0; --d) {
+                R.ws[d] = st;
+                st *= R.e[d] > 0 ? R.e[d] : 1;
+            }
+            R.H = H;
+            R.sink_lo = 0;
+            R.sink_up = 0;
+            R.kept = 0;
+            R.dropped = 0;
+        }
+        __syncthreads();
+        const int H = R.H;
+        if (H < 0) {   // window too large: counted as empty, the call fails
+            if (!EMIT && threadIdx.x == 0) o.row_ptr[row] = 0;
+            __syncthreads();
+            continue;
+        }
+        for (int h = threadIdx.x; h < H; h += blockDim.x) {
+            hu[h] = 0;
+            hl[h] = 0;
+        }
+        __syncthreads();
+        unsigned my_sl = 0, my_su = 0;
+        for (int64_t s = threadIdx.x; s < S; s += blockDim.x) {
+            int a[IMPACT_MAX_DIM], b[IMPACT_MAX_DIM];
+            bool inside = true, outside = false, single = true;
+            for (int d = 0; d < n; ++d) {
+                const ImpactDim &g = D.dim[d];
+                const double *E = D.edges + g.edge_off;
+                const double w = samples[(int64_t)d * S + s];
+                a[d] = cell_of(E, g.N, g.inv_h, w + R.mlo[d]);
+                b[d] = cell_of(E, g.N, g.inv_h, w + R.mhi[d]);
+                inside = inside && a[d] >= 0 && b[d] <= g.N - 1;
+                outside = outside || b[d] < 0 || a[d] > g.N - 1;
+                single = single && a[d] == b[d];
+            }
+            my_su += inside ? 0u : 1u;
+            if (outside) {
+                ++my_sl;
+                continue;
+            }
+            int c[IMPACT_MAX_DIM];
+            int h = 0;
+            for (int d = 0; d < n; ++d) {
+                // the met cells, relative to the window (inside it by
+                // construction; the clamps only bound malformed input)
+                const int top = R.e[d] - 1;
+                a[d] = min(max(max(a[d], 0) - R.o[d], 0), top);
+                b[d] = min(max(min(b[d], D.dim[d].N - 1) - R.o[d], a[d]), top);
+                c[d] = a[d];
+                h += c[d] * R.ws[d];
+            }
+            if (single) atomicAdd(&hl[h], 1u);
+            while (true) {   // every cell of the met box, in C order
+                atomicAdd(&hu[h], 1u);
+                int d = n - 1;
+                while (d >= 0 && c[d] == b[d]) {
+                    h -= (c[d] - a[d]) * R.ws[d];
+                    c[d] = a[d];
+                    --d;
+                }
+                if (d < 0) break;
+                ++c[d];
+                h += R.ws[d];
+            }
+        }
+        atomicAdd(&R.sink_lo, my_sl);
+        atomicAdd(&R.sink_up, my_su);
+        __syncthreads();
+
+        if (!EMIT) {
+            int64_t kept = 0, dropped = 0;
+            if (cut > 0.0) {
+                for (int h = threadIdx.x; h < H; h += blockDim.x) {
+                    const unsigned u = hu[h];
+                    if ((double)u / dS >= cut) ++kept; else dropped += u;
+                }
+                atomicAdd((unsigned long long *)&R.kept, (unsigned long long)kept);
+                atomicAdd((unsigned long long *)&R.dropped, (unsigned long long)dropped);
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                o.row_ptr[row] = cut > 0.0 ? R.kept : T;
+                o.sink_lo[row] = (double)R.sink_lo / dS;
+                o.sink_up[row] = (double)R.sink_up / dS;
+                o.trunc[row] = (double)R.dropped / dS;
+                if (o.flags) o.flags[row] = 0u;
+            }
+        } else {
+            const int64_t base = o.row_ptr[row];
+            const bool f64 = D.prec == PREC_FP64_PLAIN;
+            auto put = [&](int64_t pos, int64_t t, unsigned u, unsigned l) {
+                o.col[pos] = (int32_t)t;
+                const double vu = (double)u / dS, vl = (double)l / dS;
+                if (f64) {
+                    ((double *)o.up)[pos] = vu;
+                    ((double *)o.lo)[pos] = vl;
+                } else {
+                    ((float *)o.up)[pos] = __double2float_ru(vu);
+                    ((float *)o.lo)[pos] = __double2float_rd(vl);
+                }
+            };
+            if (cut <= 0.0) {
+                // every cell of the grid, in order; outside the window the counts are 0
+                for (int64_t t = threadIdx.x; t < T; t += blockDim.x) {
+                    int64_t rest = t;
+                    int h = 0;
+                    bool in = H > 0;
+                    for (int d = n - 1; d >= 0; --d) {
+                        const int N = D.dim[d].N;
+                        const int i = (int)(rest % N) - R.o[d];
+                        rest /= N;
+                        in = in && i >= 0 && i < R.e[d];
+                        h += i * R.ws[d];
+                    }
+                    if (base + t < o.row_ptr[row + 1])
+                        put(base + t, t, in ? hu[h] : 0u, in ? hl[h] : 0u);
+                }
+            } else {
+                // the kept cells of the window in C order (ascending cell ids)
+                const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+                int64_t at = 0;
+                for (int h0 = 0; h0 < H; h0 += blockDim.x) {
+                    const int h = h0 + threadIdx.x;
+                    const bool keep = h < H && (double)hu[h] / dS >= cut;
+                    const unsigned m = __ballot_sync(0xffffffffu, keep);
+                    if (lane == 0) R.scan[wid] = __popc(m);
+                    __syncthreads();
+                    int before = 0, total = 0;
+                    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+                        if (k < wid) before += R.scan[k];
+                        total += R.scan[k];
+                    }
+                    if (keep) {
+                        int64_t t = 0;
+                        int rest = h;
+                        for (int d = 0; d < n; ++d) {
+                            const int i = rest / R.ws[d];
+                            rest -= i * R.ws[d];
+                            t += (int64_t)(i + R.o[d]) * D.dim[d].stride;
+                        }
+                        const int64_t pos =
+                            base + at + before + __popc(m & ((1u << lane) - 1u));
+                        if (pos < o.row_ptr[row + 1]) put(pos, t, hu[h], hl[h]);
+                    }
+                    at += total;
+                    __syncthreads();
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
 int grid_for(const void *kernel, int64_t rows)
 {
     int dev = 0, sms = 0, occ = 0;
@@ -688,6 +949,38 @@ cudaError_t launch_regions(const ImpactDesc *d_desc, int64_t rows, const RegionB
     else
         region_rows<false><<<(unsigned)g, 128, 0, stream>>>(d_desc, rows, boxes, cell_sum, r_lo,
                                                             r_up, a_lo, a_up);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mc_range(const double *samples, int n, int64_t S, double *range,
+                            cudaStream_t stream)
+{
+    mc_range<<<n, kMcThreads, 0, stream>>>(samples, S, range);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mc_rows(const ImpactDesc *d_desc, bool emit, int64_t rows,
+                           const double *samples, int64_t S, const double *range,
+                           const RowOutputs &o, cudaStream_t stream)
+{
+    if (rows <= 0) return cudaSuccess;
+    const int cap = IMPACT_MC_HIST_MAX;
+    const size_t smem = (size_t)cap * 2 * sizeof(unsigned);
+    const void *k = emit ? (const void *)mc_rows<true> : (const void *)mc_rows<false>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kMcThreads, smem);
+    const int64_t g = std::min<int64_t>(rows, (int64_t)sms * std::max(occ, 1));
+    if (emit)
+        mc_rows<true><<<(unsigned)g, kMcThreads, smem, stream>>>(d_desc, rows, samples, S, range,
+                                                                 cap, o);
+    else
+        mc_rows<false><<<(unsigned)g, kMcThreads, smem, stream>>>(d_desc, rows, samples, S,
+                                                                  range, cap, o);
     return cudaGetLastError();
 }
 

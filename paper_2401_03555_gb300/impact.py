@@ -35,7 +35,7 @@ ENTRY_POINTS = ("impact_plan", "impact_workspace_bytes", "impact_build", "impact
                 "impact_batch_tune", "impact_server_create", "impact_server_submit",
                 "impact_server_poll", "impact_server_release", "impact_server_stats",
                 "impact_server_destroy", "impact_synthesize", "impact_label_cells",
-                "impact_region_vectors", "impact_synthesize_ex")
+                "impact_region_vectors", "impact_synthesize_ex", "impact_build_mc")
 
 
 class ImpactError(RuntimeError):
@@ -189,6 +189,11 @@ def load(build_if_missing: bool = True):
                                           ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
                                           ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]
+        lib.impact_build_mc.restype = ctypes.c_int
+        lib.impact_build_mc.argtypes = [ctypes.POINTER(_System), ctypes.POINTER(_Grid),
+                                        ctypes.POINTER(_Inputs), ctypes.c_void_p, ctypes.c_int64,
+                                        ctypes.c_double, ctypes.c_int, ctypes.POINTER(_CSR),
+                                        ctypes.c_void_p]
         lib.impact_label_cells.restype = ctypes.c_int
         lib.impact_label_cells.argtypes = [ctypes.POINTER(_Grid), ctypes.POINTER(_Regions),
                                            ctypes.c_void_p, ctypes.c_void_p]
@@ -368,6 +373,34 @@ def build(prob, precision="fp32", stream=None, check_unsound: bool = True) -> CS
     return CSR("fp32" if prec == FP32_SOUND else "fp64", rb["row_ptr"], pb["col"][:nnz],
                pb["lo"][:nnz], pb["up"][:nnz], rb["sink_lo"], rb["sink_up"], rb["trunc"],
                rb["row_flags"])
+
+
+def build_mc(prob, samples, precision="fp64", cutoff=None, stream=None) -> CSR:
+    """impact_build_mc: the IMDP for a noise given by draws (an (S, n) array
+    of samples, e.g. L z for a full covariance L L^T); library-owned result."""
+    a = _Args(prob)
+    W = torch.as_tensor(np.asarray(samples, np.float64).reshape(-1, a.lo.shape[0]).T.copy())
+    W = W.cuda().contiguous()
+    S = int(W.shape[1])
+    c = _CSR()
+    cut = float(prob.cutoff if cutoff is None else cutoff)
+    _check(load().impact_build_mc(ctypes.byref(a.sys), ctypes.byref(a.grid), ctypes.byref(a.inp),
+                                  W.data_ptr(), S, cut, _PREC[precision], ctypes.byref(c),
+                                  ctypes.c_void_p(_stream_handle(stream))))
+    torch.cuda.synchronize()
+    rows, nnz = int(c.rows), int(c.nnz)
+    vt = torch.float32 if _PREC[precision] == FP32_SOUND else torch.float64
+    try:   # copies into torch tensors, then the library's arrays are freed
+        out = CSR(precision, _view(c.row_ptr, rows + 1, torch.int64).clone(),
+                  _view(c.col, nnz, torch.int32).clone(), _view(c.lo, nnz, vt).clone(),
+                  _view(c.up, nnz, vt).clone(), _view(c.sink_lo, rows, torch.float64).clone(),
+                  _view(c.sink_up, rows, torch.float64).clone(),
+                  _view(c.trunc, rows, torch.float64).clone(),
+                  _view(c.row_flags, rows, torch.int32).clone())
+        torch.cuda.synchronize()
+    finally:
+        _check(load().impact_free(ctypes.byref(c)))
+    return out
 
 
 class Builder:
