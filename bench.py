@@ -385,6 +385,11 @@ def run_ours(args, rank, world, local_rank):
         except Exception as exc:
             out["regions"] = {"value": None, "error": str(exc)[:300]}
         torch.cuda.empty_cache()
+        try:
+            out["sampled_noise"] = run_mc()
+        except Exception as exc:
+            out["sampled_noise"] = {"value": None, "error": str(exc)[:300]}
+        torch.cuda.empty_cache()
 
     if not args.no_serve and rank == 0:
         try:
@@ -539,6 +544,45 @@ def run_synthesis(eps=1e-6, oracle_iters=2):
         out["cpu_baseline"] = {"value": 2 * prob.rows * 2 * oracle_iters / odt,
                                "unit": "row LPs/s", "cores": 1, "kind": "oracle",
                                "sample": f"{oracle_iters} iterations of each phase"}
+    except Exception as exc:
+        out["cpu_baseline"] = {"value": None, "error": str(exc)[:200]}
+    return out
+
+
+MC_WORKLOAD = ("5-D room (11^5 cells x 9 inputs = 1,449,459 rows) with correlated noise: "
+               "covariance 0.2^2 (0.7 I + 0.3 J), 1024 seeded draws passed in, cutoff 2e-3 "
+               "(>= 2 draws); sampled-noise bounds in FP32")
+
+
+def run_mc(draws=1024, oracle_rows=4):
+    """impact_build_mc on the 5-D room with correlated noise; the oracle's
+    sampled-noise rows on a few sampled rows."""
+    import torch
+    from paper_2401_03555_gb300 import impact, workloads as W
+    prob = W.room_5d(cutoff=2e-3)
+    rng = np.random.default_rng(12)
+    C = 0.2 ** 2 * (0.7 * np.eye(5) + 0.3 * np.ones((5, 5)))
+    w = rng.normal(size=(draws, 5)) @ np.linalg.cholesky(C).T
+    impact.build_mc(prob, w, "fp32")                       # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g = impact.build_mc(prob, w, "fp32")
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    out = {"workload": MC_WORKLOAD, "rows": int(prob.rows), "pairs": int(g.nnz), "ms": dt * 1e3,
+           "value": g.nnz / dt, "unit": "pairs/s", "row_draws_per_s": prob.rows * draws / dt,
+           "path": "impact_build_mc (one block per row: shared-memory histograms of the cells "
+                   "each moved image box meets / lies in; count, scan, emit)"}
+    del g
+    try:
+        import oracle
+        rows = W.sample_rows(prob, oracle_rows, seed=6, include_boundary=False)
+        t0 = time.perf_counter()
+        ref = oracle.build_rows_mc(prob, w, rows)
+        odt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": ref.nnz / odt, "unit": "pairs/s",
+                               "rows_per_s": len(rows) / odt, "cores": oracle.max_threads(),
+                               "kind": "oracle", "sample": f"{len(rows)} sampled rows"}
     except Exception as exc:
         out["cpu_baseline"] = {"value": None, "error": str(exc)[:200]}
     return out

@@ -429,10 +429,11 @@ impact_status impact_synthesize(const impact_csr *imdp, impact_precision precisi
  * A target is kept iff up >= cutoff (cutoff 0: every cell); trunc is the
  * dropped up mass. Values are count / n_samples (FP64 exactly as divided;
  * FP32: lo rounded down, up rounded up). sys, grid and inputs as for
- * impact_build (sigma is not used); n_samples in [1, 2^31 - 1]. The cells
- * within reach of a row's moved boxes must number at most 12288 (IMPACT_ERR_ARG
- * otherwise). Ownership, capacity and errors as impact_build; synchronizes
- * `stream` once between the passes.
+ * impact_build (sigma is not used); n_samples in [1, 2^24], every draw
+ * finite. The cells within reach of a row's moved boxes must number at most
+ * 12288, and at most 64 along one dimension (IMPACT_ERR_ARG otherwise).
+ * Ownership, capacity and errors as impact_build; synchronizes `stream`
+ * once between the passes.
  */
 impact_status impact_build_mc(const impact_system *sys, const impact_grid *grid,
                               const impact_inputs *inputs, const double *samples,

@@ -633,6 +633,41 @@ region_rows(const ImpactDesc *__restrict__ Dp, int64_t rows, RegionBoxes B, bool
 // ---------------------------------------------------------------------------
 
 constexpr int kMcThreads = 256;
+constexpr int kMcThr = IMPACT_MC_EDGES_MAX + 1;   // thresholds per (row, dimension, end)
+
+// Order-preserving integer key of a finite double (-0 and +0 share key 0):
+// x < y exactly when key(x) < key(y). Comparisons of keys are integer work,
+// which matters here: FP64 issue is scarce on this part.
+__device__ __forceinline__ long long dkey(double x)
+{
+    if (x == 0.0) return 0;
+    const long long b = __double_as_longlong(x);
+    return b >= 0 ? b : (b ^ 0x7fffffffffffffffll);
+}
+
+// Per-call tables: the draws' keys (dimension-major, like the draws), the
+// per-dimension least and largest draw, the values u / S for every count u
+// (FP64, and FP32 rounded down / up) and a flag for non-finite draws.
+__global__ void __launch_bounds__(kMcThreads)
+mc_prep(const double *__restrict__ samples, int n, int64_t S, long long *__restrict__ keys,
+        double *__restrict__ val, float *__restrict__ val_dn, float *__restrict__ val_up,
+        unsigned *__restrict__ bad)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)n * S;
+         i += stride) {
+        const double w = samples[i];
+        if (!isfinite(w)) atomicOr(bad, 1u);
+        keys[i] = dkey(w);
+    }
+    const double dS = (double)S;
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u <= S; u += stride) {
+        const double v = (double)u / dS;
+        val[u] = v;
+        val_dn[u] = __double2float_rd(v);
+        val_up[u] = __double2float_ru(v);
+    }
+}
 
 // Per-dimension least and largest draw: range[2d], range[2d + 1].
 __global__ void __launch_bounds__(kMcThreads)
@@ -675,26 +710,98 @@ __device__ __forceinline__ int cell_of(const double *__restrict__ E, int N, doub
     return i;
 }
 
+// Neighbouring doubles of a finite x (bit arithmetic; 0 steps to the least
+// subnormal of either sign).
+__device__ __forceinline__ double step_up(double x)
+{
+    if (x == 0.0) return __longlong_as_double(1ll);
+    const long long b = __double_as_longlong(x);
+    return __longlong_as_double(x > 0.0 ? b + 1 : b - 1);
+}
+__device__ __forceinline__ double step_down(double x)
+{
+    if (x == 0.0) return -__longlong_as_double(1ll);
+    const long long b = __double_as_longlong(x);
+    return __longlong_as_double(x > 0.0 ? b - 1 : b + 1);
+}
+
+// The least double w whose rounded sum w + m reaches the edge E (gt: passes
+// it). RN addition is monotone in w, so these w form an up-set; the guess
+// E - m is moved a few ulps, and bisection over the keys' order finishes the
+// rare case where the guess is far off (|m| much larger than |E - m|).
+__device__ double threshold_of(double m, double E, bool gt)
+{
+    auto ok = [&](double w) {
+        const double y = w + m;
+        return gt ? y > E : y >= E;
+    };
+    double w = E - m;
+    for (int k = 0; k < 2; ++k) {
+        if (ok(w)) {
+            const double p = step_down(w);
+            if (!ok(p)) return w;
+            w = p;
+        } else {
+            w = step_up(w);
+        }
+    }
+    // bracket [lo, hi] with ok(hi) and not ok(lo), then bisection on the
+    // order of doubles (the sign is handled by the keys' order)
+    double span = fmax(fabs(m), fabs(E)) * 0x1p-50 + 0x1p-1000;
+    double lo = w - span, hi = w + span;
+    for (int k = 0; k < 64 && ok(lo); ++k) lo -= (span *= 2.0);
+    for (int k = 0; k < 64 && !ok(hi); ++k) hi += (span *= 2.0);
+    for (int k = 0; k < 128; ++k) {
+        const long long kl = dkey(lo), kh = dkey(hi);
+        if (kh - kl <= 1) break;
+        // midpoint in key order, back to a double
+        const long long km = kl + (kh - kl) / 2;
+        const double mid = km >= 0 ? __longlong_as_double(km)
+                                   : __longlong_as_double(km ^ 0x7fffffffffffffffll);
+        if (ok(mid)) hi = mid; else lo = mid;
+    }
+    return hi;
+}
+
 struct McRow {
     double mlo[IMPACT_MAX_DIM], mhi[IMPACT_MAX_DIM];
     int o[IMPACT_MAX_DIM], e[IMPACT_MAX_DIM];   // window: first cell and extent per dimension
     int ws[IMPACT_MAX_DIM];                      // window strides (C order)
     int H;                                       // window cells (0: the draws all leave)
     unsigned sink_lo, sink_up;
-    int64_t kept, dropped, base;
+    unsigned long long kept, dropped;
     int scan[kMcThreads / 32];
+    // keys of the thresholds of edges o .. o + e, for the low and the high
+    // end of the image: the draw's cell is o - 1 + #{k: key(w) >= thr[k]}
+    long long thr_lo[IMPACT_MAX_DIM][kMcThr], thr_hi[IMPACT_MAX_DIM][kMcThr];
 };
+
+// #{k < cnt: t[k] <= key}, t ascending (binary search).
+__device__ __forceinline__ int count_le(const long long *t, int cnt, long long key)
+{
+    int lo = 0, hi = cnt;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (t[mid] <= key) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
 
 // One block per row (grid-stride over the rows). The draws move the row's
 // image box; a block-wide histogram in shared memory counts, for every cell
 // of the row's window, the draws whose moved box meets it (hu) and lies in it
-// (hl). The count pass writes the row's kept count, sink and dropped mass;
-// the emit pass repeats the histogram and writes the kept cells in ascending
-// order (cutoff 0 keeps every cell of the grid, as the dense definition does).
+// (hl). The cell of a moved end is found by integer comparisons of the draw's
+// key with per-row thresholds (the FP64 decision of the definition, made
+// exactly once per row and edge). The count pass writes the row's kept count,
+// sink and dropped mass; the emit pass repeats the histogram and writes the
+// kept cells in ascending order (cutoff 0 keeps every cell of the grid, as the
+// dense definition does).
 template <bool EMIT>
 __global__ void __launch_bounds__(kMcThreads)
-mc_rows(const ImpactDesc *__restrict__ Dp, int64_t rows, const double *__restrict__ samples,
-        int64_t S, const double *__restrict__ range, int hist_cap, RowOutputs o)
+mc_rows(const ImpactDesc *__restrict__ Dp, int64_t rows, const long long *__restrict__ keys,
+        int64_t S, const double *__restrict__ range, const double *__restrict__ val,
+        const float *__restrict__ val_dn, const float *__restrict__ val_up, unsigned kmin,
+        int hist_cap, RowOutputs o)
 {
     extern __shared__ __align__(16) unsigned char mc_smem[];
     __shared__ McRow R;
@@ -703,33 +810,54 @@ mc_rows(const ImpactDesc *__restrict__ Dp, int64_t rows, const double *__restric
     const ImpactDesc &D = *Dp;
     const int n = D.n;
     const double dS = (double)S;
-    const double cut = D.cutoff;
+    const bool dense = D.cutoff <= 0.0;   // cutoff 0: every cell is kept
     const int64_t T = D.cells;
     if (EMIT && o.capacity >= 0 && o.row_ptr[o.total_at] > o.capacity) {
         if (threadIdx.x == 0 && blockIdx.x == 0) atomicOr(o.status, IMPACT_STATUS_CAPACITY);
         return;
     }
     for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
-        if (threadIdx.x == 0) {
+        // the row's image and window: one thread per dimension
+        if (threadIdx.x < (unsigned)n) {
+            const int d = threadIdx.x;
             int idx[IMPACT_MAX_DIM];
             int j;
             decode_row(D, row, idx, j);
+            double lo, hi;
+            image_dim<false>(D, row, idx, j, d, lo, hi);
+            const double mlo = fmin(lo, hi), mhi = fmax(lo, hi);   // ordered ends
+            R.mlo[d] = mlo;
+            R.mhi[d] = mhi;
+            const ImpactDim &g = D.dim[d];
+            const double *E = D.edges + g.edge_off;
+            const int a = max(cell_of(E, g.N, g.inv_h, range[2 * d] + mlo), 0);
+            const int b = min(cell_of(E, g.N, g.inv_h, range[2 * d + 1] + mhi), g.N - 1);
+            R.o[d] = a;
+            R.e[d] = b >= a ? b - a + 1 : 0;
+        }
+        __syncthreads();
+        // the thresholds of every (dimension, edge, end), one per thread
+        for (int q = threadIdx.x; q < n * 2 * kMcThr; q += blockDim.x) {
+            const int d = q / (2 * kMcThr), r = q - d * (2 * kMcThr);
+            const int end = r / kMcThr, k = r - end * kMcThr;
+            const int ext = R.e[d];
+            if (ext == 0 || ext > IMPACT_MC_EDGES_MAX || k > ext) continue;
+            const ImpactDim &g = D.dim[d];
+            const int edge = R.o[d] + k;
+            const bool gt = edge == g.N;   // beyond the last edge: leaves the domain
+            const long long t = dkey(threshold_of(end ? R.mhi[d] : R.mlo[d],
+                                                  D.edges[g.edge_off + edge], gt));
+            if (end) R.thr_hi[d][k] = t; else R.thr_lo[d][k] = t;
+        }
+        if (threadIdx.x == 0) {
             int64_t Hw = 1;
+            bool wide = false;
             for (int d = 0; d < n; ++d) {
-                double lo, hi;
-                image_dim<false>(D, row, idx, j, d, lo, hi);
-                R.mlo[d] = fmin(lo, hi);   // ordered ends (caller images included)
-                R.mhi[d] = fmax(lo, hi);
-                const ImpactDim &g = D.dim[d];
-                const double *E = D.edges + g.edge_off;
-                const int a = max(cell_of(E, g.N, g.inv_h, range[2 * d] + R.mlo[d]), 0);
-                const int b = min(cell_of(E, g.N, g.inv_h, range[2 * d + 1] + R.mhi[d]), g.N - 1);
-                R.o[d] = a;
-                R.e[d] = b >= a ? b - a + 1 : 0;
                 Hw *= R.e[d];   // at most the grid's cell count
+                wide = wide || R.e[d] > IMPACT_MC_EDGES_MAX;
             }
             int H = Hw < (int64_t)hist_cap ? (int)Hw : hist_cap;
-            if (Hw > hist_cap) {
+            if (Hw > hist_cap || wide) {
                 atomicOr(o.status, IMPACT_STATUS_MC_WINDOW);
                 H = -1;
             }
@@ -757,86 +885,134 @@ mc_rows(const ImpactDesc *__restrict__ Dp, int64_t rows, const double *__restric
         }
         __syncthreads();
         unsigned my_sl = 0, my_su = 0;
-        for (int64_t s = threadIdx.x; s < S; s += blockDim.x) {
-            int a[IMPACT_MAX_DIM], b[IMPACT_MAX_DIM];
-            bool inside = true, outside = false, single = true;
-            for (int d = 0; d < n; ++d) {
-                const ImpactDim &g = D.dim[d];
-                const double *E = D.edges + g.edge_off;
-                const double w = samples[(int64_t)d * S + s];
-                a[d] = cell_of(E, g.N, g.inv_h, w + R.mlo[d]);
-                b[d] = cell_of(E, g.N, g.inv_h, w + R.mhi[d]);
-                inside = inside && a[d] >= 0 && b[d] <= g.N - 1;
-                outside = outside || b[d] < 0 || a[d] > g.N - 1;
-                single = single && a[d] == b[d];
-            }
-            my_su += inside ? 0u : 1u;
-            if (outside) {
-                ++my_sl;
-                continue;
-            }
-            int c[IMPACT_MAX_DIM];
-            int h = 0;
-            for (int d = 0; d < n; ++d) {
-                // the met cells, relative to the window (inside it by
-                // construction; the clamps only bound malformed input)
-                const int top = R.e[d] - 1;
-                a[d] = min(max(max(a[d], 0) - R.o[d], 0), top);
-                b[d] = min(max(min(b[d], D.dim[d].N - 1) - R.o[d], a[d]), top);
-                c[d] = a[d];
-                h += c[d] * R.ws[d];
-            }
-            if (single) atomicAdd(&hl[h], 1u);
-            while (true) {   // every cell of the met box, in C order
-                atomicAdd(&hu[h], 1u);
-                int d = n - 1;
-                while (d >= 0 && c[d] == b[d]) {
-                    h -= (c[d] - a[d]) * R.ws[d];
-                    c[d] = a[d];
-                    --d;
+        if (H > 0)
+            for (int64_t s = threadIdx.x; s < S; s += blockDim.x) {
+                // per dimension: the cells of the moved ends (integer
+                // comparisons with the row's thresholds), the met range
+                // relative to the window, and whether it spans two cells
+                bool inside = true, outside = false, single = true, wide = false;
+                int hb = 0, m2 = 0;
+                unsigned pk = 0;   // dims whose met range spans two cells, 3 bits each
+                int A[IMPACT_MAX_DIM], Bd[IMPACT_MAX_DIM];
+#pragma unroll
+                for (int d = 0; d < IMPACT_MAX_DIM; ++d) {
+                    if (d < n) {
+                        const long long kw = keys[(int64_t)d * S + s];
+                        const int ext = R.e[d], N = D.dim[d].N;
+                        const int a = R.o[d] - 1 + count_le(R.thr_lo[d], ext + 1, kw);
+                        const int b = R.o[d] - 1 + count_le(R.thr_hi[d], ext + 1, kw);
+                        inside = inside && a >= 0 && b <= N - 1;
+                        outside = outside || b < 0 || a > N - 1;
+                        single = single && a == b;
+                        // relative to the window (inside it by construction;
+                        // the clamps only bound malformed input)
+                        const int top = ext - 1;
+                        const int ad = min(max(max(a, 0) - R.o[d], 0), top);
+                        const int bd = min(max(min(b, N - 1) - R.o[d], ad), top);
+                        A[d] = ad;
+                        Bd[d] = bd;
+                        hb += ad * R.ws[d];
+                        if (bd - ad == 1) {
+                            pk |= (unsigned)d << (3 * m2);
+                            ++m2;
+                        } else if (bd - ad > 1) {
+                            wide = true;
+                        }
+                    }
                 }
-                if (d < 0) break;
-                ++c[d];
-                h += R.ws[d];
+                my_su += inside ? 0u : 1u;
+                if (outside) {
+                    ++my_sl;
+                    continue;
+                }
+                if (single) atomicAdd(&hl[hb], 1u);
+                atomicAdd(&hu[hb], 1u);
+                if (!wide) {
+                    // the other cells of a box of 2^m2 cells, in Gray-code
+                    // order: one stride added or taken away per cell
+                    int h = hb;
+                    unsigned gray = 0;
+                    for (unsigned k = 1; k < (1u << m2); ++k) {
+                        const int j = __ffs(k) - 1;
+                        const int dim = (pk >> (3 * j)) & 7;
+                        const unsigned bit = 1u << j;
+                        h += (gray & bit) ? -R.ws[dim] : R.ws[dim];
+                        gray ^= bit;
+                        atomicAdd(&hu[h], 1u);
+                    }
+                } else {
+                    // a range of three or more cells somewhere: odometer walk
+                    int c[IMPACT_MAX_DIM];
+                    for (int d = 0; d < n; ++d) c[d] = A[d];
+                    int h = hb;
+                    while (true) {
+                        int d = n - 1;
+                        while (d >= 0 && c[d] == Bd[d]) {
+                            h -= (c[d] - A[d]) * R.ws[d];
+                            c[d] = A[d];
+                            --d;
+                        }
+                        if (d < 0) break;
+                        ++c[d];
+                        h += R.ws[d];
+                        atomicAdd(&hu[h], 1u);
+                    }
+                }
             }
+        else   // every draw leaves the domain whole
+            for (int64_t s = threadIdx.x; s < S; s += blockDim.x) {
+                ++my_sl;
+                ++my_su;
+            }
+        // block totals: a warp reduction, then one shared atomic per warp
+        // (all threads on one shared word would serialise)
+        my_sl = __reduce_add_sync(0xffffffffu, my_sl);
+        my_su = __reduce_add_sync(0xffffffffu, my_su);
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(&R.sink_lo, my_sl);
+            atomicAdd(&R.sink_up, my_su);
         }
-        atomicAdd(&R.sink_lo, my_sl);
-        atomicAdd(&R.sink_up, my_su);
         __syncthreads();
 
         if (!EMIT) {
-            int64_t kept = 0, dropped = 0;
-            if (cut > 0.0) {
+            unsigned kept = 0;
+            unsigned long long dropped = 0;
+            if (!dense) {
                 for (int h = threadIdx.x; h < H; h += blockDim.x) {
                     const unsigned u = hu[h];
-                    if ((double)u / dS >= cut) ++kept; else dropped += u;
+                    if (u >= kmin) ++kept; else dropped += u;
                 }
-                atomicAdd((unsigned long long *)&R.kept, (unsigned long long)kept);
-                atomicAdd((unsigned long long *)&R.dropped, (unsigned long long)dropped);
+                kept = __reduce_add_sync(0xffffffffu, kept);
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1)
+                    dropped += __shfl_xor_sync(0xffffffffu, dropped, off);
+                if ((threadIdx.x & 31) == 0) {
+                    atomicAdd(&R.kept, (unsigned long long)kept);
+                    atomicAdd(&R.dropped, dropped);
+                }
             }
             __syncthreads();
             if (threadIdx.x == 0) {
-                o.row_ptr[row] = cut > 0.0 ? R.kept : T;
+                o.row_ptr[row] = dense ? T : (int64_t)R.kept;
                 o.sink_lo[row] = (double)R.sink_lo / dS;
                 o.sink_up[row] = (double)R.sink_up / dS;
                 o.trunc[row] = (double)R.dropped / dS;
                 if (o.flags) o.flags[row] = 0u;
             }
         } else {
-            const int64_t base = o.row_ptr[row];
+            const int64_t base = o.row_ptr[row], end = o.row_ptr[row + 1];
             const bool f64 = D.prec == PREC_FP64_PLAIN;
             auto put = [&](int64_t pos, int64_t t, unsigned u, unsigned l) {
                 o.col[pos] = (int32_t)t;
-                const double vu = (double)u / dS, vl = (double)l / dS;
                 if (f64) {
-                    ((double *)o.up)[pos] = vu;
-                    ((double *)o.lo)[pos] = vl;
+                    ((double *)o.up)[pos] = val[u];
+                    ((double *)o.lo)[pos] = val[l];
                 } else {
-                    ((float *)o.up)[pos] = __double2float_ru(vu);
-                    ((float *)o.lo)[pos] = __double2float_rd(vl);
+                    ((float *)o.up)[pos] = val_up[u];
+                    ((float *)o.lo)[pos] = val_dn[l];
                 }
             };
-            if (cut <= 0.0) {
+            if (dense) {
                 // every cell of the grid, in order; outside the window the counts are 0
                 for (int64_t t = threadIdx.x; t < T; t += blockDim.x) {
                     int64_t rest = t;
@@ -849,8 +1025,7 @@ mc_rows(const ImpactDesc *__restrict__ Dp, int64_t rows, const double *__restric
                         in = in && i >= 0 && i < R.e[d];
                         h += i * R.ws[d];
                     }
-                    if (base + t < o.row_ptr[row + 1])
-                        put(base + t, t, in ? hu[h] : 0u, in ? hl[h] : 0u);
+                    if (base + t < end) put(base + t, t, in ? hu[h] : 0u, in ? hl[h] : 0u);
                 }
             } else {
                 // the kept cells of the window in C order (ascending cell ids)
@@ -858,7 +1033,7 @@ mc_rows(const ImpactDesc *__restrict__ Dp, int64_t rows, const double *__restric
                 int64_t at = 0;
                 for (int h0 = 0; h0 < H; h0 += blockDim.x) {
                     const int h = h0 + threadIdx.x;
-                    const bool keep = h < H && (double)hu[h] / dS >= cut;
+                    const bool keep = h < H && hu[h] >= kmin;
                     const unsigned m = __ballot_sync(0xffffffffu, keep);
                     if (lane == 0) R.scan[wid] = __popc(m);
                     __syncthreads();
@@ -877,7 +1052,7 @@ mc_rows(const ImpactDesc *__restrict__ Dp, int64_t rows, const double *__restric
                         }
                         const int64_t pos =
                             base + at + before + __popc(m & ((1u << lane) - 1u));
-                        if (pos < o.row_ptr[row + 1]) put(pos, t, hu[h], hl[h]);
+                        if (pos < end) put(pos, t, hu[h], hl[h]);
                     }
                     at += total;
                     __syncthreads();
@@ -952,16 +1127,22 @@ cudaError_t launch_regions(const ImpactDesc *d_desc, int64_t rows, const RegionB
     return cudaGetLastError();
 }
 
-cudaError_t launch_mc_range(const double *samples, int n, int64_t S, double *range,
-                            cudaStream_t stream)
+cudaError_t launch_mc_prep(const double *samples, int n, int64_t S, long long *keys,
+                           double *val, float *val_dn, float *val_up, unsigned *bad,
+                           double *range, cudaStream_t stream)
 {
+    const int64_t items = std::max<int64_t>((int64_t)n * S, S + 1);
+    const int64_t g = std::min<int64_t>((items + kMcThreads - 1) / kMcThreads, 152 * 16);
+    mc_prep<<<(unsigned)g, kMcThreads, 0, stream>>>(samples, n, S, keys, val, val_dn, val_up,
+                                                     bad);
     mc_range<<<n, kMcThreads, 0, stream>>>(samples, S, range);
     return cudaGetLastError();
 }
 
 cudaError_t launch_mc_rows(const ImpactDesc *d_desc, bool emit, int64_t rows,
-                           const double *samples, int64_t S, const double *range,
-                           const RowOutputs &o, cudaStream_t stream)
+                           const long long *keys, int64_t S, const double *range,
+                           const double *val, const float *val_dn, const float *val_up,
+                           unsigned kmin, const RowOutputs &o, cudaStream_t stream)
 {
     if (rows <= 0) return cudaSuccess;
     const int cap = IMPACT_MC_HIST_MAX;
@@ -976,11 +1157,11 @@ cudaError_t launch_mc_rows(const ImpactDesc *d_desc, bool emit, int64_t rows,
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kMcThreads, smem);
     const int64_t g = std::min<int64_t>(rows, (int64_t)sms * std::max(occ, 1));
     if (emit)
-        mc_rows<true><<<(unsigned)g, kMcThreads, smem, stream>>>(d_desc, rows, samples, S, range,
-                                                                 cap, o);
+        mc_rows<true><<<(unsigned)g, kMcThreads, smem, stream>>>(
+            d_desc, rows, keys, S, range, val, val_dn, val_up, kmin, cap, o);
     else
-        mc_rows<false><<<(unsigned)g, kMcThreads, smem, stream>>>(d_desc, rows, samples, S,
-                                                                  range, cap, o);
+        mc_rows<false><<<(unsigned)g, kMcThreads, smem, stream>>>(
+            d_desc, rows, keys, S, range, val, val_dn, val_up, kmin, cap, o);
     return cudaGetLastError();
 }
 

@@ -57,16 +57,21 @@ struct RegionBoxes {
     int last[IMPACT_REGION_BOXES][IMPACT_MAX_DIM];    // last cell index per dimension
 };
 
-// Sampled noise (Monte-Carlo integration): per-dimension range of the draws,
-// then the count and emit passes over a per-row histogram of the cells the
-// moved image box meets / lies in. Draws: dimension-major [n][S].
+// Sampled noise (Monte-Carlo integration): per-call tables (the draws'
+// order-preserving integer keys, their per-dimension range, the values u / S,
+// a flag for non-finite draws), then the count and emit passes over a
+// per-row histogram of the cells the moved image box meets / lies in.
+// Draws: dimension-major [n][S].
 #define IMPACT_MC_HIST_MAX 12288          // window cells one block's histogram holds
-#define IMPACT_STATUS_MC_WINDOW 0x10u     // some row's window exceeded IMPACT_MC_HIST_MAX
-cudaError_t launch_mc_range(const double *samples, int n, int64_t S, double *range,
-                            cudaStream_t stream);
+#define IMPACT_MC_EDGES_MAX 64            // window cells per dimension
+#define IMPACT_STATUS_MC_WINDOW 0x10u     // some row's window exceeded the limits above
+cudaError_t launch_mc_prep(const double *samples, int n, int64_t S, long long *keys,
+                           double *val, float *val_dn, float *val_up, unsigned *bad,
+                           double *range, cudaStream_t stream);
 cudaError_t launch_mc_rows(const ImpactDesc *d_desc, bool emit, int64_t rows,
-                           const double *samples, int64_t S, const double *range,
-                           const RowOutputs &o, cudaStream_t stream);
+                           const long long *keys, int64_t S, const double *range,
+                           const double *val, const float *val_dn, const float *val_up,
+                           unsigned kmin, const RowOutputs &o, cudaStream_t stream);
 
 // Labels of every cell (0 free, 1 target, 2 avoid; avoid wins).
 cudaError_t launch_labels(const RegionBoxes &boxes, int64_t total_cells, uint8_t *labels,

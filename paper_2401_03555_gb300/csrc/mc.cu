@@ -47,8 +47,8 @@ extern "C" impact_status impact_build_mc(const impact_system *sys, const impact_
     if (!sys || !grid || !inputs || !out) return fail(IMPACT_ERR_ARG, "null argument");
     if (precision != IMPACT_FP32_SOUND && precision != IMPACT_FP64_PLAIN)
         return fail(IMPACT_ERR_ARG, "unknown precision");
-    if (n_samples < 1 || n_samples > (int64_t)INT32_MAX)
-        return fail(IMPACT_ERR_ARG, "n_samples must be in [1, 2^31 - 1]");
+    if (n_samples < 1 || n_samples > ((int64_t)1 << 24))
+        return fail(IMPACT_ERR_ARG, "n_samples must be in [1, 2^24]");
     if (!(cutoff >= 0.0 && cutoff < 1.0)) return fail(IMPACT_ERR_ARG, "cutoff must be in [0, 1)");
     if (!is_device_ptr(samples)) return fail(IMPACT_ERR_ARG, "samples must be a device array");
     const int n = grid->n;
@@ -87,16 +87,33 @@ extern "C" impact_status impact_build_mc(const impact_system *sys, const impact_
     impact_csr no_ws = *out;
     no_ws.workspace = nullptr;
     if ((s = get_work(B, &no_ws, st, W)) != IMPACT_OK) return s;
-    double *range = nullptr;
+    // per-call tables: draw keys [n][S], range [n][2], values u / S for
+    // u = 0..S (FP64, FP32 down, FP32 up), the non-finite flag
+    const int64_t S = n_samples;
+    const size_t t_keys = (size_t)n * S * 8, t_range = (size_t)n * 16, t_val = (size_t)(S + 1) * 8;
+    const size_t t_f = (size_t)(S + 1) * 4;
+    const size_t total = t_keys + t_range + t_val + 2 * t_f + 16;
+    unsigned char *tab = nullptr;
     s = upload(B, W, st);
-    if (s == IMPACT_OK && cudaMallocAsync((void **)&range, (size_t)n * 2 * 8, st) != cudaSuccess)
-        s = fail(IMPACT_ERR_OOM, "sample range");
+    if (s == IMPACT_OK && cudaMallocAsync((void **)&tab, total, st) != cudaSuccess)
+        s = fail(IMPACT_ERR_OOM, "sampled-noise tables");
     auto done = [&](impact_status r) {
-        if (range) cudaFreeAsync(range, st);
+        if (tab) cudaFreeAsync(tab, st);
         impact_status q = release(W, st);
         return r != IMPACT_OK ? r : q;
     };
     if (s != IMPACT_OK) return done(s);
+    long long *keys = (long long *)tab;
+    double *range = (double *)(tab + t_keys);
+    double *val = (double *)(tab + t_keys + t_range);
+    float *val_dn = (float *)(tab + t_keys + t_range + t_val);
+    float *val_up = (float *)(tab + t_keys + t_range + t_val + t_f);
+    unsigned *bad = (unsigned *)(tab + t_keys + t_range + t_val + 2 * t_f);
+    // the least count u with u / S >= cutoff (the definition's FP64 test)
+    const double dS = (double)S;
+    int64_t kmin = cutoff > 0.0 ? (int64_t)ceil(cutoff * dS) : 0;
+    while (kmin > 0 && (double)(kmin - 1) / dS >= cutoff) --kmin;
+    while (cutoff > 0.0 && (double)kmin / dS < cutoff) ++kmin;
     RowOutputs o;
     memset(&o, 0, sizeof(o));
     o.row_ptr = out->row_ptr;
@@ -108,21 +125,27 @@ extern "C" impact_status impact_build_mc(const impact_system *sys, const impact_
     o.capacity = -1;
     o.total_at = B.rows;
     const ImpactDesc *desc = W.desc(0);
-    cudaError_t e = launch_mc_range(samples, n, n_samples, range, st);
-    if (e == cudaSuccess) e = launch_mc_rows(desc, false, B.rows, samples, n_samples, range, o, st);
+    cudaError_t e = cudaMemsetAsync(bad, 0, 4, st);
+    if (e == cudaSuccess)
+        e = launch_mc_prep(samples, n, S, keys, val, val_dn, val_up, bad, range, st);
+    if (e == cudaSuccess)
+        e = launch_mc_rows(desc, false, B.rows, keys, S, range, val, val_dn, val_up,
+                           (unsigned)kmin, o, st);
     if (e == cudaSuccess) e = launch_scan(out->row_ptr, B.rows, W.scan(), st);
     if (e != cudaSuccess) return done(fail(IMPACT_ERR_CUDA, cudaGetErrorString(e)));
     int64_t nnz = 0;
-    uint32_t status = 0;
+    uint32_t status = 0, nonfinite = 0;
     if (cudaMemcpyAsync(&nnz, out->row_ptr + B.rows, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaMemcpyAsync(&status, W.status(), 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(&nonfinite, bad, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
         return done(fail(IMPACT_ERR_CUDA, "count pass failed"));
+    if (nonfinite) return done(fail(IMPACT_ERR_ARG, "the draws must be finite"));
     if (status & IMPACT_STATUS_MC_WINDOW)
         return done(fail(IMPACT_ERR_ARG, "a row's cells within reach of the draws exceed " +
-                                             std::to_string(IMPACT_MC_HIST_MAX) +
-                                             " (raise the cutoff's share of the window or "
-                                             "use a coarser grid)"));
+                                             std::to_string(IMPACT_MC_HIST_MAX) + " (or " +
+                                             std::to_string(IMPACT_MC_EDGES_MAX) +
+                                             " in one dimension): use a coarser grid"));
     int64_t capacity = out->nnz;
     if (lib_owned) {
         const size_t k = (size_t)std::max<int64_t>(nnz, 1);
@@ -143,7 +166,8 @@ extern "C" impact_status impact_build_mc(const impact_system *sys, const impact_
     o.lo = view.lo;
     o.up = view.up;
     o.capacity = capacity;
-    e = launch_mc_rows(desc, true, B.rows, samples, n_samples, range, o, st);
+    e = launch_mc_rows(desc, true, B.rows, keys, S, range, val, val_dn, val_up, (unsigned)kmin,
+                       o, st);
     if (e != cudaSuccess) return done(fail(IMPACT_ERR_CUDA, cudaGetErrorString(e)));
     if (cudaMemcpyAsync(&status, W.status(), 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
