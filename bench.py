@@ -74,6 +74,9 @@ def parse_args(argv=None):
     p.add_argument("--no-batched", action="store_true",
                    help="skip the batched workload (256 seeded systems, graphs, autotuner)")
     p.add_argument("--cpu-rows", type=int, default=0, help="oracle sample size (0: auto)")
+    p.add_argument("--case", choices=["synth", "regions", "mc"], default=None,
+                   help="run one small invocation of that leg and exit (a target for "
+                        "profilers; prints no JSON line)")
     p.add_argument("--cells", type=int, default=11,
                    help="cells per dimension (11 = the benchmark workload; smaller values "
                         "give the reduced case used for detailed kernel profiles)")
@@ -786,8 +789,36 @@ def run_reference(args, rank, world):
                                         "d2h_bytes_per_step": 0}}
 
 
+def run_case(which):
+    """One small invocation of a leg, for a profiler to capture: synthesis on
+    the 21^2 robot (3 iterations per phase), region vectors and sampled noise
+    (1024 draws) on the 7^5-cell room."""
+    import torch
+    from paper_2401_03555_gb300 import impact, workloads as W
+    if which == "synth":
+        prob = W.robot_2d()
+        lab = impact.label_cells(prob, [([3, 3], [7, 7])], [([-7, -7], [-3, -3])])
+        g = impact.synthesize(impact.build(prob, "fp64"), prob, lab, eps=1e-6, max_iters=3)
+        print("synthesis iterations", g.iterations)
+    elif which == "regions":
+        prob = W.room_5d(cells_per_dim=7)
+        v = impact.region_vectors(prob, [([19.0] * 5, [21.0] * 5)],
+                                  [([17.0] * 5, [17.6, 23, 23, 23, 23])], "box", "fp32")
+        torch.cuda.synchronize()
+        print("region vectors, max R_max", float(v.r_up.max()))
+    else:
+        rng = np.random.default_rng(12)
+        C = 0.2 ** 2 * (0.7 * np.eye(5) + 0.3 * np.ones((5, 5)))
+        prob = W.room_5d(cells_per_dim=7, cutoff=2e-3)
+        w = rng.normal(size=(1024, 5)) @ np.linalg.cholesky(C).T
+        print("sampled-noise pairs", impact.build_mc(prob, w, "fp32").nnz)
+
+
 def main(argv=None):
     args = parse_args(argv)
+    if args.case:
+        run_case(args.case)
+        return
     rank, world, local_rank = dist_env()
     if args.impl == "reference":
         out = run_reference(args, rank, world)
