@@ -25,6 +25,7 @@
 // and V1; the largest |V1 - V0| is gathered with an atomic max on the bits of
 // a non-negative double.
 #include <cuda_runtime.h>
+#include <limits.h>
 #include <math.h>
 #include <stdint.h>
 #include <string.h>
@@ -56,6 +57,15 @@ __device__ __forceinline__ double warp_sum(double v)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
+}
+
+// Order-preserving integer key of a finite double (-0 and +0 share key 0):
+// x <= y exactly when okey(x) <= okey(y).
+__device__ __forceinline__ long long okey(double x)
+{
+    if (x == 0.0) return 0;
+    const long long b = __double_as_longlong(x);
+    return b >= 0 ? b : (b ^ 0x7fffffffffffffffll);
 }
 
 struct RowRef {
@@ -130,38 +140,45 @@ __device__ double row_lp(const RowRef &R, const int32_t *__restrict__ col,
     if (rest <= 0.0) {
         res = slov;
     } else if (R.b - R.a <= 32 * kCache) {
-        // short rows: each lane keeps its successors' values and widths in
-        // registers for the whole bisection
-        double cv[kCache], cw[kCache];
+        // short rows: each lane keeps its successors' values, as integer
+        // order keys, and widths, in fixed point (2^-52 units), in registers
+        // for the whole bisection. The passes then compare and sum integers
+        // only (FP64 issue is scarce on this part); the final value is taken
+        // in FP64 at the bracket found.
+        long long ck[kCache], cwf[kCache];
 #pragma unroll
         for (int k = 0; k < kCache; ++k) {
             const int64_t i = R.a + lane + 32 * k;
             const bool in = i < R.b && !out(col[i]);
-            cv[k] = in ? val(V[col[i]]) : 2.0;   // 2: never <= x
-            cw[k] = in ? (double)up[i] - (double)lo[i] : 0.0;
+            ck[k] = in ? okey(val(V[col[i]])) : LLONG_MAX;
+            cwf[k] = in ? __double2ll_rn(((double)up[i] - (double)lo[i]) * 0x1p52) : 0ll;
         }
-        auto Gc = [&](double x, double &gv) {
-            double g = 0.0, v2 = 0.0;
+        long long xk[3], xwf[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            xk[k] = okey(val(R.xv[k]));
+            xwf[k] = __double2ll_rn(R.xw[k] * 0x1p52);
+        }
+        const long long rest_f = __double2ll_rn(rest * 0x1p52);
+        auto Gf = [&](long long kx) {
+            long long g = 0;
 #pragma unroll
             for (int k = 0; k < kCache; ++k)
-                if (cv[k] <= x) {
-                    g += cw[k];
-                    v2 += cw[k] * cv[k];
-                }
-            g = warp_sum(g);
-            v2 = warp_sum(v2);
-            extras(x, g, v2);
-            gv = v2;
+                if (ck[k] <= kx) g += cwf[k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                if (xk[k] <= kx) g += xwf[k];
             return g;
         };
         double xl = -1.0, xh = 1.0;
         for (int it = 0; it < kBisect; ++it) {
             const double xm = 0.5 * (xl + xh);
-            double gv;
-            if (Gc(xm, gv) >= rest) xh = xm; else xl = xm;
+            if (Gf(okey(xm)) >= rest_f) xh = xm; else xl = xm;
         }
         double gv;
-        const double g = Gc(xl, gv);
+        const double g = G(xl, gv);
         const double x = maximize ? (high ? xl : xh) : (high ? xh : xl);
         res = slov + gv + (rest - g) * fmax(x, 0.0);
     } else {
