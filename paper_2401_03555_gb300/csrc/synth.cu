@@ -63,9 +63,15 @@ __device__ __forceinline__ double warp_sum(double v)
 // x <= y exactly when okey(x) <= okey(y).
 __device__ __forceinline__ long long okey(double x)
 {
-    if (x == 0.0) return 0;
     const long long b = __double_as_longlong(x);
+    if ((b & 0x7fffffffffffffffll) == 0) return 0;   // +0 and -0, without an FP64 compare
     return b >= 0 ? b : (b ^ 0x7fffffffffffffffll);
+}
+
+// The double whose key is k (the inverse of okey; key -1 gives -0).
+__device__ __forceinline__ double from_okey(long long k)
+{
+    return __longlong_as_double(k >= 0 ? k : (k ^ 0x7fffffffffffffffll));
 }
 
 struct RowRef {
@@ -172,11 +178,14 @@ __device__ double row_lp(const RowRef &R, const int32_t *__restrict__ col,
                 if (xk[k] <= kx) g += xwf[k];
             return g;
         };
-        double xl = -1.0, xh = 1.0;
-        for (int it = 0; it < kBisect; ++it) {
-            const double xm = 0.5 * (xl + xh);
-            if (Gf(okey(xm)) >= rest_f) xh = xm; else xl = xm;
+        // bisection in key order, down to adjacent doubles: integer work
+        // only, and the same trip count on every lane
+        long long kl = okey(-1.0), kh = okey(1.0);
+        while (kh - kl > 1) {
+            const long long km = kl + ((kh - kl) >> 1);
+            if (Gf(km) >= rest_f) kh = km; else kl = km;
         }
+        const double xl = from_okey(kl), xh = from_okey(kh);
         double gv;
         const double g = G(xl, gv);
         const double x = maximize ? (high ? xl : xh) : (high ? xh : xl);
