@@ -40,7 +40,6 @@
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kBisect = 52;   // bracket width 2^-52 of [0, 1]
 constexpr int kCache = 16;    // successors per lane kept in registers (rows <= 512)
 
 #define CK(expr)                                                                              \
@@ -89,11 +88,13 @@ struct RowRef {
 template <typename VT>
 __device__ double row_lp(const RowRef &R, const int32_t *__restrict__ col,
                          const VT *__restrict__ lo, const VT *__restrict__ up,
-                         const uint8_t *__restrict__ excl, const double *__restrict__ V,
+                         const long long *__restrict__ wfix, const uint8_t *__restrict__ excl,
+                         const double *__restrict__ V, const long long *__restrict__ K,
                          bool maximize, bool high)
 {
     const int lane = threadIdx.x & 31;
-    // the value as seen by the min LP (max LP: 1 - v)
+    // the value as seen by the min LP (max LP: 1 - v); K holds the keys of
+    // these values per cell
     auto val = [&](double v) { return maximize ? 1.0 - v : v; };
     auto out = [&](int32_t t) { return excl != nullptr && excl[t] != 0; };
     // sums over the successors: lo, lo * v
@@ -113,95 +114,86 @@ __device__ double row_lp(const RowRef &R, const int32_t *__restrict__ col,
         slov += R.xlo[x] * val(R.xv[x]);
     }
     const double rest = 1.0 - slo;
-    auto extras = [&](double x, double &g, double &v2) {
+    if (rest <= 0.0) return maximize ? 1.0 - slov : slov;
+    // the further successors: keys and fixed-point widths
+    long long xk[3], xwf[3];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const double v = val(R.xv[k]);
-            if (v <= x) {
-                g += R.xw[k];
-                v2 += R.xw[k] * v;
-            }
-        }
-    };
-    // mass of the successors with value <= x, and their weighted value
-    auto G = [&](double x, double &gv) {
-        double g = 0.0, v2 = 0.0;
-        for (int64_t i = R.a + lane; i < R.b; i += 32) {
-            const int32_t t = col[i];
-            if (out(t)) continue;
-            const double v = val(V[t]);
-            if (v <= x) {
-                const double w = (double)up[i] - (double)lo[i];
-                g += w;
-                v2 += w * v;
-            }
-        }
-        g = warp_sum(g);
-        v2 = warp_sum(v2);
-        extras(x, g, v2);
-        gv = v2;
+    for (int k = 0; k < 3; ++k) {
+        xk[k] = okey(val(R.xv[k]));
+        xwf[k] = __double2ll_rn(R.xw[k] * 0x1p52);
+    }
+    const long long rest_f = __double2ll_rn(rest * 0x1p52);
+    auto finish = [&](long long g, long long kx) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            if (xk[k] <= kx) g += xwf[k];
         return g;
     };
-    double res;
-    if (rest <= 0.0) {
-        res = slov;
-    } else if (R.b - R.a <= 32 * kCache) {
-        // short rows: each lane keeps its successors' values, as integer
-        // order keys, and widths, in fixed point (2^-52 units), in registers
-        // for the whole bisection. The passes then compare and sum integers
-        // only (FP64 issue is scarce on this part); the final value is taken
-        // in FP64 at the bracket found.
+    // G(x): mass (2^-52 units) of the successors whose value is <= x, x given
+    // by its key. The bisection below runs in key order down to adjacent
+    // doubles: integer work only, the same trip count on every lane (FP64
+    // issue is scarce on this part).
+    long long kl = okey(-1.0), kh = okey(1.0);   // G(-1) = 0 < rest; G(1) >= rest
+    if (R.b - R.a <= 32 * kCache) {
+        // short rows: each lane keeps its successors' keys and widths in
+        // registers for the whole bisection
         long long ck[kCache], cwf[kCache];
 #pragma unroll
         for (int k = 0; k < kCache; ++k) {
             const int64_t i = R.a + lane + 32 * k;
             const bool in = i < R.b && !out(col[i]);
-            ck[k] = in ? okey(val(V[col[i]])) : LLONG_MAX;
-            cwf[k] = in ? __double2ll_rn(((double)up[i] - (double)lo[i]) * 0x1p52) : 0ll;
+            ck[k] = in ? K[col[i]] : LLONG_MAX;
+            cwf[k] = in ? wfix[i] : 0ll;
         }
-        long long xk[3], xwf[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            xk[k] = okey(val(R.xv[k]));
-            xwf[k] = __double2ll_rn(R.xw[k] * 0x1p52);
-        }
-        const long long rest_f = __double2ll_rn(rest * 0x1p52);
-        auto Gf = [&](long long kx) {
+        while (kh - kl > 1) {
+            const long long km = kl + ((kh - kl) >> 1);
             long long g = 0;
 #pragma unroll
             for (int k = 0; k < kCache; ++k)
-                if (ck[k] <= kx) g += cwf[k];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
-#pragma unroll
-            for (int k = 0; k < 3; ++k)
-                if (xk[k] <= kx) g += xwf[k];
-            return g;
-        };
-        // bisection in key order, down to adjacent doubles: integer work
-        // only, and the same trip count on every lane
-        long long kl = okey(-1.0), kh = okey(1.0);
+                if (ck[k] <= km) g += cwf[k];
+            if (finish(g, km) >= rest_f) kh = km; else kl = km;
+        }
+    } else {
+        // long rows: every pass reads the keys and widths again (from L2)
         while (kh - kl > 1) {
             const long long km = kl + ((kh - kl) >> 1);
-            if (Gf(km) >= rest_f) kh = km; else kl = km;
+            long long g = 0;
+            for (int64_t i = R.a + lane; i < R.b; i += 32) {
+                const int32_t t = col[i];
+                if (!out(t) && K[t] <= km) g += wfix[i];
+            }
+            if (finish(g, km) >= rest_f) kh = km; else kl = km;
         }
-        const double xl = from_okey(kl), xh = from_okey(kh);
-        double gv;
-        const double g = G(xl, gv);
-        const double x = maximize ? (high ? xl : xh) : (high ? xh : xl);
-        res = slov + gv + (rest - g) * fmax(x, 0.0);
-    } else {
-        double xl = -1.0, xh = 1.0;   // G(xl) = 0 < rest; G(1) >= rest by the row invariants
-        for (int it = 0; it < kBisect; ++it) {
-            const double xm = 0.5 * (xl + xh);
-            double gv;
-            if (G(xm, gv) >= rest) xh = xm; else xl = xm;
-        }
-        double gv;
-        const double g = G(xl, gv);
-        const double x = maximize ? (high ? xl : xh) : (high ? xh : xl);
-        res = slov + gv + (rest - g) * fmax(x, 0.0);
     }
+    const double xl = from_okey(kl), xh = from_okey(kh);
+    // the final value in FP64 at the bracket: the mass below it, its
+    // weighted value, and the rest valued at the bracket's end that keeps
+    // V0 below and V1 above the exact update
+    double g = 0.0, gv = 0.0;
+    for (int64_t i = R.a + lane; i < R.b; i += 32) {
+        const int32_t t = col[i];
+        if (out(t)) continue;
+        const double v = val(V[t]);
+        if (v <= xl) {
+            const double w = (double)up[i] - (double)lo[i];
+            g += w;
+            gv += w * v;
+        }
+    }
+    g = warp_sum(g);
+    gv = warp_sum(gv);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const double v = val(R.xv[k]);
+        if (v <= xl) {
+            g += R.xw[k];
+            gv += R.xw[k] * v;
+        }
+    }
+    const double x = maximize ? (high ? xl : xh) : (high ? xh : xl);
+    const double res = slov + gv + (rest - g) * fmax(x, 0.0);
     return maximize ? 1.0 - res : res;
 }
 
@@ -226,9 +218,10 @@ row_values(Phase ph, int64_t rows, int n_inputs, const uint8_t *__restrict__ lab
            const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
            const VT *__restrict__ lo, const VT *__restrict__ up,
            const double *__restrict__ sink_lo, const double *__restrict__ sink_up,
-           const double *__restrict__ trunc, Regions rg, const double *__restrict__ V0,
-           const double *__restrict__ V1, const int32_t *__restrict__ policy,
-           double *__restrict__ R0, double *__restrict__ R1)
+           const double *__restrict__ trunc, const long long *__restrict__ wfix, Regions rg,
+           const double *__restrict__ V0, const double *__restrict__ V1,
+           const long long *__restrict__ K0, const long long *__restrict__ K1,
+           const int32_t *__restrict__ policy, double *__restrict__ R0, double *__restrict__ R1)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -265,8 +258,8 @@ row_values(Phase ph, int64_t rows, int n_inputs, const uint8_t *__restrict__ lab
         R.xw[2] = trunc[r];
         R.xv[2] = ph.maximize ? 1.0 : 0.0;
         // V0 never rises above, V1 never falls below the exact update
-        const double a = row_lp(R, col, lo, up, excl, V0, ph.maximize, false);
-        const double b = row_lp(R, col, lo, up, excl, V1, ph.maximize, true);
+        const double a = row_lp(R, col, lo, up, wfix, excl, V0, K0, ph.maximize, false);
+        const double b = row_lp(R, col, lo, up, wfix, excl, V1, K1, ph.maximize, true);
         if (lane == 0) {
             R0[r] = a;
             R1[r] = b;
@@ -291,7 +284,8 @@ __device__ __forceinline__ double worst(const double *__restrict__ p, int W, boo
 __global__ void __launch_bounds__(kThreads)
 cell_update(Phase ph, int64_t cells, int n_inputs, const uint8_t *__restrict__ labels,
             const double *__restrict__ R0, const double *__restrict__ R1,
-            double *__restrict__ N0, double *__restrict__ N1, int32_t *__restrict__ policy,
+            double *__restrict__ N0, double *__restrict__ N1, long long *__restrict__ KN0,
+            long long *__restrict__ KN1, int32_t *__restrict__ policy,
             unsigned long long *__restrict__ diff)
 {
     const bool reach = ph.spec == IMPACT_REACH_AVOID;
@@ -330,6 +324,9 @@ cell_update(Phase ph, int64_t cells, int n_inputs, const uint8_t *__restrict__ l
         n1 = fmin(fmax(n1, 0.0), 1.0);
         N0[c] = n0;
         N1[c] = n1;
+        // the keys of the values the next iteration's LPs compare
+        KN0[c] = okey(ph.maximize ? 1.0 - n0 : n0);
+        KN1[c] = okey(ph.maximize ? 1.0 - n1 : n1);
         dmax = fmax(dmax, fabs(n1 - n0));
     }
 #pragma unroll
@@ -341,20 +338,37 @@ cell_update(Phase ph, int64_t cells, int n_inputs, const uint8_t *__restrict__ l
 // V0 from 0 and V1 from 1 on the free cells (from 0 both, for a finite
 // horizon); the labelled cells hold their absorbing value.
 __global__ void __launch_bounds__(kThreads)
-init_values(int spec, bool horizon, int64_t cells, const uint8_t *__restrict__ labels,
-            double *__restrict__ V0, double *__restrict__ V1)
+init_values(int spec, bool horizon, bool maximize, int64_t cells,
+            const uint8_t *__restrict__ labels, double *__restrict__ V0, double *__restrict__ V1,
+            long long *__restrict__ K0, long long *__restrict__ K1)
 {
     const bool reach = spec == IMPACT_REACH_AVOID;
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < cells;
          c += (int64_t)gridDim.x * blockDim.x) {
         const uint8_t lab = labels[c];
+        double a, b;
         if (lab == 0) {
-            V0[c] = 0.0;
-            V1[c] = horizon ? 0.0 : 1.0;
+            a = 0.0;
+            b = horizon ? 0.0 : 1.0;
         } else {
-            V0[c] = V1[c] = (reach ? lab == 1 : lab == 2) ? 1.0 : 0.0;
+            a = b = (reach ? lab == 1 : lab == 2) ? 1.0 : 0.0;
         }
+        V0[c] = a;
+        V1[c] = b;
+        K0[c] = okey(maximize ? 1.0 - a : a);
+        K1[c] = okey(maximize ? 1.0 - b : b);
     }
+}
+
+// Widths up - lo of every pair in 2^-52 units (the LP passes sum integers).
+template <typename VT>
+__global__ void __launch_bounds__(kThreads)
+pair_widths(int64_t nnz, const VT *__restrict__ lo, const VT *__restrict__ up,
+            long long *__restrict__ wfix)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz;
+         i += (int64_t)gridDim.x * blockDim.x)
+        wfix[i] = __double2ll_rn(((double)up[i] - (double)lo[i]) * 0x1p52);
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -425,9 +439,13 @@ extern "C" impact_status impact_synthesize_ex(const impact_csr *imdp, impact_pre
         return fail(IMPACT_ERR_ARG, "the region vectors must be device arrays");
     cudaStream_t st = (cudaStream_t)stream;
     double *buf = nullptr, *rbuf = nullptr;
+    long long *kbuf = nullptr, *wfix = nullptr;
     unsigned long long *d_diff = nullptr, *h_diff = nullptr;
     const int64_t rows = imdp->rows;
+    const int64_t nnz = imdp->nnz;
     CK(cudaMallocAsync((void **)&buf, (size_t)cells * 4 * sizeof(double), st));
+    CK(cudaMallocAsync((void **)&kbuf, (size_t)cells * 4 * sizeof(long long), st));
+    CK(cudaMallocAsync((void **)&wfix, (size_t)std::max<int64_t>(nnz, 1) * sizeof(long long), st));
     CK(cudaMallocAsync((void **)&rbuf, (size_t)rows * 2 * sizeof(double), st));
     CK(cudaMallocAsync((void **)&d_diff, sizeof(unsigned long long), st));
     CK(cudaMallocHost((void **)&h_diff, sizeof(unsigned long long)));
@@ -442,8 +460,18 @@ extern "C" impact_status impact_synthesize_ex(const impact_csr *imdp, impact_pre
     const int g_rows = grid_of(rows, kThreads / 32);
     impact_status status = IMPACT_OK;
     int its[2] = {0, 0};
+    if (nnz > 0) {
+        const int g_nnz = grid_of(nnz, kThreads);
+        if (precision == IMPACT_FP32_SOUND)
+            pair_widths<float><<<g_nnz, kThreads, 0, st>>>(nnz, (const float *)imdp->lo,
+                                                           (const float *)imdp->up, wfix);
+        else
+            pair_widths<double><<<g_nnz, kThreads, 0, st>>>(nnz, (const double *)imdp->lo,
+                                                            (const double *)imdp->up, wfix);
+    }
     for (int phase = 0; phase < 2 && status == IMPACT_OK; ++phase) {
         double *V0 = buf, *V1 = buf + cells, *N0 = buf + 2 * cells, *N1 = buf + 3 * cells;
+        long long *K0 = kbuf, *K1 = kbuf + cells, *KN0 = kbuf + 2 * cells, *KN1 = kbuf + 3 * cells;
         Phase ph;
         ph.spec = spec;
         ph.choose = phase == 0;
@@ -452,7 +480,8 @@ extern "C" impact_status impact_synthesize_ex(const impact_csr *imdp, impact_pre
         // LP -> V1, safety max LP -> V1 (P_min = 1 - V1), min LP -> V0
         ph.pol_v1 = lp1_max;
         ph.n_disturb = W;
-        init_values<<<g_cells, kThreads, 0, st>>>(spec, horizon, cells, labels, V0, V1);
+        init_values<<<g_cells, kThreads, 0, st>>>(spec, horizon, ph.maximize, cells, labels, V0,
+                                                  V1, K0, K1);
         int it = 0;
         while (it < limit) {
             cudaMemsetAsync(d_diff, 0, sizeof(unsigned long long), st);
@@ -461,14 +490,14 @@ extern "C" impact_status impact_synthesize_ex(const impact_csr *imdp, impact_pre
                 row_values<float><<<g_rows, kThreads, 0, st>>>(
                     ph, rows, n_inputs, labels, imdp->row_ptr, imdp->col,
                     (const float *)imdp->lo, (const float *)imdp->up, imdp->sink_lo,
-                    imdp->sink_up, imdp->trunc, rg, V0, V1, policy, R0, R1);
+                    imdp->sink_up, imdp->trunc, wfix, rg, V0, V1, K0, K1, policy, R0, R1);
             else
                 row_values<double><<<g_rows, kThreads, 0, st>>>(
                     ph, rows, n_inputs, labels, imdp->row_ptr, imdp->col,
                     (const double *)imdp->lo, (const double *)imdp->up, imdp->sink_lo,
-                    imdp->sink_up, imdp->trunc, rg, V0, V1, policy, R0, R1);
+                    imdp->sink_up, imdp->trunc, wfix, rg, V0, V1, K0, K1, policy, R0, R1);
             cell_update<<<g_cells, kThreads, 0, st>>>(ph, cells, n_inputs, labels, R0, R1, N0, N1,
-                                                      policy, d_diff);
+                                                      KN0, KN1, policy, d_diff);
             cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) {
                 status = fail(IMPACT_ERR_CUDA, cudaGetErrorString(e));
@@ -476,6 +505,8 @@ extern "C" impact_status impact_synthesize_ex(const impact_csr *imdp, impact_pre
             }
             std::swap(V0, N0);
             std::swap(V1, N1);
+            std::swap(K0, KN0);
+            std::swap(K1, KN1);
             ++it;
             if (horizon) continue;   // a fixed number of steps: no stopping test
             // the stopping test of Alg. 3/4 on the vectors just computed
@@ -506,6 +537,8 @@ extern "C" impact_status impact_synthesize_ex(const impact_csr *imdp, impact_pre
             status = fail(IMPACT_ERR_CUDA, "synthesis phase failed");
     }
     cudaFreeAsync(buf, st);
+    cudaFreeAsync(kbuf, st);
+    cudaFreeAsync(wfix, st);
     cudaFreeAsync(rbuf, st);
     cudaFreeAsync(d_diff, st);
     cudaStreamSynchronize(st);
