@@ -35,8 +35,11 @@ def cases():
     img.cutoff = 0.01
     lin = W.random_linear(5, min_cells=200, max_cells=2000)
     lin.cutoff = 5e-3
+    uni = W.unicycle_3d(nx=8, ny=8, nth=7, cutoff=5e-3)
     return [
         ("robot full covariance", robot, correlated(rng, 4000, [0.75, 0.75], 0.6), None),
+        ("unicycle correlated", uni, correlated(rng, 2000, [0.3, 0.3, 0.2], 0.5),
+         W.sample_rows(uni, 24, seed=5)),
         ("room 4^5 correlated", room, correlated(rng, 3000, [0.2] * 5, 0.3),
          W.sample_rows(room, 24, seed=3)),
         ("wide images", img, rng.normal(size=(5000, 2)) * 0.9, None),
