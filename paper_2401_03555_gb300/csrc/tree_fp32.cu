@@ -462,7 +462,6 @@ setup_fp32(const BatchIndex *__restrict__ B, uint32_t *__restrict__ status,
 //   bq (32 float4) + seg (kSeg bytes)          leaf runs of one batch
 struct Hdr {
     int ta[IMPACT_MAX_DIM], tw[IMPACT_MAX_DIM], pk[IMPACT_MAX_DIM], toff[IMPACT_MAX_DIM];
-    int first[IMPACT_MAX_DIM];
     float swr[IMPACT_MAX_DIM];
 };
 static_assert(sizeof(Hdr) <= kHdr, "row header does not fit");
@@ -601,39 +600,32 @@ tree_fp32(const BatchIndex *__restrict__ B, int warp_smem, int64_t *__restrict__
         const int K = D.tree_k[EMIT ? 1 : 0];
         const int Lp = n - 1 - (K == 1 ? 1 : 2);   // level of the batch parents (-1: the root)
         const unsigned char *rr = B->rec[q] + (row - B->row_begin[q]) * (int64_t)D.rec_stride;
-        // 1. the row record: per-dimension scalars, then the trimmed tables
+        // 1. the row record: per-dimension scalars, and the U, L, T tables
+        // copied whole in the record's own layout (U, L, T of tcap entries
+        // each, dimension k at rec_off[k]), so that every load of the row is
+        // issued at once; dimension k's trimmed window starts at
+        // rec_off[k] + first[k]. The record is 16-byte aligned (the workspace
+        // is 256-byte aligned and the stride a multiple of 16).
         if (lane < n) {
             const int4 hi = reinterpret_cast<const int4 *>(rr)[3 * lane];
             const float4 hc = reinterpret_cast<const float4 *>(rr)[3 * lane + 2];
             H.ta[lane] = hi.x;
             H.tw[lane] = hi.y;
-            H.first[lane] = hi.z;
+            H.toff[lane] = D.dim[lane].rec_off + hi.z;
             H.pk[lane] = hi.w;
             H.swr[lane] = hc.z;
         }
+        {
+            const int nf = 3 * tcap, n4 = nf >> 2;
+            const float4 *src4 = reinterpret_cast<const float4 *>(rr + 48 * n);
+            float4 *dst4 = reinterpret_cast<float4 *>(S.U);
+            for (int i = lane; i < n4; i += 32) dst4[i] = src4[i];
+            const float *src = reinterpret_cast<const float *>(rr + 48 * n);
+            for (int i = 4 * n4 + lane; i < nf; i += 32) S.U[i] = src[i];
+        }
         __syncwarp();
         bool empty = false;
-        {
-            int tsum = 0;
-            for (int k = 0; k < n; ++k) {
-                if (lane == 0) H.toff[k] = tsum;
-                tsum += H.tw[k];
-                empty |= (H.tw[k] == 0);
-            }
-        }
-        __syncwarp();
-        {
-            const float *RA = reinterpret_cast<const float *>(rr + 48 * n);
-            for (int k = 0; k < n; ++k) {
-                const int src = D.dim[k].rec_off + H.first[k], dst = H.toff[k], tw = H.tw[k];
-                for (int i = lane; i < tw; i += 32) {
-                    S.U[dst + i] = RA[src + i];
-                    S.L[dst + i] = RA[tcap + src + i];
-                    S.T[dst + i] = RA[2 * tcap + src + i];
-                }
-            }
-        }
-        __syncwarp();
+        for (int k = 0; k < n; ++k) empty |= (H.tw[k] == 0);
         if (!EMIT && lane < n) {   // prefix and suffix sums of U and L per dimension
             const int off = H.toff[lane], po = off + lane, tw = H.tw[lane];
             float a = 0.0f, b = 0.0f, c = 0.0f, e = 0.0f;
