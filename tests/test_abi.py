@@ -125,3 +125,24 @@ def test_batch_plan_rejects_bad_tuning(lib, field, value, msg):
     t = impact.tuning(**{field: value})
     with pytest.raises(impact.ImpactError, match=msg):
         impact.Batch([W.robot_2d(cells_per_dim=5)], "fp32", tune=t)
+
+
+def test_plan_accepts_the_largest_dimension(lib):
+    prob = W.random_linear(2, min_cells=5000, max_cells=7000, dims=(8,))
+    assert prob.n == 8
+    for precision in ("fp32", "fp64"):
+        rows, nnz_bound, _ = impact.plan(prob, precision)
+        assert rows == prob.rows
+        assert rows <= nnz_bound <= prob.rows * prob.total_cells
+
+
+def test_plan_rejects_more_than_eight_dimensions(lib):
+    n = 9
+    prob = W.Problem(name="9d", kind=W.AFFINE, lo=np.full(n, -1.0), hi=np.full(n, 1.0),
+                     cells=np.full(n, 2, np.int32), inputs=np.zeros((1, 1)),
+                     sigma=np.full(n, 0.3), cutoff=1e-8, A=0.9 * np.eye(n),
+                     B=np.zeros((n, 1)), c=np.zeros(n))
+    with pytest.raises(impact.ImpactError) as e:
+        impact.plan(prob, "fp32")
+    assert e.value.status == impact.IMPACT_ERR_ARG
+    assert "[1, 8]" in str(e.value)

@@ -152,3 +152,22 @@ def test_table1_grid_counts(entry):
     # rows of the transition matrices: |X| x |U| x |W| (Def. 3.1 / Table 1)
     assert prob.rows * int(wpts) == int(nrows)
     assert np.allclose(hi - lo, cells * np.array(vec(seta)))
+
+
+def eight_dim_case():
+    """The largest dimension the boundary accepts: a seeded 8-D linear system
+    on 3^8 cells (coupled A, two or three input dimensions)."""
+    prob = W.random_linear(2, min_cells=5000, max_cells=7000, dims=(8,))
+    assert prob.n == 8
+    return prob, W.sample_rows(prob, 3, seed=12, include_boundary=False)
+
+
+def test_eight_dimensions_contain_sampled_probabilities(orc):
+    prob, rows = eight_dim_case()
+    P.pin_mc_containment(orc, prob, rows, samples=24)
+
+
+def test_eight_dimensions_invariants_and_axis_sums(orc):
+    prob, rows = eight_dim_case()
+    P.pin_invariants(orc, prob, rows)
+    P.pin_separable_sum(orc, prob, rows)
