@@ -227,14 +227,15 @@ def emit_traffic(alg_bytes):
 # CPU oracle baseline (bounded sample)
 # --------------------------------------------------------------------------
 
-def cpu_oracle_sample(prob, rows_target: int, seed: int = 0):
-    """Time the CPU oracle on a seeded sample of rows; returns a dict."""
+def cpu_oracle_sample(prob, rows_target: int, seed: int = 0, threads: int = 0):
+    """Time the CPU oracle on a seeded sample of rows (all OpenMP threads, or
+    `threads` of them); returns a dict."""
     import oracle
     orc = oracle.default()
-    threads = orc.max_threads()
+    threads = threads or orc.max_threads()
     rows = np.sort(np.random.default_rng(seed).choice(prob.rows, size=rows_target, replace=False))
     t0 = time.perf_counter()
-    res = orc.build_rows(prob, rows)
+    res = orc.build_rows(prob, rows, threads=threads)
     dt = time.perf_counter() - t0
     return {"value": res.nnz / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{len(rows)} seeded random rows of the {prob.rows} (dense scan of "
@@ -407,6 +408,13 @@ def run_ours(args, rank, world, local_rank):
             out["cpu_baseline"] = cpu_oracle_sample(prob, n_rows)
         except Exception as exc:  # the oracle is a baseline, not the product
             out["cpu_baseline"] = {"value": None, "error": str(exc)[:200]}
+        try:   # the same oracle on one core, on a proportionally smaller sample
+            cores = int(out["cpu_baseline"].get("cores") or 1)
+            one = cpu_oracle_sample(prob, max(1, n_rows // max(cores, 1)), seed=1, threads=1)
+            out["cpu_baseline"]["single_core"] = {k: one[k] for k in
+                                                  ("value", "unit", "cores", "sample", "seconds")}
+        except Exception as exc:
+            out["cpu_baseline"]["single_core"] = {"value": None, "error": str(exc)[:200]}
     return out
 
 
