@@ -62,6 +62,11 @@ def test_plan_dense_bound_is_exact(lib):
     (lambda p: setattr(p, "hi", p.lo.copy()), "lo < hi"),
     (lambda p: setattr(p, "cells", np.zeros(p.n, np.int32)), "cells"),
     (lambda p: setattr(p, "cells", np.full(p.n, 50000, np.int32)), "2^31"),
+    (lambda p: setattr(p, "inputs", np.zeros((0, 2))), "inputs.count"),
+    (lambda p: setattr(p, "sigma", np.full(p.n, np.nan)), "sigma"),
+    (lambda p: setattr(p, "hi", np.full(p.n, np.inf)), "finite lo < hi"),
+    (lambda p: (setattr(p, "inputs", np.zeros((1, 9))), setattr(p, "B", np.zeros((p.n, 9)))),
+     "inputs.m"),
 ])
 def test_plan_rejects_bad_arguments(lib, mutate, msg):
     prob = W.room_5d()
@@ -146,3 +151,12 @@ def test_plan_rejects_more_than_eight_dimensions(lib):
         impact.plan(prob, "fp32")
     assert e.value.status == impact.IMPACT_ERR_ARG
     assert "[1, 8]" in str(e.value)
+
+
+def test_plan_rejects_a_unicycle_of_other_dimension(lib):
+    prob = W.unicycle_3d(nx=5, ny=5, nth=5)
+    prob.lo, prob.hi = np.r_[prob.lo, 0.0], np.r_[prob.hi, 1.0]
+    prob.cells = np.r_[prob.cells, 2].astype(np.int32)
+    prob.sigma = np.r_[prob.sigma, 0.3]
+    with pytest.raises(impact.ImpactError, match="unicycle needs n = 3"):
+        impact.plan(prob, "fp32")
