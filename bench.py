@@ -49,9 +49,9 @@ def workload_name(cells=11):
 
 
 WORKLOAD = workload_name()
-# kernels one count + emit step launches: setup, tree count, three scan
-# stages, tree emit
-LAUNCHES_PER_STEP = 6
+# kernels one step launches: the one-pass walk (the graph's resets are memset
+# nodes, not kernels)
+LAUNCHES_PER_STEP = 1
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -198,15 +198,16 @@ def hbm_peak():
         return 6800.0, "fallback"
 
 
-def emit_traffic(alg_bytes):
-    """DRAM bytes of one emit launch, from the committed ncu summary.
+def walk_traffic(alg_bytes):
+    """DRAM bytes of one launch of the one-pass kernel, from the committed ncu
+    summary.
 
-    The summary records the DRAM traffic per algorithmic byte of the emit
-    kernel and the hash of the source it was captured on; the figure is used
-    only while that source is unchanged (None otherwise)."""
+    The summary records the DRAM traffic per algorithmic byte of the kernel
+    and the hash of the source it was captured on; the figure is used only
+    while that source is unchanged (None otherwise)."""
     import hashlib
-    prof = os.path.join(ROOT, "profiles", "room5d_fp32_tree_kernels_ncu.txt")
-    src = os.path.join(ROOT, "paper_2401_03555_gb300", "csrc", "tree_fp32.cu")
+    prof = os.path.join(ROOT, "profiles", "room5d_fp32_walk_ncu.txt")
+    src = os.path.join(ROOT, "paper_2401_03555_gb300", "csrc", "walk_fp32.cu")
     try:
         text = open(prof).read()
         digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
@@ -223,24 +224,109 @@ def emit_traffic(alg_bytes):
     return int(ratio * alg_bytes)
 
 
+def run_two_pass(prob, nnz, rbuf, pbuf, wbuf, flush, stream, dev, reps=3):
+    """impact_count then impact_emit (the two-call path for callers that size
+    their arrays from the count), each pass timed with CUDA events."""
+    import ctypes
+    import torch
+    from paper_2401_03555_gb300 import impact
+    a = impact._Args(prob)
+    lib = impact.load()
+    sh = ctypes.c_void_p(int(stream.cuda_stream))
+    cms, ems = [], []
+    for it in range(reps + 1):
+        flush.fill_(1.0)
+        s, m, e = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        c = impact._csr_struct(rbuf, pbuf, capacity=nnz, workspace=wbuf)
+        s.record(stream)
+        impact._check(lib.impact_count(ctypes.byref(a.sys), ctypes.byref(a.grid),
+                                       ctypes.byref(a.inp), a.sigma_ptr, a.cutoff,
+                                       impact.FP32_SOUND, ctypes.byref(c), sh))
+        m.record(stream)
+        c.nnz = nnz
+        impact._check(lib.impact_emit(ctypes.byref(a.sys), ctypes.byref(a.grid),
+                                      ctypes.byref(a.inp), a.sigma_ptr, a.cutoff,
+                                      impact.FP32_SOUND, ctypes.byref(c), sh))
+        e.record(stream)
+        e.synchronize()
+        if it > 0:
+            cms.append(s.elapsed_time(m))
+            ems.append(m.elapsed_time(e))
+    peak, _ = hbm_peak()
+    cm, em = sum(cms) / len(cms), sum(ems) / len(ems)
+    emit_bytes = nnz * 12 + prob.rows * 16
+    return {"count_ms": round(cm, 3), "emit_ms": round(em, 3), "step_ms": round(cm + em, 3),
+            "value": nnz / ((cm + em) / 1e3), "unit": UNIT,
+            "emit_frac": round(emit_bytes / (em / 1e3) / 1e9 / peak, 4),
+            "path": "impact_count (walk COUNT: row pointers by look-back, row terms) + "
+                    "impact_emit (walk EMIT at those row pointers), each synchronized"}
+
+
+def oracle_sample_rows(prob, rows_target: int, seed: int = 0):
+    """The seeded row sample the oracle baseline times."""
+    return np.sort(np.random.default_rng(seed).choice(prob.rows, size=rows_target, replace=False))
+
+
+def fetch_rows(rbuf, pbuf, rows):
+    """The GPU CSR of the given rows, copied to the host."""
+    rp = rbuf["row_ptr"].cpu().numpy()
+    out = {"row_ptr": rp, "rows": rows}
+    spans = [(int(rp[r]), int(rp[r + 1])) for r in rows]
+    for k in ("col", "lo", "up"):
+        out[k] = [pbuf[k][a:b].cpu().numpy() for a, b in spans]
+    for k in ("sink_lo", "sink_up", "trunc"):
+        out[k] = rbuf[k].cpu().numpy()[rows]
+    return out
+
+
+def sample_parity(prob, gpu, ref):
+    """The GPU rows against the oracle's on the same rows: largest
+    differences and the FP32-sound bracketing (the parity test's rules)."""
+    dlo = dup = 0.0
+    bracket = True
+    missing = 0
+    for k in range(len(gpu["rows"])):
+        oc, olo, oup = ref.row(k)
+        gc = gpu["col"][k]
+        _, gi, oi = np.intersect1d(gc, oc, return_indices=True)
+        missing += len(oc) - len(oi)
+        lo = gpu["lo"][k].astype(np.float64)[gi]
+        up = gpu["up"][k].astype(np.float64)[gi]
+        if len(gi):
+            dlo = max(dlo, float(np.max(np.abs(lo - olo[oi]))))
+            dup = max(dup, float(np.max(np.abs(up - oup[oi]))))
+            bracket &= bool(np.all(lo <= olo[oi]) and np.all(up >= oup[oi]))
+        extra = np.setdiff1d(np.arange(len(gc)), gi)
+        bracket &= bool(np.all(gpu["up"][k][extra] >= prob.cutoff))
+    dsl = float(np.max(np.abs(gpu["sink_lo"] - ref.sink_lo)))
+    dsu = float(np.max(np.abs(gpu["sink_up"] - ref.sink_up)))
+    dtr = float(np.max(np.abs(gpu["trunc"] - ref.trunc)))
+    bracket &= bool(np.all(gpu["sink_lo"] <= ref.sink_lo) and np.all(gpu["sink_up"] >= ref.sink_up))
+    ok = bracket and missing == 0 and max(dlo, dup, dsl, dsu, dtr) <= 2e-6
+    return {"rows": len(gpu["rows"]), "max_dlo": dlo, "max_dup": dup,
+            "max_dsink": max(dsl, dsu), "max_dtrunc": dtr, "missing_pairs": int(missing),
+            "bracketing": bracket, "within_2e-6": ok}
+
+
 # --------------------------------------------------------------------------
 # CPU oracle baseline (bounded sample)
 # --------------------------------------------------------------------------
 
-def cpu_oracle_sample(prob, rows_target: int, seed: int = 0, threads: int = 0):
+def cpu_oracle_sample(prob, rows_target: int, seed: int = 0, threads: int = 0, keep=False):
     """Time the CPU oracle on a seeded sample of rows (all OpenMP threads, or
-    `threads` of them); returns a dict."""
+    `threads` of them); returns a dict (and the oracle's rows with keep)."""
     import oracle
     orc = oracle.default()
     threads = threads or orc.max_threads()
-    rows = np.sort(np.random.default_rng(seed).choice(prob.rows, size=rows_target, replace=False))
+    rows = oracle_sample_rows(prob, rows_target, seed)
     t0 = time.perf_counter()
     res = orc.build_rows(prob, rows, threads=threads)
     dt = time.perf_counter() - t0
-    return {"value": res.nnz / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{len(rows)} seeded random rows of the {prob.rows} (dense scan of "
-                      f"{prob.total_cells} targets per row), {res.nnz} pairs in {dt:.2f} s",
-            "rows_per_s": len(rows) / dt, "seconds": dt}
+    out = {"value": res.nnz / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": f"{len(rows)} seeded random rows of the {prob.rows} (dense scan of "
+                     f"{prob.total_cells} targets per row), {res.nnz} pairs in {dt:.2f} s",
+           "rows_per_s": len(rows) / dt, "seconds": dt}
+    return (out, res) if keep else out
 
 
 def auto_cpu_rows(prob):
@@ -265,39 +351,28 @@ def run_ours(args, rank, world, local_rank):
     rows = prob.rows
 
     # exact sizes from one build, then caller-owned buffers reused every step
-    first = impact.build(prob, "fp32")
-    nnz = first.nnz
-    del first
+    nnz = impact.build(prob, "fp32").nnz
     torch.cuda.empty_cache()
     rbuf = impact.alloc_rows(rows, dev)
     pbuf = impact.alloc_pairs(nnz, "fp32", dev)
     wbuf = impact.alloc_workspace(prob, "fp32", dev)
-    args_c = impact._Args(prob)
-    lib = impact.load()
-    import ctypes
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
-    sh = ctypes.c_void_p(int(stream.cuda_stream))
+    # one step = the whole build replayed from a CUDA graph: resets of the
+    # status, row counter and offset words, then ONE persistent kernel that
+    # sets up every row's factor tables, counts its pairs, finds its offset
+    # from the rows before it and writes its pairs and row terms
+    graph = impact.Batch([prob], "fp32").graph(rbuf, pbuf, nnz, wbuf, stream)
 
     def step():
-        c = impact._csr_struct(rbuf, pbuf, capacity=nnz, workspace=wbuf)
-        s = lib.impact_count(ctypes.byref(args_c.sys), ctypes.byref(args_c.grid),
-                             ctypes.byref(args_c.inp), args_c.sigma_ptr, args_c.cutoff,
-                             impact.FP32_SOUND, ctypes.byref(c), sh)
-        impact._check(s)
-        mid.record(stream)
-        c.nnz = nnz
-        impact._check(lib.impact_emit(ctypes.byref(args_c.sys), ctypes.byref(args_c.grid),
-                                      ctypes.byref(args_c.inp), args_c.sigma_ptr, args_c.cutoff,
-                                      impact.FP32_SOUND, ctypes.byref(c), sh))
-        return int(c.nnz)
+        graph.launch(stream)
 
     for _ in range(args.warmup):
-        mid = torch.cuda.Event(enable_timing=True)
         step()
     torch.cuda.synchronize(dev)
+    assert graph.result() == nnz
 
-    step_ms, emit_ms = [], []
+    step_ms = []
     barrier(world)
     torch.cuda.synchronize(dev)
     t_wall = time.perf_counter()
@@ -305,36 +380,36 @@ def run_ours(args, rank, world, local_rank):
         for _ in range(args.steps):
             flush.fill_(1.0)                      # evict L2 between steps
             s = torch.cuda.Event(enable_timing=True)
-            mid = torch.cuda.Event(enable_timing=True)
             e = torch.cuda.Event(enable_timing=True)
             s.record(stream)
-            got = step()
+            step()
             e.record(stream)
             e.synchronize()
-            assert got == nnz
             step_ms.append(s.elapsed_time(e))
-            emit_ms.append(mid.elapsed_time(e))
         torch.cuda.synchronize(dev)
     barrier(world)
     wall_s = time.perf_counter() - t_wall
+    assert graph.result() == nnz
     ms_local = sum(step_ms) / len(step_ms)
     ms = max_over_ranks(ms_local, world, dev)
     total_pairs = sum_over_ranks(float(nnz), world, dev)
     value = total_pairs / (ms / 1e3)
 
-    # roofline of the emit kernel: algorithmic bytes = 12 B per pair written
-    # (int32 col + f32 lo + f32 up) + 16 B per row read (two row pointers)
+    # roofline of the one kernel of the step: algorithmic bytes = 12 B per
+    # pair written (int32 col + f32 lo + f32 up) + 36 B per row written
+    # (row_ptr, sink_lo, sink_up, trunc: 8 each; row_flags 4); the time is
+    # the whole graph replay (its resets included), so the fraction is a
+    # lower bound for the kernel alone
     peak, peak_kind = hbm_peak()
-    emit_avg = sum(emit_ms) / len(emit_ms)
-    alg_bytes = nnz * 12 + rows * 16
-    achieved = alg_bytes / (emit_avg / 1e3) / 1e9
+    alg_bytes = nnz * 12 + rows * 36
+    achieved = alg_bytes / (ms_local / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": emit_traffic(alg_bytes),
-                "kernel": "tree_fp32<emit>", "peak_source": peak_kind,
-                "traffic_source": "ncu dram__bytes_read+write of the emit kernel on the 7^5-cell "
-                                  "case, scaled per algorithmic byte "
-                                  "(profiles/room5d_fp32_tree_kernels_ncu.txt)",
-                "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": round(emit_avg, 3)}
+                "frac": round(achieved / peak, 4), "traffic": walk_traffic(alg_bytes),
+                "kernel": "walk_fp32<FUSED>", "peak_source": peak_kind,
+                "traffic_source": "ncu dram__bytes_read+write of the one-pass kernel, scaled "
+                                  "per algorithmic byte (profiles/room5d_fp32_walk_ncu.txt)",
+                "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": round(ms_local, 3),
+                "bytes_model": "12 B/pair + 36 B/row written"}
     clk = clocks.summary()
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -346,7 +421,20 @@ def run_ours(args, rank, world, local_rank):
                       "l2": f"flushed between steps (512 MiB write); output {nnz * 12 / 1e9:.1f} GB"},
            "roofline": roofline, "clocks": clk,
            "gpu_launches": LAUNCHES_PER_STEP * args.steps, "wall_s": round(wall_s, 3)}
-    del pbuf, flush, wbuf
+
+    # the two-call path (impact_count, then impact_emit at its row pointers):
+    # each pass timed on its own
+    out["two_pass"] = run_two_pass(prob, nnz, rbuf, pbuf, wbuf, flush, stream, dev)
+
+    # rows the oracle baseline will sample: their GPU values, kept for the
+    # parity check after the oracle has run
+    sample_rows = None
+    if rank == 0 and not args.no_cpu:
+        n_rows = args.cpu_rows or auto_cpu_rows(prob)
+        sample_rows = oracle_sample_rows(prob, n_rows, seed=0)
+        gpu_rows = fetch_rows(rbuf, pbuf, sample_rows)
+    graph.close()
+    del pbuf, flush, wbuf, rbuf
     torch.cuda.empty_cache()
 
     # end to end through the public API with the CSR read back to pinned host
@@ -404,8 +492,9 @@ def run_ours(args, rank, world, local_rank):
 
     if rank == 0 and not args.no_cpu:
         try:
-            n_rows = args.cpu_rows or auto_cpu_rows(prob)
-            out["cpu_baseline"] = cpu_oracle_sample(prob, n_rows)
+            out["cpu_baseline"], ref = cpu_oracle_sample(prob, n_rows, keep=True)
+            # the same rows of the timed build against the oracle
+            out["cpu_baseline"]["parity"] = sample_parity(prob, gpu_rows, ref)
         except Exception as exc:  # the oracle is a baseline, not the product
             out["cpu_baseline"] = {"value": None, "error": str(exc)[:200]}
         try:   # the same oracle on one core, on a proportionally smaller sample
@@ -494,15 +583,57 @@ def run_batched(dev, stream, reps=2, cap_pairs=8_000_000_000):
     for g in graphs:
         g.close()
     del graphs, wss, pb, rbuf
-    ms = min(ms_tuned, ms_default)
-    return {"workload": BATCHED_WORKLOAD, "systems": len(probs), "rows": int(full.rows),
-            "pairs": int(total), "groups": len(groups), "group_sizes": [len(g) for g in groups],
-            "value": total / (ms_tuned / 1e3), "unit": UNIT, "ms_per_pass": ms_tuned,
-            "ms_per_pass_default_shapes": ms_default, "tuning": best.as_dict(),
-            "tune_s": round(tune_s, 2), "count_all_s": round(count_all_s, 3),
-            "gpu_launches_per_pass": LAUNCHES_PER_STEP * len(groups),
-            "path": "impact_graph_launch per group (count + scan + emit, one persistent "
-                    "launch per kernel over every system of the group)"}
+    torch.cuda.empty_cache()
+    peak, peak_kind = hbm_peak()
+    alg_bytes = int(total) * 12 + int(full.rows) * 36
+    achieved = alg_bytes / (ms_tuned / 1e3) / 1e9
+    out = {"workload": BATCHED_WORKLOAD, "systems": len(probs), "rows": int(full.rows),
+           "pairs": int(total), "groups": len(groups), "group_sizes": [len(g) for g in groups],
+           "value": total / (ms_tuned / 1e3), "unit": UNIT, "ms_per_pass": ms_tuned,
+           "ms_per_pass_default_shapes": ms_default, "tuning": best.as_dict(),
+           "tune_s": round(tune_s, 2), "count_all_s": round(count_all_s, 3),
+           "gpu_launches_per_pass": LAUNCHES_PER_STEP * len(groups),
+           "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                        "unit": "GB/s", "frac": round(achieved / peak, 4),
+                        "peak_source": peak_kind, "algorithmic_bytes_per_pass": alg_bytes,
+                        "bytes_model": "12 B/pair + 36 B/row written",
+                        "time": "every group's graph replay, back to back"},
+           "path": "impact_graph_launch per group (one persistent one-pass launch over "
+                   "every system of the group)"}
+    out["fp64_plain"] = batched_fp64_sample(probs, dev)
+    return out
+
+
+def batched_fp64_sample(probs, dev, pairs_target=150_000_000):
+    """FP32-sound against FP64 plain on the first systems of the batched
+    workload (about `pairs_target` pairs: the FP64 plain kernel evaluates erfc
+    in FP64 per pair and dimension, so the whole workload would take minutes)."""
+    import torch
+    from paper_2401_03555_gb300 import impact
+    take, acc = [], 0
+    for p in probs:
+        take.append(p)
+        acc += impact.plan(p, "fp32")[1]
+        if acc >= pairs_target * 2:   # the plan's bound is about twice the pairs
+            break
+    res = {}
+    for prec in ("fp32", "fp64"):
+        b = impact.Batch(take, prec)
+        b.build()                                 # warm-up (and sizes)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        r = b.build()
+        torch.cuda.synchronize(dev)
+        dt = time.perf_counter() - t0
+        res[prec] = (r.csr.nnz, dt)
+        del r
+        torch.cuda.empty_cache()
+    (n32, t32), (n64, t64) = res["fp32"], res["fp64"]
+    return {"systems": len(take), "pairs_fp32": n32, "pairs_fp64": n64,
+            "fp32_value": n32 / t32, "fp64_value": n64 / t64,
+            "fp32_over_fp64": (n32 / t32) / (n64 / t64), "unit": UNIT,
+            "path": "impact_batch_count + impact_batch_emit (library-sized arrays), "
+                    "wall time of each precision"}
 
 
 SYNTH_WORKLOAD = ("reach-avoid controller for the 2-D robot (21^2 cells, 9 inputs, dense "

@@ -161,13 +161,21 @@ impact_status impact_plan(const impact_system *sys, const impact_grid *grid,
 
 /*
  * impact_build -- the whole abstraction (Alg. 2) on `stream` (a cudaStream_t;
- * NULL is the legacy default stream). Runs the count pass, the row-pointer
- * scan and the emit pass. Synchronizes `stream` once at the end (and once
- * after the scan when the library allocates) to report nnz and status.
+ * NULL is the legacy default stream). With caller-owned col/lo/up
+ * (capacity out->nnz) the FP32-sound build is one pass: each row counts its
+ * pairs, finds its offset from the rows before it and writes them. With
+ * library-owned output (and for FP64_PLAIN) it runs the count pass, the
+ * row pointers and then the emit pass. Synchronizes `stream` once at the end
+ * (and once after the count when the library allocates) to report nnz and
+ * status.
  * Errors: IMPACT_ERR_ARG, IMPACT_ERR_OOM, IMPACT_ERR_CUDA;
  *         IMPACT_ERR_CAPACITY when caller-owned col/lo/up hold fewer than the
  *         needed pairs (out->nnz then holds the needed count, row_ptr and the
- *         row terms are valid, col/lo/up are untouched);
+ *         row terms are valid; col/lo/up hold the pairs of the rows that fit
+ *         (FP32) or are untouched (FP64));
+ *         IMPACT_ERR_TIMEOUT when a row's bounded wait for the offsets of the
+ *         rows before it gave up (the output is incomplete; the device and
+ *         the library stay usable);
  *         IMPACT_ERR_UNSOUND when row_flags != NULL and some row check failed
  *         (the output is complete; row_flags tells which rows).
  */
@@ -178,7 +186,7 @@ impact_status impact_build(const impact_system *sys, const impact_grid *grid,
 /*
  * impact_workspace_bytes -- host-only: the device scratch one build uses (the
  * uploaded descriptor and tables, the scan partial sums and, for
- * IMPACT_FP32_SOUND, one record of per-row factor tables per row).
+ * IMPACT_FP32_SOUND, one 8-byte offset word per row).
  */
 impact_status impact_workspace_bytes(const impact_system *sys, const impact_grid *grid,
                                      const impact_inputs *inputs, const double *sigma,
@@ -189,8 +197,9 @@ impact_status impact_workspace_bytes(const impact_system *sys, const impact_grid
  * out->row_ptr (rows+1 entries), sink_lo, sink_up, trunc and row_flags, then
  * synchronizes `stream` and stores the total pair count in out->nnz.
  * col/lo/up are not touched and may be NULL. With a workspace of at least
- * impact_workspace_bytes bytes, the per-row tables stay in it for a following
- * impact_emit with the same arguments and the same workspace.
+ * impact_workspace_bytes bytes, the uploaded descriptor and tables stay in it
+ * for a following impact_emit with the same arguments and the same workspace.
+ * Errors as impact_build (IMPACT_ERR_TIMEOUT included).
  */
 impact_status impact_count(const impact_system *sys, const impact_grid *grid,
                            const impact_inputs *inputs, const double *sigma, double cutoff,
@@ -199,10 +208,16 @@ impact_status impact_count(const impact_system *sys, const impact_grid *grid,
 /*
  * impact_emit -- second half: given out->row_ptr from impact_count with the
  * same arguments, writes col/lo/up (capacity out->nnz >= row_ptr[rows]).
- * Asynchronous on `stream`; no synchronization. If out->workspace is the one
- * impact_count filled for these arguments, its tables are reused; otherwise
- * (NULL, or filled for other arguments: IMPACT_ERR_ARG) pass NULL and the
- * tables are recomputed.
+ * Synchronizes `stream` once at the end to read the status. If
+ * out->workspace is the one impact_count filled for these arguments, its
+ * uploaded tables are reused; otherwise (NULL, or filled for other arguments:
+ * IMPACT_ERR_ARG) pass NULL and the tables are uploaded again. Each row's factor tables are recomputed
+ * on the device either way.
+ * Errors: IMPACT_ERR_ARG; IMPACT_ERR_CAPACITY when row_ptr[rows] > out->nnz
+ *         (nothing written); IMPACT_ERR_CUDA when row_ptr does not match the
+ *         arguments (a row whose pair count differs from its row_ptr range,
+ *         or a range outside [0, out->nnz)): such a row writes nothing
+ *         outside its own range, and the others are complete.
  */
 impact_status impact_emit(const impact_system *sys, const impact_grid *grid,
                           const impact_inputs *inputs, const double *sigma, double cutoff,
@@ -228,26 +243,30 @@ typedef struct {
 } impact_request;
 
 /*
- * Launch shapes of the FP32-sound prefix-tree walk (impact_batch_tune picks
- * them). Zero fields take the defaults: 4 warps per block, 6144 (count) and
- * 8192 (emit) bytes of shared memory per warp for the node rings, count_k
- * chosen per build.
- *   count_warps, emit_warps              warps per block, 1..8
- *   count_smem_target, emit_smem_target  bytes per warp, 2048..49152
- *   count_k, emit_k                      how the walk handles the last
- *                                        dimensions: 1 leaf batches, 2 (count
- *                                        only) the last two dimensions serially
- *                                        per lane, 3 the last two dimensions
- *                                        lane-parallel (0: chosen per build)
+ * Launch shapes of the FP32-sound walk (impact_batch_tune picks them), and
+ * fault-injection knobs for testing the failure paths without a GPU fault.
+ * Zero fields take the defaults.
+ *   count_warps   warps per block of the count pass and of the one-pass build
+ *                 (caller-owned output), 1..8 (default 4)
+ *   emit_warps    warps per block of the emit pass, 1..8 (default 4)
+ *   spin_limit    sleeps of about 0.1 us that a row's offset look-back waits
+ *                 for the rows before it before the call gives up with
+ *                 IMPACT_ERR_TIMEOUT (0: 2^24, far beyond any real wait)
+ *   reserved      must be 0
+ *   stall_row     r + 1: row r never publishes its pair count, so every row
+ *                 after it waits until spin_limit runs out (0: off)
+ *   fault_row     r + 1: row r's row check sees a lower-bound sum of 2, so it
+ *                 is flagged IMPACT_ROW_LO_SUM_ABOVE_ONE and the call returns
+ *                 IMPACT_ERR_UNSOUND (needs row_flags; 0: off)
  * Shapes change speed only: results are bitwise identical for every shape.
  */
 typedef struct {
     int count_warps;
     int emit_warps;
-    int count_smem_target;
-    int emit_smem_target;
-    int count_k;
-    int emit_k;
+    int spin_limit;
+    int reserved;
+    int64_t stall_row;
+    int64_t fault_row;
 } impact_tuning;
 
 /*
@@ -276,14 +295,16 @@ impact_status impact_batch_build(const impact_request *reqs, int count,
                                  impact_csr *out, void *stream);
 
 /*
- * CUDA graph of a batch's whole pipeline (count, scan, emit) into fixed
+ * CUDA graph of a batch's whole pipeline (FP32: the one-pass build; FP64:
+ * count, scan, emit) into fixed
  * caller-owned arrays: out->col/lo/up with capacity out->nnz and the row
  * arrays, all DEVICE memory that must outlive the graph. The descriptors and
  * tables are uploaded once here (into out->workspace when given, else into
  * scratch the graph owns); each impact_graph_launch replays the build
  * asynchronously on `stream`. After synchronizing that stream,
  * impact_graph_result returns the launch's status and nnz (IMPACT_ERR_CAPACITY
- * when the capacity was short: then col/lo/up are untouched). The request
+ * when the capacity was short: then col/lo/up hold the pairs of the rows that
+ * fit (FP32) or are untouched (FP64)). The request
  * arguments are read during impact_graph_create only.
  */
 typedef struct impact_graph impact_graph;
@@ -295,15 +316,13 @@ impact_status impact_graph_result(impact_graph *graph, int64_t *nnz);
 impact_status impact_graph_destroy(impact_graph *graph);
 
 /*
- * impact_batch_tune -- the autotuner: times the FP32 count pass over warps
- * per block {4,8} x shared-memory targets {4096,6144,8192,12288} x count_k
- * {1,2,3}, then the emit pass over warps x targets x emit_k {1,3} with the
- * best count shape,
- * each the best of `reps` runs, on this batch, and writes the fastest shape
- * to *best and its count + emit milliseconds to *best_ms (may be NULL).
- * `out` as for impact_batch_emit with the capacity of a previous count
- * (col == NULL tunes the count pass only). Synchronizes `stream`; its own
- * scratch is allocated and freed stream-ordered. FP32_SOUND only.
+ * impact_batch_tune -- the autotuner: times the one-pass build (or, when
+ * out->col == NULL, the count pass) over 2, 4, 6 and 8 warps per block, then
+ * the emit pass over the same, each the best of `reps` runs on this batch,
+ * and writes the fastest shape to *best and the first pass's milliseconds to
+ * *best_ms (may be NULL). `out` as for impact_batch_emit with the capacity of
+ * a previous count. Synchronizes `stream`; its own scratch is allocated and
+ * freed stream-ordered. FP32_SOUND only.
  */
 impact_status impact_batch_tune(const impact_request *reqs, int count,
                                 impact_precision precision, impact_csr *out, int reps,
@@ -561,12 +580,37 @@ const char *impact_last_error(void);
 /* Library ABI version (major*100 + minor). */
 int impact_version(void);
 
+/* ------------------------------------------------------------------------
+ * Failure injection for tests of the out-of-memory paths: the failure is
+ * made on the host, so no GPU is exhausted or faulted. The paper has no
+ * counterpart (its tool has no failure handling to test).
+ * ------------------------------------------------------------------------ */
+
+/*
+ * impact_debug_fail_alloc -- the n-th device or pinned-host allocation the
+ * library makes from now on (counting across all threads) fails as if the
+ * device were out of memory, without allocating; the entry point that made it
+ * returns IMPACT_ERR_OOM after releasing everything it took. n = 0 turns the
+ * injection off; after the failure it is off again.
+ * Errors: IMPACT_ERR_ARG when n < 0.
+ */
+impact_status impact_debug_fail_alloc(int64_t n);
+
+/*
+ * impact_debug_live_bytes -- bytes of device and of pinned host memory the
+ * library currently holds through its own allocations (workspaces, scratch,
+ * library-owned results, server groups; not the caller's arrays, and not the
+ * fixed scratch of impact_scan_rows_static). Either pointer may be NULL.
+ */
+impact_status impact_debug_live_bytes(int64_t *device_bytes, int64_t *host_bytes);
+
 /* Largest `rows` that impact_scan_rows_static accepts. */
 #define IMPACT_SCAN_STATIC_MAX_ROWS (1LL << 27)
 
 /*
- * impact_scan_rows_static -- the row-pointer scan of impact_count, for callers
- * that must not allocate device memory. The paper has no counterpart: this is
+ * impact_scan_rows_static -- the row-pointer scan (the one the FP64-plain count
+ * pass and impact_build_mc run), for callers that must not allocate device
+ * memory. The paper has no counterpart: this is
  * a deployment convenience, not part of the method.
  *
  * Who needs it: code that cannot call cudaMalloc (or cudaMallocAsync) at the
@@ -593,7 +637,9 @@ int impact_version(void);
  * device) race and must be serialized by the caller.
  *
  * Errors: IMPACT_ERR_ARG when rows < 1, rows > IMPACT_SCAN_STATIC_MAX_ROWS or
- * row_ptr is NULL; IMPACT_ERR_CUDA when the address lookup or a launch fails.
+ * row_ptr is not device (or managed) memory (checked with
+ * cudaPointerGetAttributes, which allocates nothing); IMPACT_ERR_CUDA when the
+ * address lookup or a launch fails.
  */
 impact_status impact_scan_rows_static(int64_t *row_ptr, int64_t rows, void *stream);
 

@@ -107,10 +107,13 @@ def _row_value(csr, r, V, sink_v, trunc_v, maximize, labels=None, regions=None, 
 
 def interval_iteration(csr, labels, n_inputs: int, spec: int = REACH_AVOID, eps: float = 1e-6,
                        max_iters: int = 10000, optimistic: bool = False, horizon: int = 0,
-                       n_disturb: int = 1, regions=None) -> SynthResult:
+                       n_disturb: int = 1, regions=None, phase2_policy=None) -> SynthResult:
     """Alg. 3 / Alg. 4 with the sorting-method LP. `csr` covers every row in
     order (oracle.build_rows(prob) with rows None); `regions` is None or the
-    four region vectors over all rows."""
+    four region vectors over all rows. `phase2_policy` (cells,) replaces the
+    policy of phase 1 in phase 2 (the paper fixes "the" policy for the second
+    bound; where inputs tie, another optimal choice is equally valid, and this
+    evaluates the second bound under it)."""
     labels = np.asarray(labels, np.int8)
     cells = labels.shape[0]
     W = int(n_disturb)
@@ -183,6 +186,8 @@ def interval_iteration(csr, labels, n_inputs: int, spec: int = REACH_AVOID, eps:
         return V0, V1, it, converged
 
     V0a, V1a, it1, ok1 = phase(lp1_max, True)
+    if phase2_policy is not None:
+        policy[:] = np.where(free, np.asarray(phase2_policy, np.int32), 0)
     V0b, V1b, it2, ok2 = phase(lp2_max, False)
     # (V0, V1) of the min-LP phase and of the max-LP phase
     (mn0, mn1), (mx0, mx1) = ((V0b, V1b), (V0a, V1a)) if lp1_max else ((V0a, V1a), (V0b, V1b))

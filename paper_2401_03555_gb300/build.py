@@ -20,7 +20,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libimpact.so")
-SOURCES = ["api.cu", "plan.cu", "kernels.cu", "static_scan.cu", "tree_fp32.cu", "server.cu",
+SOURCES = ["api.cu", "alloc.cu", "plan.cu", "kernels.cu", "static_scan.cu", "walk_fp32.cu", "server.cu",
            "synth.cu", "mc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "../../include/impact.h"
+#include "alloc.h"
 #include "impact_desc.h"
 #include "kernels.h"
 #include "pipeline.h"
@@ -61,20 +62,15 @@ impact_status tuning_of(const impact_tuning *t, Tuning &T)
     if (!t) return IMPACT_OK;
     if (t->count_warps) T.count_warps = t->count_warps;
     if (t->emit_warps) T.emit_warps = t->emit_warps;
-    if (t->count_smem_target) T.count_smem = t->count_smem_target;
-    if (t->emit_smem_target) T.emit_smem = t->emit_smem_target;
-    T.count_k = t->count_k;
-    T.emit_k = t->emit_k;
     if (T.count_warps < 1 || T.count_warps > IMPACT_TREE_WARPS_MAX || T.emit_warps < 1 ||
         T.emit_warps > IMPACT_TREE_WARPS_MAX)
         return fail(IMPACT_ERR_ARG, "tuning: warps per block must be in [1, 8]");
-    if (T.count_smem < 2048 || T.count_smem > 48 * 1024 || T.emit_smem < 2048 ||
-        T.emit_smem > 48 * 1024)
-        return fail(IMPACT_ERR_ARG, "tuning: shared-memory target must be in [2048, 49152]");
-    if (T.count_k < 0 || T.count_k > 3)
-        return fail(IMPACT_ERR_ARG, "tuning: count_k must be 0, 1, 2 or 3");
-    if (T.emit_k != 0 && T.emit_k != 1 && T.emit_k != 3)
-        return fail(IMPACT_ERR_ARG, "tuning: emit_k must be 0, 1 or 3");
+    if (t->spin_limit < 0 || t->stall_row < 0 || t->fault_row < 0 || t->reserved != 0)
+        return fail(IMPACT_ERR_ARG,
+                    "tuning: spin_limit, stall_row and fault_row must be >= 0, reserved 0");
+    T.faults.spin_limit = t->spin_limit;
+    T.faults.stall_row = t->stall_row - 1;
+    T.faults.fault_row = t->fault_row - 1;
     return IMPACT_OK;
 }
 
@@ -94,13 +90,11 @@ impact_status make_batch(const impact_request *reqs, int count, impact_precision
     B.plans.assign(count, Plan());
     B.images.assign(count, nullptr);
     B.row_begin.assign(count + 1, 0);
-    B.unit_begin.assign(count + 1, 0);
     B.prec = precision;
     uint64_t h = 1469598103934665603ull;
     for (int q = 0; q < count; ++q) {
         const impact_request &r = reqs[q];
-        s = impact::make_plan(r.sys, r.grid, r.inputs, r.sigma, r.cutoff, precision, B.tune,
-                              B.plans[q]);
+        s = impact::make_plan(r.sys, r.grid, r.inputs, r.sigma, r.cutoff, precision, B.plans[q]);
         if (s != IMPACT_OK) {
             if (count > 1) g_last_error = "request " + std::to_string(q) + ": " + g_last_error;
             return s;
@@ -108,20 +102,17 @@ impact_status make_batch(const impact_request *reqs, int count, impact_precision
         const Plan &P = B.plans[q];
         B.images[q] = r.sys->dev_images;
         B.row_begin[q + 1] = B.row_begin[q] + P.rows;
-        const int64_t rpw = 32 / P.desc.n;
-        B.unit_begin[q + 1] = B.unit_begin[q] + (P.rows + rpw - 1) / rpw;
         B.nnz_bound = (B.nnz_bound > INT64_MAX - P.nnz_bound) ? INT64_MAX
                                                               : B.nnz_bound + P.nnz_bound;
-        B.smem_count = std::max(B.smem_count, P.desc.tree_smem_count);
-        B.smem_emit = std::max(B.smem_emit, P.desc.tree_smem_emit);
+        B.walk_core = std::max(B.walk_core, P.desc.walk_core);
+        B.nm = std::max(B.nm, P.desc.n);
         h = mix(h, P.hash);
     }
     B.rows = B.row_begin[count];
-    B.units = B.unit_begin[count];
-    h = mix(h, (uint64_t)B.tune.count_warps | ((uint64_t)B.tune.emit_warps << 8) |
-                   ((uint64_t)B.tune.count_k << 16) | ((uint64_t)B.tune.emit_k << 24));
-    h = mix(h, (uint64_t)B.tune.count_smem | ((uint64_t)B.tune.emit_smem << 32));
-    B.hash = h;
+    if (B.prec == PREC_FP32_SOUND &&
+        walk_smem_bytes(B.walk_core, B.nm, true) > IMPACT_WALK_SMEM_MAX)
+        return fail(IMPACT_ERR_ARG, "the batch's windows need more shared memory than a warp has");
+    B.hash = h;   // launch shapes change no result: they are not part of the identity
     return IMPACT_OK;
 }
 
@@ -138,9 +129,7 @@ BatchLayout batch_layout(const Batch &B)
     const int count = B.count();
     L.index = put(sizeof(BatchIndex));
     L.row_begin = put((size_t)(count + 1) * 8);
-    L.unit_begin = put((size_t)(count + 1) * 8);
     L.descs = put((size_t)count * 8);
-    L.recs = put((size_t)count * 8);
     L.tables.resize(count);
     L.tl.resize(count);
     for (int q = 0; q < count; ++q) {
@@ -151,11 +140,7 @@ BatchLayout batch_layout(const Batch &B)
     L.status = put(64);
     L.counter = put(64);
     L.scan = put((size_t)impact::scan_scratch_elems(B.rows) * 8);
-    L.rec.resize(count);
-    for (int q = 0; q < count; ++q) {
-        const Plan &P = B.plans[q];
-        L.rec[q] = put(B.prec == PREC_FP32_SOUND ? (size_t)P.rows * P.desc.rec_stride : 0);
-    }
+    L.lb = put(B.prec == PREC_FP32_SOUND ? (size_t)B.rows * 8 : 0);
     L.total = o;
     return L;
 }
@@ -191,16 +176,39 @@ impact_status get_work(const Batch &B, const impact_csr *out, cudaStream_t st, W
         W.owned = false;
         return IMPACT_OK;
     }
-    CK(cudaMallocAsync((void **)&W.base, W.L.total, st));
+    CK(dev_malloc_async(&W.base, W.L.total, st));
     W.owned = true;
     return IMPACT_OK;
 }
 
 impact_status release(Work &W, cudaStream_t st)
 {
-    if (W.owned && W.base) CK(cudaFreeAsync(W.base, st));
+    unsigned char *b = W.base;
     W.base = nullptr;
+    if (W.owned && b) CK(dev_free_async(b, st));
     return IMPACT_OK;
+}
+
+// Releases a library-owned workspace on every return path that did not
+// release it already.
+struct WorkHold {
+    Work &W;
+    cudaStream_t st;
+    ~WorkHold() { release(W, st); }
+};
+
+// Frees the arrays of a library-owned result (stream-ordered) and clears
+// them, keeping the caller's workspace fields.
+void free_owned(impact_csr *out, cudaStream_t st)
+{
+    void *ptrs[] = {out->row_ptr, out->col, out->lo, out->up, out->sink_lo,
+                    out->sink_up, out->trunc, out->row_flags};
+    for (void *p : ptrs) dev_free_async(p, st);
+    void *ws = out->workspace;
+    int64_t wsb = out->workspace_bytes;
+    memset(out, 0, sizeof(*out));
+    out->workspace = ws;
+    out->workspace_bytes = wsb;
 }
 
 // Copies the batch index, the descriptors and the tables into the workspace.
@@ -213,20 +221,14 @@ impact_status upload(const Batch &B, Work &W, cudaStream_t st)
     memset(&bi, 0, sizeof(bi));
     bi.count = count;
     bi.rows = B.rows;
-    bi.units = B.units;
     bi.row_begin = (const int64_t *)(W.base + L.row_begin);
-    bi.unit_begin = (const int64_t *)(W.base + L.unit_begin);
     bi.desc = (const ImpactDesc *const *)(W.base + L.descs);
-    bi.rec = (unsigned char *const *)(W.base + L.recs);
     bi.next_row = W.counter();
     memcpy(host.data() + L.index, &bi, sizeof(bi));
     memcpy(host.data() + L.row_begin, B.row_begin.data(), (size_t)(count + 1) * 8);
-    memcpy(host.data() + L.unit_begin, B.unit_begin.data(), (size_t)(count + 1) * 8);
     for (int q = 0; q < count; ++q) {
         const ImpactDesc *d = W.desc(q);
-        unsigned char *r = B.prec == PREC_FP32_SOUND ? W.base + L.rec[q] : nullptr;
         memcpy(host.data() + L.descs + 8 * (size_t)q, &d, 8);
-        memcpy(host.data() + L.recs + 8 * (size_t)q, &r, 8);
         impact::pack_tables(B.plans[q], host.data() + L.tables[q], W.base + L.tables[q],
                             B.images[q]);
     }
@@ -272,9 +274,14 @@ impact_status check_row_arrays(const impact_csr *out)
 
 impact_status status_result(uint32_t status)
 {
+    if (status & IMPACT_STATUS_TIMEOUT)
+        return fail(IMPACT_ERR_TIMEOUT, "a row's look-back wait for the rows before it gave up");
+    if (status & IMPACT_STATUS_INTERNAL)
+        return fail(IMPACT_ERR_CUDA, "internal: the walk's step guard ran out");
     if (status & IMPACT_STATUS_TABLE_OVERFLOW)
         return fail(IMPACT_ERR_ARG,
-                    "a row's windows exceeded the per-row factor staging (raise the cutoff)");
+                    "a row's window exceeded the planner's bound (caller images wider than "
+                    "128 cells in a dimension): raise the cutoff or use fewer cells");
     if (status & IMPACT_STATUS_EMIT_MISMATCH)
         return fail(IMPACT_ERR_CUDA, "internal: the emit pass disagreed with the count pass");
     if (status & IMPACT_STATUS_UNSOUND)
@@ -296,46 +303,80 @@ impact::RowOutputs shifted(const impact::RowOutputs &o, int64_t rb, int64_t rows
     return s;
 }
 
-// count pass + scan: row_ptr, sink_lo, sink_up, trunc, row_flags
-impact_status run_count(const Batch &B, const Work &W, const impact_csr *out, cudaStream_t st)
+// FP32 walk launches of one pass over the batch's rows, in chunks of
+// `chunk_rows` rows (0: one launch) in row order on `st`; `counter` is the
+// pass's row counter, reset before each launch.
+cudaError_t walk_pass(const Batch &B, const Work &W, int mode, int warps,
+                      const impact::RowOutputs &o, unsigned long long *counter,
+                      int64_t chunk_rows, cudaStream_t st)
+{
+    const int64_t step = chunk_rows > 0 ? chunk_rows : std::max<int64_t>(B.rows, 1);
+    for (int64_t r0 = 0; r0 < B.rows; r0 += step) {
+        cudaError_t e = cudaMemsetAsync(counter, 0, 8, st);
+        if (e == cudaSuccess)
+            e = impact::launch_walk_fp32(W.index(), r0, std::min(B.rows, r0 + step), B.nm,
+                                         B.walk_core, warps, mode, o,
+                                         mode == WALK_EMIT ? nullptr : W.lb(), B.tune.faults, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// count pass: row_ptr (row pointers and the total), sink_lo, sink_up, trunc,
+// row_flags. FP32: one walk whose look-back writes the row pointers; FP64:
+// per-row counts, then the scan.
+impact_status run_count(const Batch &B, const Work &W, const impact_csr *out, cudaStream_t st,
+                        int64_t chunk_rows)
 {
     CK(cudaMemsetAsync(W.status(), 0, 64, st));
     impact::RowOutputs o{out->row_ptr, nullptr, nullptr, nullptr, out->sink_lo, out->sink_up,
                          out->trunc, out->row_flags, W.status(), -1, B.rows};
     if (B.prec == PREC_FP32_SOUND) {
-        CK(cudaMemsetAsync(W.counter(), 0, 16, st));
-        CK(impact::launch_setup_fp32(W.index(), B.units, W.status(), out->sink_lo, out->sink_up,
-                                     out->trunc, st));
-        CK(impact::launch_tree_fp32(W.index(), B.rows, B.smem_count, B.tune.count_warps, false, o,
-                                    st));
-    } else {
-        for (int q = 0; q < B.count(); ++q)
-            CK(impact::launch_rows(W.desc(q), B.prec, false, 0, B.plans[q].rows,
-                                   shifted(o, B.row_begin[q], B.rows), st));
+        if (B.rows > 0) CK(cudaMemsetAsync(W.lb(), 0, (size_t)B.rows * 8, st));
+        else CK(cudaMemsetAsync(out->row_ptr, 0, 8, st));
+        CK(walk_pass(B, W, WALK_COUNT, B.tune.count_warps, o, W.counter(), chunk_rows, st));
+        return IMPACT_OK;
     }
+    for (int q = 0; q < B.count(); ++q)
+        CK(impact::launch_rows(W.desc(q), B.prec, false, 0, B.plans[q].rows,
+                               shifted(o, B.row_begin[q], B.rows), st));
     CK(impact::launch_scan(out->row_ptr, B.rows, W.scan(), st));
     return IMPACT_OK;
 }
 
-// emit pass; `tables_ready`: the FP32 records in W are valid for B
+// emit pass at the row pointers in out->row_ptr
 impact_status run_emit(const Batch &B, const Work &W, const impact_csr *out, int64_t capacity,
-                       bool tables_ready, cudaStream_t st)
+                       cudaStream_t st, int64_t chunk_rows)
 {
     impact::RowOutputs o{out->row_ptr, out->col, out->lo, out->up, nullptr, nullptr, nullptr,
                          nullptr, W.status(), capacity, B.rows};
     if (B.prec == PREC_FP32_SOUND) {
-        if (!tables_ready) {   // rebuild the records; the row outputs stay as counted
-            CK(impact::launch_setup_fp32(W.index(), B.units, W.status(), nullptr, nullptr, nullptr,
-                                         st));
-        }
-        CK(cudaMemsetAsync(W.counter() + 1, 0, 8, st));
-        CK(impact::launch_tree_fp32(W.index(), B.rows, B.smem_emit, B.tune.emit_warps, true, o,
-                                    st));
+        CK(walk_pass(B, W, WALK_EMIT, B.tune.emit_warps, o, W.counter() + 1, chunk_rows, st));
     } else {
         for (int q = 0; q < B.count(); ++q)
             CK(impact::launch_rows(W.desc(q), B.prec, true, 0, B.plans[q].rows,
                                    shifted(o, B.row_begin[q], B.rows), st));
     }
+    return IMPACT_OK;
+}
+
+// the whole build into arrays of known capacity: FP32 in one pass (each row
+// finds its offset by the look-back and writes its pairs), FP64 as count,
+// scan and emit
+impact_status run_fused(const Batch &B, const Work &W, const impact_csr *out, int64_t capacity,
+                        cudaStream_t st, int64_t chunk_rows)
+{
+    if (B.prec != PREC_FP32_SOUND) {
+        impact_status s = run_count(B, W, out, st, chunk_rows);
+        if (s != IMPACT_OK) return s;
+        return run_emit(B, W, out, capacity, st, chunk_rows);
+    }
+    CK(cudaMemsetAsync(W.status(), 0, 64, st));
+    if (B.rows > 0) CK(cudaMemsetAsync(W.lb(), 0, (size_t)B.rows * 8, st));
+    else CK(cudaMemsetAsync(out->row_ptr, 0, 8, st));
+    impact::RowOutputs o{out->row_ptr, out->col, out->lo, out->up, out->sink_lo, out->sink_up,
+                         out->trunc, out->row_flags, W.status(), capacity, B.rows};
+    CK(walk_pass(B, W, WALK_FUSED, B.tune.count_warps, o, W.counter(), chunk_rows, st));
     return IMPACT_OK;
 }
 
@@ -374,6 +415,7 @@ impact_status do_count(const Batch &B, impact_csr *out, cudaStream_t st)
     configure_pool_once();
     Work W;
     if ((s = get_work(B, out, st, W)) != IMPACT_OK) return s;
+    WorkHold hold{W, st};
     if (!W.owned) ws_tag(W.base, 0);
     if ((s = upload(B, W, st)) != IMPACT_OK) return s;
     if ((s = run_count(B, W, out, st)) != IMPACT_OK) return s;
@@ -394,6 +436,7 @@ impact_status do_emit(const Batch &B, impact_csr *out, cudaStream_t st)
 {
     impact_status s;
     if (!is_device_ptr(out->row_ptr)) return fail(IMPACT_ERR_ARG, "row_ptr must be a device array");
+    if (out->nnz < 0) return fail(IMPACT_ERR_ARG, "out->nnz (the capacity) must be >= 0");
     impact_csr view;
     if ((s = pair_view(out, view)) != IMPACT_OK) return s;
     configure_pool_once();
@@ -406,57 +449,58 @@ impact_status do_emit(const Batch &B, impact_csr *out, cudaStream_t st)
     }
     Work W;
     if ((s = get_work(B, out, st, W)) != IMPACT_OK) return s;
+    WorkHold hold{W, st};
     if (!ready) {
         if ((s = upload(B, W, st)) != IMPACT_OK) return s;
     } else {
         CK(cudaMemsetAsync(W.status(), 0, 64, st));
     }
-    if ((s = run_emit(B, W, &view, out->nnz, ready, st)) != IMPACT_OK) return s;
+    if ((s = run_emit(B, W, &view, out->nnz, st)) != IMPACT_OK) return s;
+    uint32_t status = 0;
+    CK(cudaMemcpyAsync(&status, W.status(), 4, cudaMemcpyDeviceToHost, st));
     if ((s = release(W, st)) != IMPACT_OK) return s;
+    CK(cudaStreamSynchronize(st));
     out->rows = B.rows;
-    return IMPACT_OK;
+    if (status & IMPACT_STATUS_CAPACITY)
+        return fail(IMPACT_ERR_CAPACITY, "row_ptr[rows] exceeds the capacity out->nnz");
+    return status_result(status);
 }
 
-impact_status do_build(const Batch &B, impact_csr *out, cudaStream_t st)
+impact_status build_into(const Batch &B, impact_csr *out, bool lib_owned, cudaStream_t st)
 {
     impact_status s;
-    configure_pool_once();
-    const bool lib_owned = (out->col == nullptr);
     const size_t vbytes = B.prec == PREC_FP32_SOUND ? 4 : 8;
     if (lib_owned) {
-        void *ws = out->workspace;
-        int64_t wsb = out->workspace_bytes;
-        memset(out, 0, sizeof(*out));
-        out->workspace = ws;
-        out->workspace_bytes = wsb;
-        CK(cudaMallocAsync((void **)&out->row_ptr, (B.rows + 1) * 8, st));
-        CK(cudaMallocAsync((void **)&out->sink_lo, B.rows * 8, st));
-        CK(cudaMallocAsync((void **)&out->sink_up, B.rows * 8, st));
-        CK(cudaMallocAsync((void **)&out->trunc, B.rows * 8, st));
-        CK(cudaMallocAsync((void **)&out->row_flags, B.rows * 4, st));
-        out->owned = 1;
-    } else {
-        if ((s = check_row_arrays(out)) != IMPACT_OK) return s;
+        CK(dev_malloc_async(&out->row_ptr, (B.rows + 1) * 8, st));
+        CK(dev_malloc_async(&out->sink_lo, B.rows * 8, st));
+        CK(dev_malloc_async(&out->sink_up, B.rows * 8, st));
+        CK(dev_malloc_async(&out->trunc, B.rows * 8, st));
+        CK(dev_malloc_async(&out->row_flags, B.rows * 4, st));
     }
     Work W;
     if ((s = get_work(B, out, st, W)) != IMPACT_OK) return s;
+    WorkHold hold{W, st};
     if (!W.owned) ws_tag(W.base, 0);
     if ((s = upload(B, W, st)) != IMPACT_OK) return s;
-    if ((s = run_count(B, W, out, st)) != IMPACT_OK) return s;
     int64_t capacity = out->nnz;
-    if (lib_owned) {
+    if (lib_owned) {   // the output size is known after the count pass
+        if ((s = run_count(B, W, out, st)) != IMPACT_OK) return s;
         int64_t nnz = 0;
         CK(cudaMemcpyAsync(&nnz, out->row_ptr + B.rows, 8, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         size_t k = (size_t)std::max<int64_t>(nnz, 1);
-        CK(cudaMallocAsync((void **)&out->col, k * 4, st));
-        CK(cudaMallocAsync(&out->lo, k * vbytes, st));
-        CK(cudaMallocAsync(&out->up, k * vbytes, st));
+        CK(dev_malloc_async(&out->col, k * 4, st));
+        CK(dev_malloc_async(&out->lo, k * vbytes, st));
+        CK(dev_malloc_async(&out->up, k * vbytes, st));
         capacity = nnz;
+        impact_csr view;
+        if ((s = pair_view(out, view)) != IMPACT_OK) return s;
+        if ((s = run_emit(B, W, &view, capacity, st)) != IMPACT_OK) return s;
+    } else {   // caller capacity: one pass
+        impact_csr view;
+        if ((s = pair_view(out, view)) != IMPACT_OK) return s;
+        if ((s = run_fused(B, W, &view, capacity, st)) != IMPACT_OK) return s;
     }
-    impact_csr view;
-    if ((s = pair_view(out, view)) != IMPACT_OK) return s;
-    if ((s = run_emit(B, W, &view, capacity, true, st)) != IMPACT_OK) return s;
     int64_t nnz = 0;
     uint32_t status = 0;
     CK(cudaMemcpyAsync(&nnz, out->row_ptr + B.rows, 8, cudaMemcpyDeviceToHost, st));
@@ -469,6 +513,34 @@ impact_status do_build(const Batch &B, impact_csr *out, cudaStream_t st)
         return fail(IMPACT_ERR_CAPACITY, "output capacity " + std::to_string(capacity) +
                                              " < needed pairs " + std::to_string(nnz));
     return status_result(status);
+}
+
+impact_status do_build(const Batch &B, impact_csr *out, cudaStream_t st)
+{
+    configure_pool_once();
+    const bool lib_owned = (out->col == nullptr);
+    if (lib_owned) {
+        void *ws = out->workspace;
+        int64_t wsb = out->workspace_bytes;
+        memset(out, 0, sizeof(*out));
+        out->workspace = ws;
+        out->workspace_bytes = wsb;
+        out->owned = 1;
+    } else {
+        impact_status s;
+        if ((s = check_row_arrays(out)) != IMPACT_OK) return s;
+        if (out->nnz < 0) return fail(IMPACT_ERR_ARG, "out->nnz (the capacity) must be >= 0");
+    }
+    impact_status s = build_into(B, out, lib_owned, st);
+    // a library-owned result that failed is released whole (an UNSOUND one is
+    // complete and is kept: row_flags tells which rows)
+    if (lib_owned && s != IMPACT_OK && s != IMPACT_ERR_UNSOUND) {
+        std::string msg = g_last_error;
+        free_owned(out, st);
+        cudaStreamSynchronize(st);
+        fail(s, msg);
+    }
+    return s;
 }
 
 impact_request single(const impact_system *sys, const impact_grid *grid,
@@ -711,6 +783,7 @@ impact_status impact_graph_create(const impact_request *reqs, int count,
     if ((s = make_batch(reqs, count, precision, tuning, B)) != IMPACT_OK) return s;
     if ((s = check_row_arrays(out)) != IMPACT_OK) return s;
     if (!out->col) return fail(IMPACT_ERR_ARG, "a graph writes into caller-owned col/lo/up");
+    if (out->nnz < 0) return fail(IMPACT_ERR_ARG, "out->nnz (the capacity) must be >= 0");
     impact_csr view;
     if ((s = pair_view(out, view)) != IMPACT_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
@@ -722,8 +795,8 @@ impact_status impact_graph_create(const impact_request *reqs, int count,
     auto cleanup = [&](impact_status r) {
         if (g->exec) cudaGraphExecDestroy(g->exec);
         if (g->graph) cudaGraphDestroy(g->graph);
-        if (g->h_result) cudaFreeHost(g->h_result);
-        if (g->own_ws) cudaFree(g->own_ws);
+        host_free(g->h_result);
+        dev_free(g->own_ws);
         delete g;
         return r;
     };
@@ -733,11 +806,11 @@ impact_status impact_graph_create(const impact_request *reqs, int count,
         W.base = (unsigned char *)out->workspace;
         ws_tag(W.base, 0);
     } else {
-        cudaError_t e = cudaMalloc((void **)&g->own_ws, W.L.total);
+        cudaError_t e = dev_malloc(&g->own_ws, W.L.total);
         if (e != cudaSuccess) return cleanup(fail(IMPACT_ERR_OOM, cudaGetErrorString(e)));
         W.base = g->own_ws;
     }
-    if (cudaMallocHost((void **)&g->h_result, 16) != cudaSuccess)
+    if (host_malloc(&g->h_result, 16) != cudaSuccess)
         return cleanup(fail(IMPACT_ERR_OOM, "pinned result word"));
     if ((s = upload(B, W, st)) != IMPACT_OK) return cleanup(s);
     if (cudaStreamSynchronize(st) != cudaSuccess)
@@ -749,8 +822,7 @@ impact_status impact_graph_create(const impact_request *reqs, int count,
     impact_csr o = view;
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
     if (e == cudaSuccess) {
-        s = run_count(B, W, &o, cs);
-        if (s == IMPACT_OK) s = run_emit(B, W, &o, g->capacity, true, cs);
+        s = run_fused(B, W, &o, g->capacity, cs);
         if (s == IMPACT_OK) {
             cudaMemcpyAsync(g->h_result, o.row_ptr + B.rows, 8, cudaMemcpyDeviceToHost, cs);
             cudaMemcpyAsync(g->h_result + 1, W.status(), 4, cudaMemcpyDeviceToHost, cs);
@@ -795,8 +867,8 @@ impact_status impact_graph_destroy(impact_graph *graph)
     if (!graph) return IMPACT_OK;
     if (graph->exec) cudaGraphExecDestroy(graph->exec);
     if (graph->graph) cudaGraphDestroy(graph->graph);
-    if (graph->h_result) cudaFreeHost(graph->h_result);
-    if (graph->own_ws) cudaFree(graph->own_ws);
+    host_free(graph->h_result);
+    dev_free(graph->own_ws);
     delete graph;
     return IMPACT_OK;
 }
@@ -819,25 +891,26 @@ impact_status impact_batch_tune(const impact_request *reqs, int count,
     configure_pool_once();
     Batch B0;
     if ((s = make_batch(reqs, count, precision, nullptr, B0)) != IMPACT_OK) return s;
-    bool any3 = false;
-    for (const Plan &P : B0.plans) any3 |= P.desc.n >= 3;
     Work W;
     impact_csr wout = *out;
     wout.workspace = nullptr;   // the tuner keeps its own scratch
     if ((s = get_work(B0, &wout, st, W)) != IMPACT_OK) return s;
+    WorkHold hold{W, st};
+    if ((s = upload(B0, W, st)) != IMPACT_OK) return s;
+    if ((s = run_count(B0, W, out, st)) != IMPACT_OK) return s;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    auto timed = [&](const impact_tuning &t, bool emit, double &ms) -> impact_status {
-        Batch B;
-        impact_status r = make_batch(reqs, count, precision, &t, B);
-        if (r != IMPACT_OK) return r;
-        if ((r = upload(B, W, st)) != IMPACT_OK) return r;
-        if ((r = run_count(B, W, out, st)) != IMPACT_OK) return r;
+    // pass 0: count, 1: emit, 2: count and emit in one pass
+    auto timed = [&](int warps, int pass, double &ms) -> impact_status {
+        Batch B = B0;
+        B.tune.count_warps = B.tune.emit_warps = warps;
         ms = 1e30;
         for (int i = 0; i < reps; ++i) {
             CK(cudaEventRecord(e0, st));
-            r = emit ? run_emit(B, W, out, out->nnz, true, st) : run_count(B, W, out, st);
+            impact_status r = pass == 0   ? run_count(B, W, out, st)
+                              : pass == 1 ? run_emit(B, W, out, out->nnz, st)
+                                          : run_fused(B, W, out, out->nnz, st);
             if (r != IMPACT_OK) return r;
             CK(cudaEventRecord(e1, st));
             CK(cudaEventSynchronize(e1));
@@ -850,56 +923,38 @@ impact_status impact_batch_tune(const impact_request *reqs, int count,
         if (status & ~IMPACT_STATUS_UNSOUND) ms = 1e30;   // a shape that cannot run this batch
         return IMPACT_OK;
     };
-    const int warps[2] = {4, 8};
-    const int smem[4] = {4096, 6144, 8192, 12288};
-    impact_tuning cur;
-    memset(&cur, 0, sizeof(cur));
-    double best_count = 1e30, best_emit = 1e30;
-    impact_tuning tb = cur;
-    for (int k = (any3 ? 1 : 0); k <= (any3 ? 3 : 0) && s == IMPACT_OK; ++k)
-        for (int w : warps)
-            for (int m : smem) {
-                impact_tuning t = cur;
-                t.count_warps = w;
-                t.count_smem_target = m;
-                t.count_k = k;
-                double ms;
-                s = timed(t, false, ms);
-                if (s != IMPACT_OK) break;
-                if (ms < best_count) {
-                    best_count = ms;
-                    tb = t;
-                }
-            }
     const bool can_emit = out->col != nullptr;
-    if (s == IMPACT_OK && can_emit) {
-        const impact_tuning base = tb;
-        for (int k = (any3 ? 1 : 0); k <= (any3 ? 3 : 0) && s == IMPACT_OK; k += 2)
-            for (int w : warps)
-                for (int m : smem) {
-                    impact_tuning t = base;
-                    t.emit_warps = w;
-                    t.emit_smem_target = m;
-                    t.emit_k = k;
-                    double ms;
-                    s = timed(t, true, ms);
-                    if (s != IMPACT_OK) break;
-                    if (ms < best_emit) {
-                        best_emit = ms;
-                        tb = t;
-                    }
-                }
+    const int warps[4] = {2, 4, 6, 8};
+    impact_tuning tb;
+    memset(&tb, 0, sizeof(tb));
+    double best_a = 1e30, best_b = 1e30;
+    // the count (or, with output arrays, the one-pass) shape, then the emit shape
+    for (int w : warps) {
+        double ms;
+        if ((s = timed(w, can_emit ? 2 : 0, ms)) != IMPACT_OK) break;
+        if (ms < best_a) {
+            best_a = ms;
+            tb.count_warps = w;
+        }
     }
+    if (s == IMPACT_OK && can_emit)
+        for (int w : warps) {
+            double ms;
+            if ((s = timed(w, 1, ms)) != IMPACT_OK) break;
+            if (ms < best_b) {
+                best_b = ms;
+                tb.emit_warps = w;
+            }
+        }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     impact_status r2 = release(W, st);
     if (s != IMPACT_OK) return s;
     if (r2 != IMPACT_OK) return r2;
-    if (best_count >= 1e30) return fail(IMPACT_ERR_ARG, "no launch shape ran this batch");
+    if (best_a >= 1e30) return fail(IMPACT_ERR_ARG, "no launch shape ran this batch");
     if (tb.emit_warps == 0) tb.emit_warps = IMPACT_TREE_WARPS;
-    if (tb.emit_smem_target == 0) tb.emit_smem_target = IMPACT_TREE_SMEM_EMIT;
     *best = tb;
-    if (best_ms) *best_ms = best_count + (can_emit ? best_emit : 0.0);
+    if (best_ms) *best_ms = best_a;
     return IMPACT_OK;
 }
 
@@ -910,7 +965,7 @@ impact_status impact_free(impact_csr *out)
     void *ptrs[] = {out->row_ptr, out->col, out->lo, out->up, out->sink_lo,
                     out->sink_up, out->trunc, out->row_flags};
     for (void *p : ptrs)
-        if (p) CK(cudaFree(p));
+        if (p) CK(dev_free(p));
     void *ws = out->workspace;
     int64_t wsb = out->workspace_bytes;
     memset(out, 0, sizeof(*out));
@@ -964,6 +1019,7 @@ impact_status impact_region_vectors(const impact_system *sys, const impact_grid 
     Work W;
     s = get_work(batch, nullptr, st, W);
     if (s != IMPACT_OK) return s;
+    WorkHold hold{W, st};
     s = upload(batch, W, st);
     if (s == IMPACT_OK) {
         cudaError_t e = launch_regions(W.desc(0), batch.rows, B, mode == IMPACT_REGION_CELL_SUM,

@@ -22,11 +22,10 @@ struct ImpactDim {
     int N;                // number of cells
     int stride;           // C-order column stride
     int edge_off;         // offset of this dim's N+1 FP64 edges in the edge table
-    int wcap;             // largest window (cells) a row can stage in this dim
+    int wcap;             // largest window (cells) of a row in this dim
     float delta_cells;    // delta / h
     uint32_t div_m;       // fast division by N: q = (umulhi(x, div_m) + x) >> div_s
     int div_s;
-    int rec_off;          // FP32 path: offset (entries) of this dim's tables in a row record
 };
 
 // Kinds (match impact_kind) and precisions (match impact_precision).
@@ -75,18 +74,10 @@ struct ImpactDesc {
     // to place the windows, with slack).
     uint32_t inp_div_m;       // fast division by n_inputs
     int inp_div_s;
-    int rec_stride;           // bytes per row record in the workspace
-    int tsum_cap;             // factor entries a row record holds (all dims)
-    int tree_k[2];            // prefix-tree walk, [0] count pass, [1] emit pass: how the
-                              // last dimensions are walked: 1 leaf batches, 2 two
-                              // dimensions serially per lane (count), 3 two dimensions
-                              // lane-parallel
-    int ring_log2[2][IMPACT_MAX_DIM];   // prefix-tree walk: log2 capacity of the node ring
-                                        // of each level, [0] count pass, [1] emit pass
-    int ring_off[2][IMPACT_MAX_DIM];    // prefix-tree walk: first node of each ring
-    int pool_cap[2];          // prefix-tree walk: nodes of all rings, per pass
-    int tree_smem_count;      // prefix-tree walk: shared-memory bytes per warp, count pass
-    int tree_smem_emit;       // prefix-tree walk: shared-memory bytes per warp, emit pass
+    int tsum_cap;             // window targets of a row, all dims (at most)
+    int edge_cap;             // window edges of a row plus 2 domain edges per dim, + 1 each
+    int walk_core;            // shared-memory bytes of one warp of the walk (no epilogue)
+    int pad2;
     const float2 *ea;         // per dim: N+1 edges in erf units, offset edge_off
     const float2 *ta_lo;      // AFFINE [n][n][Nmax]: min term A_dk x_k in erf units of d
     const float2 *ta_hi;      //                      max term
@@ -101,17 +92,12 @@ struct ImpactDesc {
 };
 
 // Several builds handled by one launch of each FP32 kernel: problem q owns the
-// global rows [row_begin[q], row_begin[q+1]) of the concatenated output and
-// the setup units [unit_begin[q], unit_begin[q+1]) (a unit is the 32/n rows
-// one warp prepares); a single build is a batch of one.
+// global rows [row_begin[q], row_begin[q+1]) of the concatenated output; a
+// single build is a batch of one.
 struct BatchIndex {
     int count;                          // problems
     int64_t rows;                       // total rows
-    int64_t units;                      // setup work units: 32/n rows of one problem
     const int64_t *row_begin;           // [count + 1]
-    const int64_t *unit_begin;          // [count + 1]
     const ImpactDesc *const *desc;      // [count] device descriptors
-    unsigned char *const *rec;          // [count] FP32 per-row records
     unsigned long long *next_row;       // [2] row counters of the count / emit walk
 };
-

@@ -228,29 +228,31 @@ rows_fp64(const ImpactDesc *__restrict__ Dp, int64_t row_begin, int64_t row_end,
             total += S.w[d];
         }
         __syncwarp();
-        if (total > kTab) {
-            if (lane == 0) {
-                atomicOr(status, IMPACT_STATUS_TABLE_OVERFLOW);
-                if (!EMIT) row_ptr[row] = 0;
-            }
-            continue;
-        }
         // upper factors of the window (used only to trim the windows and for
-        // the truncated-mass sums; the pairs below recompute every factor)
-        for (int e = lane; e < total; e += 32) {
-            int d = 0;
-            while (d + 1 < n && e >= S.cum[d + 1]) ++d;
-            const ImpactDim &g = D.dim[d];
-            S.U[e] = up64(g, D.edges + g.edge_off, S.a[d] + e - S.cum[d], S.mlo[d], S.mhi[d]);
+        // the truncated-mass sums; the pairs below recompute every factor),
+        // staged when they fit, else evaluated again where they are read
+        const bool staged = total <= kTab;
+        if (staged) {
+            for (int e = lane; e < total; e += 32) {
+                int d = 0;
+                while (d + 1 < n && e >= S.cum[d + 1]) ++d;
+                const ImpactDim &g = D.dim[d];
+                S.U[e] = up64(g, D.edges + g.edge_off, S.a[d] + e - S.cum[d], S.mlo[d], S.mhi[d]);
+            }
         }
         __syncwarp();
         bool empty = false;
         for (int d = 0; d < n; ++d) {
             const int base = S.cum[d], W = S.w[d];
+            const ImpactDim &gd = D.dim[d];
+            auto Uw = [&](int t) {
+                return staged ? S.U[base + t]
+                              : up64(gd, D.edges + gd.edge_off, S.a[d] + t, S.mlo[d], S.mhi[d]);
+            };
             int first = -1, last = -1;
             for (int c0 = 0; c0 < W; c0 += 32) {
                 int t = c0 + lane;
-                bool pass = t < W && S.U[base + t] >= cut;
+                bool pass = t < W && Uw(t) >= cut;
                 unsigned bal = __ballot_sync(0xffffffffu, pass);
                 if (bal) {
                     if (first < 0) first = c0 + __ffs(bal) - 1;
@@ -261,7 +263,7 @@ rows_fp64(const ImpactDesc *__restrict__ Dp, int64_t row_begin, int64_t row_end,
             for (int c0 = 0; c0 < W; c0 += 32) {
                 int t = c0 + lane;
                 if (t < W) {
-                    double v = S.U[base + t];
+                    double v = Uw(t);
                     if (first >= 0 && t >= first && t <= last) sw += v;
                     else ow += v;
                 }

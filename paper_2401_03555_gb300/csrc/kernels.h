@@ -7,19 +7,18 @@
 
 #include "impact_desc.h"
 
-#define IMPACT_TABLE_MAX 512              // factor entries staged per row (all dims), FP64
-#define IMPACT_WINDOW_MAX 64              // FP32 path: window cells per (row, dim)
-#define IMPACT_TSUM_MAX 256               // FP32 path: factor entries per row record
-#define IMPACT_TREE_SEG 512               // FP32 path: pairs staged per leaf batch
-#define IMPACT_TREE_HDR 256               // FP32 path: per-row scalars per warp (bytes)
-#define IMPACT_TREE_SMEM_COUNT 6144       // FP32 path: per-warp shared memory aimed for, count (default)
-#define IMPACT_TREE_SMEM_EMIT 8192        // FP32 path: per-warp shared memory aimed for, emit (default)
-#define IMPACT_TREE_WARPS 4               // FP32 path: warps per block of the walk (default)
+#define IMPACT_TABLE_MAX 512              // FP64: window factors a warp stages (wider: re-evaluated)
+#define IMPACT_WALK_CAP 128               // FP32 walk: nodes per level list (one chunk)
+#define IMPACT_WALK_EPI 16                // FP32 walk: rows per FP64 epilogue batch of a warp
+#define IMPACT_WALK_SMEM_MAX (200 * 1024) // FP32 walk: shared memory of one warp at most
+#define IMPACT_TREE_WARPS 4               // FP32 walk: warps per block (default)
 #define IMPACT_TREE_WARPS_MAX 8
-#define IMPACT_STATUS_TABLE_OVERFLOW 0x1u // some row's windows exceeded IMPACT_TABLE_MAX
+#define IMPACT_STATUS_TABLE_OVERFLOW 0x1u // a row's window exceeded the planner's bound
 #define IMPACT_STATUS_UNSOUND 0x2u        // some row check proved a violation
 #define IMPACT_STATUS_CAPACITY 0x4u       // emit skipped: output capacity too small
 #define IMPACT_STATUS_EMIT_MISMATCH 0x8u  // emit found a different pair count than count
+#define IMPACT_STATUS_TIMEOUT 0x20u       // a bounded look-back wait gave up
+#define IMPACT_STATUS_INTERNAL 0x40u      // the walk's step guard ran out (broken invariant)
 
 namespace impact {
 
@@ -83,17 +82,23 @@ cudaError_t launch_regions(const ImpactDesc *d_desc, int64_t rows, const RegionB
                            bool cell_sum, bool sound, double *r_lo, double *r_up, double *a_lo,
                            double *a_up, cudaStream_t stream);
 
-// FP32-sound table path (tree_fp32.cu), every launch over a whole batch.
-int64_t record_stride(int n, int tsum_cap);
-int tree_smem_bytes(int tsum_cap, int pool_cap, bool emit);
-// `units`: warp units of the batch (BatchIndex::units); the row outputs may
-// be null (records rebuilt for an emit pass).
-cudaError_t launch_setup_fp32(const BatchIndex *d_index, int64_t units, uint32_t *status,
-                              double *sink_lo, double *sink_up, double *trunc, cudaStream_t stream);
-// `warp_smem`: shared-memory bytes of one warp (the largest of the batch);
-// `warps`: warps per block (1..8).
-cudaError_t launch_tree_fp32(const BatchIndex *d_index, int64_t rows, int warp_smem, int warps,
-                             bool emit, const RowOutputs &o, cudaStream_t stream);
+// FP32-sound path (walk_fp32.cu): one persistent kernel per pass over the
+// global rows [row_begin, row_end) of a batch (the row counter of the pass
+// zeroed before each launch; launches of one pass in row order on one
+// stream). `core_max`: the largest walk_core_bytes of the batch; `nm`: its
+// largest n; `lb`: one 8-byte look-back word per row, zeroed before the first
+// launch of a COUNT or FUSED pass.
+enum { WALK_COUNT = 0, WALK_EMIT = 1, WALK_FUSED = 2 };
+struct WalkFaults {
+    int spin_limit = 0;        // look-back sleeps before giving up (0: the default)
+    int64_t stall_row = -1;    // this row never publishes its count (-1: none)
+    int64_t fault_row = -1;    // this row's checks see an impossible sum (-1: none)
+};
+int walk_core_bytes(int n, int tsum_cap, int edge_cap);
+int walk_smem_bytes(int core_max, int nm, bool count);
+cudaError_t launch_walk_fp32(const BatchIndex *d_index, int64_t row_begin, int64_t row_end,
+                             int nm, int core_max, int warps, int mode, const RowOutputs &o,
+                             unsigned long long *lb, const WalkFaults &f, cudaStream_t stream);
 cudaError_t launch_scan(int64_t *row_ptr, int64_t n, int64_t *scratch, cudaStream_t stream);
 
 }  // namespace impact

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "../../include/impact.h"
+#include "alloc.h"
 #include "kernels.h"
 #include "pipeline.h"
 #include "plan.h"
@@ -26,6 +27,7 @@ impact_status release(Work &W, cudaStream_t st);
 bool is_device_ptr(const void *p);
 impact_status check_row_arrays(const impact_csr *out);
 impact_status pair_view(const impact_csr *out, impact_csr &v);
+void free_owned(impact_csr *out, cudaStream_t st);
 }  // namespace impact
 
 using namespace impact;
@@ -72,21 +74,30 @@ extern "C" impact_status impact_build_mc(const impact_system *sys, const impact_
     configure_pool_once();
     const bool lib_owned = (out->col == nullptr);
     const size_t vbytes = precision == IMPACT_FP32_SOUND ? 4 : 8;
+    // a library-owned result that fails is released whole
+    auto give_back = [&](impact_status r) {
+        if (lib_owned && r != IMPACT_OK) {
+            free_owned(out, st);
+            cudaStreamSynchronize(st);
+        }
+        return r;
+    };
     if (lib_owned) {
         memset(out, 0, sizeof(*out));
-        CK(cudaMallocAsync((void **)&out->row_ptr, (B.rows + 1) * 8, st));
-        CK(cudaMallocAsync((void **)&out->sink_lo, B.rows * 8, st));
-        CK(cudaMallocAsync((void **)&out->sink_up, B.rows * 8, st));
-        CK(cudaMallocAsync((void **)&out->trunc, B.rows * 8, st));
-        CK(cudaMallocAsync((void **)&out->row_flags, B.rows * 4, st));
         out->owned = 1;
+        cudaError_t e = dev_malloc_async(&out->row_ptr, (B.rows + 1) * 8, st);
+        if (e == cudaSuccess) e = dev_malloc_async(&out->sink_lo, B.rows * 8, st);
+        if (e == cudaSuccess) e = dev_malloc_async(&out->sink_up, B.rows * 8, st);
+        if (e == cudaSuccess) e = dev_malloc_async(&out->trunc, B.rows * 8, st);
+        if (e == cudaSuccess) e = dev_malloc_async(&out->row_flags, B.rows * 4, st);
+        if (e != cudaSuccess) return give_back(fail(IMPACT_ERR_OOM, "row arrays"));
     } else if ((s = check_row_arrays(out)) != IMPACT_OK) {
         return s;
     }
     Work W;
     impact_csr no_ws = *out;
     no_ws.workspace = nullptr;
-    if ((s = get_work(B, &no_ws, st, W)) != IMPACT_OK) return s;
+    if ((s = get_work(B, &no_ws, st, W)) != IMPACT_OK) return give_back(s);
     // per-call tables: draw keys [n][S], range [n][2], values u / S for
     // u = 0..S (FP64, FP32 down, FP32 up), the non-finite flag
     const int64_t S = n_samples;
@@ -95,12 +106,12 @@ extern "C" impact_status impact_build_mc(const impact_system *sys, const impact_
     const size_t total = t_keys + t_range + t_val + 2 * t_f + 16;
     unsigned char *tab = nullptr;
     s = upload(B, W, st);
-    if (s == IMPACT_OK && cudaMallocAsync((void **)&tab, total, st) != cudaSuccess)
+    if (s == IMPACT_OK && dev_malloc_async(&tab, total, st) != cudaSuccess)
         s = fail(IMPACT_ERR_OOM, "sampled-noise tables");
     auto done = [&](impact_status r) {
-        if (tab) cudaFreeAsync(tab, st);
+        dev_free_async(tab, st);
         impact_status q = release(W, st);
-        return r != IMPACT_OK ? r : q;
+        return give_back(r != IMPACT_OK ? r : q);
     };
     if (s != IMPACT_OK) return done(s);
     long long *keys = (long long *)tab;
@@ -149,9 +160,9 @@ extern "C" impact_status impact_build_mc(const impact_system *sys, const impact_
     int64_t capacity = out->nnz;
     if (lib_owned) {
         const size_t k = (size_t)std::max<int64_t>(nnz, 1);
-        if (cudaMallocAsync((void **)&out->col, k * 4, st) != cudaSuccess ||
-            cudaMallocAsync(&out->lo, k * vbytes, st) != cudaSuccess ||
-            cudaMallocAsync(&out->up, k * vbytes, st) != cudaSuccess)
+        if (dev_malloc_async(&out->col, k * 4, st) != cudaSuccess ||
+            dev_malloc_async(&out->lo, k * vbytes, st) != cudaSuccess ||
+            dev_malloc_async(&out->up, k * vbytes, st) != cudaSuccess)
             return done(fail(IMPACT_ERR_OOM, "pair arrays"));
         capacity = nnz;
     }

@@ -18,10 +18,10 @@ struct Batch {
     std::vector<Plan> plans;
     std::vector<const double *> images;   // per build: device images (IMAGES kind)
     std::vector<int64_t> row_begin;       // [count + 1] first global row of each build
-    std::vector<int64_t> unit_begin;      // [count + 1] first setup unit (32/n rows)
-    int64_t rows = 0, units = 0, nnz_bound = 0;
+    int64_t rows = 0, nnz_bound = 0;
     int prec = 0;
-    int smem_count = 0, smem_emit = 0;    // largest per-warp bytes of the walk
+    int walk_core = 0;                    // largest per-warp bytes of the walk (no epilogue)
+    int nm = 1;                           // largest dimension n of the batch
     Tuning tune;
     uint64_t hash = 0;
     int count() const { return (int)plans.size(); }
@@ -32,12 +32,12 @@ impact_status make_batch(const impact_request *reqs, int count, impact_precision
 
 // Offsets (bytes, 256-aligned) of everything in the device workspace.
 struct BatchLayout {
-    size_t index = 0, row_begin = 0, unit_begin = 0, descs = 0, recs = 0;
+    size_t index = 0, row_begin = 0, descs = 0;
     std::vector<size_t> tables;            // per build: its descriptor and tables
     std::vector<impact::TableLayout> tl;
     size_t upload_end = 0;                 // [0, upload_end) is copied from the host
     size_t status = 0, counter = 0, scan = 0;
-    std::vector<size_t> rec;               // per build: FP32 per-row records
+    size_t lb = 0;                         // FP32: one look-back word per row
     size_t total = 0;
 };
 
@@ -52,6 +52,7 @@ struct Work {
     uint32_t *status() const { return (uint32_t *)(base + L.status); }
     unsigned long long *counter() const { return (unsigned long long *)(base + L.counter); }
     int64_t *scan() const { return (int64_t *)(base + L.scan); }
+    unsigned long long *lb() const { return (unsigned long long *)(base + L.lb); }
     const ImpactDesc *desc(int q) const
     {
         return (const ImpactDesc *)(base + L.tables[q] + L.tl[q].desc);
@@ -60,11 +61,18 @@ struct Work {
 
 // Copies the batch index, the descriptors and the tables into W (stream-ordered).
 impact_status upload(const Batch &B, Work &W, cudaStream_t st);
-// count pass + row-pointer scan into out's row arrays.
-impact_status run_count(const Batch &B, const Work &W, const impact_csr *out, cudaStream_t st);
-// emit pass into out's pair arrays (`tables_ready`: W holds B's FP32 records).
+// The passes below launch the FP32 walk over all rows at once, or in chunks
+// of `chunk_rows` rows one after another on `st` (so that work on other
+// streams can take SMs between chunks); the FP64 kernels ignore chunk_rows.
+// count pass into out's row arrays (row pointers included).
+impact_status run_count(const Batch &B, const Work &W, const impact_csr *out, cudaStream_t st,
+                        int64_t chunk_rows = 0);
+// emit pass into out's pair arrays at the row pointers of a count pass.
 impact_status run_emit(const Batch &B, const Work &W, const impact_csr *out, int64_t capacity,
-                       bool tables_ready, cudaStream_t st);
+                       cudaStream_t st, int64_t chunk_rows = 0);
+// FP32: count and emit in one pass (capacity known); FP64: count, scan, emit.
+impact_status run_fused(const Batch &B, const Work &W, const impact_csr *out, int64_t capacity,
+                        cudaStream_t st, int64_t chunk_rows = 0);
 // Maps the device status word of a finished pipeline to a status code.
 impact_status status_result(uint32_t status);
 void configure_pool_once();

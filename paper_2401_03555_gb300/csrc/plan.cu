@@ -1,8 +1,8 @@
 // plan.cu -- the host planner: validates one build's arguments and computes,
 // in FP64 on the host, every per-build constant the kernels read (grid edges,
 // per-term image tables, input offsets, window margins, plateau and
-// out-of-domain constants, FP32 pair tables, tree-walk ring sizes), and packs
-// them with the descriptor into the layout of the device tables.
+// out-of-domain constants, FP32 pair tables, the walk's shared-memory sizes),
+// and packs them with the descriptor into the layout of the device tables.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -135,7 +135,7 @@ double normal_quantile_upper(double p)
 
 impact_status make_plan(const impact_system *sys, const impact_grid *grid,
                         const impact_inputs *inputs, const double *sigma, double cutoff,
-                        impact_precision precision, const Tuning &T, Plan &P)
+                        impact_precision precision, Plan &P)
 {
     if (!sys || !grid || !inputs || !sigma) return fail(IMPACT_ERR_ARG, "null argument");
     const int n = grid->n;
@@ -315,9 +315,11 @@ impact_status make_plan(const impact_system *sys, const impact_grid *grid,
         width[2] = D.dim[2].h;
     }
     // window widths: image width + 2 delta, plus the 2-cell slack and rounding
+    // (caller images: the image width is unknown here, so rows whose window
+    // is wider than 128 cells are refused at run time)
     int64_t box = 1;
-    int need = 0;
-    int tsum = 0;
+    int64_t need = 0;
+    int64_t tsum = 0;
     for (int d = 0; d < n; ++d) {
         ImpactDim &g = D.dim[d];
         int64_t w = g.N;
@@ -325,100 +327,35 @@ impact_status make_plan(const impact_system *sys, const impact_grid *grid,
             double cw = ceil((width[d] + 2.0 * g.delta) * g.inv_h) + 4.0;
             if (cw < (double)g.N) w = (int64_t)cw;
         }
-        box *= w;
-        need += (int)w;
-        g.wcap = (int)std::min<int64_t>(w, IMPACT_WINDOW_MAX);
+        box = std::min<int64_t>(box * w, cells);
+        need += w;
+        g.wcap = (int)(sys->kind == IMPACT_IMAGES ? std::min<int64_t>(w, 128) : w);
         g.delta_cells = isfinite(g.delta) ? (float)(g.delta * g.inv_h) : INFINITY;
         div_magic((uint32_t)g.N, g.div_m, g.div_s);
-        if (precision == IMPACT_FP32_SOUND && sys->kind != IMPACT_IMAGES && w > IMPACT_WINDOW_MAX)
-            return fail(IMPACT_ERR_ARG,
-                        "dimension " + std::to_string(d) + " needs a window of " +
-                            std::to_string(w) + " cells (FP32 limit " +
-                            std::to_string(IMPACT_WINDOW_MAX) +
-                            "): raise the cutoff or use fewer cells");
         tsum += g.wcap;
     }
     div_magic((uint32_t)n_inputs, D.inp_div_m, D.inp_div_s);
-    P.table_need = (sys->kind == IMPACT_IMAGES) ? -1 : need;
+    P.table_need = (sys->kind == IMPACT_IMAGES) ? -1 : (int)std::min<int64_t>(need, INT32_MAX);
     if (box > cells) box = cells;
     P.nnz_bound = box * rows;
-    if (precision == IMPACT_FP64_PLAIN && P.table_need > IMPACT_TABLE_MAX)
-        return fail(IMPACT_ERR_ARG,
-                    "the per-row windows need " + std::to_string(P.table_need) +
-                        " staged factors (limit " + std::to_string(IMPACT_TABLE_MAX) +
-                        "): raise the cutoff or use fewer cells");
     if (precision == IMPACT_FP32_SOUND) {
-        if (tsum > IMPACT_TSUM_MAX)
+        // the walk stages a row's window tables (8 bytes per target) and,
+        // during its setup, both image ends of every window edge (48 bytes
+        // per edge) in one warp's shared memory; wide windows (cutoff 0 on a
+        // fine grid, wide noise) need more of it and fewer warps per SM
+        // (at most 4096 window targets: the walk's candidate division by a
+        // window width, umulhi(e, ceil(2^32 / tw)), is exact for e < 128 tw
+        // while 128 tw^2 < 2^32)
+        if (tsum > 4096 ||
+            impact::walk_smem_bytes(impact::walk_core_bytes(n, (int)tsum, (int)tsum + 3 * n), n,
+                                    true) > IMPACT_WALK_SMEM_MAX)
             return fail(IMPACT_ERR_ARG,
                         "the per-row windows need " + std::to_string(tsum) +
-                            " staged factors (FP32 limit " + std::to_string(IMPACT_TSUM_MAX) +
-                            "): raise the cutoff or use fewer cells");
-        D.tsum_cap = tsum;
-        D.rec_stride = (int)impact::record_stride(n, tsum);
-        int ro = 0;
-        for (int d = 0; d < n; ++d) {
-            D.dim[d].rec_off = ro;
-            ro += D.dim[d].wcap;
-        }
-        // prefix-tree walk. The last dimensions: K = 1 leaf batches under the
-        // nodes of level n - 2; K = 2 (count pass) each lane walks the last two
-        // dimensions of a level n - 3 node serially (no stores to coalesce);
-        // K = 3 the last two dimensions lane-parallel (middle nodes numbered
-        // across the warp, leaf batches of them). Defaults from measurements
-        // on the 5-D, 7-D and unicycle workloads: count 2 for n >= 4 with a
-        // narrow last window, else 3; emit 3. Levels 0..Lp keep a ring of
-        // nodes each, a power of two: level 0 holds the root's children, the
-        // deepest level room for a full batch plus one parent's children; rings
-        // start large (fewer, fuller steps) and shrink from the largest while a
-        // warp's shared memory exceeds the target (more warps per SM).
-        D.tree_k[0] = n < 3 ? 1
-                      : (T.count_k >= 1 && T.count_k <= 3)
-                          ? T.count_k
-                          : ((n >= 4 && D.dim[n - 1].wcap <= 16) ? 2 : 3);
-        D.tree_k[1] = n < 3 ? 1 : (T.emit_k == 1 || T.emit_k == 3 ? T.emit_k : 3);
-        int worst = 0;
-        for (int pass = 0; pass < 2; ++pass) {
-            const int K = D.tree_k[pass];
-            const int Lp = n - 1 - (K == 1 ? 1 : 2);
-            int lg[IMPACT_MAX_DIM] = {0}, lmin[IMPACT_MAX_DIM] = {0};
-            auto log2_ceil = [](int v) {
-                int l = 0;
-                while ((1 << l) < v) ++l;
-                return l;
-            };
-            for (int k = 0; k <= Lp; ++k) {
-                const int w = D.dim[k].wcap;
-                const int need = (k == Lp) ? 32 + w : w;
-                lmin[k] = log2_ceil(need);
-                lg[k] = (k == 0 && k < Lp) ? lmin[k]
-                                           : std::max(lmin[k], log2_ceil(k == Lp ? 1024 : 512));
-            }
-            auto bytes = [&]() {
-                int pool = 0;
-                for (int k = 0; k <= Lp; ++k) pool += 1 << lg[k];
-                return impact::tree_smem_bytes(tsum, std::max(pool, 1), pass == 1);
-            };
-            const int target = pass == 0 ? T.count_smem : T.emit_smem;
-            while (bytes() > target) {
-                int big = -1;
-                for (int k = 0; k <= Lp; ++k)
-                    if (lg[k] > lmin[k] && (big < 0 || lg[k] > lg[big])) big = k;
-                if (big < 0) break;
-                --lg[big];
-            }
-            int pool = 0;
-            for (int k = 0; k < IMPACT_MAX_DIM; ++k) {
-                D.ring_log2[pass][k] = k <= Lp ? lg[k] : 0;
-                D.ring_off[pass][k] = pool;
-                if (k <= Lp) pool += 1 << lg[k];
-            }
-            D.pool_cap[pass] = std::max(pool, 1);
-            worst = std::max(worst, bytes());
-        }
-        D.tree_smem_count = impact::tree_smem_bytes(tsum, D.pool_cap[0], false);
-        D.tree_smem_emit = impact::tree_smem_bytes(tsum, D.pool_cap[1], true);
-        if ((int64_t)worst * std::max(T.count_warps, T.emit_warps) > 200 * 1024)
-            return fail(IMPACT_ERR_ARG, "the per-row windows are too wide for the FP32 tree walk");
+                            " factor entries, more than one warp's shared memory holds: "
+                            "raise the cutoff or use fewer cells");
+        D.tsum_cap = (int)tsum;
+        D.edge_cap = (int)tsum + 3 * n;
+        D.walk_core = impact::walk_core_bytes(n, D.tsum_cap, D.edge_cap);
         // tables in erf units (x / (sigma sqrt2)) as FP32 pairs, and in cells
         for (int d = 0; d < n; ++d) {
             const ImpactDim &g = D.dim[d];

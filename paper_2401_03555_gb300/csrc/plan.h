@@ -16,14 +16,12 @@ namespace impact {
 // Sets the thread's last-error message and returns `s` (api.cu).
 impact_status fail(impact_status s, const std::string &msg);
 
-// Launch shapes of the FP32 walk (impact_tuning with the defaults filled in).
+// Launch shapes of the FP32 walk (impact_tuning with the defaults filled in)
+// and its fault-injection knobs.
 struct Tuning {
     int count_warps = IMPACT_TREE_WARPS;
     int emit_warps = IMPACT_TREE_WARPS;
-    int count_smem = IMPACT_TREE_SMEM_COUNT;
-    int emit_smem = IMPACT_TREE_SMEM_EMIT;
-    int count_k = 0;   // 0: chosen per problem (1, 2, 3: see ImpactDesc::tree_k)
-    int emit_k = 0;    // 0: chosen per problem (1 or 3)
+    WalkFaults faults;
 };
 
 struct Plan {
@@ -50,7 +48,7 @@ TableLayout table_layout(const Plan &p);
 
 impact_status make_plan(const impact_system *sys, const impact_grid *grid,
                         const impact_inputs *inputs, const double *sigma, double cutoff,
-                        impact_precision precision, const Tuning &T, Plan &P);
+                        impact_precision precision, Plan &P);
 
 // Writes the descriptor and tables of P into `host` (table_layout(P).total
 // bytes) with every pointer set for the copy that will sit at `dev_base`.

@@ -31,6 +31,7 @@
 #include <vector>
 
 #include "../../include/impact.h"
+#include "alloc.h"
 #include "pipeline.h"
 
 namespace {
@@ -149,11 +150,11 @@ void impact_server::free_group(Group *g)
     cudaStream_t st = g->stream;
     void *ptrs[] = {g->row_ptr, g->sink_lo, g->sink_up, g->trunc, g->flags,
                     g->col, g->lo, g->up};
-    for (void *p : ptrs)
-        if (p) cudaFreeAsync(p, st);
-    if (g->W.base) cudaFreeAsync(g->W.base, st);
-    if (g->h_ptr) cudaFreeHost(g->h_ptr);
-    if (g->h_status) cudaFreeHost(g->h_status);
+    for (void *p : ptrs) impact::dev_free_async(p, st);
+    impact::dev_free_async(g->W.base, st);
+    if (g->h_ptr || g->h_status) cudaStreamSynchronize(st);   // pinned words the stream writes
+    impact::host_free(g->h_ptr);
+    impact::host_free(g->h_status);
     if (g->ev_count) cudaEventDestroy(g->ev_count);
     if (g->ev_emit) cudaEventDestroy(g->ev_emit);
     used -= g->held;
@@ -207,14 +208,14 @@ void impact_server::admit()
     g->W.L = impact::batch_layout(g->B);
     g->ws_bytes = align_up((int64_t)g->W.L.total);
     g->row_bytes = align_up(row_bytes_of(g->rows));
-    cudaError_t e = cudaMallocAsync((void **)&g->W.base, g->W.L.total, st);
-    if (e == cudaSuccess) e = cudaMallocAsync((void **)&g->row_ptr, (g->rows + 1) * 8, st);
-    if (e == cudaSuccess) e = cudaMallocAsync((void **)&g->sink_lo, g->rows * 8, st);
-    if (e == cudaSuccess) e = cudaMallocAsync((void **)&g->sink_up, g->rows * 8, st);
-    if (e == cudaSuccess) e = cudaMallocAsync((void **)&g->trunc, g->rows * 8, st);
-    if (e == cudaSuccess) e = cudaMallocAsync((void **)&g->flags, g->rows * 4, st);
-    if (e == cudaSuccess) e = cudaMallocHost((void **)&g->h_ptr, (take.size() + 1) * 8);
-    if (e == cudaSuccess) e = cudaMallocHost((void **)&g->h_status, 64);
+    cudaError_t e = impact::dev_malloc_async(&g->W.base, g->W.L.total, st);
+    if (e == cudaSuccess) e = impact::dev_malloc_async(&g->row_ptr, (g->rows + 1) * 8, st);
+    if (e == cudaSuccess) e = impact::dev_malloc_async(&g->sink_lo, g->rows * 8, st);
+    if (e == cudaSuccess) e = impact::dev_malloc_async(&g->sink_up, g->rows * 8, st);
+    if (e == cudaSuccess) e = impact::dev_malloc_async(&g->trunc, g->rows * 8, st);
+    if (e == cudaSuccess) e = impact::dev_malloc_async(&g->flags, g->rows * 4, st);
+    if (e == cudaSuccess) e = impact::host_malloc(&g->h_ptr, (take.size() + 1) * 8);
+    if (e == cudaSuccess) e = impact::host_malloc(&g->h_status, 64);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev_count, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev_emit, cudaEventDisableTiming);
     g->held = g->ws_bytes + g->row_bytes;
@@ -287,9 +288,9 @@ bool impact_server::step()
             cudaStream_t st = g->stream;
             const size_t vb = per_pair == 12 ? 4 : 8;
             const size_t k = (size_t)std::max<int64_t>(g->nnz, 1);
-            cudaError_t e = cudaMallocAsync((void **)&g->col, k * 4, st);
-            if (e == cudaSuccess) e = cudaMallocAsync(&g->lo, k * vb, st);
-            if (e == cudaSuccess) e = cudaMallocAsync(&g->up, k * vb, st);
+            cudaError_t e = impact::dev_malloc_async(&g->col, k * 4, st);
+            if (e == cudaSuccess) e = impact::dev_malloc_async(&g->lo, k * vb, st);
+            if (e == cudaSuccess) e = impact::dev_malloc_async(&g->up, k * vb, st);
             g->pair_bytes = pb;
             g->held += pb;
             used += pb;
@@ -300,7 +301,7 @@ bool impact_server::step()
             out.lo = g->lo;
             out.up = g->up;
             out.nnz = g->nnz;
-            if (s == IMPACT_OK) s = impact::run_emit(g->B, g->W, &out, g->nnz, true, st);
+            if (s == IMPACT_OK) s = impact::run_emit(g->B, g->W, &out, g->nnz, st);
             if (s == IMPACT_OK) {
                 cudaMemcpyAsync(g->h_status, g->W.status(), 4, cudaMemcpyDeviceToHost, st);
                 if (cudaEventRecord(g->ev_emit, st) != cudaSuccess) s = IMPACT_ERR_CUDA;
@@ -329,7 +330,7 @@ bool impact_server::step()
                     fail_request(r, s, impact_last_error());
                 }
             }
-            cudaFreeAsync(g->W.base, g->stream);   // records are not needed any more
+            impact::dev_free_async(g->W.base, g->stream);   // the tables are not needed any more
             g->W.base = nullptr;
             g->held -= g->ws_bytes;
             used -= g->ws_bytes;

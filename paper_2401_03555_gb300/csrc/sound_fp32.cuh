@@ -143,7 +143,8 @@ __device__ __forceinline__ void alpha_interval(int k, float kappa_hi, float kapp
 //   |xm| >= 1/2: erfc(|xm|) (the small tail) with the relative bound
 //                erfc(x - dx) <= erfc(x) exp(dx (2x + 2dx + sqrt2)) for x >= 0
 //                (from erfc(x) >= 2/sqrt(pi) e^{-x^2} / (x + sqrt(x^2 + 2))), and
-//                exp(z) - 1 <= z (1 + z) for 0 <= z <= 1.
+//                exp(z) - 1 <= z (1 + z) for 0 <= z <= 1; outside z <= 1 and
+//                dx < |xm| the bounds are the trivial [0, 1].
 // The tail that is small keeps its relative accuracy; the other is 1 minus it.
 struct TailPair {
     float p_lo, p_hi;   // T(x)
@@ -164,10 +165,17 @@ static __device__ __noinline__ TailPair tails(float xm, float dx)
         r.m_lo = __fmul_rd(0.5f, __fadd_rd(1.0f, ylo));
         return r;
     }
+    float z = __fmul_ru(dx, __fadd_ru(__fmul_ru(2.0f, __fadd_ru(ax, dx)), 1.4143f));
+    if (!(z <= 1.0f) || !(dx < ax)) {
+        // the relative bound needs z <= 1 and an interval that stays on one
+        // side of 0; wider argument intervals (never met by the callers,
+        // whose dx is a few ulp) get the trivial bracket
+        r.p_lo = r.m_lo = 0.0f;
+        r.p_hi = r.m_hi = 1.0f;
+        return r;
+    }
     float y = erfcf(ax);
     float le = lib_err(y, K_ERFC);
-    float z = __fmul_ru(dx, __fadd_ru(__fmul_ru(2.0f, __fadd_ru(ax, dx)), 1.4143f));
-    z = fminf(z, 1.0f);
     float rho = __fmul_ru(z, __fadd_ru(1.0f, z));
     float shi = __fmul_ru(0.5f, __fmul_ru(__fadd_ru(y, le), __fadd_ru(1.0f, rho)));
     float slo = __fmul_rd(0.5f, __fmul_rd(fmaxf(__fsub_rd(y, le), 0.0f), __fsub_rd(1.0f, rho)));

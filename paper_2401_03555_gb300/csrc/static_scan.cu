@@ -1,7 +1,7 @@
 // static_scan.cu -- the row-pointer scan for callers that cannot allocate.
 //
 // impact_scan_rows_static turns per-row pair counts into CSR row pointers in
-// place, like the scan inside impact_count, but its scratch (one partial sum
+// place, like the scan of the FP64-plain count pass, but its scratch (one partial sum
 // per tile of rows) lives in a fixed file-scope device array instead of
 // memory allocated per call. Nothing here calls cudaMalloc, cudaFree or any
 // allocating library routine.
@@ -39,6 +39,15 @@ extern "C" impact_status impact_scan_rows_static(int64_t *row_ptr, int64_t rows,
                                         std::to_string((long long)IMPACT_SCAN_STATIC_MAX_ROWS) +
                                         "] for the allocation-free scan");
     if (!row_ptr) return fail(IMPACT_ERR_ARG, "null row_ptr");
+    {   // a host or stale pointer would reach the kernels: refuse it
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, row_ptr) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(IMPACT_ERR_ARG, "row_ptr must be a device array");
+        }
+        if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+            return fail(IMPACT_ERR_ARG, "row_ptr must be a device array");
+    }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return fail(IMPACT_ERR_CUDA, cudaGetErrorString(e));

@@ -35,6 +35,7 @@
 #include <vector>
 
 #include "../../include/impact.h"
+#include "alloc.h"
 #include "plan.h"
 
 namespace {
@@ -443,12 +444,32 @@ extern "C" impact_status impact_synthesize_ex(const impact_csr *imdp, impact_pre
     unsigned long long *d_diff = nullptr, *h_diff = nullptr;
     const int64_t rows = imdp->rows;
     const int64_t nnz = imdp->nnz;
-    CK(cudaMallocAsync((void **)&buf, (size_t)cells * 4 * sizeof(double), st));
-    CK(cudaMallocAsync((void **)&kbuf, (size_t)cells * 4 * sizeof(long long), st));
-    CK(cudaMallocAsync((void **)&wfix, (size_t)std::max<int64_t>(nnz, 1) * sizeof(long long), st));
-    CK(cudaMallocAsync((void **)&rbuf, (size_t)rows * 2 * sizeof(double), st));
-    CK(cudaMallocAsync((void **)&d_diff, sizeof(unsigned long long), st));
-    CK(cudaMallocHost((void **)&h_diff, sizeof(unsigned long long)));
+    auto free_all = [&]() {
+        impact::dev_free_async(buf, st);
+        impact::dev_free_async(kbuf, st);
+        impact::dev_free_async(wfix, st);
+        impact::dev_free_async(rbuf, st);
+        impact::dev_free_async(d_diff, st);
+        cudaStreamSynchronize(st);
+        impact::host_free(h_diff);
+    };
+    {
+        cudaError_t e = impact::dev_malloc_async(&buf, (size_t)cells * 4 * sizeof(double), st);
+        if (e == cudaSuccess)
+            e = impact::dev_malloc_async(&kbuf, (size_t)cells * 4 * sizeof(long long), st);
+        if (e == cudaSuccess)
+            e = impact::dev_malloc_async(
+                &wfix, (size_t)std::max<int64_t>(nnz, 1) * sizeof(long long), st);
+        if (e == cudaSuccess)
+            e = impact::dev_malloc_async(&rbuf, (size_t)rows * 2 * sizeof(double), st);
+        if (e == cudaSuccess) e = impact::dev_malloc_async(&d_diff, sizeof(unsigned long long), st);
+        if (e == cudaSuccess) e = impact::host_malloc(&h_diff, sizeof(unsigned long long));
+        if (e != cudaSuccess) {
+            free_all();
+            return fail(e == cudaErrorMemoryAllocation ? IMPACT_ERR_OOM : IMPACT_ERR_CUDA,
+                        std::string("synthesis scratch: ") + cudaGetErrorString(e));
+        }
+    }
     const bool reach = spec == IMPACT_REACH_AVOID;
     // the LP that bounds satisfaction from below: reach-avoid the min LP,
     // safety the max LP of the unsafe value; phase 1 optimises the inputs on
@@ -536,13 +557,7 @@ extern "C" impact_status impact_synthesize_ex(const impact_csr *imdp, impact_pre
         if (horizon && cudaStreamSynchronize(st) != cudaSuccess)
             status = fail(IMPACT_ERR_CUDA, "synthesis phase failed");
     }
-    cudaFreeAsync(buf, st);
-    cudaFreeAsync(kbuf, st);
-    cudaFreeAsync(wfix, st);
-    cudaFreeAsync(rbuf, st);
-    cudaFreeAsync(d_diff, st);
-    cudaStreamSynchronize(st);
-    cudaFreeHost(h_diff);
+    free_all();
     if (iterations) {
         iterations[0] = its[0];
         iterations[1] = its[1];

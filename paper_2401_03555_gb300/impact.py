@@ -35,7 +35,8 @@ ENTRY_POINTS = ("impact_plan", "impact_workspace_bytes", "impact_build", "impact
                 "impact_batch_tune", "impact_server_create", "impact_server_submit",
                 "impact_server_poll", "impact_server_release", "impact_server_stats",
                 "impact_server_destroy", "impact_synthesize", "impact_label_cells",
-                "impact_region_vectors", "impact_synthesize_ex", "impact_build_mc")
+                "impact_region_vectors", "impact_synthesize_ex", "impact_build_mc",
+                "impact_debug_fail_alloc", "impact_debug_live_bytes")
 
 
 class ImpactError(RuntimeError):
@@ -76,8 +77,8 @@ class _Request(ctypes.Structure):
 
 class _Tuning(ctypes.Structure):
     _fields_ = [("count_warps", ctypes.c_int), ("emit_warps", ctypes.c_int),
-                ("count_smem_target", ctypes.c_int), ("emit_smem_target", ctypes.c_int),
-                ("count_k", ctypes.c_int), ("emit_k", ctypes.c_int)]
+                ("spin_limit", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("stall_row", ctypes.c_int64), ("fault_row", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -146,6 +147,10 @@ def load(build_if_missing: bool = True):
         lib.impact_version.argtypes = []
         lib.impact_scan_rows_static.restype = ctypes.c_int
         lib.impact_scan_rows_static.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
+        lib.impact_debug_fail_alloc.restype = ctypes.c_int
+        lib.impact_debug_fail_alloc.argtypes = [ctypes.c_int64]
+        lib.impact_debug_live_bytes.restype = ctypes.c_int
+        lib.impact_debug_live_bytes.argtypes = [ctypes.POINTER(ctypes.c_int64)] * 2
         breq = [ctypes.POINTER(_Request), ctypes.c_int, ctypes.c_int, ctypes.POINTER(_Tuning)]
         lib.impact_batch_plan.restype = ctypes.c_int
         lib.impact_batch_plan.argtypes = breq + [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_int64)] * 3
@@ -294,7 +299,7 @@ def plan(prob, precision="fp32"):
 
 
 def workspace_bytes(prob, precision="fp32") -> int:
-    """Device scratch bytes of one build (descriptor, tables, scan, row records)."""
+    """Device scratch bytes of one build (descriptor, tables, scan, offset words)."""
     a = _Args(prob, need_images=False)
     if prob.kind == 2:
         a.sys.dev_images = 1
@@ -456,8 +461,9 @@ def build_library_owned(prob, precision="fp32", stream=None):
 def scan_rows_static(row_ptr: torch.Tensor, rows: int, stream=None) -> None:
     """In-place exclusive scan of per-row counts (row_ptr[0..rows)) into CSR
     row pointers with the allocation-free entry point impact_scan_rows_static."""
-    if row_ptr.dtype != torch.int64 or not row_ptr.is_cuda or row_ptr.numel() < rows + 1:
-        raise ValueError("row_ptr must be a CUDA int64 tensor of rows+1 entries")
+    if (row_ptr.dtype != torch.int64 or not row_ptr.is_cuda or row_ptr.numel() < rows + 1
+            or not row_ptr.is_contiguous()):
+        raise ValueError("row_ptr must be a contiguous CUDA int64 tensor of rows+1 entries")
     _check(load().impact_scan_rows_static(ctypes.c_void_p(row_ptr.data_ptr()), int(rows),
                                           ctypes.c_void_p(_stream_handle(stream))))
 
@@ -466,14 +472,31 @@ def version() -> int:
     return int(load().impact_version())
 
 
+def fail_alloc(n: int) -> None:
+    """impact_debug_fail_alloc: the n-th allocation the library makes from now
+    on fails as out of memory (0: off)."""
+    _check(load().impact_debug_fail_alloc(ctypes.c_int64(int(n))))
+
+
+def live_bytes():
+    """impact_debug_live_bytes: (device, pinned host) bytes the library holds."""
+    d, h = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().impact_debug_live_bytes(ctypes.byref(d), ctypes.byref(h)))
+    return int(d.value), int(h.value)
+
+
 # --------------------------------------------------------------------------
 # batches: several builds per launch (impact_batch_*), CUDA graphs, autotuner
 # --------------------------------------------------------------------------
 
-def tuning(count_warps=0, emit_warps=0, count_smem_target=0, emit_smem_target=0, count_k=0,
-           emit_k=0):
-    """An impact_tuning (zero fields take the library defaults)."""
-    return _Tuning(count_warps, emit_warps, count_smem_target, emit_smem_target, count_k, emit_k)
+def tuning(count_warps=0, emit_warps=0, spin_limit=0, stall_row=None, fault_row=None):
+    """An impact_tuning (zero fields take the library defaults). `stall_row`
+    and `fault_row` are fault injection for the failure-path tests: row r never
+    publishes its pair count (the rows after it time out), or row r's row
+    check sees an impossible lower-bound sum (IMPACT_ERR_UNSOUND)."""
+    return _Tuning(count_warps, emit_warps, spin_limit, 0,
+                   0 if stall_row is None else int(stall_row) + 1,
+                   0 if fault_row is None else int(fault_row) + 1)
 
 
 @dataclass

@@ -77,13 +77,18 @@ def test_plan_rejects_bad_arguments(lib, mutate, msg):
     assert msg in str(e.value)
 
 
-@pytest.mark.parametrize("precision, msg", [("fp32", "window of 400 cells"),
-                                             ("fp64", "staged factors")])
-def test_plan_rejects_windows_beyond_staging(lib, precision, msg):
-    prob = W.robot_2d(cells_per_dim=400)   # dense: a 400-cell window per dimension
+def test_plan_accepts_wide_fp32_windows(lib):
+    """Dense 400^2 robot: a 400-cell window per dimension fits one warp's
+    shared memory (8 bytes per window target, 48 per edge during setup)."""
+    rows, nnz_bound, _ = impact.plan(W.robot_2d(cells_per_dim=400), "fp32")
+    assert rows == 400 * 400 * 9 and nnz_bound == rows * 400 * 400
+
+
+def test_plan_rejects_windows_beyond_one_warp(lib):
+    prob = W.robot_2d(cells_per_dim=4000)   # dense: 8000 window targets per row
     with pytest.raises(impact.ImpactError) as e:
-        impact.plan(prob, precision)
-    assert msg in str(e.value)
+        impact.plan(prob, "fp32")
+    assert e.value.status == impact.IMPACT_ERR_ARG and "shared memory" in str(e.value)
 
 
 def test_fast_division_constants_are_exact():
@@ -123,9 +128,8 @@ def test_batch_plan_names_the_failing_request(lib):
 
 
 @pytest.mark.parametrize("field,value,msg", [("count_warps", 9, "warps"),
-                                              ("emit_smem_target", 100, "shared-memory"),
-                                              ("count_k", 4, "count_k"),
-                                              ("emit_k", 2, "emit_k")])
+                                              ("emit_warps", -1, "warps"),
+                                              ("spin_limit", -5, "spin_limit")])
 def test_batch_plan_rejects_bad_tuning(lib, field, value, msg):
     t = impact.tuning(**{field: value})
     with pytest.raises(impact.ImpactError, match=msg):

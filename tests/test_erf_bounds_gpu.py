@@ -25,19 +25,3 @@ def test_erf_erfc_ulp_bounds_exhaustive(tmp_path):
     print(f"max ulp error: erff {max_erf:.3f}, erfcf {max_erfc:.3f}")
     assert max_erf <= 2.0
     assert max_erfc <= 5.0
-
-
-def test_fp64_fma_rate_probe(tmp_path):
-    """Measures the FP64 and FP32 FMA rates (the FP64 one bounds the FP64-plain
-    build and explains where the synthesis kernel spent its time)."""
-    src = os.path.join(HERE, "cuda", "fp64_rate.cu")
-    lib = str(tmp_path / "libfprate.so")
-    subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-shared",
-                    "-Xcompiler", "-fPIC", src, "-o", lib], check=True)
-    f = ctypes.CDLL(lib).fp_rate
-    f.restype = ctypes.c_int
-    f64, f32 = ctypes.c_double(), ctypes.c_double()
-    assert f(ctypes.byref(f64), ctypes.byref(f32)) == 0
-    print(f"FMA rate: FP64 {f64.value / 1e12:.3f} TFLOP/s, FP32 {f32.value / 1e12:.1f} TFLOP/s, "
-          f"ratio {f32.value / f64.value:.0f}")
-    assert f64.value > 0 and f32.value > f64.value

@@ -54,6 +54,8 @@ SMALL = {
     "linear-seed3": lambda: W.random_linear(3, min_cells=300, max_cells=3000),
     "linear-seed8": lambda: W.random_linear(8, min_cells=300, max_cells=3000),
     "building7d-3": lambda: W.building_7d(cells_per_dim=3),
+    # the boundary's largest dimension: 8-D coupled linear system, 3^8 cells
+    "linear-8d": lambda: W.random_linear(2, min_cells=5000, max_cells=7000, dims=(8,)),
 }
 
 
@@ -90,6 +92,33 @@ def test_full_size_sampled_rows(orc, name, precision):
     rep, csr = run_and_compare(orc, prob, precision, rows, builder=True)
     flags = csr.row_flags
     assert int((flags != 0).sum()) == 0
+
+
+def wide_unicycle():
+    """A unicycle on a fine grid of a small domain with cutoff 1e-10: in x
+    and y the window spans all 70 cells (the noise reaches 44 cells)."""
+    p = W.unicycle_3d(nx=70, ny=70, nth=3, cutoff=1e-10)
+    p.lo, p.hi = np.array([-1.5, -1.5, -np.pi]), np.array([1.5, 1.5, np.pi])
+    p.inputs = p.inputs[[3, 17]]
+    return p
+
+
+WIDE = {
+    "robot2d-80-dense": (lambda: W.robot_2d(cells_per_dim=80), 40),
+    "unicycle-70x70x3-1e-10": (wide_unicycle, 30),
+}
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("name", list(WIDE))
+def test_wide_windows_sampled_rows(orc, name, precision):
+    """Windows of more than 64 cells per dimension (the first FP32 walk
+    refused them): dense builds and a small cutoff on a fine grid."""
+    make, count = WIDE[name]
+    prob = make()
+    rows = W.sample_rows(prob, count, seed=5)
+    rep, csr = run_and_compare(orc, prob, precision, rows, builder=True)
+    assert rep.pairs > 64 * len(rows)
 
 
 def test_fp32_vs_fp64_gpu_bracketing_full(orc):

@@ -51,3 +51,11 @@ def test_static_scan_single_row_and_limit():
     status = impact.load().impact_scan_rows_static(big.data_ptr(), (1 << 27) + 1, None)
     assert status == impact.IMPACT_ERR_ARG
     assert "allocation-free" in impact.load().impact_last_error().decode()
+    # a host array is refused before any launch
+    host = torch.zeros(8, dtype=torch.int64)
+    status = impact.load().impact_scan_rows_static(host.data_ptr(), 4, None)
+    assert status == impact.IMPACT_ERR_ARG
+    assert "device array" in impact.load().impact_last_error().decode()
+    # a strided view is refused by the binding (the kernel reads rows+1 in a row)
+    with pytest.raises(ValueError):
+        impact.scan_rows_static(torch.zeros(16, dtype=torch.int64, device="cuda")[::2], 4)
