@@ -795,6 +795,7 @@ def serve_stream(srv, probs, gaps):
     tickets = [None] * len(probs)
     ready = [threading.Event() for _ in probs]
     lat = [None] * len(probs)
+    parts = [None] * len(probs)
     t_start = time.perf_counter()
 
     def client():
@@ -812,10 +813,23 @@ def serve_stream(srv, probs, gaps):
     for i in range(len(probs)):
         ready[i].wait()
         _, lat[i] = srv.poll(tickets[i], wait=True)
+        parts[i] = srv.timing(tickets[i])
         srv.release(tickets[i])
     th.join()
     wall = time.perf_counter() - t_start
+    serve_stream.parts = parts
     return np.array(lat), wall
+
+
+def latency_breakdown(lat, parts):
+    """Where latency went: each phase's p50 / p99 over the requests, and the
+    mean of each phase over the slowest 1% of the requests."""
+    keys = ("queue", "count", "emit_wait", "emit")
+    arr = {k: np.array([p[k] for p in parts]) for k in keys}
+    slow = np.argsort(lat)[-max(1, len(lat) // 100):]
+    return {"p50_ms": {k: float(np.percentile(arr[k], 50)) for k in keys},
+            "p99_ms": {k: float(np.percentile(arr[k], 99)) for k in keys},
+            "slowest_1pct_mean_ms": {k: float(arr[k][slow].mean()) for k in keys}}
 
 
 def run_serving(count=500, seed=1, load=0.7):
@@ -831,6 +845,7 @@ def run_serving(count=500, seed=1, load=0.7):
         gaps = np.random.default_rng(seed + 1000).exponential(1.0 / rate, size=len(probs))
         gaps[0] = 0.0
         lat, wall = serve_stream(srv, probs, gaps.tolist())
+        parts = serve_stream.parts
         st2 = srv.stats()
     pairs_stream = st2["pairs"] - pairs
     return {"workload": SERVED_WORKLOAD, "requests": len(probs),
@@ -843,6 +858,7 @@ def run_serving(count=500, seed=1, load=0.7):
                       "p50_ms": float(np.percentile(lat_b, 50)),
                       "p99_ms": float(np.percentile(lat_b, 99))},
             "groups": st2["groups"], "budget_bytes": st2["budget"],
+            "breakdown": latency_breakdown(lat, parts),
             "path": "impact_server_submit / impact_server_poll / impact_server_release "
                     "(continuous batching, admission by device-memory footprint)"}
 

@@ -335,7 +335,10 @@ impact_status impact_batch_tune(const impact_request *reqs, int count,
  * device-memory budget, runs them together as one batch count, emits each
  * counted group as soon as its exact output fits the budget, and overlaps
  * groups on a pool of streams, so requests that arrive while others are on
- * the device join the next group. Results stay on the device until released.
+ * the device join the next group. Small groups (at most 2^18 rows) run on a
+ * high-priority stream; larger ones run each pass in launches of 2^18 rows,
+ * so the SMs they free between launches go to the small groups first.
+ * Results stay on the device until released.
  * Each result is bitwise the same alone and in any mix (same kernels and
  * launch shapes per row). The paper has no counterpart (it builds one
  * abstraction per program run).
@@ -383,6 +386,19 @@ impact_status impact_server_submit(impact_server *server, const impact_request *
  */
 impact_status impact_server_poll(impact_server *server, int64_t ticket, int wait_ms, int *done,
                                  impact_csr *result, double *latency_ms);
+
+/*
+ * impact_server_timing -- where a finished request's latency went, as seen
+ * by the scheduler thread (any pointer may be NULL): queue_ms from submission
+ * until its group was launched, count_ms until the group's count pass was
+ * seen finished, emit_wait_ms until its emit pass was launched (waiting for
+ * output memory or for earlier groups), emit_ms until the emit was seen
+ * finished. The four add up to the latency of impact_server_poll.
+ * Errors: IMPACT_ERR_ARG for an unknown, released, failed or unfinished
+ * request.
+ */
+impact_status impact_server_timing(impact_server *server, int64_t ticket, double *queue_ms,
+                                   double *count_ms, double *emit_wait_ms, double *emit_ms);
 
 /* Frees a finished request's result (its group's memory goes once every
  * request of the group is released). Errors: IMPACT_ERR_ARG when in flight. */

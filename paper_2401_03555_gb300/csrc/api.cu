@@ -90,6 +90,7 @@ impact_status make_batch(const impact_request *reqs, int count, impact_precision
     B.plans.assign(count, Plan());
     B.images.assign(count, nullptr);
     B.row_begin.assign(count + 1, 0);
+    B.unit_begin.assign(count + 1, 0);
     B.prec = precision;
     uint64_t h = 1469598103934665603ull;
     for (int q = 0; q < count; ++q) {
@@ -102,16 +103,15 @@ impact_status make_batch(const impact_request *reqs, int count, impact_precision
         const Plan &P = B.plans[q];
         B.images[q] = r.sys->dev_images;
         B.row_begin[q + 1] = B.row_begin[q] + P.rows;
+        const int64_t rpw = 32 / P.desc.n;
+        B.unit_begin[q + 1] = B.unit_begin[q] + (P.rows + rpw - 1) / rpw;
         B.nnz_bound = (B.nnz_bound > INT64_MAX - P.nnz_bound) ? INT64_MAX
                                                               : B.nnz_bound + P.nnz_bound;
         B.walk_core = std::max(B.walk_core, P.desc.walk_core);
-        B.nm = std::max(B.nm, P.desc.n);
         h = mix(h, P.hash);
     }
     B.rows = B.row_begin[count];
-    if (B.prec == PREC_FP32_SOUND &&
-        walk_smem_bytes(B.walk_core, B.nm, true) > IMPACT_WALK_SMEM_MAX)
-        return fail(IMPACT_ERR_ARG, "the batch's windows need more shared memory than a warp has");
+    B.units = B.unit_begin[count];
     B.hash = h;   // launch shapes change no result: they are not part of the identity
     return IMPACT_OK;
 }
@@ -129,7 +129,9 @@ BatchLayout batch_layout(const Batch &B)
     const int count = B.count();
     L.index = put(sizeof(BatchIndex));
     L.row_begin = put((size_t)(count + 1) * 8);
+    L.unit_begin = put((size_t)(count + 1) * 8);
     L.descs = put((size_t)count * 8);
+    L.recs = put((size_t)count * 8);
     L.tables.resize(count);
     L.tl.resize(count);
     for (int q = 0; q < count; ++q) {
@@ -141,6 +143,11 @@ BatchLayout batch_layout(const Batch &B)
     L.counter = put(64);
     L.scan = put((size_t)impact::scan_scratch_elems(B.rows) * 8);
     L.lb = put(B.prec == PREC_FP32_SOUND ? (size_t)B.rows * 8 : 0);
+    L.rec.resize(count);
+    for (int q = 0; q < count; ++q) {
+        const Plan &P = B.plans[q];
+        L.rec[q] = put(B.prec == PREC_FP32_SOUND ? (size_t)P.rows * P.desc.rec_stride : 0);
+    }
     L.total = o;
     return L;
 }
@@ -221,14 +228,20 @@ impact_status upload(const Batch &B, Work &W, cudaStream_t st)
     memset(&bi, 0, sizeof(bi));
     bi.count = count;
     bi.rows = B.rows;
+    bi.units = B.units;
     bi.row_begin = (const int64_t *)(W.base + L.row_begin);
+    bi.unit_begin = (const int64_t *)(W.base + L.unit_begin);
     bi.desc = (const ImpactDesc *const *)(W.base + L.descs);
+    bi.rec = (unsigned char *const *)(W.base + L.recs);
     bi.next_row = W.counter();
     memcpy(host.data() + L.index, &bi, sizeof(bi));
     memcpy(host.data() + L.row_begin, B.row_begin.data(), (size_t)(count + 1) * 8);
+    memcpy(host.data() + L.unit_begin, B.unit_begin.data(), (size_t)(count + 1) * 8);
     for (int q = 0; q < count; ++q) {
         const ImpactDesc *d = W.desc(q);
+        unsigned char *r = B.prec == PREC_FP32_SOUND ? W.base + L.rec[q] : nullptr;
         memcpy(host.data() + L.descs + 8 * (size_t)q, &d, 8);
+        memcpy(host.data() + L.recs + 8 * (size_t)q, &r, 8);
         impact::pack_tables(B.plans[q], host.data() + L.tables[q], W.base + L.tables[q],
                             B.images[q]);
     }
@@ -314,9 +327,9 @@ cudaError_t walk_pass(const Batch &B, const Work &W, int mode, int warps,
     for (int64_t r0 = 0; r0 < B.rows; r0 += step) {
         cudaError_t e = cudaMemsetAsync(counter, 0, 8, st);
         if (e == cudaSuccess)
-            e = impact::launch_walk_fp32(W.index(), r0, std::min(B.rows, r0 + step), B.nm,
+            e = impact::launch_walk_fp32(W.index(), r0, std::min(B.rows, r0 + step),
                                          B.walk_core, warps, mode, o,
-                                         mode == WALK_EMIT ? nullptr : W.lb(), B.tune.faults, st);
+                                         mode == WALK_FUSED ? W.lb() : nullptr, B.tune.faults, st);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -332,9 +345,10 @@ impact_status run_count(const Batch &B, const Work &W, const impact_csr *out, cu
     impact::RowOutputs o{out->row_ptr, nullptr, nullptr, nullptr, out->sink_lo, out->sink_up,
                          out->trunc, out->row_flags, W.status(), -1, B.rows};
     if (B.prec == PREC_FP32_SOUND) {
-        if (B.rows > 0) CK(cudaMemsetAsync(W.lb(), 0, (size_t)B.rows * 8, st));
-        else CK(cudaMemsetAsync(out->row_ptr, 0, 8, st));
+        CK(impact::launch_setup_fp32(W.index(), B.units, W.status(), out->sink_lo, out->sink_up,
+                                     out->trunc, st));
         CK(walk_pass(B, W, WALK_COUNT, B.tune.count_warps, o, W.counter(), chunk_rows, st));
+        CK(impact::launch_scan(out->row_ptr, B.rows, W.scan(), st));
         return IMPACT_OK;
     }
     for (int q = 0; q < B.count(); ++q)
@@ -346,11 +360,14 @@ impact_status run_count(const Batch &B, const Work &W, const impact_csr *out, cu
 
 // emit pass at the row pointers in out->row_ptr
 impact_status run_emit(const Batch &B, const Work &W, const impact_csr *out, int64_t capacity,
-                       cudaStream_t st, int64_t chunk_rows)
+                       bool records_ready, cudaStream_t st, int64_t chunk_rows)
 {
     impact::RowOutputs o{out->row_ptr, out->col, out->lo, out->up, nullptr, nullptr, nullptr,
                          nullptr, W.status(), capacity, B.rows};
     if (B.prec == PREC_FP32_SOUND) {
+        if (!records_ready)   // rebuild the records; the row outputs stay as counted
+            CK(impact::launch_setup_fp32(W.index(), B.units, W.status(), nullptr, nullptr,
+                                         nullptr, st));
         CK(walk_pass(B, W, WALK_EMIT, B.tune.emit_warps, o, W.counter() + 1, chunk_rows, st));
     } else {
         for (int q = 0; q < B.count(); ++q)
@@ -369,9 +386,11 @@ impact_status run_fused(const Batch &B, const Work &W, const impact_csr *out, in
     if (B.prec != PREC_FP32_SOUND) {
         impact_status s = run_count(B, W, out, st, chunk_rows);
         if (s != IMPACT_OK) return s;
-        return run_emit(B, W, out, capacity, st, chunk_rows);
+        return run_emit(B, W, out, capacity, true, st, chunk_rows);
     }
     CK(cudaMemsetAsync(W.status(), 0, 64, st));
+    CK(impact::launch_setup_fp32(W.index(), B.units, W.status(), out->sink_lo, out->sink_up,
+                                 out->trunc, st));
     if (B.rows > 0) CK(cudaMemsetAsync(W.lb(), 0, (size_t)B.rows * 8, st));
     else CK(cudaMemsetAsync(out->row_ptr, 0, 8, st));
     impact::RowOutputs o{out->row_ptr, out->col, out->lo, out->up, out->sink_lo, out->sink_up,
@@ -455,7 +474,7 @@ impact_status do_emit(const Batch &B, impact_csr *out, cudaStream_t st)
     } else {
         CK(cudaMemsetAsync(W.status(), 0, 64, st));
     }
-    if ((s = run_emit(B, W, &view, out->nnz, st)) != IMPACT_OK) return s;
+    if ((s = run_emit(B, W, &view, out->nnz, ready, st)) != IMPACT_OK) return s;
     uint32_t status = 0;
     CK(cudaMemcpyAsync(&status, W.status(), 4, cudaMemcpyDeviceToHost, st));
     if ((s = release(W, st)) != IMPACT_OK) return s;
@@ -495,7 +514,7 @@ impact_status build_into(const Batch &B, impact_csr *out, bool lib_owned, cudaSt
         capacity = nnz;
         impact_csr view;
         if ((s = pair_view(out, view)) != IMPACT_OK) return s;
-        if ((s = run_emit(B, W, &view, capacity, st)) != IMPACT_OK) return s;
+        if ((s = run_emit(B, W, &view, capacity, true, st)) != IMPACT_OK) return s;
     } else {   // caller capacity: one pass
         impact_csr view;
         if ((s = pair_view(out, view)) != IMPACT_OK) return s;
@@ -909,7 +928,7 @@ impact_status impact_batch_tune(const impact_request *reqs, int count,
         for (int i = 0; i < reps; ++i) {
             CK(cudaEventRecord(e0, st));
             impact_status r = pass == 0   ? run_count(B, W, out, st)
-                              : pass == 1 ? run_emit(B, W, out, out->nnz, st)
+                              : pass == 1 ? run_emit(B, W, out, out->nnz, true, st)
                                           : run_fused(B, W, out, out->nnz, st);
             if (r != IMPACT_OK) return r;
             CK(cudaEventRecord(e1, st));

@@ -23,6 +23,7 @@ struct ImpactDim {
     int stride;           // C-order column stride
     int edge_off;         // offset of this dim's N+1 FP64 edges in the edge table
     int wcap;             // largest window (cells) of a row in this dim
+    int rec_off;          // FP32 path: first entry of this dim's table in a row record
     float delta_cells;    // delta / h
     uint32_t div_m;       // fast division by N: q = (umulhi(x, div_m) + x) >> div_s
     int div_s;
@@ -75,9 +76,9 @@ struct ImpactDesc {
     uint32_t inp_div_m;       // fast division by n_inputs
     int inp_div_s;
     int tsum_cap;             // window targets of a row, all dims (at most)
-    int edge_cap;             // window edges of a row plus 2 domain edges per dim, + 1 each
-    int walk_core;            // shared-memory bytes of one warp of the walk (no epilogue)
-    int pad2;
+    int rec_stride;           // bytes per row record in the workspace
+    int leaf_cap;             // leaf-table entries a warp of the walk stages
+    int walk_core;            // shared-memory bytes of one warp of the walk
     const float2 *ea;         // per dim: N+1 edges in erf units, offset edge_off
     const float2 *ta_lo;      // AFFINE [n][n][Nmax]: min term A_dk x_k in erf units of d
     const float2 *ta_hi;      //                      max term
@@ -92,12 +93,16 @@ struct ImpactDesc {
 };
 
 // Several builds handled by one launch of each FP32 kernel: problem q owns the
-// global rows [row_begin[q], row_begin[q+1]) of the concatenated output; a
-// single build is a batch of one.
+// global rows [row_begin[q], row_begin[q+1]) of the concatenated output and
+// the setup units [unit_begin[q], unit_begin[q+1]) (a unit is the 32/n rows
+// one warp prepares); a single build is a batch of one.
 struct BatchIndex {
     int count;                          // problems
     int64_t rows;                       // total rows
+    int64_t units;                      // setup work units: 32/n rows of one problem
     const int64_t *row_begin;           // [count + 1]
+    const int64_t *unit_begin;          // [count + 1]
     const ImpactDesc *const *desc;      // [count] device descriptors
+    unsigned char *const *rec;          // [count] FP32 per-row records
     unsigned long long *next_row;       // [2] row counters of the count / emit walk
 };

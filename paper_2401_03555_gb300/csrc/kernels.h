@@ -8,8 +8,8 @@
 #include "impact_desc.h"
 
 #define IMPACT_TABLE_MAX 512              // FP64: window factors a warp stages (wider: re-evaluated)
-#define IMPACT_WALK_CAP 128               // FP32 walk: nodes per level list (one chunk)
-#define IMPACT_WALK_EPI 16                // FP32 walk: rows per FP64 epilogue batch of a warp
+#define IMPACT_WALK_CAP 64                // FP32 walk: nodes per level list (one chunk)
+#define IMPACT_LEAF_STAGE 256             // FP32 walk: leaf-table entries a warp stages
 #define IMPACT_WALK_SMEM_MAX (200 * 1024) // FP32 walk: shared memory of one warp at most
 #define IMPACT_TREE_WARPS 4               // FP32 walk: warps per block (default)
 #define IMPACT_TREE_WARPS_MAX 8
@@ -82,22 +82,28 @@ cudaError_t launch_regions(const ImpactDesc *d_desc, int64_t rows, const RegionB
                            bool cell_sum, bool sound, double *r_lo, double *r_up, double *a_lo,
                            double *a_up, cudaStream_t stream);
 
-// FP32-sound path (walk_fp32.cu): one persistent kernel per pass over the
-// global rows [row_begin, row_end) of a batch (the row counter of the pass
+// FP32-sound path (walk_fp32.cu). The setup kernel writes one record per
+// row (record_stride bytes: per-dimension entries, then the window tables)
+// and, when the row arrays are given, the sink bounds and the mass outside
+// the window box; the walk kernels read the records. A walk launch covers
+// the global rows [row_begin, row_end) of a batch (the pass's row counter
 // zeroed before each launch; launches of one pass in row order on one
-// stream). `core_max`: the largest walk_core_bytes of the batch; `nm`: its
-// largest n; `lb`: one 8-byte look-back word per row, zeroed before the first
-// launch of a COUNT or FUSED pass.
+// stream). `core_max`: the largest walk_core_bytes of the batch; `lb`: one
+// 8-byte look-back word per row, zeroed before the first launch of a FUSED
+// pass. COUNT writes per-row counts (a scan makes them row pointers), FUSED
+// the row pointers themselves.
 enum { WALK_COUNT = 0, WALK_EMIT = 1, WALK_FUSED = 2 };
 struct WalkFaults {
     int spin_limit = 0;        // look-back sleeps before giving up (0: the default)
     int64_t stall_row = -1;    // this row never publishes its count (-1: none)
     int64_t fault_row = -1;    // this row's checks see an impossible sum (-1: none)
 };
-int walk_core_bytes(int n, int tsum_cap, int edge_cap);
-int walk_smem_bytes(int core_max, int nm, bool count);
+int64_t record_stride(int n, int tsum_cap);
+int walk_core_bytes(int n, int tsum_cap, int leaf_cap);
+cudaError_t launch_setup_fp32(const BatchIndex *d_index, int64_t units, uint32_t *status,
+                              double *sink_lo, double *sink_up, double *trunc, cudaStream_t stream);
 cudaError_t launch_walk_fp32(const BatchIndex *d_index, int64_t row_begin, int64_t row_end,
-                             int nm, int core_max, int warps, int mode, const RowOutputs &o,
+                             int core_max, int warps, int mode, const RowOutputs &o,
                              unsigned long long *lb, const WalkFaults &f, cudaStream_t stream);
 cudaError_t launch_scan(int64_t *row_ptr, int64_t n, int64_t *scratch, cudaStream_t stream);
 

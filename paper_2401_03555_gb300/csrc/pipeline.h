@@ -18,10 +18,10 @@ struct Batch {
     std::vector<Plan> plans;
     std::vector<const double *> images;   // per build: device images (IMAGES kind)
     std::vector<int64_t> row_begin;       // [count + 1] first global row of each build
-    int64_t rows = 0, nnz_bound = 0;
+    std::vector<int64_t> unit_begin;      // [count + 1] first setup unit (32/n rows)
+    int64_t rows = 0, units = 0, nnz_bound = 0;
     int prec = 0;
-    int walk_core = 0;                    // largest per-warp bytes of the walk (no epilogue)
-    int nm = 1;                           // largest dimension n of the batch
+    int walk_core = 0;                    // largest per-warp shared-memory bytes of the walk
     Tuning tune;
     uint64_t hash = 0;
     int count() const { return (int)plans.size(); }
@@ -32,12 +32,13 @@ impact_status make_batch(const impact_request *reqs, int count, impact_precision
 
 // Offsets (bytes, 256-aligned) of everything in the device workspace.
 struct BatchLayout {
-    size_t index = 0, row_begin = 0, descs = 0;
+    size_t index = 0, row_begin = 0, unit_begin = 0, descs = 0, recs = 0;
     std::vector<size_t> tables;            // per build: its descriptor and tables
     std::vector<impact::TableLayout> tl;
     size_t upload_end = 0;                 // [0, upload_end) is copied from the host
     size_t status = 0, counter = 0, scan = 0;
     size_t lb = 0;                         // FP32: one look-back word per row
+    std::vector<size_t> rec;               // per build: FP32 per-row records
     size_t total = 0;
 };
 
@@ -67,9 +68,10 @@ impact_status upload(const Batch &B, Work &W, cudaStream_t st);
 // count pass into out's row arrays (row pointers included).
 impact_status run_count(const Batch &B, const Work &W, const impact_csr *out, cudaStream_t st,
                         int64_t chunk_rows = 0);
-// emit pass into out's pair arrays at the row pointers of a count pass.
+// emit pass into out's pair arrays at the row pointers of a count pass
+// (`records_ready`: W holds the FP32 row records of that count pass).
 impact_status run_emit(const Batch &B, const Work &W, const impact_csr *out, int64_t capacity,
-                       cudaStream_t st, int64_t chunk_rows = 0);
+                       bool records_ready, cudaStream_t st, int64_t chunk_rows = 0);
 // FP32: count and emit in one pass (capacity known); FP64: count, scan, emit.
 impact_status run_fused(const Batch &B, const Work &W, const impact_csr *out, int64_t capacity,
                         cudaStream_t st, int64_t chunk_rows = 0);

@@ -339,23 +339,35 @@ impact_status make_plan(const impact_system *sys, const impact_grid *grid,
     if (box > cells) box = cells;
     P.nnz_bound = box * rows;
     if (precision == IMPACT_FP32_SOUND) {
-        // the walk stages a row's window tables (8 bytes per target) and,
-        // during its setup, both image ends of every window edge (48 bytes
-        // per edge) in one warp's shared memory; wide windows (cutoff 0 on a
-        // fine grid, wide noise) need more of it and fewer warps per SM
-        // (at most 4096 window targets: the walk's candidate division by a
-        // window width, umulhi(e, ceil(2^32 / tw)), is exact for e < 128 tw
-        // while 128 tw^2 < 2^32)
-        if (tsum > 4096 ||
-            impact::walk_smem_bytes(impact::walk_core_bytes(n, (int)tsum, (int)tsum + 3 * n), n,
-                                    true) > IMPACT_WALK_SMEM_MAX)
+        // a row record holds the window tables of every dimension (8 bytes
+        // per target), which the walk copies into one warp's shared memory
+        // beside its node lists and the leaf table of the last two
+        // dimensions (staged up to IMPACT_LEAF_STAGE entries); wide windows
+        // (cutoff 0 on a fine grid, wide noise) need more of it and fewer
+        // warps per SM. The walk divides candidate and leaf indices by window
+        // widths as umulhi(e, ceil(2^32 / tw)), exact while e tw < 2^32: the
+        // leaf table needs wcap_m wcap_l^2 < 2^31, the node lists 64 tw^2
+        // < 2^31.
+        const int64_t wl = D.dim[n - 1].wcap, wm = n >= 2 ? D.dim[n - 2].wcap : 1;
+        int64_t wmax = 0;
+        for (int d = 0; d < n; ++d) wmax = std::max<int64_t>(wmax, D.dim[d].wcap);
+        const int leaf_cap = (int)std::min<int64_t>(wm * wl, IMPACT_LEAF_STAGE);
+        if (tsum > 4096 || wm * wl * wl >= ((int64_t)1 << 31) ||
+            IMPACT_WALK_CAP * wmax * wmax >= ((int64_t)1 << 31) ||
+            impact::walk_core_bytes(n, (int)tsum, leaf_cap) > IMPACT_WALK_SMEM_MAX)
             return fail(IMPACT_ERR_ARG,
                         "the per-row windows need " + std::to_string(tsum) +
                             " factor entries, more than one warp's shared memory holds: "
                             "raise the cutoff or use fewer cells");
         D.tsum_cap = (int)tsum;
-        D.edge_cap = (int)tsum + 3 * n;
-        D.walk_core = impact::walk_core_bytes(n, D.tsum_cap, D.edge_cap);
+        D.leaf_cap = leaf_cap;
+        D.walk_core = impact::walk_core_bytes(n, D.tsum_cap, D.leaf_cap);
+        D.rec_stride = (int)impact::record_stride(n, D.tsum_cap);
+        int ro = 0;
+        for (int d = 0; d < n; ++d) {
+            D.dim[d].rec_off = ro;
+            ro += D.dim[d].wcap;
+        }
         // tables in erf units (x / (sigma sqrt2)) as FP32 pairs, and in cells
         for (int d = 0; d < n; ++d) {
             const ImpactDim &g = D.dim[d];

@@ -55,6 +55,7 @@ struct Request {
     int64_t rows = 0;
     int64_t admit_bytes = 0;   // workspace + row arrays of this request alone
     Clock::time_point t_submit, t_done;
+    Clock::time_point t_admit, t_counted, t_emit;   // group launched, counted, emit launched
     enum State { WAITING, RUNNING, DONE, FAILED } state = WAITING;
     impact_status status = IMPACT_OK;
     std::string error;
@@ -94,6 +95,7 @@ struct Group {
     int64_t held = 0;                // bytes of this group counted in the server's `used`
     int64_t nnz = 0;
     enum State { COUNTING, COUNTED, EMITTING, DONE } state = COUNTING;
+    int64_t chunk_rows = 0;          // rows per walk launch (0: one launch)
     int live = 0;                    // requests not yet released
 };
 
@@ -104,6 +106,7 @@ struct impact_server {
     int device = 0;
     int64_t budget = 0;
     std::vector<cudaStream_t> streams;
+    cudaStream_t fast_stream = nullptr;   // high priority: small groups
     int next_stream = 0;
 
     std::mutex mu;
@@ -131,6 +134,11 @@ struct impact_server {
 namespace {
 
 int64_t row_bytes_of(int64_t rows) { return (rows + 1) * 8 + rows * (3 * 8 + 4); }
+
+// Groups of at most kSmallRows rows run on the high-priority stream in one
+// launch per pass; larger ones run their passes in chunks of kChunkRows rows.
+constexpr int64_t kSmallRows = (int64_t)1 << 18;
+constexpr int64_t kChunkRows = (int64_t)1 << 18;
 
 int64_t align_up(int64_t x) { return (x + 255) & ~(int64_t)255; }
 
@@ -166,7 +174,7 @@ void impact_server::admit()
 {
     const int max_batch = cfg.max_batch > 0 ? cfg.max_batch : 64;
     const int64_t max_rows = cfg.max_group_rows > 0 ? cfg.max_group_rows : ((int64_t)1 << 22);
-    const int max_groups = (int)streams.size() * 2;
+    const int max_groups = ((int)streams.size() + 1) * 2;
     int inflight = 0;
     for (Group *g : groups)
         if (g->state != Group::DONE) ++inflight;
@@ -201,8 +209,17 @@ void impact_server::admit()
         groups.push_back(g);
     };
     if (s != IMPACT_OK) return bail(s, impact_last_error());
-    g->stream = streams[next_stream];
-    next_stream = (next_stream + 1) % (int)streams.size();
+    // small groups go to the high-priority stream, large ones take turns on
+    // the others and run in chunks of rows, so that the SMs a large group
+    // frees between its chunks go to the small groups first
+    if (rq.size() > 0 && g->B.rows <= kSmallRows) {
+        g->stream = fast_stream;
+        g->chunk_rows = 0;
+    } else {
+        g->stream = streams[next_stream];
+        next_stream = (next_stream + 1) % (int)streams.size();
+        g->chunk_rows = kChunkRows;
+    }
     cudaStream_t st = g->stream;
     g->rows = g->B.rows;
     g->W.L = impact::batch_layout(g->B);
@@ -228,10 +245,12 @@ void impact_server::admit()
         g->state = Group::DONE;
         return;
     }
+    const Clock::time_point t_admit = Clock::now();
     for (size_t q = 0; q < take.size(); ++q) {
         take[q]->group = g;
         take[q]->index = (int)q;
         take[q]->state = Request::RUNNING;
+        take[q]->t_admit = take[q]->t_counted = take[q]->t_emit = t_admit;
     }
     impact_csr out{};
     out.row_ptr = g->row_ptr;
@@ -240,7 +259,7 @@ void impact_server::admit()
     out.trunc = g->trunc;
     out.row_flags = g->flags;
     s = impact::upload(g->B, g->W, st);
-    if (s == IMPACT_OK) s = impact::run_count(g->B, g->W, &out, st);
+    if (s == IMPACT_OK) s = impact::run_count(g->B, g->W, &out, st, g->chunk_rows);
     if (s == IMPACT_OK) {
         for (size_t q = 0; q <= take.size(); ++q)
             cudaMemcpyAsync(g->h_ptr + q, g->row_ptr + g->B.row_begin[q], 8,
@@ -273,8 +292,11 @@ bool impact_server::step()
         if (g->state == Group::COUNTING && cudaEventQuery(g->ev_count) == cudaSuccess) {
             g->state = Group::COUNTED;
             g->nnz = g->h_ptr[g->reqs.size()];
-            for (size_t q = 0; q < g->reqs.size(); ++q)
+            const Clock::time_point now = Clock::now();
+            for (size_t q = 0; q < g->reqs.size(); ++q) {
                 g->reqs[q]->nnz = g->h_ptr[q + 1] - g->h_ptr[q];
+                g->reqs[q]->t_counted = g->reqs[q]->t_emit = now;
+            }
             changed = true;
         }
         if (g->state == Group::COUNTED && !earlier_pending) {
@@ -301,7 +323,7 @@ bool impact_server::step()
             out.lo = g->lo;
             out.up = g->up;
             out.nnz = g->nnz;
-            if (s == IMPACT_OK) s = impact::run_emit(g->B, g->W, &out, g->nnz, st);
+            if (s == IMPACT_OK) s = impact::run_emit(g->B, g->W, &out, g->nnz, true, st, g->chunk_rows);
             if (s == IMPACT_OK) {
                 cudaMemcpyAsync(g->h_status, g->W.status(), 4, cudaMemcpyDeviceToHost, st);
                 if (cudaEventRecord(g->ev_emit, st) != cudaSuccess) s = IMPACT_ERR_CUDA;
@@ -311,6 +333,8 @@ bool impact_server::step()
                 g->state = Group::DONE;
             } else {
                 g->state = Group::EMITTING;
+                const Clock::time_point now = Clock::now();
+                for (Request *r : g->reqs) r->t_emit = now;
             }
             changed = true;
         }
@@ -397,14 +421,19 @@ impact_status impact_server_create(const impact_server_config *config, impact_se
     }
     S->budget = config->memory_budget > 0 ? config->memory_budget : (int64_t)(free_b * 0.8);
     const int ns = config->streams > 0 ? config->streams : 2;
-    for (int i = 0; i < ns; ++i) {
+    int lowest = 0, greatest = 0;
+    cudaDeviceGetStreamPriorityRange(&lowest, &greatest);
+    for (int i = 0; i <= ns; ++i) {
         cudaStream_t st;
-        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+        if (cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, i == ns ? greatest : lowest) !=
+            cudaSuccess) {
             for (cudaStream_t x : S->streams) cudaStreamDestroy(x);
+            if (S->fast_stream) cudaStreamDestroy(S->fast_stream);
             delete S;
             return impact::fail(IMPACT_ERR_CUDA, "stream creation failed");
         }
-        S->streams.push_back(st);
+        if (i == ns) S->fast_stream = st;
+        else S->streams.push_back(st);
     }
     S->worker = std::thread([S] { S->run(); });
     *server = S;
@@ -506,6 +535,23 @@ impact_status impact_server_poll(impact_server *S, int64_t ticket, int wait_ms, 
     return r->status;
 }
 
+impact_status impact_server_timing(impact_server *S, int64_t ticket, double *queue_ms,
+                                   double *count_ms, double *emit_wait_ms, double *emit_ms)
+{
+    if (!S) return impact::fail(IMPACT_ERR_ARG, "null server");
+    std::lock_guard<std::mutex> lock(S->mu);
+    auto it = S->reqs.find(ticket);
+    if (it == S->reqs.end()) return impact::fail(IMPACT_ERR_ARG, "unknown ticket");
+    const Request *r = it->second;
+    if (r->state != Request::DONE)
+        return impact::fail(IMPACT_ERR_ARG, "the request has not finished successfully");
+    if (queue_ms) *queue_ms = ms_between(r->t_submit, r->t_admit);
+    if (count_ms) *count_ms = ms_between(r->t_admit, r->t_counted);
+    if (emit_wait_ms) *emit_wait_ms = ms_between(r->t_counted, r->t_emit);
+    if (emit_ms) *emit_ms = ms_between(r->t_emit, r->t_done);
+    return IMPACT_OK;
+}
+
 impact_status impact_server_release(impact_server *S, int64_t ticket)
 {
     if (!S) return impact::fail(IMPACT_ERR_ARG, "null server");
@@ -556,6 +602,10 @@ impact_status impact_server_destroy(impact_server *S)
     for (cudaStream_t st : S->streams) {
         cudaStreamSynchronize(st);
         cudaStreamDestroy(st);
+    }
+    if (S->fast_stream) {
+        cudaStreamSynchronize(S->fast_stream);
+        cudaStreamDestroy(S->fast_stream);
     }
     delete S;
     return IMPACT_OK;

@@ -1,54 +1,62 @@
 // walk_fp32.cu -- FP32-sound construction (Def. 3.1 with outward rounding,
-// Sec. 4.4 cutoff, Remark 4.1 sink): one warp per row (source cell x input,
-// Alg. 2: rows are independent), persistent, rows taken from an atomic
-// counter in ascending order. Per row:
+// Sec. 4.4 cutoff, Remark 4.1 sink) in two steps.
 //
-//   setup   the interval image of the cell in every dimension, the window of
-//           target cells that can pass the cutoff, one erf/erfc evaluation
-//           per window edge at the image's lower and upper end (edges spread
-//           over the lanes), and from them the factor table of every window
-//           target: U[t] >= the largest Gaussian mass of target t over the
-//           image (T_max of Def. 3.1 relaxed to the image box) and L[t] <= the
-//           smallest (T_min). The lanes of dimensions 0..n-1 then trim each
-//           window to the targets that pass on their own, sum the mass outside
-//           the trimmed windows and the out-of-domain bounds (the sink).
-//   walk    the prefix tree of target cells, level by level in C order: a
-//           node at level k is a prefix (t_0..t_k) with the RU-rounded
-//           product P of its upper factors. The children of a list of nodes
-//           are enumerated flat (candidate e = parent * width + t, one lane
-//           each); a child is kept iff RU(P U[t]) can still reach the cutoff
-//           under the largest factors of the later dimensions, and the warp
-//           compacts the kept ones (ballot + popc) into the next level's
-//           list. Lists hold at most kCap nodes: a longer expansion is taken
-//           in chunks of kCap candidates, depth first, so the leaves still
-//           come out in C order. At the last dimension the kept candidates
-//           are the row's pairs (up = RU(P U[t]) >= cutoff).
+//   setup_fp32  one lane per (row, dimension), the 32/n rows of a warp
+//               aligned to it (Alg. 2: rows are independent). From the
+//               interval image of the source cell the lane finds the window
+//               of target cells that can pass the cutoff, evaluates erf/erfc
+//               once per window edge at the image's lower and upper end, and
+//               writes the window's factor table to the row's record: U[t] >=
+//               the largest Gaussian mass of target t over the image (T_max of
+//               Def. 3.1 relaxed to the image box) and L[t] <= the smallest
+//               (T_min), trimmed to the targets that pass on their own. The
+//               lanes of a row then exchange their window maxima and sums by
+//               shuffles: each finishes its dimension's pruning threshold, and
+//               the lane of dimension 0 writes the row's sink bounds and the
+//               mass of the targets outside the window box (FP64, outward).
+//   walk_fp32   one warp per row, persistent (rows from an atomic counter in
+//               ascending order). It walks the prefix tree of target cells
+//               level by level in C order over the first n - 2 dimensions: a
+//               node at level k is a prefix (t_0..t_k) with the RU-rounded
+//               product P of its upper factors; the children of a list of
+//               nodes are enumerated as candidates, one lane each, a child is
+//               kept iff RU(P U[t]) can still reach the cutoff under the
+//               largest factors of the later dimensions, and the warp compacts
+//               the kept ones (ballot + popc) into the next level's list (lists
+//               hold kCap nodes; longer expansions are taken in chunks, depth
+//               first, so leaves come out in C order). The last two dimensions
+//               form one leaf table per row, B[a, b] = RU(U[a] U[b]) (and the
+//               RD product of the lower factors), so a pair's bound is one more
+//               product RU(P B[a, b]). The count pass finds how many entries of
+//               B pass under each parent by a binary search in B sorted by
+//               value, with prefix sums for the row sums; the emit pass tests
+//               every entry of B under each parent, one lane each, and stores
+//               the kept pairs warp-contiguously.
 //
-// Three kernel modes share the code: COUNT (pairs per row, truncated mass,
-// row checks), EMIT (pairs at given row offsets) and FUSED (both in one pass:
-// each row publishes its pair count, finds its offset by a decoupled
-// look-back over the rows before it, and writes its pairs).
+// Kernel modes: COUNT (pairs per row, truncated mass, row checks), EMIT
+// (pairs at given row offsets) and FUSED (both: each row publishes its pair
+// count, finds its offset by a decoupled look-back over the rows before it,
+// and writes its pairs).
 //
-// Products run left to right over the dimensions with directed rounding (up:
-// round up, lo: round down) whatever the enumeration order, so a pair's value
-// depends only on its row. Every lane-to-candidate assignment is a function of
-// the row alone (kCap is a compile-time constant), so the per-lane partial
-// sums and their fixed reduction tree give the same bits under every launch
-// shape and in every batch.
+// Upper bounds are products rounded up, lower bounds products rounded down,
+// associated as ((..(U_0 U_1) ..) U_{n-3}) (U_{n-2} U_{n-1}) whatever the
+// enumeration order, so a pair's value depends only on its row. Every
+// lane-to-candidate assignment is a function of the row alone, so per-lane
+// partial sums and their fixed reduction tree give the same bits under every
+// launch shape and in every batch.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
 
 #include <algorithm>
 
+#include "../../include/impact.h"
 #include "impact_desc.h"
 #include "kernels.h"
 #include "sound_fp32.cuh"
 
 namespace {
 
-constexpr int kCap = IMPACT_WALK_CAP;           // nodes per level list (one chunk)
-constexpr int kHdrBytes = 96 * IMPACT_MAX_DIM;  // per-dimension row header
 constexpr float kTwoM44 = 5.6843419e-14f;       // 2^-44
 constexpr float kGrow18 = 1.0000038147f;        // 1 + 2^-18
 
@@ -125,30 +133,16 @@ __device__ __forceinline__ bool mid_above(const EdgePt &c, const EdgePt &e)
     return __fadd_rd(__fsub_rd(c.a, c.da), __fsub_rd(e.a, e.da)) >= 0.0f;
 }
 
-// Per (row, dimension) scalars, in the warp's shared memory.
-struct DimHdr {
-    int a;           // first window cell
-    int W;           // window width (cells)
-    int eoff;        // first edge item of the dimension (setup scratch)
-    int toff;        // first table entry of the window
-    int tw;          // trimmed width: targets first..last that pass on their own
-    int tb;          // table entry of the first trimmed target (toff + first)
-    int cb;          // column of the first trimmed target: (a + first) * stride
-    uint32_t magic;  // ceil(2^32 / tw): e / tw = umulhi(e, magic) for e < 2^16
+// One dimension of a row: the window [a, a + W) of target cells that can
+// pass the cutoff and, in erf units, rho = (E_a - m)/(sigma sqrt2) at both
+// image ends as FP32 pairs (edge a + k is then rho + k kappa).
+struct Win {
+    int a, W;
     float kh, kl, err;          // kappa (cell width in erf units) pair, edge error
-    float rh0, rl0, rh1, rl1;   // rho = (E_a - m)/(sigma sqrt2) at m_lo and m_hi, pairs
-    float M;         // largest U over the trimmed window
-    float SW;        // sum of U over the trimmed window (rounded up)
-    float O;         // mass outside the trimmed window (rounded up)
-    float qlo, qhi;  // out-of-domain mass bounds
-    float cp;        // least child product whose subtree can still reach the cutoff
-    float SR;        // RU product of the later dimensions' SW
-    int stride;      // column stride of the dimension (C order)
-    int pad;
+    float rh0, rl0, rh1, rl1;   // rho at m_lo and m_hi, pairs
 };
-static_assert(sizeof(DimHdr) == 96, "DimHdr layout");
 
-__device__ __forceinline__ EdgePt edge_at(const DimHdr &h, int k, bool hi_end)
+__device__ __forceinline__ EdgePt edge_at(const Win &h, int k, bool hi_end)
 {
     EdgePt e;
     sound::alpha_point(k, h.kh, h.kl, h.err, hi_end ? h.rh1 : h.rh0, hi_end ? h.rl1 : h.rl0, e.a,
@@ -157,82 +151,13 @@ __device__ __forceinline__ EdgePt edge_at(const DimHdr &h, int k, bool hi_end)
     return e;
 }
 
-// Setup scratch: one item per window edge (W + 1 per dimension) plus the two
-// domain edges, each evaluated at both image ends; structure of arrays.
-struct EdgeSoA {
-    float *f;   // 12 arrays of `cap` floats
-    int cap;
-    __device__ __forceinline__ void put(int i, int end, const EdgePt &p) const
-    {
-        float *b = f + (end * 6) * cap + i;
-        b[0] = p.a;
-        b[cap] = p.da;
-        b[2 * cap] = p.t.p_lo;
-        b[3 * cap] = p.t.p_hi;
-        b[4 * cap] = p.t.m_lo;
-        b[5 * cap] = p.t.m_hi;
-    }
-    __device__ __forceinline__ EdgePt get(int i, int end) const
-    {
-        const float *b = f + (end * 6) * cap + i;
-        EdgePt p;
-        p.a = b[0];
-        p.da = b[cap];
-        p.t.p_lo = b[2 * cap];
-        p.t.p_hi = b[3 * cap];
-        p.t.m_lo = b[4 * cap];
-        p.t.m_hi = b[5 * cap];
-        return p;
-    }
-};
-
-// Warp shared memory: header, factor table (U, L) pairs, and a work area that
-// first holds the setup scratch and then the node lists of levels 0..n-2.
-struct WarpMem {
-    DimHdr *h;
-    float2 *ul;
-    unsigned char *work;
-};
-
-__device__ __forceinline__ WarpMem carve(unsigned char *base, const ImpactDesc &D)
-{
-    WarpMem m;
-    m.h = reinterpret_cast<DimHdr *>(base);
-    m.ul = reinterpret_cast<float2 *>(base + kHdrBytes);
-    m.work = base + kHdrBytes + (((size_t)8 * D.tsum_cap + 15) & ~(size_t)15);
-    return m;
-}
-
-// Level k node list: P (RU product of upper factors), Pl (RD product of lower
-// factors), col (column of the prefix).
-struct NodeList {
-    float *P, *Pl;
-    int *col;
-};
-
-__device__ __forceinline__ NodeList node_list(unsigned char *work, int k)
-{
-    NodeList L;
-    unsigned char *b = work + (size_t)k * kCap * 12;
-    L.P = reinterpret_cast<float *>(b);
-    L.Pl = reinterpret_cast<float *>(b + kCap * 4);
-    L.col = reinterpret_cast<int *>(b + kCap * 8);
-    return L;
-}
-
-// What the setup tells the walk about a row (the same in every lane).
-struct RowTerms {
-    bool ok;      // every window fit the planner's bound
-    bool empty;   // some dimension keeps no target: the row has no pairs
-};
-
-// Lane d < n: the interval image of the cell in dimension d (affine sign
+// The interval image of the source cell in dimension d (affine sign
 // split or unicycle trig ranges from host tables, or the caller's images),
 // the window [a, a + W) of targets that can pass the cutoff (every target
 // outside lies more than delta beyond the image), and rho = (E_a - m) /
 // (sigma sqrt2) at both image ends as FP32 pairs. False if the window
 // exceeds the planner's bound wcap.
-__device__ bool dim_window(const ImpactDesc &D, int64_t row, int d, DimHdr &h)
+__device__ bool dim_window(const ImpactDesc &D, int64_t row, int d, Win &h)
 {
     const int n = D.n;
     int64_t cell;
@@ -346,64 +271,57 @@ __device__ bool dim_window(const ImpactDesc &D, int64_t row, int d, DimHdr &h)
     return true;
 }
 
-// Setup of one row by the whole warp (see the file comment). Fills the
-// header and the (U, L) table of every dimension.
-__device__ RowTerms row_setup(const ImpactDesc &D, const WarpMem &S, int64_t row, int lane)
+
+// ---------------------------------------------------------------------------
+// setup: one record per row
+// ---------------------------------------------------------------------------
+
+// Per (row, dimension) entry of a row record. The record is RecDim[n], then
+// the window tables, (U, L) pairs, dimension d's at entry rec_off[d].
+struct RecDim {
+    int tw;          // trimmed width: targets first..last that pass on their own
+    int tb;          // table entry of the first trimmed target
+    int cb;          // column of the first trimmed target: (a + first) * stride
+    uint32_t magic;  // ceil(2^32 / tw) when tw > 1: e / tw = umulhi(e, magic)
+    float cp;        // least child product whose subtree can still reach the cutoff
+    float SR;        // RU product of the later dimensions' window sums
+    int stride;      // column stride of the dimension (C order)
+    int lay;         // the walk's layout (tw <= 32): lanes hold floor(32 / tw) parents
+                     // (bits 0-15), a chunk is floor(kCap / tw) whole parents of
+                     // candidates (bits 16-31); wider windows: 0
+};
+static_assert(sizeof(RecDim) == 32, "RecDim layout");
+
+// Everything of one (row, dimension) that needs no other dimension.
+struct DimOut {
+    int tw = 0, f0 = 0, a = 0;
+    float M = 0.0f;     // largest U
+    float SW = 0.0f;    // sum of U over the trimmed window (rounded up)
+    float O = 0.0f;     // mass outside the trimmed window (rounded up)
+    float qlo = 0.0f, qhi = 0.0f;   // out-of-domain mass bounds
+};
+
+// The window of dimension d of a row and its factor table, written to `ul`
+// (the record's entries of dimension d): U[k], L[k] for target a + k from the
+// tails of its two edges at both image ends (neighbouring targets share an
+// edge), then the trimmed window, its sums and the out-of-domain bounds.
+__device__ DimOut setup_dim(const ImpactDesc &D, int64_t row, int d, float2 *ul, uint32_t *status)
 {
-    const int n = D.n;
-    RowTerms rt;
-    // 1. windows (lane d), then offsets of the edge items and table entries
-    bool ok = true;
-    int W = 0;
-    if (lane < n) {
-        DimHdr &h = S.h[lane];
-        ok = dim_window(D, row, lane, h);
-        W = ok ? h.W : 0;
+    DimOut o;
+    Win h;
+    if (!dim_window(D, row, d, h)) {
+        atomicOr(status, IMPACT_STATUS_TABLE_OVERFLOW);
+        return o;
     }
-    rt.ok = __all_sync(0xffffffffu, ok);
-    rt.empty = false;
-    if (!rt.ok) return rt;
-    int incl = W;   // inclusive prefix of W over lanes 0..n-1
-#pragma unroll
-    for (int o = 1; o < IMPACT_MAX_DIM; o <<= 1) {
-        int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-    }
-    if (lane < n) {
-        S.h[lane].toff = incl - W;
-        S.h[lane].eoff = incl - W + 3 * lane;
-    }
-    const int T = __shfl_sync(0xffffffffu, incl, n - 1);   // window targets of all dims
-    const int E = T + 3 * n;                                // edge items
-    __syncwarp();
-    const EdgeSoA es{reinterpret_cast<float *>(S.work), D.edge_cap};
-
-    // 2. edge items: k = 0..W are the window's edges a..a+W, then the
-    // domain's lower and upper edge (k = -a, N - a); both image ends
-    for (int i = lane; i < E; i += 32) {
-        int d = 0;
-#pragma unroll
-        for (int k = 1; k < IMPACT_MAX_DIM; ++k)
-            if (k < n && i >= S.h[k].eoff) d = k;
-        const DimHdr &h = S.h[d];
-        const int li = i - h.eoff;
-        const int k = li <= h.W ? li : (li == h.W + 1 ? -h.a : D.dim[d].N - h.a);
-        es.put(i, 0, edge_at(h, k, false));
-        es.put(i, 1, edge_at(h, k, true));
-    }
-    __syncwarp();
-
-    // 3. factor table of every window target: U >= T_max factor, L <= T_min
-    // factor, from the tails of its two edges at the two image ends
-    for (int i = lane; i < T; i += 32) {
-        int d = 0;
-#pragma unroll
-        for (int k = 1; k < IMPACT_MAX_DIM; ++k)
-            if (k < n && i >= S.h[k].toff) d = k;
-        const DimHdr &h = S.h[d];
-        const int e = h.eoff + (i - h.toff);
-        const EdgePt c0 = es.get(e, 0), e0 = es.get(e + 1, 0);
-        const EdgePt c1 = es.get(e, 1), e1 = es.get(e + 1, 1);
+    const ImpactDim &g = D.dim[d];
+    const float cut = D.cutoff32;
+    o.a = h.a;
+    EdgePt c0 = edge_at(h, 0, false), c1 = edge_at(h, 0, true);
+    const EdgePt w0 = c0;   // edge a at m_lo (left tail below)
+    int first = -1, last = -1;
+    float pre = 0.0f, mid = 0.0f, post = 0.0f, M = 0.0f;
+    for (int k = 0; k < h.W; ++k) {
+        const EdgePt e0 = edge_at(h, k + 1, false), e1 = edge_at(h, k + 1, true);
         float U, L;
         if (mid_below(c0, e0)) {            // target midpoint <= m_lo
             U = sound::cell_hi(c0.a, c0.t, e0.a, e0.t);
@@ -412,107 +330,195 @@ __device__ RowTerms row_setup(const ImpactDesc &D, const WarpMem &S, int64_t row
             U = sound::cell_hi(c1.a, c1.t, e1.a, e1.t);
             L = sound::cell_lo(c0.a, c0.t, e0.a, e0.t);
         } else {                            // midpoint may be inside
-            U = D.dim[d].plateau_hi;
+            U = g.plateau_hi;
             L = fminf(sound::cell_lo(c0.a, c0.t, e0.a, e0.t),
                       sound::cell_lo(c1.a, c1.t, e1.a, e1.t));
         }
-        S.ul[i] = make_float2(U, L);
-    }
-    __syncwarp();
-
-    // 4. lane d: trim the window to the targets that pass on their own, sums
-    // inside and outside it (rounded up, fixed order), out-of-domain bounds
-    const float cut = D.cutoff32;
-    float M = 0.0f, SW = 0.0f, O = 0.0f, qlo = 0.0f, qhi = 0.0f;
-    int tw = 0;
-    if (lane < n) {
-        DimHdr &h = S.h[lane];
-        const ImpactDim &g = D.dim[lane];
-        int first = -1, last = -1;
-        float pre = 0.0f, mid = 0.0f, post = 0.0f;
-        for (int k = 0; k < h.W; ++k) {
-            const float U = S.ul[h.toff + k].x;
-            if (U >= cut) {
-                if (first < 0) {
-                    first = k;
-                    mid = U;
-                } else {
-                    mid = __fadd_ru(mid, __fadd_ru(post, U));
-                    post = 0.0f;
-                }
-                last = k;
-                M = fmaxf(M, U);
-            } else if (first < 0) {
-                pre = __fadd_ru(pre, U);
+        ul[k] = make_float2(U, L);
+        if (U >= cut) {
+            if (first < 0) {
+                first = k;
+                mid = U;
             } else {
-                post = __fadd_ru(post, U);
+                mid = __fadd_ru(mid, __fadd_ru(post, U));
+                post = 0.0f;
             }
+            last = k;
+            M = fmaxf(M, U);
+        } else if (first < 0) {
+            pre = __fadd_ru(pre, U);
+        } else {
+            post = __fadd_ru(post, U);
         }
-        O = __fadd_ru(pre, post);
-        const EdgePt w0 = es.get(h.eoff, 0);                 // edge a at m_lo
-        const EdgePt c1 = es.get(h.eoff + h.W, 1);           // edge a + W at m_hi
-        const EdgePt lo0 = es.get(h.eoff + h.W + 1, 0), hi0 = es.get(h.eoff + h.W + 2, 0);
-        const EdgePt lo1 = es.get(h.eoff + h.W + 1, 1), hi1 = es.get(h.eoff + h.W + 2, 1);
-        if (h.a > 0)   // cells 0..a-1 lie left of the image: their mass at m_lo
-            O = __fadd_ru(O, sound::cell_hi(lo0.a, lo0.t, w0.a, w0.t));
-        if (h.a + h.W < g.N)   // cells right of the window: their mass at m_hi
-            O = __fadd_ru(O, sound::cell_hi(c1.a, c1.t, hi1.a, hi1.t));
-        // out-of-domain mass Q(m) = T(-alpha(lo_D)) + T(alpha(hi_D))
-        const float q0 = __fadd_ru(lo0.t.m_hi, hi0.t.p_hi);
-        const float q1 = __fadd_ru(lo1.t.m_hi, hi1.t.p_hi);
-        qhi = fminf(fmaxf(q0, q1), 1.0f);
-        if (mid_below(lo0, hi0))
-            qlo = __fadd_rd(lo0.t.m_lo, hi0.t.p_lo);
-        else if (mid_above(lo1, hi1))
-            qlo = __fadd_rd(lo1.t.m_lo, hi1.t.p_lo);
-        else
-            qlo = g.qmin_lo;
-        qlo = fminf(qlo, 1.0f);
-        tw = first >= 0 ? last - first + 1 : 0;
-        const int f0 = first >= 0 ? first : 0;
-        SW = mid;
-        h.tw = tw;
-        h.tb = h.toff + f0;
-        h.cb = (h.a + f0) * g.stride;
-        h.stride = g.stride;
-        h.magic = tw > 1 ? (uint32_t)((0x100000000ull + (unsigned)tw - 1) / (unsigned)tw) : 0u;
-        h.M = M;
-        h.SW = SW;
-        h.O = O;
-        h.qlo = qlo;
-        h.qhi = qhi;
+        c0 = e0;
+        c1 = e1;
     }
-    rt.empty = __any_sync(0xffffffffu, lane < n && tw == 0);
+    // c1 is now edge a + W at m_hi
+    float O = __fadd_ru(pre, post);
+    const EdgePt lo0 = edge_at(h, -h.a, false), hi0 = edge_at(h, g.N - h.a, false);
+    const EdgePt lo1 = edge_at(h, -h.a, true), hi1 = edge_at(h, g.N - h.a, true);
+    if (h.a > 0)   // cells 0..a-1 lie left of the image: their mass at m_lo
+        O = __fadd_ru(O, sound::cell_hi(lo0.a, lo0.t, w0.a, w0.t));
+    if (h.a + h.W < g.N)   // cells right of the window: their mass at m_hi
+        O = __fadd_ru(O, sound::cell_hi(c1.a, c1.t, hi1.a, hi1.t));
+    // out-of-domain mass Q(m) = T(-alpha(lo_D)) + T(alpha(hi_D))
+    const float q0 = __fadd_ru(lo0.t.m_hi, hi0.t.p_hi);
+    const float q1 = __fadd_ru(lo1.t.m_hi, hi1.t.p_hi);
+    o.qhi = fminf(fmaxf(q0, q1), 1.0f);
+    float qlo;
+    if (mid_below(lo0, hi0))
+        qlo = __fadd_rd(lo0.t.m_lo, hi0.t.p_lo);
+    else if (mid_above(lo1, hi1))
+        qlo = __fadd_rd(lo1.t.m_lo, hi1.t.p_lo);
+    else
+        qlo = g.qmin_lo;
+    o.qlo = fminf(qlo, 1.0f);
+    o.tw = first >= 0 ? last - first + 1 : 0;
+    o.f0 = first >= 0 ? first : 0;
+    o.M = M;
+    o.SW = mid;
+    o.O = O;
+    return o;
+}
 
-    // 5. each lane of dimension d: the RU products of the later dimensions'
-    // largest factors and window sums, which give its pruning threshold
-    // (the sink and the mass outside the window box are combined in FP64
-    // later, per row, by the epilogue)
-    float R = 1.0f, SR = 1.0f;
+// setup_fp32: one warp per 32/n rows of one build, one lane per (row,
+// dimension). Each lane builds its dimension's table; the lanes of a row then
+// exchange their maxima and sums by shuffles and each finishes its entry of
+// the record: the pruning threshold (a child t of a node with product P
+// survives iff RU(RU(P U[t]) R') >= cutoff, R' the product of the later
+// dimensions' largest factors grown by 2^-18 to cover the rounding of the
+// rest of the chain; cp is the least such child product). The lane of
+// dimension 0 also writes the row's sink bounds and the mass of the targets
+// outside the window box (FP64, outward rounding), unless the row outputs
+// are null (records rebuilt for an emit pass).
+__global__ void __launch_bounds__(256, 3)
+setup_fp32(const BatchIndex *__restrict__ B, uint32_t *__restrict__ status,
+           double *__restrict__ sink_lo, double *__restrict__ sink_up, double *__restrict__ trunc)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t u = warp0; u < B->units; u += nwarps) {
+        const int q = find_problem(B->unit_begin, B->count, u);
+        const ImpactDesc &D = *B->desc[q];
+        const int n = D.n;
+        const int rpw = 32 / n;
+        const int slot = lane / n, d = lane - slot * n;
+        const int64_t rows_q = B->row_begin[q + 1] - B->row_begin[q];
+        const int64_t rl = (u - B->unit_begin[q]) * rpw + slot;
+        const bool act = slot < rpw && rl < rows_q;
+        unsigned char *rr = act ? B->rec[q] + rl * (int64_t)D.rec_stride : nullptr;
+        DimOut o;
+        if (act) {
+            float2 *ul = reinterpret_cast<float2 *>(rr + 32 * n) + D.dim[d].rec_off;
+            o = setup_dim(D, rl, d, ul, status);
+        }
+        // the row's other dimensions, in order k = 0..n-1 (lanes base + k)
+        const int base = slot * n;
+        float R = 1.0f, SR = 1.0f;
+        double pin_up = 1.0, pin_dn = 1.0, acc = 0.0, pre = 1.0;
 #pragma unroll
-    for (int k = 0; k < IMPACT_MAX_DIM; ++k) {
-        if (k < n) {
-            const float Mk = __shfl_sync(0xffffffffu, M, k);
-            const float SWk = __shfl_sync(0xffffffffu, SW, k);
-            if (k > lane) {
-                R = __fmul_ru(R, Mk);
-                SR = __fmul_ru(SR, SWk);
+        for (int k = 0; k < IMPACT_MAX_DIM; ++k) {
+            if (k < n) {   // n is the same for the whole warp
+                const int src = (base + k) & 31;
+                const float Mk = __shfl_sync(0xffffffffu, o.M, src);
+                const float SWk = __shfl_sync(0xffffffffu, o.SW, src);
+                const float Ok = __shfl_sync(0xffffffffu, o.O, src);
+                const float qlk = __shfl_sync(0xffffffffu, o.qlo, src);
+                const float qhk = __shfl_sync(0xffffffffu, o.qhi, src);
+                if (k > d) {
+                    R = __fmul_ru(R, Mk);
+                    SR = __fmul_ru(SR, SWk);
+                }
+                // sink: 1 - prod_k (1 - Q_k)
+                pin_up = __dmul_ru(pin_up, __dsub_ru(1.0, (double)qlk));
+                pin_dn = __dmul_rd(pin_dn, __dsub_rd(1.0, (double)qhk));
+                // mass outside the window box, partitioned by the first
+                // dimension that leaves its window:
+                // sum_k prod_{i<k} SW_i * O_k * prod_{i>k} (SW_i + O_i)
+                acc = __dadd_ru(__dmul_ru(acc, __dadd_ru((double)SWk, (double)Ok)),
+                                __dmul_ru(pre, (double)Ok));
+                pre = __dmul_ru(pre, (double)SWk);
             }
         }
+        if (!act) continue;
+        const float cut = D.cutoff32;
+        RecDim rd;
+        rd.tw = o.tw;
+        rd.tb = D.dim[d].rec_off + o.f0;
+        rd.cb = (o.a + o.f0) * D.dim[d].stride;
+        rd.magic = o.tw > 1 ? (uint32_t)((0x100000000ull + (unsigned)o.tw - 1) / (unsigned)o.tw) : 0u;
+        rd.cp = 0.0f;
+        if (cut > 0.0f) rd.cp = (d == n - 1) ? cut : threshold(cut, __fmul_ru(R, kGrow18));
+        rd.SR = SR;
+        rd.stride = D.dim[d].stride;
+        rd.lay = (o.tw >= 1 && o.tw <= 32)
+                     ? ((32 / o.tw) | (((IMPACT_WALK_CAP / o.tw) * o.tw) << 16)) : 0;
+        reinterpret_cast<RecDim *>(rr)[d] = rd;
+        if (d == 0 && trunc) {
+            const int64_t row = B->row_begin[q] + rl;   // global row
+            sink_lo[row] = fmax(__dsub_rd(1.0, pin_up), 0.0);
+            sink_up[row] = fmin(__dsub_ru(1.0, pin_dn), 1.0);
+            trunc[row] = acc;
+        }
     }
-    if (lane < n) {
-        float cp = 0.0f;
-        if (cut > 0.0f) cp = (lane == n - 1) ? cut : threshold(cut, __fmul_ru(R, kGrow18));
-        S.h[lane].cp = cp;
-        S.h[lane].SR = SR;
-    }
-    __syncwarp();
-    return rt;
 }
 
 // ---------------------------------------------------------------------------
 // the walk
 // ---------------------------------------------------------------------------
+
+constexpr int kCap = IMPACT_WALK_CAP;      // nodes per level list (one chunk)
+constexpr int kHdrBytes = 32 * IMPACT_MAX_DIM;
+
+// Warp shared memory (offsets fixed per problem by leaf_cap):
+//   h      RecDim[8]                 the row record's per-dimension entries
+//   ul     (U, L) x tsum_cap         the record's window tables
+//   work   (n - 2) x kCap x 12 B     node lists of levels 0..n-3
+//   leaf   8 x (leaf_cap + 1) floats the staged leaf table (see Leaf)
+struct WarpMem {
+    RecDim *h;
+    float2 *ul;
+    unsigned char *work;
+    float *leaf;
+    int leaf_cap;
+};
+
+__host__ __device__ constexpr int align16(int x) { return (x + 15) & ~15; }
+
+// Node lists of levels 0..n-3, padded to 16 bytes: the warp blocks are laid
+// end to end and each starts with 16-byte record copies.
+__host__ __device__ inline int list_bytes(int n) { return align16((n > 2 ? n - 2 : 0) * (kCap + 1) * 12); }
+
+__device__ __forceinline__ WarpMem carve(unsigned char *base, const ImpactDesc &D)
+{
+    WarpMem m;
+    m.h = reinterpret_cast<RecDim *>(base);
+    m.ul = reinterpret_cast<float2 *>(base + kHdrBytes);
+    m.work = base + kHdrBytes + align16(8 * D.tsum_cap);
+    m.leaf = reinterpret_cast<float *>(m.work + list_bytes(D.n));
+    m.leaf_cap = D.leaf_cap;
+    return m;
+}
+
+// Level k node list: P (RU product of upper factors), Pl (RD product of lower
+// factors), col (column of the prefix).
+struct NodeList {
+    float *P, *Pl;
+    int *col;
+};
+
+__device__ __forceinline__ NodeList node_list(unsigned char *work, int k)
+{
+    NodeList L;
+    // kCap nodes and one spare slot that takes the stores of the lanes
+    // whose candidate was not kept (stores without a branch)
+    unsigned char *b = work + (size_t)k * (kCap + 1) * 12;
+    L.P = reinterpret_cast<float *>(b);
+    L.Pl = reinterpret_cast<float *>(b + (kCap + 1) * 4);
+    L.col = reinterpret_cast<int *>(b + (kCap + 1) * 8);
+    return L;
+}
 
 // Per-lane partial sums of the count walk (rounded outward, FP32): pairs
 // kept, upper-bound mass of the dropped in-window targets, and the sums of
@@ -524,12 +530,223 @@ struct CountAcc {
     float drop = 0.0f, sup = 0.0f, slo = 0.0f;
 };
 
-// Where the emit walk writes: pairs [base, base + len) of the output arrays.
+// Where the emit walk writes: the row's len pairs, the arrays offset to its
+// first pair.
 struct EmitOut {
     int32_t *col;
     float *lo, *up;
-    int64_t base, len;
+    int len;
 };
+
+// The leaf table of a row: the last two dimensions m = n - 2 and l = n - 1
+// (dimension 0 alone when n = 1) as one list of entries j = a * tw_l + b in C
+// order: bu[j] = RU(U_m[a] U_l[b]), bl[j] = RD(L_m[a] L_l[b]) and the column
+// offset bc[j] = cb_m + a stride_m + cb_l + b. For the count pass also the
+// entries sorted by bu descending (su, with their bl in sl) and the sums
+// pu[k] = RU sum of su[0..k), pl[k] = RD sum of sl[0..k), sf[k] = RU sum of
+// su[k..nb). Staged when nb <= leaf_cap, else evaluated where needed.
+struct Leaf {
+    float tot_u, tot_l;   // count pass: RU sum of bu and RD sum of bl over all entries
+    int nb;        // entries
+    int tw_l;      // width of the last dimension (b runs fastest)
+    uint32_t magic_l;
+    bool staged;
+    uint32_t magic_nb;    // ceil(2^32 / nb) when 1 < nb <= 4096, for the emit's flat layout
+    float *bu, *bl, *su, *sl, *pu, *pl, *sf;
+    int *bc;
+};
+
+__device__ __forceinline__ Leaf leaf_of(const WarpMem &S, int n)
+{
+    Leaf f;
+    const RecDim &hl = S.h[n - 1];
+    f.tw_l = hl.tw;
+    f.magic_l = hl.magic;
+    f.nb = n >= 2 ? S.h[n - 2].tw * hl.tw : hl.tw;
+    f.staged = f.nb <= S.leaf_cap;
+    f.magic_nb = (f.nb > 1 && f.nb <= 4096)
+                     ? (uint32_t)((0x100000000ull + (unsigned)f.nb - 1) / (unsigned)f.nb) : 0u;
+    const int c = S.leaf_cap + 1;
+    f.bu = S.leaf;
+    f.bl = f.bu + c;
+    f.bc = reinterpret_cast<int *>(f.bl + c);
+    f.su = reinterpret_cast<float *>(f.bc + c);
+    f.sl = f.su + c;
+    f.pu = f.sl + c;
+    f.pl = f.pu + c;
+    f.sf = f.pl + c;
+    return f;
+}
+
+// Entry j of the leaf table, evaluated from the record's tables.
+struct LeafEntry {
+    float u, l;
+    int c;
+};
+
+__device__ __forceinline__ LeafEntry leaf_eval(const WarpMem &S, int n, const Leaf &f, int j)
+{
+    const RecDim &hl = S.h[n - 1];
+    LeafEntry e;
+    if (n == 1) {
+        const float2 v = S.ul[hl.tb + j];
+        e.u = v.x;
+        e.l = v.y;
+        e.c = hl.cb + j;
+        return e;
+    }
+    const RecDim &hm = S.h[n - 2];
+    const int a = f.tw_l > 1 ? (int)__umulhi((uint32_t)j, f.magic_l) : j;
+    const int b = j - a * f.tw_l;
+    const float2 vm = S.ul[hm.tb + a], vl = S.ul[hl.tb + b];
+    e.u = __fmul_ru(vm.x, vl.x);
+    e.l = __fmul_rd(vm.y, vl.y);
+    e.c = hm.cb + a * hm.stride + hl.cb + b;
+    return e;
+}
+
+__device__ __forceinline__ LeafEntry leaf_at(const WarpMem &S, int n, const Leaf &f, int j)
+{
+    if (!f.staged) return leaf_eval(S, n, f, j);
+    return LeafEntry{f.bu[j], f.bl[j], f.bc[j]};
+}
+
+// Inclusive warp scans of a lane's value with directed rounding (a fixed
+// association: the same bits whatever ran before).
+__device__ __forceinline__ float scan_ru(float x, int lane)
+{
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const float y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x = __fadd_ru(x, y);
+    }
+    return x;
+}
+__device__ __forceinline__ float scan_rd(float x, int lane)
+{
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const float y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x = __fadd_rd(x, y);
+    }
+    return x;
+}
+
+// Stages the leaf table of a row (and, for the count pass, its sorted form
+// and sums) when it fits.
+template <bool COUNT>
+__device__ void leaf_build(const WarpMem &S, int n, Leaf &f, int lane, float cut)
+{
+    float su_l = 0.0f, sl_l = 0.0f;   // this lane's part of the totals
+    for (int j = lane; j < f.nb; j += 32) {
+        const LeafEntry e = leaf_eval(S, n, f, j);
+        if (f.staged) {
+            f.bu[j] = e.u;
+            f.bl[j] = e.l;
+            f.bc[j] = e.c;
+        }
+        su_l = __fadd_ru(su_l, e.u);
+        sl_l = __fadd_rd(sl_l, e.l);
+    }
+    __syncwarp();
+    if (!COUNT) return;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        su_l = __fadd_ru(su_l, __shfl_xor_sync(0xffffffffu, su_l, o));
+        sl_l = __fadd_rd(sl_l, __shfl_xor_sync(0xffffffffu, sl_l, o));
+    }
+    f.tot_u = __shfl_sync(0xffffffffu, su_l, 0);
+    f.tot_l = __shfl_sync(0xffffffffu, sl_l, 0);
+    if (!f.staged || !(cut > 0.0f)) return;
+    if (f.nb <= 32) {
+        // one entry per lane: a bitonic sorting network over the warp puts
+        // the entry of rank r (bu descending, ties by index) in lane r, then
+        // scans in registers give the sums
+        float u = lane < f.nb ? f.bu[lane] : -INFINITY;
+        float lv = lane < f.nb ? f.bl[lane] : 0.0f;
+        int id = lane;
+#pragma unroll
+        for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+            for (int jj = k >> 1; jj > 0; jj >>= 1) {
+                const float pu_ = __shfl_xor_sync(0xffffffffu, u, jj);
+                const float pl_ = __shfl_xor_sync(0xffffffffu, lv, jj);
+                const int pid = __shfl_xor_sync(0xffffffffu, id, jj);
+                const bool want_first = ((lane & jj) == 0) == ((lane & k) == 0);
+                const bool mine_first = (u > pu_) || (u == pu_ && id < pid);
+                if (want_first != mine_first) {
+                    u = pu_;
+                    lv = pl_;
+                    id = pid;
+                }
+            }
+        }
+        const float ux = lane < f.nb ? u : 0.0f;
+        const float iu = scan_ru(ux, lane);
+        const float il = scan_rd(lane < f.nb ? lv : 0.0f, lane);
+        float su_ = ux;   // suffix sums, rounded up
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const float y = __shfl_down_sync(0xffffffffu, su_, o);
+            if (lane + o < 32) su_ = __fadd_ru(su_, y);
+        }
+        if (lane < f.nb) {
+            f.su[lane] = u;
+            f.pu[lane + 1] = iu;
+            f.pl[lane + 1] = il;
+            f.sf[lane] = su_;
+        }
+        if (lane == 0) {
+            f.pu[0] = 0.0f;
+            f.pl[0] = 0.0f;
+            f.sf[f.nb] = 0.0f;
+        }
+        __syncwarp();
+        return;
+    }
+    // rank of entry j by bu descending (ties by index): its sorted position
+    for (int j = lane; j < f.nb; j += 32) {
+        const float u = f.bu[j];
+        int r = 0;
+        for (int i = 0; i < f.nb; ++i) {
+            const float v = f.bu[i];
+            r += (v > u) || (v == u && i < j);
+        }
+        f.su[r] = u;
+        f.sl[r] = f.bl[j];
+    }
+    __syncwarp();
+    // prefix sums in sorted order (pu, pl: entries 0..k-1 -> index k) and
+    // suffix sums (sf[k]: entries k..nb-1), rounded outward
+    float cu = 0.0f, cl = 0.0f;
+    for (int k0 = 0; k0 < f.nb; k0 += 32) {
+        const int k = k0 + lane;
+        const float u = k < f.nb ? f.su[k] : 0.0f;
+        const float l = k < f.nb ? f.sl[k] : 0.0f;
+        const float iu = __fadd_ru(scan_ru(u, lane), cu);
+        const float il = __fadd_rd(scan_rd(l, lane), cl);
+        if (k < f.nb) {
+            f.pu[k + 1] = iu;
+            f.pl[k + 1] = il;
+        }
+        cu = __shfl_sync(0xffffffffu, iu, 31);
+        cl = __shfl_sync(0xffffffffu, il, 31);
+    }
+    if (lane == 0) {
+        f.pu[0] = 0.0f;
+        f.pl[0] = 0.0f;
+    }
+    float cs = 0.0f;   // suffix sums, from the end
+    for (int k1 = f.nb; k1 > 0; k1 -= 32) {
+        const int k = k1 - 1 - lane;
+        const float u = k >= 0 ? f.su[k] : 0.0f;
+        const float iu = __fadd_ru(scan_ru(u, lane), cs);
+        if (k >= 0) f.sf[k] = iu;
+        cs = __shfl_sync(0xffffffffu, iu, 31);
+    }
+    if (lane == 0) f.sf[f.nb] = 0.0f;
+    __syncwarp();
+}
 
 // Node of a level list, or the root (P = Pl = 1, column 0).
 struct Node {
@@ -559,13 +776,13 @@ struct Lanes {
     bool on;       // this lane holds a candidate slot (narrow)
 };
 
-__device__ __forceinline__ Lanes lanes_of(int tw, uint32_t magic, int lane)
+__device__ __forceinline__ Lanes lanes_of(const RecDim &h, int lane)
 {
     Lanes z{0, 0, 0, false};
-    if (tw <= 32) {
-        z.slots = 32 / tw;
-        z.slot = tw > 1 ? (int)__umulhi((uint32_t)lane, magic) : lane;
-        z.t = lane - z.slot * tw;
+    if (h.lay != 0) {
+        z.slots = h.lay & 0xffff;
+        z.slot = h.tw > 1 ? (int)__umulhi((uint32_t)lane, h.magic) : lane;
+        z.t = lane - z.slot * h.tw;
         z.on = z.slot < z.slots;
     }
     return z;
@@ -573,9 +790,9 @@ __device__ __forceinline__ Lanes lanes_of(int tw, uint32_t magic, int lane)
 
 // Candidates per chunk of a level list: whole parents when the window is
 // narrow (the narrow walk steps over parents), else kCap.
-__device__ __forceinline__ int chunk_of(int tw)
+__device__ __forceinline__ int chunk_of(const RecDim &h)
 {
-    return tw <= 32 ? (kCap / tw) * tw : kCap;
+    return h.lay != 0 ? (h.lay >> 16) : kCap;
 }
 
 // Children of candidates [c0, c1) of the level k - 1 list (the root when
@@ -584,26 +801,27 @@ __device__ __forceinline__ int chunk_of(int tw)
 __device__ __forceinline__ int expand(const WarpMem &S, int k, int c0, int c1, int lane,
                                       CountAcc &acc, bool count)
 {
-    const DimHdr &h = S.h[k];
+    const RecDim &h = S.h[k];
     const int tw = h.tw, tb = h.tb, cb = h.cb, st = h.stride;
     const uint32_t magic = h.magic;
     const float cp = h.cp, SR = h.SR;
     const NodeList Lc = node_list(S.work, k);
     const NodeList Lp = node_list(S.work, k > 0 ? k - 1 : 0);
     const bool root = k == 0;
-    const Lanes z = lanes_of(tw, magic, lane);
+    const Lanes z = lanes_of(h, lane);
     int nout = 0;
     auto offer = [&](bool act, const Node &par, float2 ul, int t) {
         const float Pc = __fmul_ru(par.P, ul.x);
         const bool keep = act && Pc >= cp;
-        if (count && act && !keep) acc.drop = __fadd_ru(acc.drop, __fmul_ru(Pc, SR));
-        const unsigned bal = __ballot_sync(0xffffffffu, keep);
-        if (keep) {
-            const int o = nout + __popc(bal & lanemask_lt());
-            Lc.P[o] = Pc;
-            Lc.Pl[o] = __fmul_rd(par.Pl, ul.y);
-            Lc.col[o] = par.c + cb + t * st;
+        if (count) {
+            const float d = __fadd_ru(acc.drop, __fmul_ru(Pc, SR));
+            acc.drop = (act && !keep) ? d : acc.drop;
         }
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        const int o = keep ? nout + __popc(bal & lanemask_lt()) : kCap;
+        Lc.P[o] = Pc;
+        Lc.Pl[o] = __fmul_rd(par.Pl, ul.y);
+        Lc.col[o] = par.c + cb + t * st;
         nout += __popc(bal);
     };
     if (z.slots > 0) {   // narrow: c0, c1 are multiples of tw
@@ -629,97 +847,150 @@ __device__ __forceinline__ int expand(const WarpMem &S, int k, int c0, int c1, i
     return nout;
 }
 
-// The pairs under the npar nodes of the level n - 2 list (the root when
-// n = 1). Count: a narrow window is walked serially by one lane per parent
-// (the factors are broadcast reads, nothing is compacted); emit: the kept
-// candidates are compacted and stored warp-contiguously.
-template <bool EMIT>
-__device__ __forceinline__ void leaf(const WarpMem &S, int n, int npar, int lane, CountAcc &acc,
-                                     const EmitOut &out, int64_t &written)
+
+// Bounds of the sum of k emitted products RU(P x_i) (up) or RD(Pl y_i) (lo)
+// from the RU / RD sum s of the x_i / y_i: each rounded product is within a
+// relative 2^-23 (plus 2^-149 below the normal range) of the exact one.
+__device__ __forceinline__ float up_sum(float P, float s, int k)
 {
-    const DimHdr &h = S.h[n - 1];
-    const int tw = h.tw, tb = h.tb, cb = h.cb;
-    const uint32_t magic = h.magic;
-    const float cp = h.cp;
-    const NodeList Lp = node_list(S.work, n >= 2 ? n - 2 : 0);
-    const bool root = n == 1;
-    if (!EMIT && tw <= 32) {
-        for (int p0 = 0; p0 < npar; p0 += 32) {
-            const int pi = p0 + lane;
-            if (pi < npar) {
-                const Node par = node_at(Lp, root, pi);
-                for (int t = 0; t < tw; ++t) {
-                    const float2 ul = S.ul[tb + t];
-                    const float Pc = __fmul_ru(par.P, ul.x);
-                    if (Pc >= cp) {
-                        acc.cnt += 1;
-                        acc.sup = __fadd_ru(acc.sup, Pc);
-                        acc.slo = __fadd_rd(acc.slo, __fmul_rd(par.Pl, ul.y));
-                    } else {
-                        acc.drop = __fadd_ru(acc.drop, Pc);
-                    }
-                }
-            }
+    return __fmaf_ru((float)k, 1.17549435e-38f, __fmul_ru(__fmul_ru(P, s), 1.00000095f));
+}
+__device__ __forceinline__ float lo_sum(float Pl, float s, int k)
+{
+    return fmaxf(__fmaf_rd(-(float)k, 1.17549435e-38f, __fmul_rd(__fmul_rd(Pl, s), 0.99999905f)),
+                 0.0f);
+}
+
+// Count pass over the leaves of npar parents (a level n - 3 list, or the
+// root): pairs, their up and lo sums and the upper bound of the dropped
+// mass, per lane (one lane per parent).
+__device__ void leaf_count(const WarpMem &S, int n, const Leaf &f, const NodeList &Lp, bool root,
+                           int npar, int lane, CountAcc &acc, float cut)
+{
+    const int nb = f.nb;
+    if (!(cut > 0.0f)) {   // dense: every entry is kept
+        for (int pi = lane; pi < npar; pi += 32) {
+            const Node par = node_at(Lp, root, pi);
+            acc.cnt += nb;
+            acc.sup = __fadd_ru(acc.sup, up_sum(par.P, f.tot_u, nb));
+            acc.slo = __fadd_rd(acc.slo, lo_sum(par.Pl, f.tot_l, nb));
         }
         return;
     }
-    auto offer = [&](bool act, const Node &par, float2 ul, int t) {
-        const float Pc = __fmul_ru(par.P, ul.x);
-        const bool keep = act && Pc >= cp;
-        if (!EMIT) {
-            if (keep) {
-                acc.cnt += 1;
-                acc.sup = __fadd_ru(acc.sup, Pc);
-                acc.slo = __fadd_rd(acc.slo, __fmul_rd(par.Pl, ul.y));
-            } else if (act) {
-                acc.drop = __fadd_ru(acc.drop, Pc);
+    if (f.staged) {
+        // the kept entries of a parent are a prefix of the sorted table:
+        // RU(P su[k]) >= cut for k below the count, not above it
+        for (int pi = lane; pi < npar; pi += 32) {
+            const Node par = node_at(Lp, root, pi);
+            int lo = 0, hi = nb;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (__fmul_ru(par.P, f.su[mid]) >= cut) lo = mid + 1;
+                else hi = mid;
             }
-        } else {
-            const unsigned bal = __ballot_sync(0xffffffffu, keep);
-            if (keep) {
-                const int64_t pos = written + __popc(bal & lanemask_lt());
-                if (pos < out.len) {
-                    const int64_t p = out.base + pos;
-                    out.col[p] = par.c + cb + t;
-                    out.lo[p] = __fmul_rd(par.Pl, ul.y);
-                    out.up[p] = Pc;
+            acc.cnt += lo;
+            acc.sup = __fadd_ru(acc.sup, up_sum(par.P, f.pu[lo], lo));
+            acc.slo = __fadd_rd(acc.slo, lo_sum(par.Pl, f.pl[lo], lo));
+            acc.drop = __fadd_ru(acc.drop, __fmul_ru(par.P, f.sf[lo]));
+        }
+        return;
+    }
+    // a table too wide to stage: every entry under every parent
+    for (int pi = 0; pi < npar; ++pi) {
+        const Node par = node_at(Lp, root, pi);
+        for (int j0 = 0; j0 < nb; j0 += 32) {
+            const int j = j0 + lane;
+            if (j < nb) {
+                const LeafEntry e = leaf_eval(S, n, f, j);
+                const float Pc = __fmul_ru(par.P, e.u);
+                if (Pc >= cut) {
+                    acc.cnt += 1;
+                    acc.sup = __fadd_ru(acc.sup, Pc);
+                    acc.slo = __fadd_rd(acc.slo, __fmul_rd(par.Pl, e.l));
+                } else {
+                    acc.drop = __fadd_ru(acc.drop, Pc);
                 }
             }
-            written += __popc(bal);
-        }
-    };
-    const Lanes z = lanes_of(tw, magic, lane);
-    if (z.slots > 0) {
-        const float2 ul = z.on ? S.ul[tb + z.t] : make_float2(0.0f, 0.0f);
-        for (int pb = 0; pb < npar; pb += z.slots) {
-            const int pi = pb + z.slot;
-            const bool act = z.on && pi < npar;
-            offer(act, act ? node_at(Lp, root, pi) : Node{0.0f, 0.0f, 0}, ul, z.t);
-        }
-    } else {
-        const int total = npar * tw;
-        for (int e0 = 0; e0 < total; e0 += 32) {
-            const int e = e0 + lane;
-            const bool act = e < total;
-            const int pi = (int)__umulhi((uint32_t)e, magic);
-            const int t = e - pi * tw;
-            offer(act, act ? node_at(Lp, root, pi) : Node{0.0f, 0.0f, 0},
-                  act ? S.ul[tb + t] : make_float2(0.0f, 0.0f), t);
         }
     }
 }
 
-// Walks one row whose setup is in S (levels 0..n-2 as node lists, depth
-// first over chunks of kCap candidates, then the leaves). Returns false if
-// the step guard ran out (a broken invariant, reported as an error).
-template <bool EMIT>
-__device__ bool walk_row(const WarpMem &S, int n, int lane, CountAcc &acc, const EmitOut &out,
-                         int64_t &written)
+// Emit pass over the leaves of npar parents: each entry of the table under
+// each parent one lane; kept pairs are compacted in C order and stored
+// warp-contiguously. A table of at most 32 entries stays in registers, the
+// lanes laid out as (parent slot, entry).
+// Stores that the predicate guards, without a branch around them.
+__device__ __forceinline__ void st_if(bool p, int32_t *a, int32_t v)
 {
-    // every step advances a cursor, fills a list or leaves one: bound them by
-    // the candidates of every level (a loose, overflow-safe count)
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t@q st.global.b32 [%1], %2;\n\t}"
+                 :: "r"((int)p), "l"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_if(bool p, float *a, float v)
+{
+    st_if(p, reinterpret_cast<int32_t *>(a), __float_as_int(v));
+}
+
+template <bool ROOT>
+__device__ void leaf_emit(const WarpMem &S, int n, const Leaf &f, const NodeList &Lp, int npar,
+                          int lane, const EmitOut &out, int &written, float cut)
+{
+    const int nb = f.nb;
+    // every lane computes, the kept ones store (predicated, no divergence)
+    auto offer = [&](bool act, const Node &par, const LeafEntry &e) {
+        const float Pc = __fmul_ru(par.P, e.u);
+        const bool keep = act && Pc >= cut;
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        const int pos = written + __popc(bal & lanemask_lt());
+        const bool st = keep && pos < out.len;
+        st_if(st, out.col + pos, par.c + e.c);
+        st_if(st, out.lo + pos, __fmul_rd(par.Pl, e.l));
+        st_if(st, out.up + pos, Pc);
+        written += __popc(bal);
+    };
+    if (ROOT || nb <= 4096) {
+        // flat: candidate e = parent * nb + entry, one lane each, no lane idle
+        // but in the last step (the division is exact for e < 64 nb, nb <= 4096);
+        // lanes past the end read the last candidate and store nothing
+        const int total = npar * nb;
+        for (int e0 = 0; e0 < total; e0 += 32) {
+            const int e = min(e0 + lane, total - 1);
+            const int pi = (ROOT || nb == 1) ? (ROOT ? 0 : e) : (int)__umulhi((uint32_t)e, f.magic_nb);
+            const int j = e - pi * nb;
+            offer(e0 + lane < total, node_at(Lp, ROOT, pi), leaf_at(S, n, f, j));
+        }
+        return;
+    }
+    for (int pi = 0; pi < npar; ++pi) {
+        const Node par = node_at(Lp, ROOT, pi);
+        for (int j0 = 0; j0 < nb; j0 += 32) {
+            const int j = min(j0 + lane, nb - 1);
+            offer(j0 + lane < nb, par, leaf_at(S, n, f, j));
+        }
+    }
+}
+
+// Walks one row whose record is in S: levels 0..n-3 as node lists, depth
+// first over chunks, the leaf table under every chunk of the deepest list.
+// Returns false if the step guard ran out (a broken invariant, reported as
+// an error).
+template <bool EMIT>
+__device__ bool walk_row(const WarpMem &S, int n, const Leaf &f, int lane, CountAcc &acc,
+                         const EmitOut &out, int &written, float cut)
+{
+    if (n <= 2) {
+        if (EMIT) leaf_emit<true>(S, n, f, node_list(S.work, 0), 1, lane, out, written, cut);
+        else leaf_count(S, n, f, node_list(S.work, 0), true, 1, lane, acc, cut);
+        return true;
+    }
+    auto leaves = [&](const NodeList &Lp, int npar) {
+        if (EMIT) leaf_emit<false>(S, n, f, Lp, npar, lane, out, written, cut);
+        else leaf_count(S, n, f, Lp, false, npar, lane, acc, cut);
+    };
+    const int last = n - 3;   // deepest list level
+    // every step fills a list, leaves one or runs the leaves of one: bound
+    // them by the candidates of every level (loose, overflow-safe)
     int64_t guard = 16, prod = 1;
-    for (int k = 0; k < n; ++k) {
+    for (int k = 0; k <= last; ++k) {
         prod = min(prod * (int64_t)S.h[k].tw, (int64_t)1 << 40);
         guard += 8 * (int64_t)(k + 1) * (1 + prod / kCap);
     }
@@ -727,11 +998,9 @@ __device__ bool walk_row(const WarpMem &S, int n, int lane, CountAcc &acc, const
     int k = 0;
     while (true) {
         if (--guard < 0) return false;
-        if (k == n - 1) {
-            const int npar = n == 1 ? 1 : __shfl_sync(0xffffffffu, my_sz, n - 2);
-            leaf<EMIT>(S, n, npar, lane, acc, out, written);
-            if (n == 1) break;
-            k = n - 2;
+        if (k == last + 1) {
+            leaves(node_list(S.work, last), __shfl_sync(0xffffffffu, my_sz, last));
+            k = last;
             continue;
         }
         const int npar = k == 0 ? 1 : __shfl_sync(0xffffffffu, my_sz, k - 1);
@@ -742,7 +1011,7 @@ __device__ bool walk_row(const WarpMem &S, int n, int lane, CountAcc &acc, const
             --k;
             continue;
         }
-        const int end = min(cur + chunk_of(S.h[k].tw), total);
+        const int end = min(cur + chunk_of(S.h[k]), total);
         const int nout = expand(S, k, cur, end, lane, acc, !EMIT);
         if (lane == k) {
             my_cur = end;
@@ -753,7 +1022,6 @@ __device__ bool walk_row(const WarpMem &S, int n, int lane, CountAcc &acc, const
     }
     return true;
 }
-
 // ---------------------------------------------------------------------------
 // row offsets by decoupled look-back, and the FP64 row terms
 // ---------------------------------------------------------------------------
@@ -816,62 +1084,6 @@ __device__ bool lookback(unsigned long long *lb, int64_t row, int64_t cnt, int l
     return true;
 }
 
-// Rows whose FP64 terms wait in the warp's epilogue buffer: per slot the
-// FP32 inputs (per dimension qlo, qhi, SW, O; the row's drop, sup, slo
-// sums). Every kEpi rows one lane per row combines them in FP64, which keeps
-// the scarce FP64 issue of this part at about kEpi times fewer instructions
-// than combining each row in the whole warp.
-constexpr int kEpi = IMPACT_WALK_EPI;
-struct EpiBuf {
-    float *f;       // [4 * nm + 3][kEpi]
-    int64_t *row;   // [kEpi] global row
-    int *nd;        // [kEpi] dimensions (0: the row failed its setup)
-    int nm;         // largest n of the batch
-};
-
-__device__ __forceinline__ void epi_flush(const EpiBuf &E, int used, int lane, double *sink_lo,
-                                          double *sink_up, double *trunc, uint32_t *flags,
-                                          uint32_t *status, int64_t fault_row)
-{
-    __syncwarp();
-    if (lane < used) {
-        const int s = lane, nm = E.nm;
-        const int64_t row = E.row[s];
-        const int n = E.nd[s];
-        double pin_up = 1.0, pin_dn = 1.0, acc = 0.0, pre = 1.0;
-        for (int k = 0; k < n; ++k) {
-            const double ql = E.f[k * kEpi + s], qh = E.f[(nm + k) * kEpi + s];
-            const double sw = E.f[(2 * nm + k) * kEpi + s], o = E.f[(3 * nm + k) * kEpi + s];
-            // sink: 1 - prod_k (1 - Q_k)
-            pin_up = __dmul_ru(pin_up, __dsub_ru(1.0, ql));
-            pin_dn = __dmul_rd(pin_dn, __dsub_rd(1.0, qh));
-            // mass outside the window box, partitioned by the first dimension
-            // that leaves its window: sum_k prod_{i<k} SW_i O_k prod_{i>k} (SW_i + O_i)
-            acc = __dadd_ru(__dmul_ru(acc, __dadd_ru(sw, o)), __dmul_ru(pre, o));
-            pre = __dmul_ru(pre, sw);
-        }
-        const double drop = E.f[(4 * nm) * kEpi + s];
-        const double sup = E.f[(4 * nm + 1) * kEpi + s];
-        double slo = E.f[(4 * nm + 2) * kEpi + s];
-        const double slo_v = n > 0 ? fmax(__dsub_rd(1.0, pin_up), 0.0) : 0.0;
-        const double sup_v = n > 0 ? fmin(__dsub_ru(1.0, pin_dn), 1.0) : 0.0;
-        const double tr = __dadd_ru(acc, drop);
-        sink_lo[row] = slo_v;
-        sink_up[row] = sup_v;
-        trunc[row] = tr;
-        if (flags) {
-            if (row == fault_row) slo = 2.0;   // fault injection: a row that claims too much
-            uint32_t f = 0;
-            if (n > 0) {
-                if (__dadd_rd(slo, slo_v) > 1.0) f |= 0x1u;
-                if (__dadd_ru(__dadd_ru(sup, sup_v), tr) < 1.0) f |= 0x2u;
-            }
-            flags[row] = f;
-            if (f) atomicOr(status, IMPACT_STATUS_UNSOUND);
-        }
-    }
-    __syncwarp();
-}
 
 __device__ __forceinline__ float warp_sum_ru(float x)
 {
@@ -887,7 +1099,7 @@ __device__ __forceinline__ float warp_sum_rd(float x)
 }
 
 // ---------------------------------------------------------------------------
-// the kernel
+// the walk kernel
 // ---------------------------------------------------------------------------
 
 enum { MODE_COUNT = 0, MODE_EMIT = 1, MODE_FUSED = 2 };
@@ -895,14 +1107,14 @@ enum { MODE_COUNT = 0, MODE_EMIT = 1, MODE_FUSED = 2 };
 struct WalkArgs {
     const BatchIndex *B;
     int warp_smem;           // shared-memory bytes of one warp
-    int nm;                  // largest n of the batch
-    int64_t *row_ptr;        // COUNT / FUSED: written; EMIT: read
+    int64_t *row_ptr;        // COUNT: per-row counts; FUSED: row pointers; EMIT: read
     int32_t *col;
     float *lo, *up;
-    double *sink_lo, *sink_up, *trunc;
+    double *trunc;           // COUNT / FUSED: outside-window mass in, full truncated mass out
+    double *sink_lo, *sink_up;
     uint32_t *flags;
     uint32_t *status;        // [0] status bits, [1] look-back abort flag
-    unsigned long long *lb;  // COUNT / FUSED: look-back words, zeroed, one per row
+    unsigned long long *lb;  // FUSED: look-back words, zeroed, one per row
     int64_t capacity;        // pairs the output arrays hold (< 0: unchecked)
     int64_t total_at;        // EMIT: index of the total in row_ptr
     int spin_limit;          // look-back sleeps before giving up
@@ -911,11 +1123,6 @@ struct WalkArgs {
     int64_t stall_row;       // fault injection: this row never publishes (-1: none)
     int64_t fault_row;       // fault injection: this row's checks see a bad sum (-1: none)
 };
-
-__host__ __device__ constexpr int epi_bytes(int nm)
-{
-    return kEpi * (8 + 4 + 4 * (4 * nm + 3));
-}
 
 template <int MODE>
 __global__ void __launch_bounds__(IMPACT_TREE_WARPS_MAX * 32) walk_fp32(const WalkArgs A)
@@ -931,15 +1138,6 @@ __global__ void __launch_bounds__(IMPACT_TREE_WARPS_MAX * 32) walk_fp32(const Wa
         return;
     }
     unsigned long long *const next_row = B->next_row + (MODE == MODE_EMIT ? 1 : 0);
-    EpiBuf E;
-    {
-        unsigned char *eb = wbase + A.warp_smem - epi_bytes(A.nm);
-        E.row = reinterpret_cast<int64_t *>(eb);
-        E.nd = reinterpret_cast<int *>(eb + 8 * kEpi);
-        E.f = reinterpret_cast<float *>(eb + 12 * kEpi);
-        E.nm = A.nm;
-    }
-    int used = 0;
     bool lb_ok = true;
 
     // persistent: each warp takes the next row of the batch until none is left
@@ -952,79 +1150,91 @@ __global__ void __launch_bounds__(IMPACT_TREE_WARPS_MAX * 32) walk_fp32(const Wa
         const int q = find_problem(B->row_begin, B->count, row);
         const ImpactDesc &D = *B->desc[q];
         const int n = D.n;
+        const float cut = D.cutoff32;
         const WarpMem S = carve(wbase, D);
-        const RowTerms rt = row_setup(D, S, row - B->row_begin[q], lane);
-        bool ok = rt.ok, walked = true;
+        // the row's record: per-dimension entries, then the window tables
+        {
+            const unsigned char *rr = B->rec[q] + (row - B->row_begin[q]) * (int64_t)D.rec_stride;
+            const int4 *src = reinterpret_cast<const int4 *>(rr);
+            int4 *dh = reinterpret_cast<int4 *>(S.h);
+            for (int i = lane; i < 2 * n; i += 32) dh[i] = src[i];
+            const int nt = D.tsum_cap >> 1;   // float2 pairs, two per int4
+            const int4 *st = reinterpret_cast<const int4 *>(rr + 32 * n);
+            int4 *dt = reinterpret_cast<int4 *>(S.ul);
+            for (int i = lane; i < nt; i += 32) dt[i] = st[i];
+            if ((D.tsum_cap & 1) && lane == 0)
+                S.ul[D.tsum_cap - 1] = reinterpret_cast<const float2 *>(rr + 32 * n)[D.tsum_cap - 1];
+        }
+        __syncwarp();
+        bool empty = false;
+        for (int k = 0; k < n; ++k) empty |= (S.h[k].tw == 0);
+        Leaf f = leaf_of(S, n);
+        if (!empty) leaf_build<kCount>(S, n, f, lane, cut);
+        bool walked = true;
         int64_t base = 0, len = 0;
         if (kCount) {
             CountAcc acc;
-            const EmitOut none{nullptr, nullptr, nullptr, 0, 0};
-            int64_t w0 = 0;
-            if (ok && !rt.empty) walked = walk_row<false>(S, n, lane, acc, none, w0);
-            const bool good = ok && walked;
-            int c = good ? acc.cnt : 0;
+            const EmitOut none{nullptr, nullptr, nullptr, 0};
+            int w0 = 0;
+            if (!empty) walked = walk_row<false>(S, n, f, lane, acc, none, w0, cut);
+            int c = walked ? acc.cnt : 0;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-            const float drop = warp_sum_ru(good ? acc.drop : 0.0f);
-            const float sup = warp_sum_ru(good ? acc.sup : 0.0f);
-            const float slo = warp_sum_rd(good ? acc.slo : 0.0f);
+            const float drop = warp_sum_ru(walked ? acc.drop : 0.0f);
+            const float sup = warp_sum_ru(walked ? acc.sup : 0.0f);
+            const float slo = warp_sum_rd(walked ? acc.slo : 0.0f);
             int64_t prefix = 0;
-            lb_ok = lookback(A.lb, row, c, lane, A.status + 1, A.status, A.spin_limit,
-                             row == A.stall_row, prefix);
-            if (lane == 0 && lb_ok) {
-                A.row_ptr[row] = prefix;
-                if (row == B->rows - 1) A.row_ptr[B->rows] = prefix + c;
+            if (MODE == MODE_FUSED) {
+                lb_ok = lookback(A.lb, row, c, lane, A.status + 1, A.status, A.spin_limit,
+                                 row == A.stall_row, prefix);
+                if (lane == 0 && lb_ok) {
+                    A.row_ptr[row] = prefix;
+                    if (row == B->rows - 1) A.row_ptr[B->rows] = prefix + c;
+                }
+            } else if (lane == 0) {
+                A.row_ptr[row] = c;   // counts; the scan turns them into row pointers
             }
             base = prefix;
             len = c;
-            // the row's FP64 terms wait in the epilogue buffer
-            if (lane < n) {
-                const DimHdr &h = S.h[lane];
-                E.f[lane * kEpi + used] = good ? h.qlo : 0.0f;
-                E.f[(E.nm + lane) * kEpi + used] = good ? h.qhi : 0.0f;
-                E.f[(2 * E.nm + lane) * kEpi + used] = good ? h.SW : 0.0f;
-                E.f[(3 * E.nm + lane) * kEpi + used] = good ? h.O : 0.0f;
-            }
             if (lane == 0) {
-                E.row[used] = row;
-                E.nd[used] = good ? n : 0;
-                E.f[(4 * E.nm) * kEpi + used] = drop;
-                E.f[(4 * E.nm + 1) * kEpi + used] = sup;
-                E.f[(4 * E.nm + 2) * kEpi + used] = slo;
-            }
-            if (++used == kEpi) {
-                epi_flush(E, used, lane, A.sink_lo, A.sink_up, A.trunc, A.flags, A.status,
-                          A.fault_row);
-                used = 0;
+                // FP64 row terms: the dropped in-window mass joins the mass
+                // outside the window box; then the row checks of Def. 3.1
+                const double tr = __dadd_ru(A.trunc[row], (double)drop);
+                A.trunc[row] = tr;
+                if (A.flags) {
+                    const double slv = A.sink_lo[row], suv = A.sink_up[row];
+                    const double lo_sum = row == A.fault_row ? 2.0 : (double)slo;
+                    uint32_t fl = 0;
+                    if (__dadd_rd(lo_sum, slv) > 1.0) fl |= IMPACT_ROW_LO_SUM_ABOVE_ONE;
+                    if (__dadd_ru(__dadd_ru((double)sup, suv), tr) < 1.0)
+                        fl |= IMPACT_ROW_UP_SUM_BELOW_ONE;
+                    A.flags[row] = fl;
+                    if (fl) atomicOr(A.status, IMPACT_STATUS_UNSOUND);
+                }
             }
         } else {
             base = A.row_ptr[row];
             len = A.row_ptr[row + 1] - base;
         }
-        if (kEmit && ok && walked && lb_ok) {
+        if (kEmit && walked && lb_ok) {
             if (base < 0 || len < 0 || (A.capacity >= 0 && base + len > A.capacity)) {
                 if (lane == 0)
                     atomicOr(A.status, MODE == MODE_FUSED ? IMPACT_STATUS_CAPACITY
                                                           : IMPACT_STATUS_EMIT_MISMATCH);
             } else {
-                const EmitOut out{A.col, A.lo, A.up, base, len};
+                const EmitOut out{A.col + base, A.lo + base, A.up + base, (int)len};
                 CountAcc none;
-                int64_t written = 0;
+                int written = 0;
                 bool wok = true;
-                if (!rt.empty) wok = walk_row<true>(S, n, lane, none, out, written);
+                if (!empty) wok = walk_row<true>(S, n, f, lane, none, out, written, cut);
                 if (lane == 0 && (!wok || written != len))
                     atomicOr(A.status, wok ? IMPACT_STATUS_EMIT_MISMATCH : IMPACT_STATUS_INTERNAL);
             }
         }
-        if (lane == 0) {
-            if (!ok) atomicOr(A.status, IMPACT_STATUS_TABLE_OVERFLOW);
-            if (!walked) atomicOr(A.status, IMPACT_STATUS_INTERNAL);
-            if (MODE == MODE_EMIT && !ok) atomicOr(A.status, IMPACT_STATUS_EMIT_MISMATCH);
-        }
+        if (lane == 0 && !walked) atomicOr(A.status, IMPACT_STATUS_INTERNAL);
         if (!lb_ok) break;   // the rows after this one cannot find their offsets
+        __syncwarp();
     }
-    if (kCount && used > 0)
-        epi_flush(E, used, lane, A.sink_lo, A.sink_up, A.trunc, A.flags, A.status, A.fault_row);
 }
 
 int occupancy_grid(const void *kernel, int threads, size_t smem, int64_t work_items,
@@ -1044,27 +1254,35 @@ int occupancy_grid(const void *kernel, int threads, size_t smem, int64_t work_it
 
 namespace impact {
 
-int walk_core_bytes(int n, int tsum_cap, int edge_cap)
+int64_t record_stride(int n, int tsum_cap)
 {
-    const int64_t lists = (int64_t)std::max(n - 1, 1) * kCap * 12;
-    const int64_t edges = (int64_t)48 * edge_cap;
-    int64_t b = kHdrBytes + (((int64_t)8 * tsum_cap + 15) & ~(int64_t)15) +
-                ((std::max(lists, edges) + 15) & ~(int64_t)15);
+    return ((int64_t)32 * n + (int64_t)8 * tsum_cap + 15) / 16 * 16;
+}
+
+int walk_core_bytes(int n, int tsum_cap, int leaf_cap)
+{
+    const int64_t b = kHdrBytes + align16(8 * tsum_cap) + list_bytes(n) +
+                      align16(8 * 4 * (leaf_cap + 1));
+    static_assert(kHdrBytes % 16 == 0, "warp blocks must stay 16-byte aligned");
     return (int)std::min<int64_t>(b, INT32_MAX / 2);
 }
 
-int walk_smem_bytes(int core_max, int nm, bool count)
+cudaError_t launch_setup_fp32(const BatchIndex *d_index, int64_t units, uint32_t *status,
+                              double *sink_lo, double *sink_up, double *trunc, cudaStream_t stream)
 {
-    return core_max + (count ? epi_bytes(nm) : 0);
+    if (units <= 0) return cudaSuccess;
+    const int g = occupancy_grid((const void *)setup_fp32, 256, 0, units, 256 / 32);
+    setup_fp32<<<g, 256, 0, stream>>>(d_index, status, sink_lo, sink_up, trunc);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_walk_fp32(const BatchIndex *d_index, int64_t row_begin, int64_t row_end,
-                             int nm, int core_max, int warps, int mode, const RowOutputs &o,
+                             int core_max, int warps, int mode, const RowOutputs &o,
                              unsigned long long *lb, const WalkFaults &f, cudaStream_t stream)
 {
     const int64_t rows = row_end - row_begin;
     if (rows <= 0) return cudaSuccess;
-    const int warp_smem = walk_smem_bytes(core_max, nm, mode != MODE_EMIT);
+    const int warp_smem = (core_max + 15) & ~15;   // warp blocks start 16-byte aligned
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -1079,14 +1297,13 @@ cudaError_t launch_walk_fp32(const BatchIndex *d_index, int64_t row_begin, int64
     WalkArgs A;
     A.B = d_index;
     A.warp_smem = warp_smem;
-    A.nm = nm;
     A.row_ptr = o.row_ptr;
     A.col = o.col;
     A.lo = (float *)o.lo;
     A.up = (float *)o.up;
+    A.trunc = o.trunc;
     A.sink_lo = o.sink_lo;
     A.sink_up = o.sink_up;
-    A.trunc = o.trunc;
     A.flags = o.flags;
     A.status = o.status;
     A.lb = lb;

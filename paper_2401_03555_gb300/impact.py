@@ -36,7 +36,7 @@ ENTRY_POINTS = ("impact_plan", "impact_workspace_bytes", "impact_build", "impact
                 "impact_server_poll", "impact_server_release", "impact_server_stats",
                 "impact_server_destroy", "impact_synthesize", "impact_label_cells",
                 "impact_region_vectors", "impact_synthesize_ex", "impact_build_mc",
-                "impact_debug_fail_alloc", "impact_debug_live_bytes")
+                "impact_debug_fail_alloc", "impact_debug_live_bytes", "impact_server_timing")
 
 
 class ImpactError(RuntimeError):
@@ -184,6 +184,9 @@ def load(build_if_missing: bool = True):
                                            ctypes.POINTER(ctypes.c_double)]
         lib.impact_server_release.restype = ctypes.c_int
         lib.impact_server_release.argtypes = [ctypes.c_void_p, ctypes.c_int64]
+        lib.impact_server_timing.restype = ctypes.c_int
+        lib.impact_server_timing.argtypes = [ctypes.c_void_p, ctypes.c_int64] + \
+            [ctypes.POINTER(ctypes.c_double)] * 4
         lib.impact_server_stats.restype = ctypes.c_int
         lib.impact_server_stats.argtypes = [ctypes.c_void_p, ctypes.POINTER(_ServerStats)]
         lib.impact_server_destroy.restype = ctypes.c_int
@@ -714,6 +717,12 @@ class Server:
         return CSR(self.precision, rp - base, col_all[base:], lo_all[base:], up_all[base:],
                    _view(c.sink_lo, rows, torch.float64), _view(c.sink_up, rows, torch.float64),
                    _view(c.trunc, rows, torch.float64), _view(c.row_flags, rows, torch.int32))
+
+    def timing(self, ticket: int) -> dict:
+        """impact_server_timing: where a finished request's latency went (ms)."""
+        v = [ctypes.c_double() for _ in range(4)]
+        _check(load().impact_server_timing(self.handle, int(ticket), *[ctypes.byref(x) for x in v]))
+        return dict(zip(("queue", "count", "emit_wait", "emit"), (x.value for x in v)))
 
     def release(self, ticket: int):
         _check(load().impact_server_release(self.handle, int(ticket)))
