@@ -107,12 +107,24 @@ impact_status make_batch(const impact_request *reqs, int count, impact_precision
         B.unit_begin[q + 1] = B.unit_begin[q] + (P.rows + rpw - 1) / rpw;
         B.nnz_bound = (B.nnz_bound > INT64_MAX - P.nnz_bound) ? INT64_MAX
                                                               : B.nnz_bound + P.nnz_bound;
-        B.walk_core = std::max(B.walk_core, P.desc.walk_core);
+        if (precision == IMPACT_FP32_SOUND) {
+            B.rec_max = std::max(B.rec_max, P.desc.rec_stride);
+            for (int c = 0; c < 2; ++c)
+                B.work_max[c] = std::max(B.work_max[c],
+                                         impact::walk_work_bytes(P.desc.n, P.desc.leaf_cap, c == 1));
+        }
         h = mix(h, P.hash);
     }
     B.rows = B.row_begin[count];
     B.units = B.unit_begin[count];
     B.hash = h;   // launch shapes change no result: they are not part of the identity
+    if (precision == IMPACT_FP32_SOUND &&
+        2 * (int64_t)B.rec_max + B.work_max[1] > IMPACT_WALK_SMEM_MAX)
+        return fail(IMPACT_ERR_ARG,
+                    "the builds of this batch together need " +
+                        std::to_string(2 * (int64_t)B.rec_max + B.work_max[1]) +
+                        " bytes of shared memory per warp, more than one warp has: "
+                        "batch the widest windows separately");
     return IMPACT_OK;
 }
 
@@ -328,7 +340,7 @@ cudaError_t walk_pass(const Batch &B, const Work &W, int mode, int warps,
         cudaError_t e = cudaMemsetAsync(counter, 0, 8, st);
         if (e == cudaSuccess)
             e = impact::launch_walk_fp32(W.index(), r0, std::min(B.rows, r0 + step),
-                                         B.walk_core, warps, mode, o,
+                                         B.rec_max, B.work_max, warps, mode, o,
                                          mode == WALK_FUSED ? W.lb() : nullptr, B.tune.faults, st);
         if (e != cudaSuccess) return e;
     }

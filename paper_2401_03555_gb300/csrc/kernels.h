@@ -88,7 +88,11 @@ cudaError_t launch_regions(const ImpactDesc *d_desc, int64_t rows, const RegionB
 // the window box; the walk kernels read the records. A walk launch covers
 // the global rows [row_begin, row_end) of a batch (the pass's row counter
 // zeroed before each launch; launches of one pass in row order on one
-// stream). `core_max`: the largest walk_core_bytes of the batch; `lb`: one
+// stream). A warp's shared memory holds two record buffers of `rec_max`
+// bytes (the largest record_stride of the batch: the row being walked and the
+// next one, prefetched) and work space: `work_max` = the largest
+// walk_work_bytes of the batch for the emit pass [0] and the passes that
+// count [1]; `lb`: one
 // 8-byte look-back word per row, zeroed before the first launch of a FUSED
 // pass. COUNT writes per-row counts (a scan makes them row pointers), FUSED
 // the row pointers themselves.
@@ -99,11 +103,13 @@ struct WalkFaults {
     int64_t fault_row = -1;    // this row's checks see an impossible sum (-1: none)
 };
 int64_t record_stride(int n, int tsum_cap);
-int walk_core_bytes(int n, int tsum_cap, int leaf_cap);
+int walk_core_bytes(int n, int tsum_cap, int leaf_cap);   // both buffers and the work space
+int walk_work_bytes(int n, int leaf_cap, bool count);
 cudaError_t launch_setup_fp32(const BatchIndex *d_index, int64_t units, uint32_t *status,
                               double *sink_lo, double *sink_up, double *trunc, cudaStream_t stream);
 cudaError_t launch_walk_fp32(const BatchIndex *d_index, int64_t row_begin, int64_t row_end,
-                             int core_max, int warps, int mode, const RowOutputs &o,
+                             int rec_max, const int work_max[2], int warps, int mode,
+                             const RowOutputs &o,
                              unsigned long long *lb, const WalkFaults &f, cudaStream_t stream);
 cudaError_t launch_scan(int64_t *row_ptr, int64_t n, int64_t *scratch, cudaStream_t stream);
 

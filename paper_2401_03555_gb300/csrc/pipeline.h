@@ -21,7 +21,8 @@ struct Batch {
     std::vector<int64_t> unit_begin;      // [count + 1] first setup unit (32/n rows)
     int64_t rows = 0, units = 0, nnz_bound = 0;
     int prec = 0;
-    int walk_core = 0;                    // largest per-warp shared-memory bytes of the walk
+    int rec_max = 0;                      // FP32 walk: largest record of the batch
+    int work_max[2] = {0, 0};             // FP32 walk: largest work space, emit / count
     Tuning tune;
     uint64_t hash = 0;
     int count() const { return (int)plans.size(); }

@@ -469,13 +469,15 @@ setup_fp32(const BatchIndex *__restrict__ B, uint32_t *__restrict__ status,
 // ---------------------------------------------------------------------------
 
 constexpr int kCap = IMPACT_WALK_CAP;      // nodes per level list (one chunk)
-constexpr int kHdrBytes = 32 * IMPACT_MAX_DIM;
 
-// Warp shared memory (offsets fixed per problem by leaf_cap):
-//   h      RecDim[8]                 the row record's per-dimension entries
-//   ul     (U, L) x tsum_cap         the record's window tables
-//   work   (n - 2) x kCap x 12 B     node lists of levels 0..n-3
-//   leaf   8 x (leaf_cap + 1) floats the staged leaf table (see Leaf)
+// Warp shared memory: two record buffers of the batch's largest record (the
+// row being walked and the next one, copied in meanwhile), then the work
+// space (offsets fixed per problem by leaf_cap):
+//   h      RecDim[n]                 the row record's per-dimension entries
+//   ul     (U, L) x tsum_cap         the record's window tables, right after
+//   work   (n - 2) x (kCap + 1) x 12 B  node lists of levels 0..n-3
+//   leaf   3 x (leaf_cap + 1) words  the staged leaf table (see Leaf), and for
+//          5 x (leaf_cap + 1) words  the count pass its sorted form and sums
 struct WarpMem {
     RecDim *h;
     float2 *ul;
@@ -490,12 +492,12 @@ __host__ __device__ constexpr int align16(int x) { return (x + 15) & ~15; }
 // end to end and each starts with 16-byte record copies.
 __host__ __device__ inline int list_bytes(int n) { return align16((n > 2 ? n - 2 : 0) * (kCap + 1) * 12); }
 
-__device__ __forceinline__ WarpMem carve(unsigned char *base, const ImpactDesc &D)
+__device__ __forceinline__ WarpMem carve(unsigned char *work, unsigned char *rec, const ImpactDesc &D)
 {
     WarpMem m;
-    m.h = reinterpret_cast<RecDim *>(base);
-    m.ul = reinterpret_cast<float2 *>(base + kHdrBytes);
-    m.work = base + kHdrBytes + align16(8 * D.tsum_cap);
+    m.h = reinterpret_cast<RecDim *>(rec);
+    m.ul = reinterpret_cast<float2 *>(rec + 32 * D.n);
+    m.work = work;
     m.leaf = reinterpret_cast<float *>(m.work + list_bytes(D.n));
     m.leaf_cap = D.leaf_cap;
     return m;
@@ -605,9 +607,10 @@ __device__ __forceinline__ LeafEntry leaf_eval(const WarpMem &S, int n, const Le
     return e;
 }
 
+template <bool STAGED>
 __device__ __forceinline__ LeafEntry leaf_at(const WarpMem &S, int n, const Leaf &f, int j)
 {
-    if (!f.staged) return leaf_eval(S, n, f, j);
+    if (!STAGED) return leaf_eval(S, n, f, j);
     return LeafEntry{f.bu[j], f.bl[j], f.bc[j]};
 }
 
@@ -915,10 +918,6 @@ __device__ void leaf_count(const WarpMem &S, int n, const Leaf &f, const NodeLis
     }
 }
 
-// Emit pass over the leaves of npar parents: each entry of the table under
-// each parent one lane; kept pairs are compacted in C order and stored
-// warp-contiguously. A table of at most 32 entries stays in registers, the
-// lanes laid out as (parent slot, entry).
 // Stores that the predicate guards, without a branch around them.
 __device__ __forceinline__ void st_if(bool p, int32_t *a, int32_t v)
 {
@@ -930,33 +929,46 @@ __device__ __forceinline__ void st_if(bool p, float *a, float v)
     st_if(p, reinterpret_cast<int32_t *>(a), __float_as_int(v));
 }
 
-template <bool ROOT>
+// One candidate per lane: the kept ones are compacted in lane order after the
+// pairs already written and stored (predicated, no divergence).
+__device__ __forceinline__ void offer_pair(bool act, const Node &par, const LeafEntry &e, float cut,
+                                           const EmitOut &out, int &written)
+{
+    const float Pc = __fmul_ru(par.P, e.u);
+    const bool keep = act && Pc >= cut;
+    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+    const int pos = written + __popc(bal & lanemask_lt());
+    const bool st = keep && pos < out.len;
+    st_if(st, out.col + pos, par.c + e.c);
+    st_if(st, out.lo + pos, __fmul_rd(par.Pl, e.l));
+    st_if(st, out.up + pos, Pc);
+    written += __popc(bal);
+}
+
+// Emit pass over the leaves of npar parents: each entry of the table under
+// each parent one lane (flat: candidate e = parent * nb + entry, so no lane
+// idles but in the last step); kept pairs are compacted in C order and stored
+// warp-contiguously. A layout that keeps the table in registers and steps
+// over parents measured slower: its lanes idle when 32 is not a multiple of
+// nb, and its registers cost occupancy.
+template <bool ROOT, bool STAGED>
 __device__ void leaf_emit(const WarpMem &S, int n, const Leaf &f, const NodeList &Lp, int npar,
                           int lane, const EmitOut &out, int &written, float cut)
 {
     const int nb = f.nb;
     // every lane computes, the kept ones store (predicated, no divergence)
     auto offer = [&](bool act, const Node &par, const LeafEntry &e) {
-        const float Pc = __fmul_ru(par.P, e.u);
-        const bool keep = act && Pc >= cut;
-        const unsigned bal = __ballot_sync(0xffffffffu, keep);
-        const int pos = written + __popc(bal & lanemask_lt());
-        const bool st = keep && pos < out.len;
-        st_if(st, out.col + pos, par.c + e.c);
-        st_if(st, out.lo + pos, __fmul_rd(par.Pl, e.l));
-        st_if(st, out.up + pos, Pc);
-        written += __popc(bal);
+        offer_pair(act, par, e, cut, out, written);
     };
     if (ROOT || nb <= 4096) {
-        // flat: candidate e = parent * nb + entry, one lane each, no lane idle
-        // but in the last step (the division is exact for e < 64 nb, nb <= 4096);
-        // lanes past the end read the last candidate and store nothing
+        // the division is exact for e < 64 nb, nb <= 4096; lanes past the end
+        // read the last candidate and store nothing
         const int total = npar * nb;
         for (int e0 = 0; e0 < total; e0 += 32) {
             const int e = min(e0 + lane, total - 1);
             const int pi = (ROOT || nb == 1) ? (ROOT ? 0 : e) : (int)__umulhi((uint32_t)e, f.magic_nb);
             const int j = e - pi * nb;
-            offer(e0 + lane < total, node_at(Lp, ROOT, pi), leaf_at(S, n, f, j));
+            offer(e0 + lane < total, node_at(Lp, ROOT, pi), leaf_at<STAGED>(S, n, f, j));
         }
         return;
     }
@@ -964,7 +976,7 @@ __device__ void leaf_emit(const WarpMem &S, int n, const Leaf &f, const NodeList
         const Node par = node_at(Lp, ROOT, pi);
         for (int j0 = 0; j0 < nb; j0 += 32) {
             const int j = min(j0 + lane, nb - 1);
-            offer(j0 + lane < nb, par, leaf_at(S, n, f, j));
+            offer(j0 + lane < nb, par, leaf_at<STAGED>(S, n, f, j));
         }
     }
 }
@@ -978,12 +990,18 @@ __device__ bool walk_row(const WarpMem &S, int n, const Leaf &f, int lane, Count
                          const EmitOut &out, int &written, float cut)
 {
     if (n <= 2) {
-        if (EMIT) leaf_emit<true>(S, n, f, node_list(S.work, 0), 1, lane, out, written, cut);
+        if (EMIT) {
+            if (f.staged) leaf_emit<true, true>(S, n, f, node_list(S.work, 0), 1, lane, out, written, cut);
+            else leaf_emit<true, false>(S, n, f, node_list(S.work, 0), 1, lane, out, written, cut);
+        }
         else leaf_count(S, n, f, node_list(S.work, 0), true, 1, lane, acc, cut);
         return true;
     }
     auto leaves = [&](const NodeList &Lp, int npar) {
-        if (EMIT) leaf_emit<false>(S, n, f, Lp, npar, lane, out, written, cut);
+        if (EMIT) {
+            if (f.staged) leaf_emit<false, true>(S, n, f, Lp, npar, lane, out, written, cut);
+            else leaf_emit<false, false>(S, n, f, Lp, npar, lane, out, written, cut);
+        }
         else leaf_count(S, n, f, Lp, false, npar, lane, acc, cut);
     };
     const int last = n - 3;   // deepest list level
@@ -1102,11 +1120,32 @@ __device__ __forceinline__ float warp_sum_rd(float x)
 // the walk kernel
 // ---------------------------------------------------------------------------
 
+// 16-byte asynchronous copy global -> shared (both 16-byte aligned), and its
+// group fences.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prior() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// The problem of global row x, searched from problem q (rows only grow along
+// a warp's sequence).
+__device__ __forceinline__ int next_problem(const int64_t *__restrict__ begin, int count, int q,
+                                            int64_t x)
+{
+    if (q + 1 >= count || begin[q + 1] > x) return q;
+    return find_problem(begin, count, x);
+}
+
 enum { MODE_COUNT = 0, MODE_EMIT = 1, MODE_FUSED = 2 };
 
 struct WalkArgs {
     const BatchIndex *B;
     int warp_smem;           // shared-memory bytes of one warp
+    int rec_max;             // bytes of one record buffer
     int64_t *row_ptr;        // COUNT: per-row counts; FUSED: row pointers; EMIT: read
     int32_t *col;
     float *lo, *up;
@@ -1140,31 +1179,51 @@ __global__ void __launch_bounds__(IMPACT_TREE_WARPS_MAX * 32) walk_fp32(const Wa
     unsigned long long *const next_row = B->next_row + (MODE == MODE_EMIT ? 1 : 0);
     bool lb_ok = true;
 
-    // persistent: each warp takes the next row of the batch until none is left
-    while (true) {
-        unsigned long long taken = 0;
-        if (lane == 0) taken = atomicAdd(next_row, 1ull);
-        taken = __shfl_sync(0xffffffffu, taken, 0);
-        if (taken >= (unsigned long long)(A.row_end - A.row_begin)) break;
-        const int64_t row = A.row_begin + (int64_t)taken;   // global row of the batch
-        const int q = find_problem(B->row_begin, B->count, row);
+    // persistent: each warp takes rows from the batch's row counter. The
+    // passes that count take them two ahead: while a warp walks a row, the
+    // index of the row after the next is claimed and the next row's record is
+    // copied (cp.async) into the warp's other record buffer. The emit pass
+    // (more registers live in its walk) copies each record when it starts it.
+    constexpr bool kAhead = MODE != MODE_EMIT;
+    const unsigned long long nrows = (unsigned long long)(A.row_end - A.row_begin);
+    unsigned char *const work = wbase + (kAhead ? 2 : 1) * A.rec_max;
+    auto take = [&]() -> unsigned long long { return lane == 0 ? atomicAdd(next_row, 1ull) : 0ull; };
+    auto fetch = [&](unsigned long long t, int &q, unsigned char *dst) {
+        if (t >= nrows) return;
+        const int64_t row = A.row_begin + (int64_t)t;
+        q = next_problem(B->row_begin, B->count, q, row);
+        const int stride = B->desc[q]->rec_stride;
+        const unsigned char *src = B->rec[q] + (row - B->row_begin[q]) * (int64_t)stride;
+        for (int i = lane; i < (stride >> 4); i += 32) cp_async16(dst + 16 * i, src + 16 * i);
+    };
+    unsigned long long t_cur = __shfl_sync(0xffffffffu, take(), 0);
+    unsigned long long t_nxt = 0;
+    int q_cur = 0, b = 0;
+    if (kAhead) {
+        t_nxt = __shfl_sync(0xffffffffu, take(), 0);
+        fetch(t_cur, q_cur, wbase);
+        cp_async_commit();
+    }
+    while (t_cur < nrows) {
+        unsigned long long t_after = 0;
+        int q_nxt = q_cur;
+        if (kAhead) {
+            t_after = take();   // lane 0's claim, read after the row
+            fetch(t_nxt, q_nxt, wbase + (b ^ 1) * A.rec_max);
+            cp_async_commit();
+            cp_async_wait_prior();   // this row's record has landed
+        } else {
+            fetch(t_cur, q_cur, wbase);
+            cp_async_commit();
+            cp_async_wait_all();
+        }
+        __syncwarp();
+        const int64_t row = A.row_begin + (int64_t)t_cur;   // global row of the batch
+        const int q = q_cur;
         const ImpactDesc &D = *B->desc[q];
         const int n = D.n;
         const float cut = D.cutoff32;
-        const WarpMem S = carve(wbase, D);
-        // the row's record: per-dimension entries, then the window tables
-        {
-            const unsigned char *rr = B->rec[q] + (row - B->row_begin[q]) * (int64_t)D.rec_stride;
-            const int4 *src = reinterpret_cast<const int4 *>(rr);
-            int4 *dh = reinterpret_cast<int4 *>(S.h);
-            for (int i = lane; i < 2 * n; i += 32) dh[i] = src[i];
-            const int nt = D.tsum_cap >> 1;   // float2 pairs, two per int4
-            const int4 *st = reinterpret_cast<const int4 *>(rr + 32 * n);
-            int4 *dt = reinterpret_cast<int4 *>(S.ul);
-            for (int i = lane; i < nt; i += 32) dt[i] = st[i];
-            if ((D.tsum_cap & 1) && lane == 0)
-                S.ul[D.tsum_cap - 1] = reinterpret_cast<const float2 *>(rr + 32 * n)[D.tsum_cap - 1];
-        }
+        const WarpMem S = carve(work, wbase + b * A.rec_max, D);
         __syncwarp();
         bool empty = false;
         for (int k = 0; k < n; ++k) empty |= (S.h[k].tw == 0);
@@ -1233,8 +1292,17 @@ __global__ void __launch_bounds__(IMPACT_TREE_WARPS_MAX * 32) walk_fp32(const Wa
         }
         if (lane == 0 && !walked) atomicOr(A.status, IMPACT_STATUS_INTERNAL);
         if (!lb_ok) break;   // the rows after this one cannot find their offsets
-        __syncwarp();
+        __syncwarp();        // every lane is done with the buffer before it is refilled
+        if (kAhead) {
+            t_cur = t_nxt;
+            q_cur = q_nxt;
+            t_nxt = __shfl_sync(0xffffffffu, t_after, 0);
+            b ^= 1;
+        } else {
+            t_cur = __shfl_sync(0xffffffffu, take(), 0);
+        }
     }
+    cp_async_wait_all();
 }
 
 int occupancy_grid(const void *kernel, int threads, size_t smem, int64_t work_items,
@@ -1259,11 +1327,14 @@ int64_t record_stride(int n, int tsum_cap)
     return ((int64_t)32 * n + (int64_t)8 * tsum_cap + 15) / 16 * 16;
 }
 
+int walk_work_bytes(int n, int leaf_cap, bool count)
+{
+    return list_bytes(n) + align16((count ? 32 : 12) * (leaf_cap + 1));
+}
+
 int walk_core_bytes(int n, int tsum_cap, int leaf_cap)
 {
-    const int64_t b = kHdrBytes + align16(8 * tsum_cap) + list_bytes(n) +
-                      align16(8 * 4 * (leaf_cap + 1));
-    static_assert(kHdrBytes % 16 == 0, "warp blocks must stay 16-byte aligned");
+    const int64_t b = 2 * record_stride(n, tsum_cap) + walk_work_bytes(n, leaf_cap, true);
     return (int)std::min<int64_t>(b, INT32_MAX / 2);
 }
 
@@ -1277,12 +1348,17 @@ cudaError_t launch_setup_fp32(const BatchIndex *d_index, int64_t units, uint32_t
 }
 
 cudaError_t launch_walk_fp32(const BatchIndex *d_index, int64_t row_begin, int64_t row_end,
-                             int core_max, int warps, int mode, const RowOutputs &o,
+                             int rec_max, const int work_max[2], int warps, int mode,
+                             const RowOutputs &o,
                              unsigned long long *lb, const WalkFaults &f, cudaStream_t stream)
 {
     const int64_t rows = row_end - row_begin;
     if (rows <= 0) return cudaSuccess;
-    const int warp_smem = (core_max + 15) & ~15;   // warp blocks start 16-byte aligned
+    // record buffers and warp blocks start 16-byte aligned (record strides are
+    // multiples of 16)
+    rec_max = (rec_max + 15) & ~15;
+    const int work = work_max[mode == MODE_EMIT ? 0 : 1];
+    const int warp_smem = (mode == MODE_EMIT ? 1 : 2) * rec_max + ((work + 15) & ~15);
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -1297,6 +1373,7 @@ cudaError_t launch_walk_fp32(const BatchIndex *d_index, int64_t row_begin, int64
     WalkArgs A;
     A.B = d_index;
     A.warp_smem = warp_smem;
+    A.rec_max = rec_max;
     A.row_ptr = o.row_ptr;
     A.col = o.col;
     A.lo = (float *)o.lo;
