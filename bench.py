@@ -5,16 +5,18 @@
 
 Workload: the 5-D room-temperature system (x+ = A x + B u + 1.8 + w, A = 0.85 I
 + 0.03 ring, [17,23]^5 on an 11^5 grid, 9 inputs, sigma 0.2, cutoff 1e-8),
-FP32-sound bounds with FP64 row terms. One step is one whole build through
-the C ABI: the count pass (per-row counts, sink, truncated mass, row checks),
-the row-pointer scan and the emit pass (col/lo/up). Inputs are synthetic and
-seeded; the output (~33 GB) is far larger than L2, and L2 is also flushed
-between timed steps.
+FP32-sound bounds with FP64 row terms. One step is one whole build replayed
+from a CUDA graph made through the C ABI: the setup pass (per-row records,
+sink bounds, mass outside the window box), the count pass (per-row counts,
+truncated mass, row checks), the row-pointer scan and the emit pass
+(col/lo/up). Inputs are synthetic and seeded; the output (~33 GB) is far
+larger than L2, and L2 is also flushed between timed steps.
 
-The JSON line reports pairs/s (value), the emit kernel against the measured
-HBM copy bandwidth (roofline), the end-to-end rate with the CSR read back to
-pinned host memory (e2e), the FP64-plain GPU path on the same workload, and
-the CPU oracle timed on a bounded sample of rows (cpu_baseline).
+The JSON line reports pairs/s (value), the emit kernel (the step's largest)
+against the measured HBM copy bandwidth (roofline, with the whole step's
+fraction as step_frac), the end-to-end rate with the CSR read back to pinned
+host memory (e2e), the FP64-plain GPU path on the same workload, and the CPU
+oracle timed on a bounded sample of rows (cpu_baseline).
 
 With N > 1 (torchrun, one process per GPU) every rank builds its own copy of
 the workload: the rows of independent builds need no exchange, so the run
@@ -49,9 +51,12 @@ def workload_name(cells=11):
 
 
 WORKLOAD = workload_name()
-# kernels one step launches: the one-pass walk (the graph's resets are memset
-# nodes, not kernels)
-LAUNCHES_PER_STEP = 1
+# kernels one step launches: setup, count walk, three scan kernels, emit walk
+# (the graph's resets are memset nodes, not kernels)
+LAUNCHES_PER_STEP = 6
+# FP64 rate of the GB300 FMA pipe, measured with a dependent-chain DFMA
+# probe (2 flops per DFMA): the bound of the FP64-plain path
+FP64_PEAK_GFLOPS = 1200.0
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -74,7 +79,8 @@ def parse_args(argv=None):
     p.add_argument("--no-batched", action="store_true",
                    help="skip the batched workload (256 seeded systems, graphs, autotuner)")
     p.add_argument("--cpu-rows", type=int, default=0, help="oracle sample size (0: auto)")
-    p.add_argument("--case", choices=["synth", "regions", "mc"], default=None,
+    p.add_argument("--case", choices=["synth", "regions", "mc", "walk", "fp64", "batched"],
+                   default=None,
                    help="run one small invocation of that leg and exit (a target for "
                         "profilers; prints no JSON line)")
     p.add_argument("--cells", type=int, default=11,
@@ -198,30 +204,51 @@ def hbm_peak():
         return 6800.0, "fallback"
 
 
-def walk_traffic(alg_bytes):
-    """DRAM bytes of one launch of the one-pass kernel, from the committed ncu
-    summary.
-
-    The summary records the DRAM traffic per algorithmic byte of the kernel
-    and the hash of the source it was captured on; the figure is used only
-    while that source is unchanged (None otherwise)."""
+def profile_figure(profile, source, key):
+    """A figure recorded in a committed ncu summary (a "key: value" line), or
+    None. The summary records the sha256 prefix of the kernel source it was
+    captured on; the figure is used only while that source is unchanged."""
     import hashlib
-    prof = os.path.join(ROOT, "profiles", "room5d_fp32_walk_ncu.txt")
-    src = os.path.join(ROOT, "paper_2401_03555_gb300", "csrc", "walk_fp32.cu")
+    prof = os.path.join(ROOT, "profiles", profile)
+    src = os.path.join(ROOT, "paper_2401_03555_gb300", "csrc", source)
     try:
         text = open(prof).read()
         digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
     except OSError:
         return None
-    want, ratio = None, None
+    want, val = None, None
     for line in text.splitlines():
         if "sha256 prefix" in line:
             want = line.split("sha256 prefix")[1].strip().rstrip(".").split()[0]
-        if line.strip().startswith("traffic_bytes_per_algorithmic_byte:"):
-            ratio = float(line.split(":")[1])
-    if want is None or ratio is None or not digest.startswith(want):
+        if line.strip().startswith(key + ":"):
+            val = float(line.split(":")[1])
+    if want is None or val is None or not digest.startswith(want):
         return None
-    return int(ratio * alg_bytes)
+    return val
+
+
+def walk_traffic(alg_bytes):
+    """DRAM bytes of one launch of the emit kernel: the traffic per algorithmic
+    byte from the committed ncu summary, scaled to this launch."""
+    r = profile_figure("room5d_fp32_walk_ncu.txt", "walk_fp32.cu",
+                       "traffic_bytes_per_algorithmic_byte")
+    return None if r is None else int(r * alg_bytes)
+
+
+def fp64_roofline(pairs, ms):
+    """The FP64-plain build against the FP64 pipe: its FP64 flops per pair
+    (2 per DFMA + DADD + DMUL, counted by ncu over both passes on the 7^5 room)
+    times the pairs, over the build's time."""
+    f = profile_figure("room5d_fp64_rows_ncu.txt", "kernels.cu", "fp64_flops_per_pair")
+    out = {"bound": "fp64", "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+           "peak_source": "measured (dependent-chain DFMA probe on GB300)",
+           "flops_per_pair": f}
+    if f is None:
+        out.update({"achieved": None, "frac": None})
+    else:
+        ach = f * pairs / (ms / 1e3) / 1e9
+        out.update({"achieved": round(ach, 1), "frac": round(ach / FP64_PEAK_GFLOPS, 4)})
+    return out
 
 
 def run_two_pass(prob, nnz, rbuf, pbuf, wbuf, flush, stream, dev, reps=3):
@@ -258,7 +285,7 @@ def run_two_pass(prob, nnz, rbuf, pbuf, wbuf, flush, stream, dev, reps=3):
     return {"count_ms": round(cm, 3), "emit_ms": round(em, 3), "step_ms": round(cm + em, 3),
             "value": nnz / ((cm + em) / 1e3), "unit": UNIT,
             "emit_frac": round(emit_bytes / (em / 1e3) / 1e9 / peak, 4),
-            "path": "impact_count (walk COUNT: row pointers by look-back, row terms) + "
+            "path": "impact_count (setup, walk COUNT: per-row counts and row terms, scan) + "
                     "impact_emit (walk EMIT at those row pointers), each synchronized"}
 
 
@@ -358,10 +385,10 @@ def run_ours(args, rank, world, local_rank):
     wbuf = impact.alloc_workspace(prob, "fp32", dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
-    # one step = the whole build replayed from a CUDA graph: resets of the
-    # status, row counter and offset words, then ONE persistent kernel that
-    # sets up every row's factor tables, counts its pairs, finds its offset
-    # from the rows before it and writes its pairs and row terms
+    # one step = the whole build replayed from a CUDA graph: the setup kernel
+    # (every row's record, sink bounds, outside-window mass), the count walk,
+    # the scan of the counts into row pointers and the emit walk, with the
+    # resets of the status and row-counter words as memset nodes
     graph = impact.Batch([prob], "fp32").graph(rbuf, pbuf, nnz, wbuf, stream)
 
     def step():
@@ -395,22 +422,33 @@ def run_ours(args, rank, world, local_rank):
     total_pairs = sum_over_ranks(float(nnz), world, dev)
     value = total_pairs / (ms / 1e3)
 
-    # roofline of the one kernel of the step: algorithmic bytes = 12 B per
-    # pair written (int32 col + f32 lo + f32 up) + 36 B per row written
-    # (row_ptr, sink_lo, sink_up, trunc: 8 each; row_flags 4); the time is
-    # the whole graph replay (its resets included), so the fraction is a
-    # lower bound for the kernel alone
-    peak, peak_kind = hbm_peak()
-    alg_bytes = nnz * 12 + rows * 36
-    achieved = alg_bytes / (ms_local / 1e3) / 1e9
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": walk_traffic(alg_bytes),
-                "kernel": "walk_fp32<FUSED>", "peak_source": peak_kind,
-                "traffic_source": "ncu dram__bytes_read+write of the one-pass kernel, scaled "
-                                  "per algorithmic byte (profiles/room5d_fp32_walk_ncu.txt)",
-                "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": round(ms_local, 3),
-                "bytes_model": "12 B/pair + 36 B/row written"}
     clk = clocks.summary()
+
+    # the two-call path (impact_count, then impact_emit at its row pointers):
+    # each pass timed on its own with CUDA events on the launching stream; the
+    # emit pass is the step's largest kernel (its share of the launch list is
+    # in profiles/room5d_fp32_launch_list.txt)
+    two = run_two_pass(prob, nnz, rbuf, pbuf, wbuf, flush, stream, dev)
+
+    # roofline of the emit kernel: algorithmic bytes = 12 B per pair written
+    # (int32 col + f32 lo + f32 up) + 16 B per row (row_ptr read, two 8-byte
+    # words); step_frac: the whole step's algorithmic bytes, 12 B per pair +
+    # 36 B per row written (row_ptr, sink_lo, sink_up, trunc: 8 each;
+    # row_flags 4), over ms_per_step
+    peak, peak_kind = hbm_peak()
+    emit_bytes = nnz * 12 + rows * 16
+    achieved = emit_bytes / (two["emit_ms"] / 1e3) / 1e9
+    step_bytes = nnz * 12 + rows * 36
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": walk_traffic(emit_bytes),
+                "kernel": "walk_fp32<EMIT>", "peak_source": peak_kind,
+                "traffic_source": "ncu dram__bytes_read+write of the emit kernel per algorithmic "
+                                  "byte on the 7^5 room, scaled to this launch "
+                                  "(profiles/room5d_fp32_walk_ncu.txt)",
+                "algorithmic_bytes_per_launch": emit_bytes, "launch_ms": two["emit_ms"],
+                "bytes_model": "12 B/pair written + 16 B/row read",
+                "step_frac": round(step_bytes / (ms_local / 1e3) / 1e9 / peak, 4),
+                "step_bytes_model": "12 B/pair + 36 B/row written, over ms_per_step"}
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -422,9 +460,7 @@ def run_ours(args, rank, world, local_rank):
            "roofline": roofline, "clocks": clk,
            "gpu_launches": LAUNCHES_PER_STEP * args.steps, "wall_s": round(wall_s, 3)}
 
-    # the two-call path (impact_count, then impact_emit at its row pointers):
-    # each pass timed on its own
-    out["two_pass"] = run_two_pass(prob, nnz, rbuf, pbuf, wbuf, flush, stream, dev)
+    out["two_pass"] = two
 
     # rows the oracle baseline will sample: their GPU values, kept for the
     # parity check after the oracle has run
@@ -455,7 +491,8 @@ def run_ours(args, rank, world, local_rank):
         e.synchronize()
         ms64 = s.elapsed_time(e)
         out["fp64_plain"] = {"value": c64.nnz / (ms64 / 1e3), "unit": UNIT, "ms": ms64,
-                             "pairs": c64.nnz, "fp32_over_fp64": value / world / (c64.nnz / (ms64 / 1e3))}
+                             "pairs": c64.nnz, "fp32_over_fp64": value / world / (c64.nnz / (ms64 / 1e3)),
+                             "roofline": fp64_roofline(c64.nnz, ms64)}
         del c64
         torch.cuda.empty_cache()
 
@@ -598,8 +635,8 @@ def run_batched(dev, stream, reps=2, cap_pairs=8_000_000_000):
                         "peak_source": peak_kind, "algorithmic_bytes_per_pass": alg_bytes,
                         "bytes_model": "12 B/pair + 36 B/row written",
                         "time": "every group's graph replay, back to back"},
-           "path": "impact_graph_launch per group (one persistent one-pass launch over "
-                   "every system of the group)"}
+           "path": "impact_graph_launch per group (setup, count, scan and emit, each one "
+                   "persistent launch over every system of the group)"}
     out["fp64_plain"] = batched_fp64_sample(probs, dev)
     return out
 
@@ -944,13 +981,38 @@ def run_reference(args, rank, world):
                                         "d2h_bytes_per_step": 0}}
 
 
-def run_case(which):
+def run_case(which, cells=7):
     """One small invocation of a leg, for a profiler to capture: synthesis on
     the 21^2 robot (3 iterations per phase), region vectors and sampled noise
-    (1024 draws) on the 7^5-cell room."""
+    (1024 draws) on the 7^5-cell room; the FP32-sound build (count, then emit)
+    and the FP64-plain build of the room on `cells`^5 cells; one group of 16
+    systems of the batched workload built into caller arrays."""
     import torch
     from paper_2401_03555_gb300 import impact, workloads as W
-    if which == "synth":
+    if which == "walk":
+        prob = W.room_5d(cells_per_dim=cells)
+        b = impact.Batch([prob], "fp32")
+        rb = impact.alloc_rows(b.rows)
+        ws = b.alloc_workspace()
+        nnz = b.count(rb, ws)
+        pb = impact.alloc_pairs(max(nnz, 1), "fp32")
+        b.emit(rb, pb, max(nnz, 1), ws)
+        torch.cuda.synchronize()
+        print("pairs", nnz)
+    elif which == "fp64":
+        c = impact.build(W.room_5d(cells_per_dim=cells), "fp64")
+        torch.cuda.synchronize()
+        print("pairs", c.nnz)
+    elif which == "batched":
+        b = impact.Batch(W.batched_family(16), "fp32")
+        rb = impact.alloc_rows(b.rows)
+        ws = b.alloc_workspace()
+        nnz = b.count(rb, ws)
+        pb = impact.alloc_pairs(max(nnz, 1), "fp32")
+        b.build_into(rb, pb, max(nnz, 1), ws)
+        torch.cuda.synchronize()
+        print("pairs", nnz)
+    elif which == "synth":
         prob = W.robot_2d()
         lab = impact.label_cells(prob, [([3, 3], [7, 7])], [([-7, -7], [-3, -3])])
         g = impact.synthesize(impact.build(prob, "fp64"), prob, lab, eps=1e-6, max_iters=3)
@@ -972,7 +1034,7 @@ def run_case(which):
 def main(argv=None):
     args = parse_args(argv)
     if args.case:
-        run_case(args.case)
+        run_case(args.case, args.cells)
         return
     rank, world, local_rank = dist_env()
     if args.impl == "reference":

@@ -52,7 +52,8 @@ typedef enum {
     IMPACT_ERR_CAPACITY = 3,  /* caller buffers too small; needed nnz written back   */
     IMPACT_ERR_CUDA = 4,      /* a CUDA runtime call or a kernel launch failed       */
     IMPACT_ERR_TIMEOUT = 5,   /* a bounded device wait gave up                       */
-    IMPACT_ERR_UNSOUND = 6    /* a row check proved a row-sum invariant violated     */
+    IMPACT_ERR_UNSOUND = 6,   /* a row check proved a row-sum invariant violated     */
+    IMPACT_ERR_CANCELLED = 7  /* a served request was cancelled before it ran        */
 } impact_status;
 
 typedef enum {
@@ -161,21 +162,23 @@ impact_status impact_plan(const impact_system *sys, const impact_grid *grid,
 
 /*
  * impact_build -- the whole abstraction (Alg. 2) on `stream` (a cudaStream_t;
- * NULL is the legacy default stream). With caller-owned col/lo/up
- * (capacity out->nnz) the FP32-sound build is one pass: each row counts its
- * pairs, finds its offset from the rows before it and writes them. With
- * library-owned output (and for FP64_PLAIN) it runs the count pass, the
- * row pointers and then the emit pass. Synchronizes `stream` once at the end
- * (and once after the count when the library allocates) to report nnz and
- * status.
+ * NULL is the legacy default stream): the count pass, the row pointers and
+ * the emit pass. With caller-owned col/lo/up (capacity out->nnz) the three
+ * run back to back on the device (the emit pass compares the total with the
+ * capacity there); with library-owned output the library reads the total
+ * after the count to allocate. The batch calls can instead run the FP32-sound
+ * build into caller arrays as one pass (impact_tuning.one_pass): each row
+ * counts its pairs, finds its offset from the rows before it and writes them.
+ * Synchronizes `stream` once at the end (and once after the count when the
+ * library allocates) to report nnz and status.
  * Errors: IMPACT_ERR_ARG, IMPACT_ERR_OOM, IMPACT_ERR_CUDA;
  *         IMPACT_ERR_CAPACITY when caller-owned col/lo/up hold fewer than the
  *         needed pairs (out->nnz then holds the needed count, row_ptr and the
- *         row terms are valid; col/lo/up hold the pairs of the rows that fit
- *         (FP32) or are untouched (FP64));
- *         IMPACT_ERR_TIMEOUT when a row's bounded wait for the offsets of the
- *         rows before it gave up (the output is incomplete; the device and
- *         the library stay usable);
+ *         row terms are valid; col/lo/up are untouched, or with one_pass hold
+ *         the pairs of the rows that fit);
+ *         IMPACT_ERR_TIMEOUT (one_pass only) when a row's bounded wait for the
+ *         offsets of the rows before it gave up (the output is incomplete; the
+ *         device and the library stay usable);
  *         IMPACT_ERR_UNSOUND when row_flags != NULL and some row check failed
  *         (the output is complete; row_flags tells which rows).
  */
@@ -246,13 +249,16 @@ typedef struct {
  * Launch shapes of the FP32-sound walk (impact_batch_tune picks them), and
  * fault-injection knobs for testing the failure paths without a GPU fault.
  * Zero fields take the defaults.
- *   count_warps   warps per block of the count pass and of the one-pass build
- *                 (caller-owned output), 1..8 (default 4)
+ *   count_warps   warps per block of the count pass and of the one-pass build,
+ *                 1..8 (default 4)
  *   emit_warps    warps per block of the emit pass, 1..8 (default 4)
- *   spin_limit    sleeps of about 0.1 us that a row's offset look-back waits
- *                 for the rows before it before the call gives up with
- *                 IMPACT_ERR_TIMEOUT (0: 2^24, far beyond any real wait)
- *   reserved      must be 0
+ *   spin_limit    one_pass: sleeps of about 0.1 us that a row's offset
+ *                 look-back waits for the rows before it before the call gives
+ *                 up with IMPACT_ERR_TIMEOUT (0: 2^24, far beyond any real wait)
+ *   one_pass      1: the FP32-sound build into caller arrays (build, graph)
+ *                 runs as one walk in which each row finds its offset by a
+ *                 look-back over the rows before it; 0 (default): count, scan,
+ *                 emit. Same results; the two-pass form measured faster.
  *   stall_row     r + 1: row r never publishes its pair count, so every row
  *                 after it waits until spin_limit runs out (0: off)
  *   fault_row     r + 1: row r's row check sees a lower-bound sum of 2, so it
@@ -264,7 +270,7 @@ typedef struct {
     int count_warps;
     int emit_warps;
     int spin_limit;
-    int reserved;
+    int one_pass;
     int64_t stall_row;
     int64_t fault_row;
 } impact_tuning;
@@ -295,16 +301,16 @@ impact_status impact_batch_build(const impact_request *reqs, int count,
                                  impact_csr *out, void *stream);
 
 /*
- * CUDA graph of a batch's whole pipeline (FP32: the one-pass build; FP64:
- * count, scan, emit) into fixed
+ * CUDA graph of a batch's whole pipeline (setup, count, scan and emit, or the
+ * one-pass build with impact_tuning.one_pass) into fixed
  * caller-owned arrays: out->col/lo/up with capacity out->nnz and the row
  * arrays, all DEVICE memory that must outlive the graph. The descriptors and
  * tables are uploaded once here (into out->workspace when given, else into
  * scratch the graph owns); each impact_graph_launch replays the build
  * asynchronously on `stream`. After synchronizing that stream,
  * impact_graph_result returns the launch's status and nnz (IMPACT_ERR_CAPACITY
- * when the capacity was short: then col/lo/up hold the pairs of the rows that
- * fit (FP32) or are untouched (FP64)). The request
+ * when the capacity was short: then col/lo/up are untouched, or with one_pass
+ * hold the pairs of the rows that fit). The request
  * arguments are read during impact_graph_create only.
  */
 typedef struct impact_graph impact_graph;
@@ -316,11 +322,10 @@ impact_status impact_graph_result(impact_graph *graph, int64_t *nnz);
 impact_status impact_graph_destroy(impact_graph *graph);
 
 /*
- * impact_batch_tune -- the autotuner: times the one-pass build (or, when
- * out->col == NULL, the count pass) over 2, 4, 6 and 8 warps per block, then
- * the emit pass over the same, each the best of `reps` runs on this batch,
- * and writes the fastest shape to *best and the first pass's milliseconds to
- * *best_ms (may be NULL). `out` as for impact_batch_emit with the capacity of
+ * impact_batch_tune -- the autotuner: times the count pass over 2, 4, 6 and 8
+ * warps per block, then (unless out->col == NULL) the emit pass over the
+ * same, each the best of `reps` runs on this batch, and writes the fastest
+ * shape to *best and the sum of the two best times to *best_ms (may be NULL). `out` as for impact_batch_emit with the capacity of
  * a previous count. Synchronizes `stream`; its own scratch is allocated and
  * freed stream-ordered. FP32_SOUND only.
  */
@@ -399,6 +404,16 @@ impact_status impact_server_poll(impact_server *server, int64_t ticket, int wait
  */
 impact_status impact_server_timing(impact_server *server, int64_t ticket, double *queue_ms,
                                    double *count_ms, double *emit_wait_ms, double *emit_ms);
+
+/*
+ * impact_server_cancel -- withdraws a request that is still waiting for
+ * admission: it never reaches the device, and impact_server_poll then reports
+ * it done with IMPACT_ERR_CANCELLED (release it as any finished request).
+ * A request already admitted runs to completion.
+ * Errors: IMPACT_ERR_ARG for an unknown or released ticket, or a request that
+ * has been admitted or has finished.
+ */
+impact_status impact_server_cancel(impact_server *server, int64_t ticket);
 
 /* Frees a finished request's result (its group's memory goes once every
  * request of the group is released). Errors: IMPACT_ERR_ARG when in flight. */

@@ -65,9 +65,11 @@ impact_status tuning_of(const impact_tuning *t, Tuning &T)
     if (T.count_warps < 1 || T.count_warps > IMPACT_TREE_WARPS_MAX || T.emit_warps < 1 ||
         T.emit_warps > IMPACT_TREE_WARPS_MAX)
         return fail(IMPACT_ERR_ARG, "tuning: warps per block must be in [1, 8]");
-    if (t->spin_limit < 0 || t->stall_row < 0 || t->fault_row < 0 || t->reserved != 0)
+    if (t->spin_limit < 0 || t->stall_row < 0 || t->fault_row < 0 ||
+        (t->one_pass != 0 && t->one_pass != 1))
         return fail(IMPACT_ERR_ARG,
-                    "tuning: spin_limit, stall_row and fault_row must be >= 0, reserved 0");
+                    "tuning: spin_limit, stall_row and fault_row must be >= 0, one_pass 0 or 1");
+    T.one_pass = t->one_pass == 1;
     T.faults.spin_limit = t->spin_limit;
     T.faults.stall_row = t->stall_row - 1;
     T.faults.fault_row = t->fault_row - 1;
@@ -389,13 +391,15 @@ impact_status run_emit(const Batch &B, const Work &W, const impact_csr *out, int
     return IMPACT_OK;
 }
 
-// the whole build into arrays of known capacity: FP32 in one pass (each row
-// finds its offset by the look-back and writes its pairs), FP64 as count,
-// scan and emit
+// the whole build into arrays of known capacity with no host round trip:
+// count, scan and emit (the emit pass checks the total against the capacity
+// on the device and writes nothing when it does not fit), or for FP32 with
+// tuning one_pass a single walk in which each row finds its offset by the
+// look-back and writes its pairs
 impact_status run_fused(const Batch &B, const Work &W, const impact_csr *out, int64_t capacity,
                         cudaStream_t st, int64_t chunk_rows)
 {
-    if (B.prec != PREC_FP32_SOUND) {
+    if (B.prec != PREC_FP32_SOUND || !B.tune.one_pass) {
         impact_status s = run_count(B, W, out, st, chunk_rows);
         if (s != IMPACT_OK) return s;
         return run_emit(B, W, out, capacity, true, st, chunk_rows);
@@ -527,7 +531,7 @@ impact_status build_into(const Batch &B, impact_csr *out, bool lib_owned, cudaSt
         impact_csr view;
         if ((s = pair_view(out, view)) != IMPACT_OK) return s;
         if ((s = run_emit(B, W, &view, capacity, true, st)) != IMPACT_OK) return s;
-    } else {   // caller capacity: one pass
+    } else {   // caller capacity: no host round trip
         impact_csr view;
         if ((s = pair_view(out, view)) != IMPACT_OK) return s;
         if ((s = run_fused(B, W, &view, capacity, st)) != IMPACT_OK) return s;
@@ -932,16 +936,15 @@ impact_status impact_batch_tune(const impact_request *reqs, int count,
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    // pass 0: count, 1: emit, 2: count and emit in one pass
+    // pass 0: count, 1: emit
     auto timed = [&](int warps, int pass, double &ms) -> impact_status {
         Batch B = B0;
         B.tune.count_warps = B.tune.emit_warps = warps;
         ms = 1e30;
         for (int i = 0; i < reps; ++i) {
             CK(cudaEventRecord(e0, st));
-            impact_status r = pass == 0   ? run_count(B, W, out, st)
-                              : pass == 1 ? run_emit(B, W, out, out->nnz, true, st)
-                                          : run_fused(B, W, out, out->nnz, st);
+            impact_status r = pass == 0 ? run_count(B, W, out, st)
+                                        : run_emit(B, W, out, out->nnz, true, st);
             if (r != IMPACT_OK) return r;
             CK(cudaEventRecord(e1, st));
             CK(cudaEventSynchronize(e1));
@@ -959,10 +962,10 @@ impact_status impact_batch_tune(const impact_request *reqs, int count,
     impact_tuning tb;
     memset(&tb, 0, sizeof(tb));
     double best_a = 1e30, best_b = 1e30;
-    // the count (or, with output arrays, the one-pass) shape, then the emit shape
+    // the count shape, then (with output arrays) the emit shape
     for (int w : warps) {
         double ms;
-        if ((s = timed(w, can_emit ? 2 : 0, ms)) != IMPACT_OK) break;
+        if ((s = timed(w, 0, ms)) != IMPACT_OK) break;
         if (ms < best_a) {
             best_a = ms;
             tb.count_warps = w;
@@ -985,7 +988,7 @@ impact_status impact_batch_tune(const impact_request *reqs, int count,
     if (best_a >= 1e30) return fail(IMPACT_ERR_ARG, "no launch shape ran this batch");
     if (tb.emit_warps == 0) tb.emit_warps = IMPACT_TREE_WARPS;
     *best = tb;
-    if (best_ms) *best_ms = best_a;
+    if (best_ms) *best_ms = best_a + (can_emit && best_b < 1e30 ? best_b : 0.0);
     return IMPACT_OK;
 }
 

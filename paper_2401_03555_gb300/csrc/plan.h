@@ -21,6 +21,7 @@ impact_status fail(impact_status s, const std::string &msg);
 struct Tuning {
     int count_warps = IMPACT_TREE_WARPS;
     int emit_warps = IMPACT_TREE_WARPS;
+    bool one_pass = false;   // FP32 build into caller arrays: one walk with look-back
     WalkFaults faults;
 };
 

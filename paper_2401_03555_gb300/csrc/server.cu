@@ -552,6 +552,25 @@ impact_status impact_server_timing(impact_server *S, int64_t ticket, double *que
     return IMPACT_OK;
 }
 
+impact_status impact_server_cancel(impact_server *S, int64_t ticket)
+{
+    if (!S) return impact::fail(IMPACT_ERR_ARG, "null server");
+    std::lock_guard<std::mutex> lock(S->mu);
+    auto it = S->reqs.find(ticket);
+    if (it == S->reqs.end() || it->second->released)
+        return impact::fail(IMPACT_ERR_ARG, "unknown or released ticket");
+    Request *r = it->second;
+    if (r->state != Request::WAITING)
+        return impact::fail(IMPACT_ERR_ARG, "the request has been admitted or has finished");
+    for (auto w = S->waiting.begin(); w != S->waiting.end(); ++w)
+        if (*w == r) {
+            S->waiting.erase(w);
+            break;
+        }
+    S->fail_request(r, IMPACT_ERR_CANCELLED, "cancelled before admission");
+    return IMPACT_OK;
+}
+
 impact_status impact_server_release(impact_server *S, int64_t ticket)
 {
     if (!S) return impact::fail(IMPACT_ERR_ARG, "null server");

@@ -23,7 +23,7 @@ import torch
 from . import build as _build
 
 IMPACT_OK, IMPACT_ERR_ARG, IMPACT_ERR_OOM, IMPACT_ERR_CAPACITY = 0, 1, 2, 3
-IMPACT_ERR_CUDA, IMPACT_ERR_TIMEOUT, IMPACT_ERR_UNSOUND = 4, 5, 6
+IMPACT_ERR_CUDA, IMPACT_ERR_TIMEOUT, IMPACT_ERR_UNSOUND, IMPACT_ERR_CANCELLED = 4, 5, 6, 7
 FP64_PLAIN, FP32_SOUND = 0, 1
 _PREC = {"fp64": FP64_PLAIN, "fp32": FP32_SOUND, FP64_PLAIN: FP64_PLAIN, FP32_SOUND: FP32_SOUND}
 
@@ -36,7 +36,8 @@ ENTRY_POINTS = ("impact_plan", "impact_workspace_bytes", "impact_build", "impact
                 "impact_server_poll", "impact_server_release", "impact_server_stats",
                 "impact_server_destroy", "impact_synthesize", "impact_label_cells",
                 "impact_region_vectors", "impact_synthesize_ex", "impact_build_mc",
-                "impact_debug_fail_alloc", "impact_debug_live_bytes", "impact_server_timing")
+                "impact_debug_fail_alloc", "impact_debug_live_bytes", "impact_server_timing",
+                "impact_server_cancel")
 
 
 class ImpactError(RuntimeError):
@@ -77,7 +78,7 @@ class _Request(ctypes.Structure):
 
 class _Tuning(ctypes.Structure):
     _fields_ = [("count_warps", ctypes.c_int), ("emit_warps", ctypes.c_int),
-                ("spin_limit", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("spin_limit", ctypes.c_int), ("one_pass", ctypes.c_int),
                 ("stall_row", ctypes.c_int64), ("fault_row", ctypes.c_int64)]
 
     def as_dict(self):
@@ -184,6 +185,8 @@ def load(build_if_missing: bool = True):
                                            ctypes.POINTER(ctypes.c_double)]
         lib.impact_server_release.restype = ctypes.c_int
         lib.impact_server_release.argtypes = [ctypes.c_void_p, ctypes.c_int64]
+        lib.impact_server_cancel.restype = ctypes.c_int
+        lib.impact_server_cancel.argtypes = [ctypes.c_void_p, ctypes.c_int64]
         lib.impact_server_timing.restype = ctypes.c_int
         lib.impact_server_timing.argtypes = [ctypes.c_void_p, ctypes.c_int64] + \
             [ctypes.POINTER(ctypes.c_double)] * 4
@@ -492,12 +495,13 @@ def live_bytes():
 # batches: several builds per launch (impact_batch_*), CUDA graphs, autotuner
 # --------------------------------------------------------------------------
 
-def tuning(count_warps=0, emit_warps=0, spin_limit=0, stall_row=None, fault_row=None):
+def tuning(count_warps=0, emit_warps=0, spin_limit=0, stall_row=None, fault_row=None,
+           one_pass=False):
     """An impact_tuning (zero fields take the library defaults). `stall_row`
     and `fault_row` are fault injection for the failure-path tests: row r never
     publishes its pair count (the rows after it time out), or row r's row
     check sees an impossible lower-bound sum (IMPACT_ERR_UNSOUND)."""
-    return _Tuning(count_warps, emit_warps, spin_limit, 0,
+    return _Tuning(count_warps, emit_warps, spin_limit, int(bool(one_pass)),
                    0 if stall_row is None else int(stall_row) + 1,
                    0 if fault_row is None else int(fault_row) + 1)
 
@@ -717,6 +721,11 @@ class Server:
         return CSR(self.precision, rp - base, col_all[base:], lo_all[base:], up_all[base:],
                    _view(c.sink_lo, rows, torch.float64), _view(c.sink_up, rows, torch.float64),
                    _view(c.trunc, rows, torch.float64), _view(c.row_flags, rows, torch.int32))
+
+    def cancel(self, ticket: int):
+        """impact_server_cancel: withdraw a request still waiting for admission
+        (poll then raises ImpactError with IMPACT_ERR_CANCELLED)."""
+        _check(load().impact_server_cancel(self.handle, int(ticket)))
 
     def timing(self, ticket: int) -> dict:
         """impact_server_timing: where a finished request's latency went (ms)."""

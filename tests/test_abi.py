@@ -136,6 +136,13 @@ def test_batch_plan_rejects_bad_tuning(lib, field, value, msg):
         impact.Batch([W.robot_2d(cells_per_dim=5)], "fp32", tune=t)
 
 
+def test_batch_plan_rejects_a_one_pass_flag_other_than_0_or_1(lib):
+    t = impact.tuning()
+    t.one_pass = 2
+    with pytest.raises(impact.ImpactError, match="one_pass"):
+        impact.Batch([W.robot_2d(cells_per_dim=5)], "fp32", tune=t)
+
+
 def test_plan_accepts_the_largest_dimension(lib):
     prob = W.random_linear(2, min_cells=5000, max_cells=7000, dims=(8,))
     assert prob.n == 8

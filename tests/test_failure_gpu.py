@@ -40,19 +40,20 @@ def assert_same(a, b):
         assert torch.equal(getattr(a, f), getattr(b, f)), f
 
 
-@pytest.mark.parametrize("one_pass", [False, True])
-def test_row_check_fires_on_exactly_the_faulted_row(one_pass):
+@pytest.mark.parametrize("mode", ["count", "build", "one_pass"])
+def test_row_check_fires_on_exactly_the_faulted_row(mode):
     prob = small()
     ref = impact.build(prob, "fp32")
     bad = 17
-    b = impact.Batch([prob], "fp32", tune=impact.tuning(fault_row=bad))
+    b = impact.Batch([prob], "fp32",
+                     tune=impact.tuning(fault_row=bad, one_pass=mode == "one_pass"))
     rb = impact.alloc_rows(b.rows)
     with pytest.raises(impact.ImpactError) as e:
-        if one_pass:
+        if mode == "count":
+            b.count(rb)
+        else:
             pb = impact.alloc_pairs(ref.nnz, "fp32")
             b.build_into(rb, pb, ref.nnz)
-        else:
-            b.count(rb)
     assert e.value.status == impact.IMPACT_ERR_UNSOUND
     flags = rb["row_flags"].cpu().numpy()
     assert np.flatnonzero(flags).tolist() == [bad]
@@ -93,7 +94,7 @@ def test_look_back_wait_times_out_and_the_device_stays_usable():
     prob = small()
     ref = impact.build(prob, "fp32")
     b = impact.Batch([prob], "fp32", tune=impact.tuning(stall_row=prob.rows // 2,
-                                                        spin_limit=2000))
+                                                        spin_limit=2000, one_pass=True))
     rb = impact.alloc_rows(b.rows)
     pb = impact.alloc_pairs(ref.nnz, "fp32")
     with pytest.raises(impact.ImpactError) as e:
@@ -107,18 +108,28 @@ def test_look_back_wait_times_out_and_the_device_stays_usable():
     assert_same(csr_of(rb, pb, nnz), ref)
 
 
-def test_one_pass_build_reports_short_capacity():
+@pytest.mark.parametrize("one_pass", [False, True])
+def test_build_into_short_capacity_reports_the_needed_pairs(one_pass):
     prob = small()
     ref = impact.build(prob, "fp32")
-    b = impact.Batch([prob], "fp32")
+    b = impact.Batch([prob], "fp32", tune=impact.tuning(one_pass=one_pass))
     rb = impact.alloc_rows(b.rows)
     pb = impact.alloc_pairs(ref.nnz - 1, "fp32")
+    pb["col"].fill_(-7)
     c = impact._csr_struct(rb, pb, capacity=ref.nnz - 1)
-    st = impact.load().impact_batch_build(b.reqs, 1, b.prec, None, ctypes.byref(c), None)
+    st = impact.load().impact_batch_build(b.reqs, 1, b.prec, b._tp(),
+                                          ctypes.byref(c), None)
     assert st == impact.IMPACT_ERR_CAPACITY
     assert int(c.nnz) == ref.nnz                       # the needed count comes back
     assert torch.equal(rb["row_ptr"], ref.row_ptr)     # row pointers and terms are valid
     assert torch.equal(rb["trunc"], ref.trunc)
+    col = pb["col"].cpu()
+    if one_pass:   # the rows that fit are written
+        fit = int(np.searchsorted(ref.row_ptr.cpu().numpy(), ref.nnz - 1, side="right")) - 1
+        end = int(ref.row_ptr[fit])
+        assert torch.equal(col[:end], ref.col[:end].cpu())
+    else:          # the emit pass saw the short capacity and wrote nothing
+        assert bool((col == -7).all())
 
 
 def _oom_sweep(call, check=None, limit=40):

@@ -115,3 +115,35 @@ def test_request_larger_than_the_budget_fails_cleanly():
         t2 = srv.submit(W.robot_2d(cells_per_dim=3))   # still serves what fits
         assert srv.poll(t2, wait=True)[0]
         srv.release(t2)
+
+
+def test_cancel_withdraws_a_waiting_request():
+    """A kept result holds the budget, so the next request waits; cancelling
+    it keeps it off the device, and the server goes on serving."""
+    prob = W.room_5d(cells_per_dim=5)
+    one = impact.build(prob, "fp32")
+    ws = impact.workspace_bytes(prob, "fp32")
+    budget = ws + one.nbytes() + (256 << 10)        # one request at a time (rows: 1 MB)
+    with impact.Server("fp32", memory_budget=budget) as srv:
+        t1 = srv.submit(prob)
+        assert srv.poll(t1, wait=True)[0]            # finished, result kept
+        t2 = srv.submit(prob)
+        time.sleep(0.05)
+        assert srv.stats()["waiting"] == 1
+        srv.cancel(t2)
+        assert srv.stats()["waiting"] == 0
+        with pytest.raises(impact.ImpactError) as ei:
+            srv.poll(t2, wait=True)
+        assert ei.value.status == impact.IMPACT_ERR_CANCELLED
+        with pytest.raises(impact.ImpactError):       # only waiting requests cancel
+            srv.cancel(t1)
+        srv.release(t2)
+        with pytest.raises(impact.ImpactError):       # released: unknown
+            srv.cancel(t2)
+        assert same(srv.result(t1), one)
+        srv.release(t1)
+        t3 = srv.submit(prob)                         # the budget is free again
+        assert srv.poll(t3, wait=True)[0]
+        assert same(srv.result(t3), one)
+        srv.release(t3)
+        assert srv.stats()["completed"] == 2
