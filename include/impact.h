@@ -264,6 +264,9 @@ typedef struct {
  *   fault_row     r + 1: row r's row check sees a lower-bound sum of 2, so it
  *                 is flagged IMPACT_ROW_LO_SUM_ABOVE_ONE and the call returns
  *                 IMPACT_ERR_UNSOUND (needs row_flags; 0: off)
+ *   guard_row     r + 1: row r's walk starts with its step guard spent, as if
+ *                 an invariant of the walk had broken: the call returns
+ *                 IMPACT_ERR_CUDA ("internal") (FP32 walks; 0: off)
  * Shapes change speed only: results are bitwise identical for every shape.
  */
 typedef struct {
@@ -273,6 +276,7 @@ typedef struct {
     int one_pass;
     int64_t stall_row;
     int64_t fault_row;
+    int64_t guard_row;
 } impact_tuning;
 
 /*

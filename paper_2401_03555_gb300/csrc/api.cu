@@ -65,14 +65,16 @@ impact_status tuning_of(const impact_tuning *t, Tuning &T)
     if (T.count_warps < 1 || T.count_warps > IMPACT_TREE_WARPS_MAX || T.emit_warps < 1 ||
         T.emit_warps > IMPACT_TREE_WARPS_MAX)
         return fail(IMPACT_ERR_ARG, "tuning: warps per block must be in [1, 8]");
-    if (t->spin_limit < 0 || t->stall_row < 0 || t->fault_row < 0 ||
+    if (t->spin_limit < 0 || t->stall_row < 0 || t->fault_row < 0 || t->guard_row < 0 ||
         (t->one_pass != 0 && t->one_pass != 1))
         return fail(IMPACT_ERR_ARG,
-                    "tuning: spin_limit, stall_row and fault_row must be >= 0, one_pass 0 or 1");
+                    "tuning: spin_limit, stall_row, fault_row and guard_row must be >= 0, "
+                    "one_pass 0 or 1");
     T.one_pass = t->one_pass == 1;
     T.faults.spin_limit = t->spin_limit;
     T.faults.stall_row = t->stall_row - 1;
     T.faults.fault_row = t->fault_row - 1;
+    T.faults.guard_row = t->guard_row - 1;
     return IMPACT_OK;
 }
 

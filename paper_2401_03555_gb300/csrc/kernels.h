@@ -101,6 +101,7 @@ struct WalkFaults {
     int spin_limit = 0;        // look-back sleeps before giving up (0: the default)
     int64_t stall_row = -1;    // this row never publishes its count (-1: none)
     int64_t fault_row = -1;    // this row's checks see an impossible sum (-1: none)
+    int64_t guard_row = -1;    // this row's walk starts with its step guard spent (-1: none)
 };
 int64_t record_stride(int n, int tsum_cap);
 int walk_core_bytes(int n, int tsum_cap, int leaf_cap);   // both buffers and the work space

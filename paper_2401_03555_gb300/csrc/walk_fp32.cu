@@ -1161,6 +1161,7 @@ struct WalkArgs {
     int64_t row_end;
     int64_t stall_row;       // fault injection: this row never publishes (-1: none)
     int64_t fault_row;       // fault injection: this row's checks see a bad sum (-1: none)
+    int64_t guard_row;       // fault injection: this row's step guard starts spent (-1: none)
 };
 
 template <int MODE>
@@ -1235,7 +1236,8 @@ __global__ void __launch_bounds__(IMPACT_TREE_WARPS_MAX * 32) walk_fp32(const Wa
             CountAcc acc;
             const EmitOut none{nullptr, nullptr, nullptr, 0};
             int w0 = 0;
-            if (!empty) walked = walk_row<false>(S, n, f, lane, acc, none, w0, cut);
+            if (row == A.guard_row) walked = false;
+            else if (!empty) walked = walk_row<false>(S, n, f, lane, acc, none, w0, cut);
             int c = walked ? acc.cnt : 0;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
@@ -1285,7 +1287,8 @@ __global__ void __launch_bounds__(IMPACT_TREE_WARPS_MAX * 32) walk_fp32(const Wa
                 CountAcc none;
                 int written = 0;
                 bool wok = true;
-                if (!empty) wok = walk_row<true>(S, n, f, lane, none, out, written, cut);
+                if (row == A.guard_row) wok = false;
+                else if (!empty) wok = walk_row<true>(S, n, f, lane, none, out, written, cut);
                 if (lane == 0 && (!wok || written != len))
                     atomicOr(A.status, wok ? IMPACT_STATUS_EMIT_MISMATCH : IMPACT_STATUS_INTERNAL);
             }
@@ -1391,6 +1394,7 @@ cudaError_t launch_walk_fp32(const BatchIndex *d_index, int64_t row_begin, int64
     A.row_end = row_end;
     A.stall_row = f.stall_row;
     A.fault_row = f.fault_row;
+    A.guard_row = f.guard_row;
     // persistent grid: as many blocks as fit at once (rows are taken dynamically)
     const int g = occupancy_grid(k, threads, smem, rows, warps);
     if (mode == MODE_COUNT)

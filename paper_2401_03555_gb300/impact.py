@@ -79,7 +79,8 @@ class _Request(ctypes.Structure):
 class _Tuning(ctypes.Structure):
     _fields_ = [("count_warps", ctypes.c_int), ("emit_warps", ctypes.c_int),
                 ("spin_limit", ctypes.c_int), ("one_pass", ctypes.c_int),
-                ("stall_row", ctypes.c_int64), ("fault_row", ctypes.c_int64)]
+                ("stall_row", ctypes.c_int64), ("fault_row", ctypes.c_int64),
+                ("guard_row", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -496,14 +497,16 @@ def live_bytes():
 # --------------------------------------------------------------------------
 
 def tuning(count_warps=0, emit_warps=0, spin_limit=0, stall_row=None, fault_row=None,
-           one_pass=False):
-    """An impact_tuning (zero fields take the library defaults). `stall_row`
-    and `fault_row` are fault injection for the failure-path tests: row r never
-    publishes its pair count (the rows after it time out), or row r's row
-    check sees an impossible lower-bound sum (IMPACT_ERR_UNSOUND)."""
+           one_pass=False, guard_row=None):
+    """An impact_tuning (zero fields take the library defaults). `stall_row`,
+    `fault_row` and `guard_row` are fault injection for the failure-path
+    tests: row r never publishes its pair count (one_pass: the rows after it
+    time out), row r's row check sees an impossible lower-bound sum
+    (IMPACT_ERR_UNSOUND), or row r's walk starts with its step guard spent
+    (IMPACT_ERR_CUDA, internal)."""
+    opt = lambda r: 0 if r is None else int(r) + 1
     return _Tuning(count_warps, emit_warps, spin_limit, int(bool(one_pass)),
-                   0 if stall_row is None else int(stall_row) + 1,
-                   0 if fault_row is None else int(fault_row) + 1)
+                   opt(stall_row), opt(fault_row), opt(guard_row))
 
 
 @dataclass

@@ -129,7 +129,8 @@ def test_batch_plan_names_the_failing_request(lib):
 
 @pytest.mark.parametrize("field,value,msg", [("count_warps", 9, "warps"),
                                               ("emit_warps", -1, "warps"),
-                                              ("spin_limit", -5, "spin_limit")])
+                                              ("spin_limit", -5, "spin_limit"),
+                                              ("guard_row", -6, "guard_row")])
 def test_batch_plan_rejects_bad_tuning(lib, field, value, msg):
     t = impact.tuning(**{field: value})
     with pytest.raises(impact.ImpactError, match=msg):

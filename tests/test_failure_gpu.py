@@ -88,6 +88,43 @@ def test_emit_reports_a_row_pointer_that_does_not_match():
     assert torch.equal(pb["col"][ok], ref.col[ok]) and torch.equal(pb["up"][ok], ref.up[ok])
 
 
+@pytest.mark.parametrize("mode", ["count", "build"])
+def test_a_spent_step_guard_is_an_internal_error_and_the_library_recovers(mode):
+    """The walk's step guard bounds every row's depth-first loop; when it runs
+    out (a broken invariant) the row is reported, not looped on."""
+    prob = small()
+    ref = impact.build(prob, "fp32")
+    b = impact.Batch([prob], "fp32", tune=impact.tuning(guard_row=prob.rows // 3))
+    rb = impact.alloc_rows(b.rows)
+    with pytest.raises(impact.ImpactError) as e:
+        if mode == "count":
+            b.count(rb)
+        else:
+            pb = impact.alloc_pairs(ref.nnz, "fp32")
+            b.build_into(rb, pb, ref.nnz)
+    assert e.value.status == impact.IMPACT_ERR_CUDA
+    assert "step guard" in str(e.value)
+    assert_same(impact.build(prob, "fp32"), ref)
+
+
+def test_a_caller_image_wider_than_the_window_cap_is_refused():
+    """Caller-supplied images are not bounded by the planner: one row whose
+    image spans 135 cells of a dimension (the cap is 128) makes the setup
+    kernel report the overflow, and the call fails with IMPACT_ERR_ARG."""
+    base = W.robot_2d(cells_per_dim=150)
+    rng = np.random.default_rng(9)
+    pts = rng.uniform(-9.0, 9.0, size=(base.rows, 2))
+    img = np.stack([pts, pts], axis=2)
+    img[base.rows // 2, 0] = (-9.0, 9.0)
+    prob = W.with_images(base, img)
+    with pytest.raises(impact.ImpactError) as e:
+        impact.build(prob, "fp32")
+    assert e.value.status == impact.IMPACT_ERR_ARG
+    assert "window" in str(e.value)
+    img[base.rows // 2, 0] = (-1.0, 1.0)               # 15 cells: builds
+    assert impact.build(W.with_images(base, img), "fp32").nnz > 0
+
+
 def test_look_back_wait_times_out_and_the_device_stays_usable():
     """The one-pass build (caller arrays): each row waits, boundedly, for the
     pair counts of the rows before it."""
@@ -170,9 +207,9 @@ def test_out_of_memory_paths_release_everything():
         return impact.Batch([prob, W.robot_2d(cells_per_dim=7)], "fp32").count(rb)
     assert _oom_sweep(count_scratch) >= 2
 
-    def one_pass_scratch():   # impact_batch_build into caller arrays, library workspace
+    def build_into_scratch():   # impact_batch_build into caller arrays, library workspace
         return impact.Batch([prob], "fp32").build_into(rb, pb, ref.nnz)
-    assert _oom_sweep(one_pass_scratch, lambda n: n == ref.nnz) >= 2
+    assert _oom_sweep(build_into_scratch, lambda n: n == ref.nnz) >= 2
 
     def graph():
         g = impact.Batch([prob], "fp32").graph(rb, pb, ref.nnz)

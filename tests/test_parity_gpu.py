@@ -104,7 +104,7 @@ def wide_unicycle():
 
 
 WIDE = {
-    "robot2d-80-dense": (lambda: W.robot_2d(cells_per_dim=80), 40),
+    "robot2d-100-dense": (lambda: W.robot_2d(cells_per_dim=100), 40),
     "unicycle-70x70x3-1e-10": (wide_unicycle, 30),
 }
 
