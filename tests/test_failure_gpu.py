@@ -16,6 +16,7 @@
 """
 
 import ctypes
+import dataclasses
 
 import numpy as np
 import pytest
@@ -111,7 +112,8 @@ def test_a_caller_image_wider_than_the_window_cap_is_refused():
     """Caller-supplied images are not bounded by the planner: one row whose
     image spans 135 cells of a dimension (the cap is 128) makes the setup
     kernel report the overflow, and the call fails with IMPACT_ERR_ARG."""
-    base = W.robot_2d(cells_per_dim=150)
+    # cutoff 1e-8: a point image's window is about 2 x 32 noise cells wide
+    base = dataclasses.replace(W.robot_2d(cells_per_dim=150), cutoff=1e-8)
     rng = np.random.default_rng(9)
     pts = rng.uniform(-9.0, 9.0, size=(base.rows, 2))
     img = np.stack([pts, pts], axis=2)
