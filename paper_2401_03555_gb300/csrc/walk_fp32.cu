@@ -553,6 +553,7 @@ struct Leaf {
     int tw_l;      // width of the last dimension (b runs fastest)
     uint32_t magic_l;
     bool staged;
+    bool sorted;          // count pass: su, sl, pu, pl, sf are built
     uint32_t magic_nb;    // ceil(2^32 / nb) when 1 < nb <= 4096, for the emit's flat layout
     float *bu, *bl, *su, *sl, *pu, *pl, *sf;
     int *bc;
@@ -566,6 +567,7 @@ __device__ __forceinline__ Leaf leaf_of(const WarpMem &S, int n)
     f.magic_l = hl.magic;
     f.nb = n >= 2 ? S.h[n - 2].tw * hl.tw : hl.tw;
     f.staged = f.nb <= S.leaf_cap;
+    f.sorted = false;
     f.magic_nb = (f.nb > 1 && f.nb <= 4096)
                      ? (uint32_t)((0x100000000ull + (unsigned)f.nb - 1) / (unsigned)f.nb) : 0u;
     const int c = S.leaf_cap + 1;
@@ -660,7 +662,10 @@ __device__ void leaf_build(const WarpMem &S, int n, Leaf &f, int lane, float cut
     }
     f.tot_u = __shfl_sync(0xffffffffu, su_l, 0);
     f.tot_l = __shfl_sync(0xffffffffu, sl_l, 0);
-    if (!f.staged || !(cut > 0.0f)) return;
+    // a row of at most two dimensions has one parent (the root): testing
+    // its entries directly costs less than sorting them
+    if (!f.staged || !(cut > 0.0f) || n <= 2) return;
+    f.sorted = true;
     if (f.nb <= 32) {
         // one entry per lane: a bitonic sorting network over the warp puts
         // the entry of rank r (bu descending, ties by index) in lane r, then
@@ -880,7 +885,7 @@ __device__ void leaf_count(const WarpMem &S, int n, const Leaf &f, const NodeLis
         }
         return;
     }
-    if (f.staged) {
+    if (f.sorted) {
         // the kept entries of a parent are a prefix of the sorted table:
         // RU(P su[k]) >= cut for k below the count, not above it
         for (int pi = lane; pi < npar; pi += 32) {
@@ -898,7 +903,8 @@ __device__ void leaf_count(const WarpMem &S, int n, const Leaf &f, const NodeLis
         }
         return;
     }
-    // a table too wide to stage: every entry under every parent
+    // the root's table, or a table too wide to stage: every entry under
+    // every parent
     for (int pi = 0; pi < npar; ++pi) {
         const Node par = node_at(Lp, root, pi);
         for (int j0 = 0; j0 < nb; j0 += 32) {
