@@ -83,6 +83,8 @@ def parse_args(argv=None):
                    default=None,
                    help="run one small invocation of that leg and exit (a target for "
                         "profilers; prints no JSON line)")
+    p.add_argument("--systems", type=int, default=16,
+                   help="--case batched: the first this many systems of the batched workload")
     p.add_argument("--cells", type=int, default=11,
                    help="cells per dimension (11 = the benchmark workload; smaller values "
                         "give the reduced case used for detailed kernel profiles)")
@@ -981,12 +983,12 @@ def run_reference(args, rank, world):
                                         "d2h_bytes_per_step": 0}}
 
 
-def run_case(which, cells=7):
+def run_case(which, cells=7, systems=16):
     """One small invocation of a leg, for a profiler to capture: synthesis on
     the 21^2 robot (3 iterations per phase), region vectors and sampled noise
     (1024 draws) on the 7^5-cell room; the FP32-sound build (count, then emit)
-    and the FP64-plain build of the room on `cells`^5 cells; one group of 16
-    systems of the batched workload built into caller arrays."""
+    and the FP64-plain build of the room on `cells`^5 cells; one group of the
+    first `systems` systems of the batched workload built into caller arrays."""
     import torch
     from paper_2401_03555_gb300 import impact, workloads as W
     if which == "walk":
@@ -1004,7 +1006,7 @@ def run_case(which, cells=7):
         torch.cuda.synchronize()
         print("pairs", c.nnz)
     elif which == "batched":
-        b = impact.Batch(W.batched_family(16), "fp32")
+        b = impact.Batch(W.batched_family(systems), "fp32")
         rb = impact.alloc_rows(b.rows)
         ws = b.alloc_workspace()
         nnz = b.count(rb, ws)
@@ -1034,7 +1036,7 @@ def run_case(which, cells=7):
 def main(argv=None):
     args = parse_args(argv)
     if args.case:
-        run_case(args.case, args.cells)
+        run_case(args.case, args.cells, args.systems)
         return
     rank, world, local_rank = dist_env()
     if args.impl == "reference":
