@@ -359,9 +359,12 @@ def cpu_oracle_sample(prob, rows_target: int, seed: int = 0, threads: int = 0, k
 
 
 def auto_cpu_rows(prob):
-    """About 10-30 s of oracle work on this host (each row is a dense scan)."""
-    import oracle
-    threads = max(1, oracle.default().max_threads())
+    """About 10-30 s of oracle work on this host (each row is a dense scan).
+    The thread count is the one OpenMP will use, read without loading the
+    oracle: loading it starts the OpenMP runtime, after which the end-to-end
+    leg's pinned host buffers measured half the copy bandwidth."""
+    threads = int(os.environ.get("OMP_NUM_THREADS", "0") or 0) or len(os.sched_getaffinity(0))
+    threads = max(1, threads)
     per_row_s = 0.17 * prob.total_cells / 161051.0 * prob.n / 5.0
     return int(max(threads, min(4096, 15.0 * threads / max(per_row_s, 1e-6))))
 
