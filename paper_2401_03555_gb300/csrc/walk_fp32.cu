@@ -970,7 +970,19 @@ __device__ void leaf_emit(const WarpMem &S, int n, const Leaf &f, const NodeList
         // the division is exact for e < 64 nb, nb <= 4096; lanes past the end
         // read the last candidate and store nothing
         const int total = npar * nb;
-        for (int e0 = 0; e0 < total; e0 += 32) {
+        int e0 = 0;
+        // two candidates per lane and step, both loaded before either ballot
+        for (; e0 + 32 < total; e0 += 64) {
+            const int ea = e0 + lane, eb = min(e0 + 32 + lane, total - 1);
+            const int pa = (ROOT || nb == 1) ? (ROOT ? 0 : ea) : (int)__umulhi((uint32_t)ea, f.magic_nb);
+            const int pb = (ROOT || nb == 1) ? (ROOT ? 0 : eb) : (int)__umulhi((uint32_t)eb, f.magic_nb);
+            const Node node_a = node_at(Lp, ROOT, pa), node_b = node_at(Lp, ROOT, pb);
+            const LeafEntry leaf_a = leaf_at<STAGED>(S, n, f, ea - pa * nb);
+            const LeafEntry leaf_b = leaf_at<STAGED>(S, n, f, eb - pb * nb);
+            offer(true, node_a, leaf_a);
+            offer(e0 + 32 + lane < total, node_b, leaf_b);
+        }
+        for (; e0 < total; e0 += 32) {
             const int e = min(e0 + lane, total - 1);
             const int pi = (ROOT || nb == 1) ? (ROOT ? 0 : e) : (int)__umulhi((uint32_t)e, f.magic_nb);
             const int j = e - pi * nb;
