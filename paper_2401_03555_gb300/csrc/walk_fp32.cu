@@ -469,6 +469,7 @@ setup_fp32(const BatchIndex *__restrict__ B, uint32_t *__restrict__ status,
 // ---------------------------------------------------------------------------
 
 constexpr int kCap = IMPACT_WALK_CAP;      // nodes per level list (one chunk)
+constexpr int kClaimBytes = 32;            // per warp: the claimed row range, rows per claim
 
 // Warp shared memory: two record buffers of the batch's largest record (the
 // row being walked and the next one, copied in meanwhile), then the work
@@ -1163,6 +1164,7 @@ enum { MODE_COUNT = 0, MODE_EMIT = 1, MODE_FUSED = 2 };
 struct WalkArgs {
     const BatchIndex *B;
     int warp_smem;           // shared-memory bytes of one warp
+    int row_block;           // rows a warp claims per atomic
     int rec_max;             // bytes of one record buffer
     int64_t *row_ptr;        // COUNT: per-row counts; FUSED: row pointers; EMIT: read
     int32_t *col;
@@ -1198,15 +1200,40 @@ __global__ void __launch_bounds__(IMPACT_TREE_WARPS_MAX * 32) walk_fp32(const Wa
     unsigned long long *const next_row = B->next_row + (MODE == MODE_EMIT ? 1 : 0);
     bool lb_ok = true;
 
-    // persistent: each warp takes rows from the batch's row counter. The
-    // passes that count take them two ahead: while a warp walks a row, the
-    // index of the row after the next is claimed and the next row's record is
-    // copied (cp.async) into the warp's other record buffer. The emit pass
-    // (more registers live in its walk) copies each record when it starts it.
+    // persistent: each warp takes rows from the batch's row counter,
+    // A.row_block consecutive rows per atomic (one counter serves every warp
+    // of the grid: claiming short rows one by one queues the atomics), in
+    // ascending order. The passes that count take them two ahead: while a
+    // warp walks a row, the index of the row after the next is known and the
+    // next row's record is copied (cp.async) into the warp's other record
+    // buffer. The emit pass (more registers live in its walk) copies each
+    // record when it starts it.
     constexpr bool kAhead = MODE != MODE_EMIT;
     const unsigned long long nrows = (unsigned long long)(A.row_end - A.row_begin);
     unsigned char *const work = wbase + (kAhead ? 2 : 1) * A.rec_max;
-    auto take = [&]() -> unsigned long long { return lane == 0 ? atomicAdd(next_row, 1ull) : 0ull; };
+    // the warp's claimed rows [claim[0], claim[1]) and the rows per claim
+    // (claim[2]), in the last bytes of its block (not registers: the walk
+    // needs all of them)
+    unsigned long long *const claim =
+        reinterpret_cast<unsigned long long *>(wbase + A.warp_smem - kClaimBytes);
+    if (lane == 0) {
+        claim[0] = claim[1] = 0;
+        claim[2] = (unsigned long long)A.row_block;
+    }
+    __syncwarp();
+    auto take = [&]() -> unsigned long long {
+        unsigned long long t = claim[0];
+        if (t == claim[1]) {   // warp-uniform: every lane reads the same words
+            unsigned long long c = 0;
+            if (lane == 0) c = atomicAdd(next_row, claim[2]);
+            t = __shfl_sync(0xffffffffu, c, 0);
+            if (lane == 0) claim[1] = t + claim[2];
+        }
+        __syncwarp();
+        if (lane == 0) claim[0] = t + 1;
+        __syncwarp();
+        return t;
+    };
     auto fetch = [&](unsigned long long t, int &q, unsigned char *dst) {
         if (t >= nrows) return;
         const int64_t row = A.row_begin + (int64_t)t;
@@ -1215,11 +1242,11 @@ __global__ void __launch_bounds__(IMPACT_TREE_WARPS_MAX * 32) walk_fp32(const Wa
         const unsigned char *src = B->rec[q] + (row - B->row_begin[q]) * (int64_t)stride;
         for (int i = lane; i < (stride >> 4); i += 32) cp_async16(dst + 16 * i, src + 16 * i);
     };
-    unsigned long long t_cur = __shfl_sync(0xffffffffu, take(), 0);
+    unsigned long long t_cur = take();
     unsigned long long t_nxt = 0;
     int q_cur = 0, b = 0;
     if (kAhead) {
-        t_nxt = __shfl_sync(0xffffffffu, take(), 0);
+        t_nxt = take();
         fetch(t_cur, q_cur, wbase);
         cp_async_commit();
     }
@@ -1227,7 +1254,7 @@ __global__ void __launch_bounds__(IMPACT_TREE_WARPS_MAX * 32) walk_fp32(const Wa
         unsigned long long t_after = 0;
         int q_nxt = q_cur;
         if (kAhead) {
-            t_after = take();   // lane 0's claim, read after the row
+            t_after = take();
             fetch(t_nxt, q_nxt, wbase + (b ^ 1) * A.rec_max);
             cp_async_commit();
             cp_async_wait_prior();   // this row's record has landed
@@ -1317,10 +1344,10 @@ __global__ void __launch_bounds__(IMPACT_TREE_WARPS_MAX * 32) walk_fp32(const Wa
         if (kAhead) {
             t_cur = t_nxt;
             q_cur = q_nxt;
-            t_nxt = __shfl_sync(0xffffffffu, t_after, 0);
+            t_nxt = t_after;
             b ^= 1;
         } else {
-            t_cur = __shfl_sync(0xffffffffu, take(), 0);
+            t_cur = take();
         }
     }
     cp_async_wait_all();
@@ -1379,7 +1406,7 @@ cudaError_t launch_walk_fp32(const BatchIndex *d_index, int64_t row_begin, int64
     // multiples of 16)
     rec_max = (rec_max + 15) & ~15;
     const int work = work_max[mode == MODE_EMIT ? 0 : 1];
-    const int warp_smem = (mode == MODE_EMIT ? 1 : 2) * rec_max + ((work + 15) & ~15);
+    const int warp_smem = (mode == MODE_EMIT ? 1 : 2) * rec_max + ((work + 15) & ~15) + kClaimBytes;
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -1415,6 +1442,12 @@ cudaError_t launch_walk_fp32(const BatchIndex *d_index, int64_t row_begin, int64
     A.guard_row = f.guard_row;
     // persistent grid: as many blocks as fit at once (rows are taken dynamically)
     const int g = occupancy_grid(k, threads, smem, rows, warps);
+    // rows per claim: 4 in the count pass (its rows are short: the atomics
+    // cost more than the last claims' imbalance), else up to 4 while that
+    // imbalance (up to 3 rows per warp) stays under 1/256 of each warp's rows
+    A.row_block = mode == MODE_COUNT
+                      ? 4
+                      : (int)std::max<int64_t>(1, std::min<int64_t>(4, rows / ((int64_t)g * warps * 256)));
     if (mode == MODE_COUNT)
         walk_fp32<MODE_COUNT><<<g, threads, smem, stream>>>(A);
     else if (mode == MODE_EMIT)
