@@ -470,6 +470,7 @@ setup_fp32(const BatchIndex *__restrict__ B, uint32_t *__restrict__ status,
 
 constexpr int kCap = IMPACT_WALK_CAP;      // nodes per level list (one chunk)
 constexpr int kClaimBytes = 32;            // per warp: the claimed row range, rows per claim
+constexpr int kTrimMin = 512;              // emit: candidates of a chunk worth trimming its table for
 
 // Warp shared memory: two record buffers of the batch's largest record (the
 // row being walked and the next one, copied in meanwhile), then the work
@@ -477,8 +478,9 @@ constexpr int kClaimBytes = 32;            // per warp: the claimed row range, r
 //   h      RecDim[n]                 the row record's per-dimension entries
 //   ul     (U, L) x tsum_cap         the record's window tables, right after
 //   work   (n - 2) x (kCap + 1) x 12 B  node lists of levels 0..n-3
-//   leaf   3 x (leaf_cap + 1) words  the staged leaf table (see Leaf), and for
-//          5 x (leaf_cap + 1) words  the count pass its sorted form and sums
+//   leaf   3 x (leaf_cap + 1) words  the staged leaf table (see Leaf), and
+//          5 x (leaf_cap + 1) words  the count pass's sorted form and sums, or
+//                                    the emit pass's table trimmed per chunk
 struct WarpMem {
     RecDim *h;
     float2 *ul;
@@ -962,7 +964,47 @@ template <bool ROOT, bool STAGED>
 __device__ void leaf_emit(const WarpMem &S, int n, const Leaf &f, const NodeList &Lp, int npar,
                           int lane, const EmitOut &out, int &written, float cut)
 {
-    const int nb = f.nb;
+    int nb = f.nb;
+    uint32_t magic = f.magic_nb;
+    // the table walked: upper, lower and column columns leaf_cap + 1 words
+    // apart (the staged table, or its trimmed copy in the count pass's space)
+    const float *tu = f.bu;
+    const int cs = S.leaf_cap + 1;
+    if (STAGED && !ROOT && cut > 0.0f && npar * nb >= kTrimMin) {
+        // entries that no parent of these can keep: RU(P x) is monotone in P,
+        // so an entry below the cutoff under the largest P is below it under
+        // every P. The rest, in C order, form the table walked below; the
+        // pairs are the same. (A pass over the table and a division: worth it
+        // only when the parents and the table are large.)
+        float pm = 0.0f;
+        for (int pi = lane; pi < npar; pi += 32) pm = fmaxf(pm, node_at(Lp, ROOT, pi).P);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) pm = fmaxf(pm, __shfl_xor_sync(0xffffffffu, pm, o));
+        float *const su = f.su;
+        int nt = 0;
+        for (int j0 = 0; j0 < f.nb; j0 += 32) {
+            const int j = j0 + lane;
+            const float u = j < f.nb ? f.bu[j] : 0.0f;
+            const bool k = j < f.nb && __fmul_ru(pm, u) >= cut;
+            const unsigned bal = __ballot_sync(0xffffffffu, k);
+            if (k) {
+                const int o = nt + __popc(bal & lanemask_lt());
+                su[o] = u;
+                su[o + cs] = f.bl[j];
+                su[o + 2 * cs] = f.bu[j + 2 * cs];   // the column's bits
+            }
+            nt += __popc(bal);
+        }
+        __syncwarp();
+        if (nt == 0) return;
+        nb = nt;
+        magic = nt > 1 ? 0xffffffffu / (unsigned)nt + 1u : 0u;   // ceil(2^32 / nt)
+        tu = su;
+    }
+    auto entry = [&](int j) -> LeafEntry {
+        if (!STAGED) return leaf_eval(S, n, f, j);
+        return LeafEntry{tu[j], tu[j + cs], __float_as_int(tu[j + 2 * cs])};
+    };
     // every lane computes, the kept ones store (predicated, no divergence)
     auto offer = [&](bool act, const Node &par, const LeafEntry &e) {
         offer_pair(act, par, e, cut, out, written);
@@ -975,19 +1017,19 @@ __device__ void leaf_emit(const WarpMem &S, int n, const Leaf &f, const NodeList
         // two candidates per lane and step, both loaded before either ballot
         for (; e0 + 32 < total; e0 += 64) {
             const int ea = e0 + lane, eb = min(e0 + 32 + lane, total - 1);
-            const int pa = (ROOT || nb == 1) ? (ROOT ? 0 : ea) : (int)__umulhi((uint32_t)ea, f.magic_nb);
-            const int pb = (ROOT || nb == 1) ? (ROOT ? 0 : eb) : (int)__umulhi((uint32_t)eb, f.magic_nb);
+            const int pa = (ROOT || nb == 1) ? (ROOT ? 0 : ea) : (int)__umulhi((uint32_t)ea, magic);
+            const int pb = (ROOT || nb == 1) ? (ROOT ? 0 : eb) : (int)__umulhi((uint32_t)eb, magic);
             const Node node_a = node_at(Lp, ROOT, pa), node_b = node_at(Lp, ROOT, pb);
-            const LeafEntry leaf_a = leaf_at<STAGED>(S, n, f, ea - pa * nb);
-            const LeafEntry leaf_b = leaf_at<STAGED>(S, n, f, eb - pb * nb);
+            const LeafEntry leaf_a = entry(ea - pa * nb);
+            const LeafEntry leaf_b = entry(eb - pb * nb);
             offer(true, node_a, leaf_a);
             offer(e0 + 32 + lane < total, node_b, leaf_b);
         }
         for (; e0 < total; e0 += 32) {
             const int e = min(e0 + lane, total - 1);
-            const int pi = (ROOT || nb == 1) ? (ROOT ? 0 : e) : (int)__umulhi((uint32_t)e, f.magic_nb);
+            const int pi = (ROOT || nb == 1) ? (ROOT ? 0 : e) : (int)__umulhi((uint32_t)e, magic);
             const int j = e - pi * nb;
-            offer(e0 + lane < total, node_at(Lp, ROOT, pi), leaf_at<STAGED>(S, n, f, j));
+            offer(e0 + lane < total, node_at(Lp, ROOT, pi), entry(j));
         }
         return;
     }
@@ -995,7 +1037,7 @@ __device__ void leaf_emit(const WarpMem &S, int n, const Leaf &f, const NodeList
         const Node par = node_at(Lp, ROOT, pi);
         for (int j0 = 0; j0 < nb; j0 += 32) {
             const int j = min(j0 + lane, nb - 1);
-            offer(j0 + lane < nb, par, leaf_at<STAGED>(S, n, f, j));
+            offer(j0 + lane < nb, par, entry(j));
         }
     }
 }
@@ -1377,7 +1419,7 @@ int64_t record_stride(int n, int tsum_cap)
 
 int walk_work_bytes(int n, int leaf_cap, bool count)
 {
-    return list_bytes(n) + align16((count ? 32 : 12) * (leaf_cap + 1));
+    return list_bytes(n) + align16((count ? 32 : 24) * (leaf_cap + 1));
 }
 
 int walk_core_bytes(int n, int tsum_cap, int leaf_cap)
