@@ -172,3 +172,40 @@ def test_plan_rejects_a_unicycle_of_other_dimension(lib):
     prob.sigma = np.r_[prob.sigma, 0.3]
     with pytest.raises(impact.ImpactError, match="unicycle needs n = 3"):
         impact.plan(prob, "fp32")
+
+
+STRUCTS = [("_System", "impact_system"), ("_Grid", "impact_grid"), ("_Inputs", "impact_inputs"),
+           ("_CSR", "impact_csr"), ("_Request", "impact_request"), ("_Tuning", "impact_tuning"),
+           ("_Regions", "impact_regions"), ("_SynthOptions", "impact_synth_options"),
+           ("_ServerConfig", "impact_server_config"), ("_ServerStats", "impact_server_stats_t")]
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Every ctypes mirror in the binding has the size and field offsets that
+    a C compiler gives the header's struct (host-only: gcc and the header)."""
+    import ctypes
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    header = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                          "include", "impact.h")
+    lines = ["#include <stdio.h>", "#include <stddef.h>", f'#include "{header}"',
+             "int main(void) {"]
+    want = []
+    for py, c in STRUCTS:
+        st = getattr(impact, py)
+        lines.append(f'  printf("%zu\\n", sizeof({c}));')
+        want.append(ctypes.sizeof(st))
+        for name, _ in st._fields_:
+            lines.append(f'  printf("%zu\\n", offsetof({c}, {name}));')
+            want.append(getattr(st, name).offset)
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-o", str(exe), str(src)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True,
+                                          text=True).stdout.split()]
+    assert got == want
