@@ -658,13 +658,15 @@ __device__ void leaf_build(const WarpMem &S, int n, Leaf &f, int lane, float cut
     }
     __syncwarp();
     if (!COUNT) return;
+    if (!(cut > 0.0f)) {   // the totals serve the dense count only
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        su_l = __fadd_ru(su_l, __shfl_xor_sync(0xffffffffu, su_l, o));
-        sl_l = __fadd_rd(sl_l, __shfl_xor_sync(0xffffffffu, sl_l, o));
+        for (int o = 16; o > 0; o >>= 1) {
+            su_l = __fadd_ru(su_l, __shfl_xor_sync(0xffffffffu, su_l, o));
+            sl_l = __fadd_rd(sl_l, __shfl_xor_sync(0xffffffffu, sl_l, o));
+        }
+        f.tot_u = __shfl_sync(0xffffffffu, su_l, 0);
+        f.tot_l = __shfl_sync(0xffffffffu, sl_l, 0);
     }
-    f.tot_u = __shfl_sync(0xffffffffu, su_l, 0);
-    f.tot_l = __shfl_sync(0xffffffffu, sl_l, 0);
     // a row of at most two dimensions has one parent (the root): testing
     // its entries directly costs less than sorting them
     if (!f.staged || !(cut > 0.0f) || n <= 2) return;
@@ -672,29 +674,28 @@ __device__ void leaf_build(const WarpMem &S, int n, Leaf &f, int lane, float cut
     if (f.nb <= 32) {
         // one entry per lane: a bitonic sorting network over the warp puts
         // the entry of rank r (bu descending, ties by index) in lane r, then
-        // scans in registers give the sums
-        float u = lane < f.nb ? f.bu[lane] : -INFINITY;
-        float lv = lane < f.nb ? f.bl[lane] : 0.0f;
-        int id = lane;
+        // scans in registers give the sums. The sort key is the bits of bu
+        // inverted (bu >= 0, so its bits grow with it) above the index:
+        // ascending keys are bu descending, ties by index; lanes past the
+        // table hold the largest key and sort last.
+        const bool in = lane < f.nb;
+        unsigned long long key = ~0ull;
+        if (in)
+            key = ((unsigned long long)(~__float_as_uint(f.bu[lane])) << 32) | (unsigned)lane;
 #pragma unroll
         for (int k = 2; k <= 32; k <<= 1) {
 #pragma unroll
             for (int jj = k >> 1; jj > 0; jj >>= 1) {
-                const float pu_ = __shfl_xor_sync(0xffffffffu, u, jj);
-                const float pl_ = __shfl_xor_sync(0xffffffffu, lv, jj);
-                const int pid = __shfl_xor_sync(0xffffffffu, id, jj);
+                const unsigned long long pk = __shfl_xor_sync(0xffffffffu, key, jj);
                 const bool want_first = ((lane & jj) == 0) == ((lane & k) == 0);
-                const bool mine_first = (u > pu_) || (u == pu_ && id < pid);
-                if (want_first != mine_first) {
-                    u = pu_;
-                    lv = pl_;
-                    id = pid;
-                }
+                if (want_first != (key < pk)) key = pk;
             }
         }
-        const float ux = lane < f.nb ? u : 0.0f;
+        const float u = in ? __uint_as_float(~(unsigned)(key >> 32)) : 0.0f;
+        const float lv = in ? f.bl[(int)(key & 0xffffffffu)] : 0.0f;
+        const float ux = u;
         const float iu = scan_ru(ux, lane);
-        const float il = scan_rd(lane < f.nb ? lv : 0.0f, lane);
+        const float il = scan_rd(lv, lane);
         float su_ = ux;   // suffix sums, rounded up
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
